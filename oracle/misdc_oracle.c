@@ -1,0 +1,1022 @@
+/*
+ * Plain serial FP64 CPU oracle for the multi-implicit SDC schemes of
+ * Hamon, Day & Minion (arXiv:1801.01201).
+ *
+ * TEST INFRASTRUCTURE ONLY: the independent checker of the CUDA library.
+ * Only tests, the smoke check and the benchmark's CPU-baseline leg load it.
+ * Nothing here is shared with the CUDA path.
+ *
+ * Everything is written for clarity, not speed: loops follow the paper's
+ * equations term by term, in the paper's order and notation. Readings of
+ * passages that are silent, ambiguous or garbled are stated where they are
+ * used.
+ *
+ * Pins (tests/test_oracle_*.py) fix this code against the paper: the worked
+ * three-node tables, the collocation (Lobatto IIIA / Pade) fixed point of the
+ * sweeps, the sweep counts behind Tables 1-3, time order on the nonlinear test
+ * PDE, finite-difference Jacobians, detailed balance, conservation, and dense
+ * brute-force solves on tiny grids.
+ */
+#include "misdc_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define R_UNIV 8.314462618
+
+/* ======================================================================= */
+/* Quadrature tables (Sec. 3.1, eq. "weights" and the LU trick)            */
+/* ======================================================================= */
+
+/* Legendre P_M(x) and P'_M(x) by the three-term recurrence. */
+static void legendre(int M, long double x, long double *p, long double *dp) {
+  long double p0 = 1.0L, p1 = x;
+  if (M == 0) { *p = 1.0L; *dp = 0.0L; return; }
+  for (int k = 2; k <= M; ++k) {
+    long double pk = ((2.0L * k - 1.0L) * x * p1 - (k - 1.0L) * p0) / k;
+    p0 = p1; p1 = pk;
+  }
+  *p = p1;
+  /* (1 - x^2) P'_M = M (P_{M-1} - x P_M) */
+  *dp = M * (p0 - x * p1) / (1.0L - x * x);
+}
+
+/* Gauss-Lobatto nodes on [0,1]: endpoints plus the roots of P'_M. */
+static int lobatto_nodes(int M, long double *tau) {
+  tau[0] = 0.0L; tau[M] = 1.0L;
+  for (int j = 1; j < M; ++j) {
+    long double x = -cosl(3.14159265358979323846264338327950288L * j / M);
+    for (int it = 0; it < 100; ++it) {
+      long double p, dp;
+      legendre(M, x, &p, &dp);
+      /* Legendre ODE: (1-x^2) P'' = 2x P' - M(M+1) P */
+      long double d2p = (2.0L * x * dp - M * (M + 1.0L) * p) / (1.0L - x * x);
+      long double step = dp / d2p;
+      x -= step;
+      if (fabsl(step) < 1e-19L) break;
+    }
+    tau[j] = 0.5L * (x + 1.0L);
+  }
+  return 0;
+}
+
+/* integral over [a,b] of the Lagrange basis polynomial L_j on nodes tau */
+static long double lagrange_integral(int M, const long double *tau, int j,
+                                     long double a, long double b) {
+  long double c[64];
+  memset(c, 0, sizeof(c));
+  c[0] = 1.0L;
+  int deg = 0;
+  for (int k = 0; k <= M; ++k) {
+    if (k == j) continue;
+    long double den = tau[j] - tau[k];
+    /* multiply by (t - tau_k)/den */
+    for (int p = deg + 1; p >= 0; --p) {
+      long double v = (p > 0 ? c[p - 1] : 0.0L) - tau[k] * c[p];
+      c[p] = v / den;
+    }
+    ++deg;
+  }
+  long double s = 0.0L;
+  for (int p = 0; p <= deg; ++p)
+    s += c[p] * (powl(b, p + 1) - powl(a, p + 1)) / (p + 1);
+  return s;
+}
+
+int or_lobatto(int M, double *tau_out, double *Q, double *S, double *QI, double *QE) {
+  if (M < 1 || M > 16) return 1;
+  long double tau[17];
+  lobatto_nodes(M, tau);
+  for (int m = 0; m <= M; ++m) if (tau_out) tau_out[m] = (double)tau[m];
+  long double Qt[16][16], U[16][16], L[16][16];
+  for (int m = 1; m <= M; ++m)
+    for (int j = 0; j <= M; ++j) {
+      long double q = lagrange_integral(M, tau, j, 0.0L, tau[m]);
+      long double s = lagrange_integral(M, tau, j, tau[m - 1], tau[m]);
+      if (Q) Q[(m - 1) * (M + 1) + j] = (double)q;
+      if (S) S[(m - 1) * (M + 1) + j] = (double)s;
+      if (j >= 1) Qt[j - 1][m - 1] = q;     /* Qt = (Q~)^T, Q~ = Q without its first column */
+    }
+  /* Doolittle LU of (Q~)^T = L U with unit-diagonal L (Weiser's LU trick):
+   * "the upper triangular matrix in the LU decomposition" is read as the U of
+   * the unit-lower / upper factorisation. */
+  for (int i = 0; i < M; ++i) {
+    for (int j = i; j < M; ++j) {
+      long double s = Qt[i][j];
+      for (int k = 0; k < i; ++k) s -= L[i][k] * U[k][j];
+      U[i][j] = s;
+    }
+    L[i][i] = 1.0L;
+    for (int j = i + 1; j < M; ++j) {
+      long double s = Qt[j][i];
+      for (int k = 0; k < i; ++k) s -= L[j][k] * U[k][i];
+      L[j][i] = s / U[i][i];
+    }
+    for (int j = 0; j < i; ++j) U[i][j] = 0.0L;
+  }
+  /* Q~I := U^T.
+   * Q~E: forward Euler integrated from t^0, q~E_{m+1,j} = dt^j/dt for every
+   * j <= m and 0 for j >= m+1. The printed definition ("q~E_{m+1,m} := dt^m/dt,
+   * q~E_{m+1,j != m+1} := 0") is read as this cumulative rule: the CISDCQ
+   * update keeps explicit terms for j <= m-1, which would vanish otherwise,
+   * and only this reading reproduces the sweep counts of Tables 1 and 2.
+   * For three nodes both readings give the same matrix. */
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      if (QI) QI[i * M + j] = (double)U[j][i];
+      if (QE) QE[i * M + j] = (j < i) ? (double)(tau[j + 2] - tau[j + 1]) : 0.0;
+    }
+  return 0;
+}
+
+/* ======================================================================= */
+/* Generic sweeps                                                          */
+/* ======================================================================= */
+
+typedef struct sweep_tables {
+  int M;
+  double tau[17], Q[16 * 17], S[16 * 17], QI[256], QE[256];
+} sweep_tables;
+
+/* weights addressed with 1-based node indices as in the paper */
+#define QW(T, t, j) ((T)->Q[((t) - 1) * ((T)->M + 1) + (j)])
+#define SW(T, t, j) ((T)->S[((t) - 1) * ((T)->M + 1) + (j)])
+#define QIW(T, t, j) ((T)->QI[((t) - 1) * (T)->M + ((j) - 1)])
+#define QEW(T, t, j) ((T)->QE[((t) - 1) * (T)->M + ((j) - 1)])
+
+static double *vec(int n) { return (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double)); }
+
+static void axpy(int n, double a, const double *x, double *y) {
+  for (int i = 0; i < n; ++i) y[i] += a * x[i];
+}
+
+/* F^(k) at all nodes */
+static void eval_all(const or_problem *p, const double *phi, double *FE, double *FD, double *FR) {
+  p->f_expl(p->ctx, phi, FE);
+  p->f_diff(p->ctx, phi, FD);
+  p->f_reac(p->ctx, phi, FR);
+}
+
+/* Delta t * Q^{0:t}(F(phi^(k))) + phi^0  (shared start of every update) */
+static void base_rhs(const or_problem *p, const sweep_tables *T, int t, double dt,
+                     const double *phi0, double *const *FEk, double *const *FDk,
+                     double *const *FRk, double *rhs) {
+  int n = p->n, M = T->M;
+  memcpy(rhs, phi0, sizeof(double) * n);
+  for (int j = 0; j <= M; ++j) {
+    double w = dt * QW(T, t, j);
+    axpy(n, w, FEk[j], rhs);
+    axpy(n, w, FDk[j], rhs);
+    axpy(n, w, FRk[j], rhs);
+  }
+}
+
+int or_sweep(const or_problem *p, int scheme, int M, int nu, double dt,
+             const double *Phi_k, double *Phi_out) {
+  sweep_tables T;
+  T.M = M;
+  if (or_lobatto(M, T.tau, T.Q, T.S, T.QI, T.QE)) return 1;
+  int n = p->n, rc = 0;
+  double *FEk[17] = {0}, *FDk[17] = {0}, *FRk[17] = {0};
+  double *cur[17] = {0}, *FEc[17] = {0}, *FDc[17] = {0}, *FRc[17] = {0};
+  double *prv[17] = {0}, *FEp[17] = {0}, *FDp[17] = {0}, *FRp[17] = {0};
+  double *AD[17] = {0}, *FEad[17] = {0}, *FDad[17] = {0};
+  const double *phik[17] = {0};
+  for (int m = 0; m <= M; ++m) {
+    phik[m] = Phi_k + (size_t)m * n;
+    FEk[m] = vec(n); FDk[m] = vec(n); FRk[m] = vec(n);
+    cur[m] = vec(n); FEc[m] = vec(n); FDc[m] = vec(n); FRc[m] = vec(n);
+    prv[m] = vec(n); FEp[m] = vec(n); FDp[m] = vec(n); FRp[m] = vec(n);
+    AD[m] = vec(n); FEad[m] = vec(n); FDad[m] = vec(n);
+    eval_all(p, phik[m], FEk[m], FDk[m], FRk[m]);
+  }
+  const double *phi0 = phik[0];
+  double *rhs = vec(n), *b = vec(n);
+  memcpy(Phi_out, Phi_k, sizeof(double) * n);   /* node 0 is fixed */
+
+  if (scheme == OR_MISDC) {
+    /* eqs. update_equation_misdc_discrete_form_D/R: node-to-node, backward
+     * Euler for D and R, forward Euler for A, quadrature S^{m:m+1}. The extra
+     * closing bracket in the printed R update is read as a typo. */
+    memcpy(cur[0], phi0, sizeof(double) * n);
+    memcpy(FEc[0], FEk[0], sizeof(double) * n);
+    for (int m = 0; m < M && !rc; ++m) {
+      int t = m + 1;
+      double dtm = dt * (T.tau[t] - T.tau[m]);
+      memcpy(rhs, cur[m], sizeof(double) * n);
+      for (int i = 0; i < n; ++i) rhs[i] += dtm * (FEc[m][i] - FEk[m][i]) - dtm * FDk[t][i];
+      for (int j = 0; j <= M; ++j) {
+        double w = dt * SW(&T, t, j);
+        axpy(n, w, FEk[j], rhs); axpy(n, w, FDk[j], rhs); axpy(n, w, FRk[j], rhs);
+      }
+      rc |= p->solve_diff(p->ctx, dtm, phik[t], rhs, AD[t]);
+      for (int i = 0; i < n; ++i) b[i] = AD[t][i] - dtm * FRk[t][i];
+      rc |= p->solve_reac(p->ctx, dtm, b, phik[t], cur[t]);
+      eval_all(p, cur[t], FEc[t], FDc[t], FRc[t]);
+    }
+    for (int m = 1; m <= M; ++m) memcpy(Phi_out + (size_t)m * n, cur[m], sizeof(double) * n);
+  } else if (scheme == OR_MISDCQ) {
+    /* eqs. update_equation_misdcq_discrete_form_D and _R */
+    for (int m = 0; m < M && !rc; ++m) {
+      int t = m + 1;
+      base_rhs(p, &T, t, dt, phi0, FEk, FDk, FRk, rhs);
+      for (int j = 1; j <= m; ++j)
+        for (int i = 0; i < n; ++i)
+          rhs[i] += dt * QEW(&T, t, j) * (FEc[j][i] - FEk[j][i])
+                  + dt * QIW(&T, t, j) * (FDc[j][i] - FDk[j][i]);
+      for (int i = 0; i < n; ++i) rhs[i] -= dt * QIW(&T, t, t) * FDk[t][i];
+      /* diffusion coefficient frozen at sweep k (there is no nested index) */
+      rc |= p->solve_diff(p->ctx, dt * QIW(&T, t, t), phik[t], rhs, AD[t]);
+      memcpy(b, AD[t], sizeof(double) * n);
+      for (int j = 1; j <= m; ++j)
+        for (int i = 0; i < n; ++i) b[i] += dt * QIW(&T, t, j) * (FRc[j][i] - FRk[j][i]);
+      for (int i = 0; i < n; ++i) b[i] -= dt * QIW(&T, t, t) * FRk[t][i];
+      rc |= p->solve_reac(p->ctx, dt * QIW(&T, t, t), b, phik[t], cur[t]);
+      eval_all(p, cur[t], FEc[t], FDc[t], FRc[t]);
+    }
+    for (int m = 1; m <= M; ++m) memcpy(Phi_out + (size_t)m * n, cur[m], sizeof(double) * n);
+  } else if (scheme == OR_IMEXQ) {
+    /* IMEXQ: explicit A, fully coupled implicit D+R with the LU weights. */
+    if (!p->solve_coupled) rc = 1;
+    for (int m = 0; m < M && !rc; ++m) {
+      int t = m + 1;
+      base_rhs(p, &T, t, dt, phi0, FEk, FDk, FRk, rhs);
+      for (int j = 1; j <= m; ++j)
+        for (int i = 0; i < n; ++i)
+          rhs[i] += dt * QEW(&T, t, j) * (FEc[j][i] - FEk[j][i])
+                  + dt * QIW(&T, t, j) * (FDc[j][i] + FRc[j][i] - FDk[j][i] - FRk[j][i]);
+      for (int i = 0; i < n; ++i) rhs[i] -= dt * QIW(&T, t, t) * (FDk[t][i] + FRk[t][i]);
+      rc |= p->solve_coupled(p->ctx, dt * QIW(&T, t, t), rhs, phik[t], cur[t]);
+      eval_all(p, cur[t], FEc[t], FDc[t], FRc[t]);
+    }
+    for (int m = 1; m <= M; ++m) memcpy(Phi_out + (size_t)m * n, cur[m], sizeof(double) * n);
+  } else if (scheme == OR_CISDCQ) {
+    /* CISDCQ-nu: eqs. update_equation_amisdcq_discrete_form_D and _R_alt.
+     * Iteration l = 0 takes its lagged values from initial_lagged_values_A/D/R:
+     * F_A and F_D at node m from the newest advection-diffusion state at node m
+     * of the current iteration (phi_AD^{m,(k+1,1)}, the reading fixed by the
+     * appendix's matrix form), F_R at nodes m and m+1 from sweep k. The lagged
+     * diffusion coefficient at node m+1 is that of sweep k when l = 0 and that
+     * of iteration l otherwise (eq. lagged_diffusion_flux). The reaction Newton
+     * starts from the iteration-l state (Sec. 3.3, S5). */
+    for (int m = 0; m <= M; ++m) {   /* iteration l = 0 is sweep k */
+      memcpy(prv[m], phik[m], sizeof(double) * n);
+      memcpy(FEp[m], FEk[m], sizeof(double) * n);
+      memcpy(FDp[m], FDk[m], sizeof(double) * n);
+      memcpy(FRp[m], FRk[m], sizeof(double) * n);
+    }
+    for (int l = 0; l < nu && !rc; ++l) {
+      for (int m = 0; m < M && !rc; ++m) {
+        int t = m + 1;
+        /* ---- diffusion step at node m+1, iteration l+1 ---- */
+        base_rhs(p, &T, t, dt, phi0, FEk, FDk, FRk, rhs);
+        for (int j = 1; j <= m - 1; ++j)
+          for (int i = 0; i < n; ++i)
+            rhs[i] += dt * QEW(&T, t, j) * (FEc[j][i] - FEk[j][i])
+                    + dt * QIW(&T, t, j) * (FDc[j][i] - FDk[j][i] + FRc[j][i] - FRk[j][i]);
+        if (m >= 1) {
+          const double *lagE = (l == 0) ? FEad[m] : FEp[m];
+          const double *lagD = (l == 0) ? FDad[m] : FDp[m];
+          const double *lagR = (l == 0) ? FRk[m] : FRp[m];
+          for (int i = 0; i < n; ++i)
+            rhs[i] += dt * QEW(&T, t, m) * (lagE[i] - FEk[m][i])
+                    + dt * QIW(&T, t, m) * (lagD[i] - FDk[m][i] + lagR[i] - FRk[m][i]);
+        }
+        const double *lagR1 = (l == 0) ? FRk[t] : FRp[t];
+        for (int i = 0; i < n; ++i)
+          rhs[i] += dt * QIW(&T, t, t) * (-FDk[t][i] + lagR1[i] - FRk[t][i]);
+        const double *coef = (l == 0) ? phik[t] : prv[t];
+        rc |= p->solve_diff(p->ctx, dt * QIW(&T, t, t), coef, rhs, AD[t]);
+        if (l == 0 && t < M) {   /* S4: lag source for the next node */
+          p->f_expl(p->ctx, AD[t], FEad[t]);
+          p->f_diff(p->ctx, AD[t], FDad[t]);
+        }
+        /* ---- reaction step at node m+1, iteration l+1 (R_alt form) ---- */
+        memcpy(b, AD[t], sizeof(double) * n);
+        if (m >= 1) {
+          const double *lagRm = (l == 0) ? FRk[m] : FRp[m];
+          for (int i = 0; i < n; ++i) b[i] += dt * QIW(&T, t, m) * (FRc[m][i] - lagRm[i]);
+        }
+        for (int i = 0; i < n; ++i) b[i] -= dt * QIW(&T, t, t) * lagR1[i];
+        const double *guess = (l == 0) ? phik[t] : prv[t];
+        rc |= p->solve_reac(p->ctx, dt * QIW(&T, t, t), b, guess, cur[t]);
+        /* S6: recompute the right-hand-side terms at the new state */
+        eval_all(p, cur[t], FEc[t], FDc[t], FRc[t]);
+      }
+      for (int m = 1; m <= M; ++m) {   /* iteration l+1 becomes the lag source */
+        double *s;
+        s = prv[m]; prv[m] = cur[m]; cur[m] = s;
+        s = FEp[m]; FEp[m] = FEc[m]; FEc[m] = s;
+        s = FDp[m]; FDp[m] = FDc[m]; FDc[m] = s;
+        s = FRp[m]; FRp[m] = FRc[m]; FRc[m] = s;
+      }
+    }
+    /* S7 */
+    for (int m = 1; m <= M; ++m) memcpy(Phi_out + (size_t)m * n, prv[m], sizeof(double) * n);
+  } else {
+    rc = 1;
+  }
+
+  for (int m = 0; m <= M; ++m) {
+    free(FEk[m]); free(FDk[m]); free(FRk[m]);
+    free(cur[m]); free(FEc[m]); free(FDc[m]); free(FRc[m]);
+    free(prv[m]); free(FEp[m]); free(FDp[m]); free(FRp[m]);
+    free(AD[m]); free(FEad[m]); free(FDad[m]);
+  }
+  free(rhs); free(b);
+  return rc;
+}
+
+int or_step(const or_problem *p, int scheme, int M, int n_sweeps, int nu,
+            double dt, const double *phi_n, double *phi_out, double *incr) {
+  int n = p->n, rc = 0;
+  size_t sz = (size_t)(M + 1) * n;
+  double *A = vec((int)sz), *B = vec((int)sz);
+  for (int m = 0; m <= M; ++m) memcpy(A + (size_t)m * n, phi_n, sizeof(double) * n);   /* I1, I2 */
+  for (int k = 0; k < n_sweeps && !rc; ++k) {
+    rc |= or_sweep(p, scheme, M, nu, dt, A, B);
+    if (incr) {
+      double s = 0.0;
+      for (int i = 0; i < n; ++i) s += fabs(B[(size_t)M * n + i] - A[(size_t)M * n + i]);
+      incr[k] = s / n;
+    }
+    double *t = A; A = B; B = t;
+  }
+  memcpy(phi_out, A + (size_t)M * n, sizeof(double) * n);
+  free(A); free(B);
+  return rc;
+}
+
+/* ======================================================================= */
+/* Linear model problem (Sec. 4, eq. linear_model_problem)                 */
+/* ======================================================================= */
+
+typedef struct lin_ctx { double a, d, r; } lin_ctx;
+static void lin_fe(void *c, const double *x, double *o) { o[0] = ((lin_ctx *)c)->a * x[0]; }
+static void lin_fd(void *c, const double *x, double *o) { o[0] = ((lin_ctx *)c)->d * x[0]; }
+static void lin_fr(void *c, const double *x, double *o) { o[0] = ((lin_ctx *)c)->r * x[0]; }
+static int lin_sd(void *c, double w, const double *coef, const double *rhs, double *x) {
+  (void)coef; x[0] = rhs[0] / (1.0 - w * ((lin_ctx *)c)->d); return 0;
+}
+static int lin_sr(void *c, double w, const double *b, const double *g, double *x) {
+  (void)g; x[0] = b[0] / (1.0 - w * ((lin_ctx *)c)->r); return 0;
+}
+static int lin_sc(void *c, double w, const double *rhs, const double *g, double *x) {
+  (void)g; lin_ctx *l = (lin_ctx *)c; x[0] = rhs[0] / (1.0 - w * (l->d + l->r)); return 0;
+}
+
+static or_problem lin_problem(lin_ctx *c) {
+  or_problem p = {1, c, lin_fe, lin_fd, lin_fr, lin_sd, lin_sr, lin_sc};
+  return p;
+}
+
+int or_linear_step(int scheme, int M, int n_sweeps, int nu, double dt,
+                   double a, double d, double r, double phi0,
+                   double *phi_out, double *incr) {
+  lin_ctx c = {a, d, r};
+  or_problem p = lin_problem(&c);
+  return or_step(&p, scheme, M, n_sweeps, nu, dt, &phi0, phi_out, incr);
+}
+
+int or_linear_G(int scheme, int M, int nu, double dt, double a, double d,
+                double r, double *G) {
+  /* The sweep is affine in Phi^(k); with phi^0 = 0 it is linear, and its
+   * matrix is the iteration matrix G of Sec. 4. */
+  lin_ctx c = {a, d, r};
+  or_problem p = lin_problem(&c);
+  double Pk[17], Po[17];
+  for (int j = 1; j <= M; ++j) {
+    for (int m = 0; m <= M; ++m) Pk[m] = (m == j) ? 1.0 : 0.0;
+    if (or_sweep(&p, scheme, M, nu, dt, Pk, Po)) return 1;
+    for (int i = 1; i <= M; ++i) G[(i - 1) * M + (j - 1)] = Po[i];
+  }
+  return 0;
+}
+
+/* ======================================================================= */
+/* Dense LU with partial pivoting (shared by the small dense solves)       */
+/* ======================================================================= */
+
+/* Solves A x = b in place (A n x n row-major is overwritten). Returns 0, or 1
+ * if a pivot is exactly zero. */
+static int dense_solve(int n, double *A, double *b) {
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    double best = fabs(A[k * n + k]);
+    for (int i = k + 1; i < n; ++i)
+      if (fabs(A[i * n + k]) > best) { best = fabs(A[i * n + k]); piv = i; }
+    if (best == 0.0) return 1;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) { double t = A[k * n + j]; A[k * n + j] = A[piv * n + j]; A[piv * n + j] = t; }
+      double t = b[k]; b[k] = b[piv]; b[piv] = t;
+    }
+    for (int i = k + 1; i < n; ++i) {
+      double l = A[i * n + k] / A[k * n + k];
+      A[i * n + k] = l;
+      for (int j = k + 1; j < n; ++j) A[i * n + j] -= l * A[k * n + j];
+      b[i] -= l * b[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < n; ++j) s -= A[i * n + j] * b[j];
+    b[i] = s / A[i * n + i];
+  }
+  return 0;
+}
+
+/* ======================================================================= */
+/* Nonlinear test PDE (Sec. 5.2, eq. nonlinear_test_pde)                   */
+/* ======================================================================= */
+
+typedef struct pde_ctx {
+  int nx; double dx, a, d, r, left, right;
+  double wg[2][2][4];   /* [side][ghost 1/2][phi_b, phi_0, phi_1, phi_2] */
+} pde_ctx;
+
+/* Ghost cell averages from the cubic through the boundary value and the
+ * first three cell averages (fourth-order Dirichlet closure; the paper does
+ * not state its boundary treatment). */
+static void pde_ghost_weights(pde_ctx *c) {
+  /* p(xi) = sum c_k xi^k, xi in cell widths from the wall into the domain */
+  long double A[4][4], inv[4][4];
+  for (int k = 0; k < 4; ++k) A[0][k] = (k == 0) ? 1.0L : 0.0L;
+  for (int row = 1; row < 4; ++row) {
+    long double a0 = row - 1, a1 = row;
+    for (int k = 0; k < 4; ++k) A[row][k] = (powl(a1, k + 1) - powl(a0, k + 1)) / (k + 1);
+  }
+  /* invert 4x4 by Gauss-Jordan */
+  long double M[4][8];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 8; ++j) M[i][j] = (j < 4) ? A[i][j] : (j - 4 == i ? 1.0L : 0.0L);
+  for (int k = 0; k < 4; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < 4; ++i) if (fabsl(M[i][k]) > fabsl(M[piv][k])) piv = i;
+    for (int j = 0; j < 8; ++j) { long double t = M[k][j]; M[k][j] = M[piv][j]; M[piv][j] = t; }
+    long double d = M[k][k];
+    for (int j = 0; j < 8; ++j) M[k][j] /= d;
+    for (int i = 0; i < 4; ++i) if (i != k) {
+      long double f = M[i][k];
+      for (int j = 0; j < 8; ++j) M[i][j] -= f * M[k][j];
+    }
+  }
+  for (int i = 0; i < 4; ++i) for (int j = 0; j < 4; ++j) inv[i][j] = M[i][j + 4];
+  for (int g = 0; g < 2; ++g) {          /* ghost g covers xi in [-(g+1), -g] */
+    long double a0 = -(g + 1), a1 = -g;
+    for (int s = 0; s < 4; ++s) {
+      long double w = 0.0L;
+      for (int k = 0; k < 4; ++k) w += (powl(a1, k + 1) - powl(a0, k + 1)) / (k + 1) * inv[k][s];
+      c->wg[0][g][s] = (double)w;
+      c->wg[1][g][s] = (double)w;
+    }
+  }
+}
+
+/* extended array e[nx+4], interior at e[2..nx+1] */
+static void pde_extend(const pde_ctx *c, const double *x, double *e) {
+  int n = c->nx;
+  for (int i = 0; i < n; ++i) e[i + 2] = x[i];
+  for (int g = 0; g < 2; ++g) {
+    const double *w = c->wg[0][g];
+    e[1 - g] = w[0] * c->left + w[1] * x[0] + w[2] * x[1] + w[3] * x[2];
+    w = c->wg[1][g];
+    e[n + 2 + g] = w[0] * c->right + w[1] * x[n - 1] + w[2] * x[n - 2] + w[3] * x[n - 3];
+  }
+}
+
+static void pde_fe(void *cv, const double *x, double *o) {
+  pde_ctx *c = (pde_ctx *)cv;
+  int n = c->nx;
+  double *e = vec(n + 4);
+  pde_extend(c, x, e);
+  for (int i = 0; i < n; ++i) {
+    int k = i + 2;
+    double fr = (7.0 * (e[k] + e[k + 1]) - (e[k - 1] + e[k + 2])) / 12.0;
+    double fl = (7.0 * (e[k - 1] + e[k]) - (e[k - 2] + e[k + 1])) / 12.0;
+    o[i] = c->a * (fr - fl) / c->dx;
+  }
+  free(e);
+}
+
+static void pde_fd(void *cv, const double *x, double *o) {
+  pde_ctx *c = (pde_ctx *)cv;
+  int n = c->nx;
+  double *e = vec(n + 4);
+  pde_extend(c, x, e);
+  for (int i = 0; i < n; ++i) {
+    int k = i + 2;
+    double gr = (15.0 * (e[k + 1] - e[k]) - (e[k + 2] - e[k - 1])) / (12.0 * c->dx);
+    double gl = (15.0 * (e[k] - e[k - 1]) - (e[k + 1] - e[k - 2])) / (12.0 * c->dx);
+    o[i] = c->d * (gr - gl) / c->dx;
+  }
+  free(e);
+}
+
+static void pde_fr(void *cv, const double *x, double *o) {
+  pde_ctx *c = (pde_ctx *)cv;
+  for (int i = 0; i < c->nx; ++i) o[i] = c->r * x[i] * (x[i] - 1.0) * (x[i] - 0.5);
+}
+
+/* x - w F_D(x) = rhs: F_D is affine, so assemble its matrix column by column
+ * and solve directly (the paper solves a banded system directly). */
+static int pde_sd(void *cv, double w, const double *coef, const double *rhs, double *x) {
+  (void)coef;
+  pde_ctx *c = (pde_ctx *)cv;
+  int n = c->nx;
+  double *A = vec(n * n), *z = vec(n), *f0 = vec(n), *fj = vec(n);
+  pde_fd(c, z, f0);
+  for (int j = 0; j < n; ++j) {
+    z[j] = 1.0;
+    pde_fd(c, z, fj);
+    z[j] = 0.0;
+    for (int i = 0; i < n; ++i) A[i * n + j] = (i == j ? 1.0 : 0.0) - w * (fj[i] - f0[i]);
+  }
+  for (int i = 0; i < n; ++i) x[i] = rhs[i] + w * f0[i];
+  int rc = dense_solve(n, A, x);
+  free(A); free(z); free(f0); free(fj);
+  return rc;
+}
+
+static int pde_sr(void *cv, double w, const double *b, const double *g, double *x) {
+  pde_ctx *c = (pde_ctx *)cv;
+  for (int i = 0; i < c->nx; ++i) {
+    double y = g[i];
+    int it;
+    for (it = 0; it < 100; ++it) {
+      double f = y - w * c->r * y * (y - 1.0) * (y - 0.5) - b[i];
+      double df = 1.0 - w * c->r * (3.0 * y * y - 3.0 * y + 0.5);
+      double dy = -f / df;
+      y += dy;
+      if (fabs(dy) <= 1e-15 * (1.0 + fabs(y))) break;
+    }
+    if (it == 100) return 1;
+    x[i] = y;
+  }
+  return 0;
+}
+
+int or_pde_step(int scheme, int M, int n_sweeps, int nu, double dt,
+                int nx, double Lx, double a, double d, double r,
+                double left, double right, const double *phi_n,
+                double *phi_out, double *incr) {
+  pde_ctx c;
+  memset(&c, 0, sizeof(c));
+  c.nx = nx; c.dx = Lx / nx; c.a = a; c.d = d; c.r = r; c.left = left; c.right = right;
+  pde_ghost_weights(&c);
+  or_problem p = {nx, &c, pde_fe, pde_fd, pde_fr, pde_sd, pde_sr, NULL};
+  return or_step(&p, scheme, M, n_sweeps, nu, dt, phi_n, phi_out, incr);
+}
+
+/* ======================================================================= */
+/* Combustion ADR (Sec. 2 and Sec. 3.3)                                    */
+/* ======================================================================= */
+/*
+ * Model readings (the paper's 1D low-Mach solver is reduced to what the
+ * hot path needs):
+ *  - constant density rho and a prescribed, discretely divergence-free face
+ *    velocity, so the continuity update S2 is trivial and the divergence
+ *    constraint / volume-discrepancy correction are not solved;
+ *  - state per cell: Y_1..Y_N and mass-specific enthalpy h (formation
+ *    enthalpy included); T is diagnosed from sum_i Y_i h_i(T) = h;
+ *  - since rho is constant, every F below is d(phi)/dt = (1/rho) times the
+ *    right-hand side of eqs. species_equation / enthalpy_equation;
+ *  - species diffusivity D_i(T) = D0_i (T/T_ref)^e and thermal diffusivity
+ *    lambda/(rho cp) = alpha0 (T/T_ref)^e; face coefficients are harmonic
+ *    means; second-order compact diffusion fluxes; fourth-order centred
+ *    advective face values;
+ *  - dominant species i0: its flux is minus the sum of the others, so after
+ *    each diffusion step Y_i0 = 1 - sum_{i != i0} Y_i;
+ *  - the differential-diffusion sum of eq. enthalpy_equation is explicit
+ *    (weights Q~E), as in step S4, with the i0 flux from the closure;
+ *  - mass-action kinetics, k_f = A T^beta exp(-Ea/(R T)), k_r = k_f/K_c,
+ *    K_c = exp(-sum_i nu_i g_i/(R T)) (p_ref/(R T))^{sum_i nu_i};
+ *  - each implicit diffusion solve ends with the flux-form reconstruction
+ *    x := rhs + w F_D[coef](x), which makes every update conservative.
+ */
+
+typedef struct adr_ctx {
+  const or_mech *m;
+  const or_adr_cfg *g;
+  int cells, N;
+  or_adr_stats *st;
+} adr_ctx;
+
+/* thermo (NASA-7, one range) */
+static double cp_R(const double *a, double T) {
+  return a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+}
+static double h_RT(const double *a, double T) {
+  return a[0] + a[1] * T / 2.0 + a[2] * T * T / 3.0 + a[3] * T * T * T / 4.0
+       + a[4] * T * T * T * T / 5.0 + a[5] / T;
+}
+static double s_R(const double *a, double T) {
+  return a[0] * log(T) + a[1] * T + a[2] * T * T / 2.0 + a[3] * T * T * T / 3.0
+       + a[4] * T * T * T * T / 4.0 + a[6];
+}
+
+double or_species_h(const or_mech *m, int i, double T) {
+  return R_UNIV / m->W[i] * T * h_RT(m->nasa7 + 7 * i, T);
+}
+double or_species_cp(const or_mech *m, int i, double T) {
+  return R_UNIV / m->W[i] * cp_R(m->nasa7 + 7 * i, T);
+}
+double or_species_s_R(const or_mech *m, int i, double T) {
+  return s_R(m->nasa7 + 7 * i, T);
+}
+
+static double mix_h(const or_mech *m, const double *Y, int stride, double T) {
+  double s = 0.0;
+  for (int i = 0; i < m->N; ++i) s += Y[(size_t)i * stride] * or_species_h(m, i, T);
+  return s;
+}
+static double mix_cp(const or_mech *m, const double *Y, int stride, double T) {
+  double s = 0.0;
+  for (int i = 0; i < m->N; ++i) s += Y[(size_t)i * stride] * or_species_cp(m, i, T);
+  return s;
+}
+
+/* T from sum_i Y_i h_i(T) = h: Newton safeguarded by bisection on [50, 6000] K,
+ * the range on which the one-range polynomials are used (cp > 0 there). */
+static int T_of_cell(const or_mech *m, const double *Y, int stride, double h, double *Tout) {
+  double lo = 50.0, hi = 6000.0;
+  if (mix_h(m, Y, stride, lo) - h > 0.0 || mix_h(m, Y, stride, hi) - h < 0.0) { *Tout = NAN; return 1; }
+  double T = 1000.0;
+  for (int it = 0; it < 200; ++it) {
+    double f = mix_h(m, Y, stride, T) - h;
+    if (f > 0.0) hi = T; else lo = T;
+    double df = mix_cp(m, Y, stride, T);
+    double Tn = T - f / df;
+    if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+    double dT = Tn - T;
+    T = Tn;
+    if (fabs(dT) <= 1e-14 * T) { *Tout = T; return 0; }
+  }
+  *Tout = T;
+  return 0;
+}
+
+int or_h_from_T(const or_mech *m, int cells, const double *Y, const double *T, double *h) {
+  for (int c = 0; c < cells; ++c) h[c] = mix_h(m, Y + c, cells, T[c]);
+  return 0;
+}
+
+int or_T_from_h(const or_mech *m, int cells, const double *Y, const double *h, double *T) {
+  int bad = 0;
+  for (int c = 0; c < cells; ++c) bad |= T_of_cell(m, Y + c, cells, h[c], &T[c]);
+  return bad;
+}
+
+/* mass-action production rates of one cell */
+void or_wdot(const or_mech *m, double rho, const double *Y, double T, double *wdot, double *q) {
+  int N = m->N;
+  double conc[512];
+  for (int i = 0; i < N; ++i) { conc[i] = rho * Y[i] / m->W[i]; wdot[i] = 0.0; }
+  for (int r = 0; r < m->R; ++r) {
+    const int *nf = m->nu_f + (size_t)r * N, *nr = m->nu_r + (size_t)r * N;
+    double kf = m->A[r] * pow(T, m->beta[r]) * exp(-m->Ea[r] / (R_UNIV * T));
+    double dg = 0.0, dn = 0.0;
+    for (int i = 0; i < N; ++i) {
+      int nu = nr[i] - nf[i];
+      if (nu) {
+        const double *a = m->nasa7 + 7 * i;
+        dg += nu * (h_RT(a, T) - s_R(a, T));
+        dn += nu;
+      }
+    }
+    double Kc = exp(-dg) * pow(m->p_ref / (R_UNIV * T), dn);
+    double kr = kf / Kc;
+    double Ff = 1.0, Fr = 1.0;
+    for (int i = 0; i < N; ++i) {
+      for (int e = 0; e < nf[i]; ++e) Ff *= conc[i];
+      for (int e = 0; e < nr[i]; ++e) Fr *= conc[i];
+    }
+    double qr = kf * Ff - kr * Fr;
+    if (q) q[r] = qr;
+    for (int i = 0; i < N; ++i) {
+      int nu = nr[i] - nf[i];
+      if (nu) wdot[i] += m->W[i] * nu * qr;
+    }
+  }
+}
+
+/* d(wdot_i)/d(Y_j, T), analytic; J[N][N+1] */
+void or_wdot_jac(const or_mech *m, double rho, const double *Y, double T, double *J) {
+  int N = m->N;
+  double conc[512];
+  for (int i = 0; i < N; ++i) conc[i] = rho * Y[i] / m->W[i];
+  memset(J, 0, sizeof(double) * (size_t)N * (N + 1));
+  for (int r = 0; r < m->R; ++r) {
+    const int *nf = m->nu_f + (size_t)r * N, *nr = m->nu_r + (size_t)r * N;
+    double kf = m->A[r] * pow(T, m->beta[r]) * exp(-m->Ea[r] / (R_UNIV * T));
+    double dg = 0.0, dn = 0.0, dh = 0.0;
+    for (int i = 0; i < N; ++i) {
+      int nu = nr[i] - nf[i];
+      if (nu) {
+        const double *a = m->nasa7 + 7 * i;
+        dg += nu * (h_RT(a, T) - s_R(a, T));
+        dh += nu * h_RT(a, T);
+        dn += nu;
+      }
+    }
+    double Kc = exp(-dg) * pow(m->p_ref / (R_UNIV * T), dn);
+    double kr = kf / Kc;
+    /* d ln kf/dT = beta/T + Ea/(R T^2);  d ln Kc/dT = sum nu h/(R T^2) - dn/T */
+    double dlnkf = m->beta[r] / T + m->Ea[r] / (R_UNIV * T * T);
+    double dlnKc = dh / T - dn / T;
+    double Ff = 1.0, Fr = 1.0;
+    for (int i = 0; i < N; ++i) {
+      for (int e = 0; e < nf[i]; ++e) Ff *= conc[i];
+      for (int e = 0; e < nr[i]; ++e) Fr *= conc[i];
+    }
+    double dqdT = kf * dlnkf * Ff - kr * (dlnkf - dlnKc) * Fr;
+    double dq[512];
+    for (int j = 0; j < N; ++j) {
+      /* d(prod_i c_i^{nu_i})/d c_j = nu_j c_j^{nu_j - 1} prod_{i != j} c_i^{nu_i} */
+      double dFf = 0.0, dFr = 0.0;
+      if (nf[j]) {
+        dFf = nf[j];
+        for (int e = 0; e < nf[j] - 1; ++e) dFf *= conc[j];
+        for (int i = 0; i < N; ++i) if (i != j) for (int e = 0; e < nf[i]; ++e) dFf *= conc[i];
+      }
+      if (nr[j]) {
+        dFr = nr[j];
+        for (int e = 0; e < nr[j] - 1; ++e) dFr *= conc[j];
+        for (int i = 0; i < N; ++i) if (i != j) for (int e = 0; e < nr[i]; ++e) dFr *= conc[i];
+      }
+      dq[j] = (kf * dFf - kr * dFr) * rho / m->W[j];
+    }
+    for (int i = 0; i < N; ++i) {
+      int nu = nr[i] - nf[i];
+      if (!nu) continue;
+      double f = m->W[i] * nu;
+      for (int j = 0; j < N; ++j) J[(size_t)i * (N + 1) + j] += f * dq[j];
+      J[(size_t)i * (N + 1) + N] += f * dqdT;
+    }
+  }
+}
+
+/* Reaction step S5: rho Y - wdt wdot(Y) = rho b with h fixed; unknowns
+ * x = (Y_1..Y_N, T); residual r_Y = Y - wdt wdot/rho - b,
+ * r_T = sum Y_i h_i(T) - hstar; plain Newton from the guess with the analytic
+ * Jacobian and dense partial-pivot LU. Stops once the applied step satisfies
+ * max_i |dY_i| <= rtol and |dT| <= rtol T. */
+int or_reaction_newton(const or_mech *m, double rho, double wdt, const double *b,
+                       double hstar, double *x, double rtol, int maxit) {
+  int N = m->N, n = N + 1;
+  double J[64 * 64], Jw[64 * 65], r[64], wd[64];   /* n <= 64 */
+  if (n > 64) return -1;
+  for (int it = 1; it <= maxit; ++it) {
+    double T = x[N];
+    or_wdot(m, rho, x, T, wd, NULL);
+    for (int i = 0; i < N; ++i) r[i] = x[i] - wdt * wd[i] / rho - b[i];
+    r[N] = mix_h(m, x, 1, T) - hstar;
+    or_wdot_jac(m, rho, x, T, Jw);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j <= N; ++j)
+        J[i * n + j] = (i == j ? 1.0 : 0.0) - wdt * Jw[i * (N + 1) + j] / rho;
+    for (int j = 0; j < N; ++j) J[N * n + j] = or_species_h(m, j, T);
+    J[N * n + N] = mix_cp(m, x, 1, T);
+    for (int i = 0; i < n; ++i) r[i] = -r[i];
+    if (dense_solve(n, J, r)) return -2;
+    double dmax = 0.0;
+    for (int i = 0; i < N; ++i) { x[i] += r[i]; if (fabs(r[i]) > dmax) dmax = fabs(r[i]); }
+    x[N] += r[N];
+    if (!(x[N] > 0.0) || !isfinite(x[N])) return -3;
+    if (dmax <= rtol && fabs(r[N]) <= rtol * x[N]) return it;
+  }
+  return -4;
+}
+
+/* periodic neighbour of cell c, offset s along direction d */
+static int nbr(const or_adr_cfg *g, int c, int d, int s) {
+  int x = c % g->nx, y = (c / g->nx) % g->ny, z = c / (g->nx * g->ny);
+  if (d == 0) x = ((x + s) % g->nx + g->nx) % g->nx;
+  else if (d == 1) y = ((y + s) % g->ny + g->ny) % g->ny;
+  else z = ((z + s) % g->nz + g->nz) % g->nz;
+  return x + g->nx * (y + g->ny * z);
+}
+
+/* theta(T) = (T/T_ref)^e at cells, harmonic mean at the low face of each cell */
+static void face_theta(const or_mech *m, const or_adr_cfg *g, int cells, const double *T, double *thf) {
+  double *th = vec(cells);
+  for (int c = 0; c < cells; ++c) th[c] = pow(T[c] / m->T_ref, m->theta_exp);
+  for (int d = 0; d < g->dim; ++d)
+    for (int c = 0; c < cells; ++c) {
+      double a = th[nbr(g, c, d, -1)], b = th[c];
+      thf[(size_t)d * cells + c] = 2.0 * a * b / (a + b);
+    }
+  free(th);
+}
+
+/* sum_d [thf(c+e)(x(c+e) - x(c)) - thf(c)(x(c) - x(c-e))] */
+static double lap_theta(const or_adr_cfg *g, int cells, const double *thf, const double *x, int c) {
+  double s = 0.0;
+  for (int d = 0; d < g->dim; ++d) {
+    int cp = nbr(g, c, d, 1), cm = nbr(g, c, d, -1);
+    s += thf[(size_t)d * cells + cp] * (x[cp] - x[c]) - thf[(size_t)d * cells + c] * (x[c] - x[cm]);
+  }
+  return s;
+}
+
+static void adr_T(adr_ctx *a, const double *phi, double *T) {
+  if (or_T_from_h(a->m, a->cells, phi, phi + (size_t)a->N * a->cells, T) && a->st) a->st->tdiag_fail++;
+}
+
+/* F_E: advection of every field plus explicit differential diffusion of h */
+static void adr_fe(void *cv, const double *phi, double *out) {
+  adr_ctx *a = (adr_ctx *)cv;
+  const or_adr_cfg *g = a->g;
+  const or_mech *m = a->m;
+  int C = a->cells, N = a->N;
+  for (int f = 0; f <= N; ++f) {
+    const double *x = phi + (size_t)f * C;
+    for (int c = 0; c < C; ++c) {
+      double s = 0.0;
+      for (int d = 0; d < g->dim; ++d) {
+        int cm2 = nbr(g, c, d, -2), cm = nbr(g, c, d, -1), cp = nbr(g, c, d, 1), cp2 = nbr(g, c, d, 2);
+        double lo = (7.0 * (x[cm] + x[c]) - (x[cm2] + x[cp])) / 12.0;     /* low face of c  */
+        double hi = (7.0 * (x[c] + x[cp]) - (x[cm] + x[cp2])) / 12.0;     /* low face of c+e */
+        s += g->vel[(size_t)d * C + cp] * hi - g->vel[(size_t)d * C + c] * lo;
+      }
+      out[(size_t)f * C + c] = -s / g->dx;
+    }
+  }
+  /* differential diffusion of h: flux/rho at each face
+   * q = sum_i hbar_i (Gamma_i/rho + alpha theta dY_i/dx), Gamma_i/rho =
+   * -D0_i theta dY_i/dx for i != i0 and minus their sum for i0 */
+  double *T = vec(C), *thf = vec(3 * C), *q = vec(3 * C);
+  adr_T(a, phi, T);
+  face_theta(m, g, C, T, thf);
+  for (int d = 0; d < g->dim; ++d)
+    for (int c = 0; c < C; ++c) {
+      int cm = nbr(g, c, d, -1);
+      double th = thf[(size_t)d * C + c];
+      double gam_i0 = 0.0, s = 0.0;
+      for (int i = 0; i < N; ++i) {
+        double dY = (phi[(size_t)i * C + c] - phi[(size_t)i * C + cm]) / g->dx;
+        double hbar = 0.5 * (or_species_h(m, i, T[cm]) + or_species_h(m, i, T[c]));
+        if (i != g->i0) {
+          double gam = -m->D0[i] * th * dY;
+          gam_i0 -= gam;
+          s += hbar * (gam + m->alpha0 * th * dY);
+        } else {
+          s += hbar * m->alpha0 * th * dY;
+        }
+      }
+      {
+        int i = g->i0;
+        double hbar = 0.5 * (or_species_h(m, i, T[cm]) + or_species_h(m, i, T[c]));
+        s += hbar * gam_i0;
+      }
+      q[(size_t)d * C + c] = s;
+    }
+  for (int c = 0; c < C; ++c) {
+    double s = 0.0;
+    for (int d = 0; d < g->dim; ++d) s += q[(size_t)d * C + nbr(g, c, d, 1)] - q[(size_t)d * C + c];
+    out[(size_t)N * C + c] += -s / g->dx;
+  }
+  free(T); free(thf); free(q);
+}
+
+/* F_D with the state's own coefficients */
+static void adr_fd(void *cv, const double *phi, double *out) {
+  adr_ctx *a = (adr_ctx *)cv;
+  const or_adr_cfg *g = a->g;
+  const or_mech *m = a->m;
+  int C = a->cells, N = a->N;
+  double *T = vec(C), *thf = vec(3 * C);
+  adr_T(a, phi, T);
+  face_theta(m, g, C, T, thf);
+  double inv = 1.0 / (g->dx * g->dx);
+  for (int c = 0; c < C; ++c) out[(size_t)g->i0 * C + c] = 0.0;
+  for (int f = 0; f <= N; ++f) {
+    if (f == g->i0) continue;
+    double k = (f < N) ? m->D0[f] : m->alpha0;
+    for (int c = 0; c < C; ++c) {
+      double v = k * inv * lap_theta(g, C, thf, phi + (size_t)f * C, c);
+      out[(size_t)f * C + c] = v;
+      if (f < N) out[(size_t)g->i0 * C + c] -= v;
+    }
+  }
+  free(T); free(thf);
+}
+
+static void adr_fr(void *cv, const double *phi, double *out) {
+  adr_ctx *a = (adr_ctx *)cv;
+  int C = a->cells, N = a->N;
+  double *T = vec(C);
+  double Y[512], wd[512];
+  adr_T(a, phi, T);
+  for (int c = 0; c < C; ++c) {
+    for (int i = 0; i < N; ++i) Y[i] = phi[(size_t)i * C + c];
+    or_wdot(a->m, a->g->rho, Y, T[c], wd, NULL);
+    for (int i = 0; i < N; ++i) out[(size_t)i * C + c] = wd[i] / a->g->rho;
+    out[(size_t)N * C + c] = 0.0;
+  }
+  free(T);
+}
+
+/* conjugate gradients on (I - cw L_theta) x = rhs (symmetric positive definite) */
+static int cg_solve(adr_ctx *a, const double *thf, double cw, const double *rhs, double *x) {
+  const or_adr_cfg *g = a->g;
+  int C = a->cells;
+  double *r = vec(C), *p = vec(C), *Ap = vec(C);
+  double bn = 0.0, rr = 0.0;
+  memcpy(x, rhs, sizeof(double) * C);
+  for (int c = 0; c < C; ++c) {
+    r[c] = rhs[c] - (x[c] - cw * lap_theta(g, C, thf, x, c));
+    p[c] = r[c];
+    rr += r[c] * r[c];
+    bn += rhs[c] * rhs[c];
+  }
+  int it, rc = 1;
+  double tol2 = g->lin_rtol * g->lin_rtol * bn;
+  for (it = 0; it < g->lin_maxit; ++it) {
+    if (rr <= tol2) { rc = 0; break; }
+    double pAp = 0.0;
+    for (int c = 0; c < C; ++c) { Ap[c] = p[c] - cw * lap_theta(g, C, thf, p, c); pAp += p[c] * Ap[c]; }
+    double al = rr / pAp, rn = 0.0;
+    for (int c = 0; c < C; ++c) { x[c] += al * p[c]; r[c] -= al * Ap[c]; rn += r[c] * r[c]; }
+    double be = rn / rr;
+    rr = rn;
+    for (int c = 0; c < C; ++c) p[c] = r[c] + be * p[c];
+  }
+  if (a->st) { a->st->lin_solves++; a->st->lin_iters += it; if (rc) a->st->lin_fail++; }
+  free(r); free(p); free(Ap);
+  return rc;
+}
+
+/* D-step solve for every field but i0, flux-form reconstruction, closure */
+static int adr_sd(void *cv, double wdt, const double *coef, const double *rhs, double *x) {
+  adr_ctx *a = (adr_ctx *)cv;
+  const or_adr_cfg *g = a->g;
+  const or_mech *m = a->m;
+  int C = a->cells, N = a->N, rc = 0;
+  double *T = vec(C), *thf = vec(3 * C), *y = vec(C);
+  adr_T(a, coef, T);
+  face_theta(m, g, C, T, thf);
+  double inv = 1.0 / (g->dx * g->dx);
+  for (int f = 0; f <= N; ++f) {
+    if (f == g->i0) continue;
+    double cw = wdt * ((f < N) ? m->D0[f] : m->alpha0) * inv;
+    const double *b = rhs + (size_t)f * C;
+    rc |= cg_solve(a, thf, cw, b, y);
+    for (int c = 0; c < C; ++c) x[(size_t)f * C + c] = b[c] + cw * lap_theta(g, C, thf, y, c);
+  }
+  for (int c = 0; c < C; ++c) {
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) if (i != g->i0) s += x[(size_t)i * C + c];
+    x[(size_t)g->i0 * C + c] = 1.0 - s;
+  }
+  free(T); free(thf); free(y);
+  return rc;
+}
+
+static int adr_sr(void *cv, double wdt, const double *b, const double *guess, double *x) {
+  adr_ctx *a = (adr_ctx *)cv;
+  const or_adr_cfg *g = a->g;
+  int C = a->cells, N = a->N, rc = 0;
+  double *Tg = vec(C);
+  adr_T(a, guess, Tg);
+  double xx[512], bb[512];
+  for (int c = 0; c < C; ++c) {
+    for (int i = 0; i < N; ++i) { xx[i] = guess[(size_t)i * C + c]; bb[i] = b[(size_t)i * C + c]; }
+    xx[N] = Tg[c];
+    double hstar = b[(size_t)N * C + c];
+    int it = or_reaction_newton(a->m, g->rho, wdt, bb, hstar, xx, g->newton_rtol, g->newton_maxit);
+    if (a->st) {
+      a->st->newton_solves++;
+      if (it > 0) { a->st->newton_iters += it; if (it > a->st->newton_maxit_seen) a->st->newton_maxit_seen = it; }
+      else a->st->newton_fail++;
+    }
+    if (it <= 0) rc = 1;
+    for (int i = 0; i < N; ++i) x[(size_t)i * C + c] = xx[i];
+    x[(size_t)N * C + c] = hstar;
+  }
+  free(Tg);
+  return rc;
+}
+
+int or_adr_step(const or_mech *mech, const or_adr_cfg *cfg, int scheme, int M,
+                int n_sweeps, int nu, double dt, const double *phi_n,
+                double *phi_out, double *incr, or_adr_stats *stats) {
+  adr_ctx a = {mech, cfg, cfg->nx * cfg->ny * cfg->nz, mech->N, stats};
+  or_problem p = {(mech->N + 1) * a.cells, &a, adr_fe, adr_fd, adr_fr, adr_sd, adr_sr, NULL};
+  return or_step(&p, scheme, M, n_sweeps, nu, dt, phi_n, phi_out, incr);
+}
+
+int or_adr_operators(const or_mech *mech, const or_adr_cfg *cfg, const double *phi,
+                     double *FE, double *FD, double *FR) {
+  adr_ctx a = {mech, cfg, cfg->nx * cfg->ny * cfg->nz, mech->N, NULL};
+  if (FE) adr_fe(&a, phi, FE);
+  if (FD) adr_fd(&a, phi, FD);
+  if (FR) adr_fr(&a, phi, FR);
+  return 0;
+}
+
+int or_adr_solve_diff(const or_mech *mech, const or_adr_cfg *cfg, double wdt,
+                      const double *coef_state, const double *rhs, double *x) {
+  adr_ctx a = {mech, cfg, cfg->nx * cfg->ny * cfg->nz, mech->N, NULL};
+  return adr_sd(&a, wdt, coef_state, rhs, x);
+}

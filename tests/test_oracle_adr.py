@@ -1,0 +1,331 @@
+"""Pins of the oracle's combustion ADR model (Sec. 2, Sec. 3.3)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1801_01201_gb300 import inputs as I
+
+R_U = 8.314462618
+
+
+@pytest.fixture(scope="module")
+def flame9():
+    mech, fl, w = I.build_workload("flame1d_128_n9")
+    return mech, fl, O.ADR(mech, fl)
+
+
+def test_thermo_derivatives(flame9):
+    mech, fl, ad = flame9
+    for i in range(mech.n_species):
+        for T in (350.0, 900.0, 1800.0, 2600.0):
+            e = 1e-4 * T
+            dh = (ad.species_h(i, T + e) - ad.species_h(i, T - e)) / (2 * e)
+            assert dh == pytest.approx(ad.species_cp(i, T), rel=1e-7)
+            # d(s/R)/dT = (cp/R)/T with molar cp/R = cp_mass W/R
+            ds = (ad.species_s_R(i, T + e) - ad.species_s_R(i, T - e)) / (2 * e)
+            assert ds == pytest.approx(ad.species_cp(i, T) * mech.W[i] / R_U / T, rel=1e-7)
+
+
+def test_temperature_roundtrip(flame9):
+    mech, fl, ad = flame9
+    h = ad.h_from_T(fl.Y, fl.T)
+    T = ad.T_from_h(fl.Y, h)
+    np.testing.assert_allclose(T, fl.T, rtol=1e-13)
+
+
+def _flux_scale(ad, Y, T):
+    """Size of the individual reaction fluxes at a slightly perturbed state."""
+    rng = np.random.default_rng(0)
+    Yp = Y * (1 + 1e-3 * rng.standard_normal(Y.shape))
+    return np.abs(ad.wdot(Yp, T)[1])
+
+
+@pytest.mark.parametrize("which", ["unburnt", "burnt", "front"])
+def test_detailed_balance_at_anchor_equilibria(flame9, which):
+    """K_c from the thermo makes every reaction balanced at the anchored equilibria."""
+    mech, fl, ad = flame9
+    if which == "unburnt":
+        Y, T = mech.Y_u, mech.T_u
+    elif which == "burnt":
+        Y, T = mech.Y_b, mech.T_b
+    else:
+        T = 1234.5
+        Y = I.equilibrium_path_composition(mech, np.array([T]))[:, 0]
+    q = ad.wdot(Y, T)[1]
+    scale = _flux_scale(ad, Y, T)
+    assert np.all(np.abs(q) <= 1e-9 * scale + 1e-300), np.abs(q) / scale
+
+
+def test_mass_and_element_conservation_of_rates(flame9):
+    mech, fl, ad = flame9
+    rng = np.random.default_rng(1)
+    for c in (3, 40, 64, 100):
+        Y = fl.Y[:, c] * (1 + 0.1 * rng.standard_normal(mech.n_species))
+        w, q = ad.wdot(Y, fl.T[c])
+        scale = np.sum(np.abs(mech.W[:, None] * (mech.nu_r - mech.nu_f).T * q[None, :]))
+        assert abs(w.sum()) <= 1e-14 * scale
+        elem = mech.elem @ (w / mech.W)
+        assert np.all(np.abs(elem) <= 1e-13 * scale / mech.W.min())
+
+
+def test_jacobian_matches_central_differences(flame9):
+    mech, fl, ad = flame9
+    rng = np.random.default_rng(2)
+    N = mech.n_species
+    for c in (10, 40, 64):
+        Y = fl.Y[:, c] * (1 + 0.05 * rng.standard_normal(N))
+        T = fl.T[c] * 1.01
+        J = ad.wdot_jac(Y, T)
+        for j in range(N + 1):
+            x = np.concatenate([Y, [T]])
+            # rates are at most quadratic in each concentration, so a central
+            # difference with a large step is exact in Y; T needs a small step
+            e = 1e-2 * abs(x[j]) if j < N else 1e-5 * x[j]
+            xp, xm = x.copy(), x.copy()
+            xp[j] += e
+            xm[j] -= e
+            wp, wm = ad.wdot(xp[:N], xp[N])[0], ad.wdot(xm[:N], xm[N])[0]
+            fd = (wp - wm) / (2 * e)
+            scale = np.max(np.abs(fd)) + np.max(np.abs(J[:, j])) + 1e-300
+            noise = 1e-13 * np.max(np.abs(wp)) / e      # round-off of the differenced rates
+            assert np.max(np.abs(fd - J[:, j])) <= 1e-6 * scale + noise, (c, j)
+
+
+def _residual(ad, mech, x, b, hstar, wdt):
+    N = mech.n_species
+    r = np.empty(N + 1)
+    r[:N] = x[:N] - wdt * ad.wdot(x[:N], x[N])[0] / ad.flame.rho - b
+    r[N] = sum(x[i] * ad.species_h(i, x[N]) for i in range(N)) - hstar
+    return r
+
+
+def test_reaction_newton_root_is_unique_and_matches_library_solver(flame9):
+    from scipy.optimize import fsolve
+    mech, fl, ad = flame9
+    N = mech.n_species
+    wdt = 1e-5 / 3
+    for c in (30, 34, 60):
+        Y = fl.Y[:, c] * (1 + 0.02 * np.cos(np.arange(N)))
+        b = Y.copy()
+        hstar = ad.h_from_T(fl.Y[:, c:c + 1], fl.T[c:c + 1])[0]
+        x0 = np.concatenate([Y, [fl.T[c]]])
+        x1, it1 = ad.reaction_newton(wdt, b, hstar, x0)
+        x2, it2 = ad.reaction_newton(wdt, b, hstar, x0 * np.r_[np.ones(N) * 0.999, 1.02])
+        assert it1 > 0 and it2 > 0
+        np.testing.assert_allclose(x1, x2, rtol=1e-11, atol=1e-14)
+        sc = np.r_[np.ones(N), 1.0 / abs(hstar)]
+
+        def f(z):
+            return _residual(ad, mech, z / sc, b, hstar, wdt) * sc
+        z = fsolve(f, x1 * sc, xtol=1e-14)
+        np.testing.assert_allclose(z / sc, x1, rtol=1e-10, atol=1e-13)
+        # residual at the root sits at the round-off floor of the stiff rate terms
+        stiff = 1.0 + wdt * np.max(np.abs(ad.wdot_jac(x1[:N], x1[N])[:, :N])) / fl.rho
+        assert np.max(np.abs(_residual(ad, mech, x1, b, hstar, wdt)[:N])) < 1e-13 * stiff
+
+
+def _smooth_state(mech, ad, nx, dx, amp=0.05, T=None):
+    x = (np.arange(nx) + 0.5) * dx
+    L = nx * dx
+    Y = np.tile(mech.Y_b[:, None], (1, nx)).copy()
+    k = 2 * np.pi / L
+    j = 0 if mech.i0 != 0 else 1
+    # exact cell averages of Y_j = Y_b,j (1 + amp sin(kx)); the dominant species absorbs the sum
+    avg = mech.Y_b[j] * (1 + amp * (np.cos(k * (x - dx / 2)) - np.cos(k * (x + dx / 2))) / (k * dx))
+    Y[mech.i0] += Y[j] - avg
+    Y[j] = avg
+    Tc = np.full(nx, mech.T_ref if T is None else T)
+    return Y, Tc, j, k, x
+
+
+def test_advection_is_fourth_order_and_conservative():
+    mech = I.make_mechanism(1801, 9, 21)
+    errs = []
+    for nx in (32, 64, 128):
+        L = 1e-2
+        dx = L / nx
+        fl = I.flame_1d(mech, 0, nx=nx, dx=dx, u=1.5)
+        Y, T, j, k, x = _smooth_state(mech, None, nx, dx)
+        fl.Y, fl.T = Y, T
+        ad = O.ADR(mech, fl)
+        phi = ad.state_from_YT(Y, T)
+        FE, FD, FR = ad.operators(phi)
+        # exact cell average of -u d/dx [Y_b,j (1 + amp sin kx)]
+        exact = -1.5 * mech.Y_b[j] * 0.05 * (np.sin(k * (x + dx / 2)) - np.sin(k * (x - dx / 2))) / dx
+        errs.append(np.max(np.abs(FE[j] - exact)))
+        assert abs(FE.sum(axis=1)).max() <= 1e-12 * np.abs(FE).max()
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 3.8), orders
+
+
+def test_diffusion_operator_fourier_eigenvalue_and_closure():
+    mech = I.make_mechanism(1801, 9, 21)
+    nx, dx = 64, 1e-4
+    fl = I.flame_1d(mech, 0, nx=nx, dx=dx)
+    Y, T, j, k, x = _smooth_state(mech, None, nx, dx)
+    fl.Y, fl.T = Y, T
+    ad = O.ADR(mech, fl)
+    phi = ad.state_from_YT(Y, T)     # T = T_ref everywhere: theta = 1
+    FE, FD, FR = ad.operators(phi)
+    lam = -4.0 / dx ** 2 * np.sin(k * dx / 2) ** 2
+    want = mech.D0[j] * lam * (Y[j] - Y[j].mean())
+    np.testing.assert_allclose(FD[j], want, rtol=1e-9, atol=1e-9 * np.abs(want).max())
+    others = [i for i in range(mech.n_species) if i != mech.i0]
+    np.testing.assert_allclose(FD[mech.i0], -FD[others].sum(axis=0), atol=1e-12 * np.abs(FD).max())
+    assert abs(FD.sum(axis=1)).max() <= 1e-10 * np.abs(FD).max()
+
+
+def test_differential_diffusion_vanishes_for_unit_lewis_numbers():
+    mech = I.make_mechanism(1801, 9, 21)
+    mech.D0 = np.full(mech.n_species, mech.alpha0)
+    mech_fl = I.flame_1d(mech, 0, nx=64, dx=1e-4)
+    ad = O.ADR(mech, mech_fl)
+    phi = ad.state_from_YT(mech_fl.Y, mech_fl.T)
+    FE, FD, FR = ad.operators(phi)
+    N = mech.n_species
+    # advective part of h alone: a state with the same h and uniform velocity
+    x = phi[N]
+    fa = -(1.0 / 1e-4) * ((7 * (x + np.roll(x, -1)) - (np.roll(x, 1) + np.roll(x, -2))) / 12
+                          - (7 * (np.roll(x, 1) + x) - (np.roll(x, 2) + np.roll(x, -1))) / 12)
+    np.testing.assert_allclose(FE[N], fa, atol=1e-9 * np.abs(fa).max())
+
+
+def test_enthalpy_flux_equals_fourier_plus_species_enthalpy_form():
+    """(F_E - F_A + F_D)(h) -> div(lambda grad T + sum h_i rho D_i grad Y_i)/rho, lambda = rho alpha cp.
+
+    An independent form of the energy flux of eq. enthalpy_equation; agreement at
+    second order on a smooth periodic state pins the sign of the differential term.
+    """
+    mech = I.make_mechanism(1801, 9, 21)
+    N = mech.n_species
+    errs = []
+    for nx in (64, 128, 256):
+        L = 1e-2
+        dx = L / nx
+        fl = I.flame_1d(mech, 0, nx=nx, dx=dx, u=0.0)
+        xc = (np.arange(nx) + 0.5) * dx
+        s = 0.5 + 0.3 * np.sin(2 * np.pi * xc / L)
+        fl.T = 1000 + 600 * np.sin(2 * np.pi * xc / L + 0.3)
+        fl.Y = I.equilibrium_path_composition(mech, 300 + 1700 * s)
+        ad = O.ADR(mech, fl)
+        phi = ad.state_from_YT(fl.Y, fl.T)
+        FE, FD, FR = ad.operators(phi)
+        got = FE[N] + FD[N]
+        # independent evaluation with centred differences of point fields
+        T = fl.T
+        th = (T / mech.T_ref) ** mech.theta_exp
+        cp = np.array([sum(fl.Y[i, c] * ad.species_cp(i, T[c]) for i in range(N)) for c in range(nx)])
+        hs = np.array([[ad.species_h(i, T[c]) for c in range(nx)] for i in range(N)])
+        D = mech.D0[:, None] * th[None, :]
+        D[mech.i0] = 0.0
+
+        def ddx(f):
+            return (np.roll(f, -1) - np.roll(f, 1)) / (2 * dx)
+        gY = np.array([ddx(fl.Y[i]) for i in range(N)])
+        flux_sp = D * gY
+        flux_sp[mech.i0] = -flux_sp.sum(axis=0)       # dominant species closes the fluxes
+        q = mech.alpha0 * th * cp * ddx(T) + np.sum(hs * flux_sp, axis=0)
+        want = ddx(q)
+        errs.append(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+    assert errs[-1] < 2e-2 and errs[0] / errs[-1] > 8.0, errs
+
+
+def _laplacian_1d(n):
+    A = -2 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+    A[0, -1] = A[-1, 0] = 1
+    return A
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 1), (4, 4, 4)])
+def test_diffusion_solve_matches_dense_direct_solve(dims):
+    mech = I.make_mechanism(1801, 9, 21)
+    nx, ny, nz = dims
+    dx = 4e-5
+    fl = I.flame_2d(mech, 0, n=8, dx=dx) if nz == 1 else I.flame_3d(mech, 0, n=4, dx=dx)
+    cells = nx * ny * nz
+    N = mech.n_species
+    ad = O.ADR(mech, fl)
+    coef = ad.state_from_YT(fl.Y, np.full(cells, mech.T_ref))      # theta = 1 everywhere
+    rng = np.random.default_rng(3)
+    rhs = coef * (1 + 0.1 * rng.standard_normal(coef.shape))
+    wdt = 0.25 * 5e-6
+    x, rc = ad.solve_diff(wdt, coef, rhs)
+    assert rc == 0
+    Lx, Ly, Lz = _laplacian_1d(nx), _laplacian_1d(ny), _laplacian_1d(nz)
+    Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    Lap = np.kron(np.kron(Iz, Iy), Lx) + np.kron(np.kron(Iz, Ly), Ix)
+    if nz > 1:
+        Lap += np.kron(np.kron(Lz, Iy), Ix)
+    for f in range(N + 1):
+        if f == mech.i0:
+            continue
+        c = wdt * (mech.D0[f] if f < N else mech.alpha0) / dx ** 2
+        want = np.linalg.solve(np.eye(cells) - c * Lap, rhs[f])
+        np.testing.assert_allclose(x[f], want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+        assert abs(x[f].sum() - rhs[f].sum()) <= 1e-13 * np.abs(rhs[f]).sum()
+    np.testing.assert_allclose(x[:N].sum(axis=0), 1.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("scheme,nu", [("CISDCQ", 2), ("MISDCQ", 1), ("MISDC", 1)])
+def test_step_invariants(scheme, nu):
+    mech = I.make_mechanism(1802, 21, 84)
+    fl = I.flame_2d(mech, 0, n=16, dx=4e-5, radius=16 * 4e-5 / 4, delta=2 * 4e-5)
+    ad = O.ADR(mech, fl)
+    phi = ad.state_from_YT(fl.Y, fl.T)
+    out, st = ad.step(phi, 5e-6, scheme, 2, 4, nu, n_steps=2)
+    N = mech.n_species
+    assert st["newton_fail"] == 0 and st["lin_fail"] == 0
+    np.testing.assert_allclose(out[:N].sum(axis=0), 1.0, atol=2e-15)
+    assert abs(out[N].sum() - phi[N].sum()) <= 1e-14 * np.abs(phi[N]).sum()
+    e0 = mech.elem @ (phi[:N] / mech.W[:, None])
+    e1 = mech.elem @ (out[:N] / mech.W[:, None])
+    np.testing.assert_allclose(e1.sum(axis=1), e0.sum(axis=1), rtol=1e-13)
+
+
+def _collocation_bruteforce(ad, phi0, dt, M=2):
+    """Newton with a finite-difference Jacobian on Phi_m = phi0 + dt sum_j q_mj F(Phi_j)."""
+    tau, Q, S, QI, QE = O.lobatto(M)
+    n = phi0.size
+    shape = phi0.shape
+
+    def F(p):
+        FE, FD, FR = ad.operators(p.reshape(shape))
+        return (FE + FD + FR).ravel()
+    F0 = F(phi0.ravel())
+
+    def G(Z):
+        Fs = [F0] + [F(Z[m * n:(m + 1) * n]) for m in range(M)]
+        out = np.empty_like(Z)
+        for m in range(M):
+            out[m * n:(m + 1) * n] = Z[m * n:(m + 1) * n] - phi0.ravel() - dt * sum(Q[m, j] * Fs[j] for j in range(M + 1))
+        return out
+    Z = np.tile(phi0.ravel(), M)
+    sc = np.tile(np.where(np.arange(n) >= shape[0] * shape[1] - shape[1], 1e-6, 1.0), M)   # h is O(1e6)
+    for _ in range(12):
+        g = G(Z)
+        J = np.empty((Z.size, Z.size))
+        for k in range(Z.size):
+            e = 1e-7 * max(abs(Z[k]), 1e-3 / sc[k])
+            Zp = Z.copy()
+            Zp[k] += e
+            J[:, k] = (G(Zp) - g) / e
+        dZ = np.linalg.solve(J, -g)
+        Z = Z + dZ
+        if np.max(np.abs(dZ * sc)) < 1e-14:
+            break
+    return Z[(M - 1) * n:].reshape(shape)
+
+
+@pytest.mark.slow
+def test_sweeps_converge_to_bruteforce_collocation():
+    mech = I.make_mechanism(7, 3, 2)
+    fl = I.flame_1d(mech, 0, nx=6, dx=1e-4, u=2.0)
+    ad = O.ADR(mech, fl)
+    phi = ad.state_from_YT(fl.Y, fl.T)
+    dt = 2e-5
+    coll = _collocation_bruteforce(ad, phi, dt)
+    N = mech.n_species
+    for scheme, nu in (("MISDCQ", 1), ("CISDCQ", 2), ("CISDCQ", 3)):
+        out, st = ad.step(phi, dt, scheme, 2, 60, nu)
+        np.testing.assert_allclose(out[:N], coll[:N], atol=1e-11)
+        np.testing.assert_allclose(out[N], coll[N], rtol=1e-11)
