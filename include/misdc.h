@@ -1,0 +1,199 @@
+/*
+ * misdc.h — C ABI of the GB300 (sm_103a) concurrent MISDC library.
+ *
+ * The library advances the constant-density species/enthalpy
+ * advection-diffusion-reaction system of Hamon, Day & Minion
+ * (arXiv:1801.01201, Sec. 2) with the spectral deferred correction sweeps of
+ * Sec. 3: serial MISDC (eqs. update_equation_misdc_discrete_form_D/R),
+ * MISDCQ (eqs. update_equation_misdcq_discrete_form_D/R) and the concurrent
+ * CISDCQ-nu (eqs. update_equation_amisdcq_discrete_form_D and _R_alt, lags
+ * initial_lagged_values_A/D/R, steps I1-I4 and S1-S7 of Sec. 3.3). In CISDCQ
+ * the diffusion step at node m+1 and the reaction step at node m run on two
+ * CUDA streams (the two "processors" of the pipelining of Sec. 3.2.2).
+ *
+ * Conventions (all entry points):
+ *  - Arrays are FP64 and laid out field-major: a state is [N+1][cells] with
+ *    Y_1..Y_N then the mass-specific enthalpy h (J/kg, formation included);
+ *    cells are x-fastest, then y, then z. Grids are periodic.
+ *  - "device" pointers are CUDA device (or managed) memory owned by the
+ *    caller; the library never frees them. "host" pointers are read during the
+ *    call only. The library owns its internal buffers (freed by
+ *    misdc_destroy).
+ *  - Calls taking a stream are stream-ordered on it (NULL = legacy default
+ *    stream) and do not synchronise unless stated. A stream-ordered call that
+ *    fails inside a kernel reports it through misdc_get_stats().status.
+ *  - Every call returns a misdc_status; on error misdc_last_error() gives a
+ *    thread-local message. No C++ exception crosses the ABI. A handle is used
+ *    by one host thread at a time.
+ *  - Units are SI (kg, m, s, mol, K, J).
+ */
+#ifndef MISDC_H
+#define MISDC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MISDC_OK = 0,
+  MISDC_E_INVALID = 1,   /* bad argument or size                               */
+  MISDC_E_CUDA = 2,      /* a CUDA runtime call failed                         */
+  MISDC_E_NEWTON = 3,    /* a reaction Newton solve hit its iteration limit    */
+  MISDC_E_MG = 4,        /* a diffusion solve missed its residual tolerance    */
+  MISDC_E_TIMEOUT = 5,   /* a bounded device wait gave up                      */
+  MISDC_E_NAN = 6,       /* non-finite value in a solve                        */
+  MISDC_E_OOM = 7,       /* device allocation failed                           */
+  MISDC_E_TDIAG = 8      /* temperature outside [50, 6000] K while diagnosing  */
+} misdc_status;
+
+typedef enum {
+  MISDC_SCHEME_MISDC = 0,    /* node-to-node MISDC (backward/forward Euler)     */
+  MISDC_SCHEME_MISDCQ = 1,   /* serial MISDC with LU-trick weights              */
+  MISDC_SCHEME_CISDCQ = 2    /* concurrent implicit SDCQ with nu nested iters   */
+} misdc_scheme;
+
+typedef enum { MISDC_PREC_FP64 = 0, MISDC_PREC_MIXED = 1 } misdc_precision;
+
+/* Mechanism (host arrays, copied at create). Mass-action kinetics:
+ * k_f = A T^beta exp(-Ea/(R T)), k_r = k_f/K_c,
+ * K_c = exp(-sum_i nu_i g_i/(R T)) (p_ref/(R T))^{sum_i nu_i}, where g_i from the
+ * NASA-7 polynomial (one temperature range) and nu = nu_r - nu_f.
+ * Each reaction may have at most 3 reactant and 3 product molecules (counting
+ * multiplicity). Diffusivities: D_i(T) = D0_i (T/T_ref)^theta_exp for species
+ * and lambda/(rho cp) = alpha0 (T/T_ref)^theta_exp for enthalpy. */
+typedef struct misdc_mech_desc {
+  int n_species;          /* N, 1..63                                  */
+  int n_reactions;        /* R, 1..1024                                */
+  const double *W;        /* [N] molar mass, kg/mol                    */
+  const double *nasa7;    /* [N][7] a1..a7                             */
+  const double *A;        /* [R] SI pre-exponential factor             */
+  const double *beta;     /* [R] temperature exponent                  */
+  const double *Ea;       /* [R] activation energy, J/mol              */
+  const int *nu_f;        /* [R][N] reactant stoichiometric coefficients */
+  const int *nu_r;        /* [R][N] product stoichiometric coefficients  */
+  const double *D0;       /* [N] species diffusivity at T_ref, m^2/s   */
+  double alpha0;          /* thermal diffusivity at T_ref, m^2/s       */
+  double T_ref, theta_exp, p_ref;
+} misdc_mech_desc;
+
+/* Periodic uniform grid: dim 1..3, nx*ny*nz cells (ny = nz = 1 in 1D). */
+typedef struct misdc_grid_desc {
+  int dim, nx, ny, nz;
+  double dx;
+} misdc_grid_desc;
+
+typedef struct misdc_opts {
+  int n_nodes;            /* M+1 Gauss-Lobatto nodes, 2..9             */
+  int n_sweeps;           /* sweeps per time step, >= 1                */
+  int nu;                 /* nested iterations (CISDCQ), >= 1          */
+  int scheme;             /* misdc_scheme                              */
+  int precision;          /* misdc_precision                           */
+  int dominant_species;   /* i0: closed by Y_i0 = 1 - sum of the others */
+  double rho;             /* constant density, kg/m^3                  */
+  double newton_rtol;     /* stop once max|dY| <= rtol, |dT| <= rtol T  */
+  int newton_maxit;       /* iteration limit per cell                  */
+  double lin_rtol;        /* diffusion solve: relative residual target  */
+  int mg_levels;          /* multigrid levels (0 = automatic)          */
+  int two_streams;        /* 1: D and R stages on separate streams     */
+  int use_graph;          /* 1: capture the step in a CUDA graph       */
+  int profile;            /* 1: time every Newton and diffusion-solve launch with CUDA events */
+} misdc_opts;
+
+typedef struct misdc_stats {
+  long long newton_solves;      /* cell solves since the last reset      */
+  long long newton_iters;       /* Newton iterations summed over cells   */
+  long long newton_fail;        /* cells that failed                     */
+  int newton_max;               /* most iterations taken by one cell     */
+  int status;                   /* misdc_status of the device work       */
+  long long lin_sweeps;         /* smoother sweeps per field, summed     */
+  double lin_resid_max;         /* largest relative residual seen        */
+  long long kernel_launches;    /* library kernels launched by misdc_step */
+} misdc_stats;
+
+typedef struct misdc_solver misdc_solver;
+
+/* Fill misdc_opts with defaults: 3 nodes, 4 sweeps, nu = 2, CISDCQ, FP64,
+ * newton_rtol 1e-12, newton_maxit 50, lin_rtol 1e-14, two streams, graph. */
+void misdc_default_opts(misdc_opts *opts);
+
+/* Create a solver. face_vel: device [3][cells] (only the first dim rows are
+ * read), the velocity normal to the low face of each cell along x, y, z; it
+ * should be discretely divergence free. The array is copied. */
+misdc_status misdc_create(const misdc_mech_desc *mech, const misdc_grid_desc *grid,
+                          const misdc_opts *opts, const double *face_vel,
+                          misdc_solver **out);
+void misdc_destroy(misdc_solver *s);
+
+/* Advance n_steps time steps of size dt (Sec. 3.3, I1-I4 and S1-S7).
+ * state: device [N+1][cells] in/out. T: device [cells] in/out temperature
+ * (input used as the first guess of the temperature diagnosis; may be NULL).
+ * Stream-ordered. */
+misdc_status misdc_step(misdc_solver *s, double *state, double *T, double dt,
+                        int n_steps, void *stream);
+
+/* Same with HOST state/T buffers: copies in, steps, copies out, and waits for
+ * the stream (the end-to-end path). */
+misdc_status misdc_step_host(misdc_solver *s, double *state_host, double *T_host,
+                             double dt, int n_steps, void *stream);
+
+/* Read and reset the accumulated statistics (synchronises the device). */
+misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *stats, int reset);
+
+/* With opts.profile = 1: device time of the reaction-Newton launches and of the
+ * diffusion solves of the most recent time step, measured with CUDA events on
+ * the streams they run on (synchronises the device). Outputs may be NULL. */
+misdc_status misdc_stage_times(misdc_solver *s, double *newton_ms, int *newton_launches,
+                               double *diffusion_ms, int *diffusion_launches);
+
+/* Quadrature tables the device uses (host outputs, may be NULL):
+ * tau[M+1], Q[M][M+1] (eq. weights), QI[M][M] = U^T of the unit-lower LU of
+ * (Q without its first column)^T, QE[M][M] = dt^j/dt for j <= m. */
+misdc_status misdc_lobatto(int n_nodes, double *tau, double *Q, double *QI, double *QE);
+
+/* ---- row-level entry points (device arrays, stream-ordered) ------------- */
+
+/* h = sum_i Y_i h_i(T) for n cells. Y [N][n], T [n], h [n]. */
+misdc_status misdc_enthalpy(misdc_solver *s, const double *Y, const double *T, double *h,
+                            int n, void *stream);
+/* T from sum_i Y_i h_i(T) = h, Newton safeguarded on [50, 6000] K. T in: guess
+ * (<= 0 means none), out: temperature. */
+misdc_status misdc_temperature(misdc_solver *s, const double *Y, const double *h, double *T,
+                               int n, void *stream);
+/* Production rates F_R = wdot/rho, [N][n] (Sec. 2, eq. species_equation). */
+misdc_status misdc_production_rates(misdc_solver *s, const double *Y, const double *T,
+                                    double *FR, int n, void *stream);
+/* Reaction step S5 for n independent cells (Sec. 3.3, eq.
+ * reaction_step_numerical_methodology):
+ * Y - wdt wdot(Y,T)/rho = b,  sum_i Y_i h_i(T) = hstar, Newton from the guess
+ * with the analytic Jacobian and partial-pivot LU, one warp per cell.
+ * b [N][n], hstar [n]; x [N+1][n] in: guess (Y, T), out: solution;
+ * FR [N][n] out: the reaction term of the solution, (Y - b)/wdt, which equals
+ * wdot/rho up to the Newton tolerance (may be NULL); iters [n] out (may be
+ * NULL): iterations, or -1 (limit), -2 (singular), -3 (non-finite or T <= 0). */
+misdc_status misdc_reaction_solve(misdc_solver *s, double wdt, const double *b,
+                                  const double *hstar, double *x, double *FR, int *iters,
+                                  int n, void *stream);
+/* Right-hand sides at a full state [N+1][cells] on the solver's grid:
+ * FE = advection (+ explicit differential diffusion of h), FD = diffusion,
+ * FR = reaction (each may be NULL). */
+misdc_status misdc_operators(misdc_solver *s, const double *state, double *FE, double *FD,
+                             double *FR, void *stream);
+/* Implicit diffusion step: x - wdt F_D[coef](x) = rhs for every field but the
+ * dominant species (closed by 1 - sum), coefficients frozen at coef_state,
+ * followed by the flux-form reconstruction x := rhs + wdt F_D[coef](x). */
+misdc_status misdc_diffusion_solve(misdc_solver *s, double wdt, const double *coef_state,
+                                   const double *rhs, double *x, void *stream);
+/* Linear combination out[o][e] = sum_k w[o][k] in[k][e] over n elements for
+ * n_out <= 8 outputs and n_in <= 16 inputs (host arrays of device pointers and
+ * weights): the spectral-integration kernel that applies Q to the node stack. */
+misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double *const *in,
+                           const double *w, size_t n, void *stream);
+
+const char *misdc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -158,6 +158,20 @@ static void eval_all(const or_problem *p, const double *phi, double *FE, double 
   p->f_reac(p->ctx, phi, FR);
 }
 
+/* Right-hand sides at the state x just produced by a reaction step
+ * x - wdt F_R(x) = b. F_A and F_D are evaluated at x (S6); the reaction term is
+ * the one the implicit equation assigns to x, F_R(x) = (x - b)/wdt (reading:
+ * the paper recomputes only the diffusion terms after S5; the reaction term
+ * of the new state is the unknown of eq. reaction_step_numerical_methodology).
+ * It equals the evaluated rate up to the Newton tolerance and does not
+ * amplify the round-off of near-equilibrium fluxes. */
+static void eval_after_reaction(const or_problem *p, const double *x, const double *b, double wdt,
+                                double *FE, double *FD, double *FR) {
+  p->f_expl(p->ctx, x, FE);
+  p->f_diff(p->ctx, x, FD);
+  for (int i = 0; i < p->n; ++i) FR[i] = (wdt > 0.0) ? (x[i] - b[i]) / wdt : 0.0;
+}
+
 /* Delta t * Q^{0:t}(F(phi^(k))) + phi^0  (shared start of every update) */
 static void base_rhs(const or_problem *p, const sweep_tables *T, int t, double dt,
                      const double *phi0, double *const *FEk, double *const *FDk,
@@ -213,7 +227,7 @@ int or_sweep(const or_problem *p, int scheme, int M, int nu, double dt,
       rc |= p->solve_diff(p->ctx, dtm, phik[t], rhs, AD[t]);
       for (int i = 0; i < n; ++i) b[i] = AD[t][i] - dtm * FRk[t][i];
       rc |= p->solve_reac(p->ctx, dtm, b, phik[t], cur[t]);
-      eval_all(p, cur[t], FEc[t], FDc[t], FRc[t]);
+      eval_after_reaction(p, cur[t], b, dtm, FEc[t], FDc[t], FRc[t]);
     }
     for (int m = 1; m <= M; ++m) memcpy(Phi_out + (size_t)m * n, cur[m], sizeof(double) * n);
   } else if (scheme == OR_MISDCQ) {
@@ -233,7 +247,7 @@ int or_sweep(const or_problem *p, int scheme, int M, int nu, double dt,
         for (int i = 0; i < n; ++i) b[i] += dt * QIW(&T, t, j) * (FRc[j][i] - FRk[j][i]);
       for (int i = 0; i < n; ++i) b[i] -= dt * QIW(&T, t, t) * FRk[t][i];
       rc |= p->solve_reac(p->ctx, dt * QIW(&T, t, t), b, phik[t], cur[t]);
-      eval_all(p, cur[t], FEc[t], FDc[t], FRc[t]);
+      eval_after_reaction(p, cur[t], b, dt * QIW(&T, t, t), FEc[t], FDc[t], FRc[t]);
     }
     for (int m = 1; m <= M; ++m) memcpy(Phi_out + (size_t)m * n, cur[m], sizeof(double) * n);
   } else if (scheme == OR_IMEXQ) {
@@ -302,7 +316,7 @@ int or_sweep(const or_problem *p, int scheme, int M, int nu, double dt,
         const double *guess = (l == 0) ? phik[t] : prv[t];
         rc |= p->solve_reac(p->ctx, dt * QIW(&T, t, t), b, guess, cur[t]);
         /* S6: recompute the right-hand-side terms at the new state */
-        eval_all(p, cur[t], FEc[t], FDc[t], FRc[t]);
+        eval_after_reaction(p, cur[t], b, dt * QIW(&T, t, t), FEc[t], FDc[t], FRc[t]);
       }
       for (int m = 1; m <= M; ++m) {   /* iteration l+1 becomes the lag source */
         double *s;
@@ -759,13 +773,16 @@ void or_wdot_jac(const or_mech *m, double rho, const double *Y, double T, double
 /* Reaction step S5: rho Y - wdt wdot(Y) = rho b with h fixed; unknowns
  * x = (Y_1..Y_N, T); residual r_Y = Y - wdt wdot/rho - b,
  * r_T = sum Y_i h_i(T) - hstar; plain Newton from the guess with the analytic
- * Jacobian and dense partial-pivot LU. Stops once the applied step satisfies
- * max_i |dY_i| <= rtol and |dT| <= rtol T. */
+ * Jacobian and dense partial-pivot LU. With d = max(max_i |dY_i|, |dT|/T) the
+ * size of the applied step, it stops once d <= rtol, or once d <= 1e-8 stops
+ * shrinking (d >= d_prev/2): the round-off floor of very stiff cells, where
+ * the step can no longer fall below rtol. */
 int or_reaction_newton(const or_mech *m, double rho, double wdt, const double *b,
                        double hstar, double *x, double rtol, int maxit) {
   int N = m->N, n = N + 1;
   double J[64 * 64], Jw[64 * 65], r[64], wd[64];   /* n <= 64 */
   if (n > 64) return -1;
+  double dprev = INFINITY;
   for (int it = 1; it <= maxit; ++it) {
     double T = x[N];
     or_wdot(m, rho, x, T, wd, NULL);
@@ -783,7 +800,11 @@ int or_reaction_newton(const or_mech *m, double rho, double wdt, const double *b
     for (int i = 0; i < N; ++i) { x[i] += r[i]; if (fabs(r[i]) > dmax) dmax = fabs(r[i]); }
     x[N] += r[N];
     if (!(x[N] > 0.0) || !isfinite(x[N])) return -3;
-    if (dmax <= rtol && fabs(r[N]) <= rtol * x[N]) return it;
+    double d = fabs(r[N]) / x[N];
+    if (dmax > d) d = dmax;
+    if (!isfinite(d)) return -3;
+    if (d <= rtol || (d <= 1e-8 && d >= 0.5 * dprev)) return it;
+    dprev = d;
   }
   return -4;
 }

@@ -1,0 +1,902 @@
+// Host engine and C ABI of libmisdc.
+//
+// One time step (Sec. 3.3): I1-I2 copy phi^n into every node; I4 evaluates the
+// right-hand sides at phi^n; each sweep k applies the quadrature Q to the node
+// stack once (S1 and the sweep-k parts of every update), then runs the
+// diffusion (S2-S4) and reaction (S5-S6) steps node by node and iteration by
+// iteration; S7 keeps iteration nu as sweep k+1.
+//
+// CISDCQ runs diffusion steps on stream sD and reaction steps on stream sR.
+// Dependencies follow the update equations: the diffusion step at node m+1 of
+// iteration l+1 needs the iteration-l reaction results at nodes m and m+1 (for
+// l >= 1) and the current-iteration reaction results at nodes < m; the reaction
+// step at node m+1 needs its own diffusion step and the reaction step at node
+// m (stream order). With three nodes the stages pair up as
+//   D1 | D2 || R1 | R2 || D1' | D2' || R1' | R2'
+// which is the two-processor pipelining of Sec. 3.2.2.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "misdc_internal.cuh"
+
+using namespace misdc;
+
+namespace {
+
+thread_local std::string g_err;
+
+misdc_status fail(misdc_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? MISDC_E_OOM : MISDC_E_CUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Gauss-Lobatto tables. Interior nodes are the roots of the Jacobi polynomial
+// P^{(1,1)}_{M-1} (proportional to P'_M), found by Newton from Chebyshev
+// guesses; integration weights come from the moment (Vandermonde) equations
+// sum_j q_{m,j} tau_j^p = tau_m^{p+1}/(p+1), p = 0..M; Q~I is the transposed
+// upper factor of Gaussian elimination without pivoting on (Q~)^T.
+// ---------------------------------------------------------------------------
+struct Tables {
+  int M = 0;
+  double tau[kMaxNodes + 1], Q[kMaxNodes][kMaxNodes + 1], S[kMaxNodes][kMaxNodes + 1];
+  double QI[kMaxNodes][kMaxNodes], QE[kMaxNodes][kMaxNodes];
+};
+
+long double jacobi11(int n, long double x, long double *dp) {
+  long double p0 = 1.0L, p1 = 2.0L * x, d0 = 0.0L, d1 = 2.0L;
+  if (n == 0) { *dp = 0.0L; return 1.0L; }
+  for (int k = 2; k <= n; ++k) {
+    // k(k+2) P_k = (2k+1)(k+1) x P_{k-1} - k(k+1) P_{k-2}
+    long double a = (2.0L * k + 1.0L) * (k + 1.0L), b = k * (k + 1.0L), c = k * (k + 2.0L);
+    long double p2 = (a * x * p1 - b * p0) / c;
+    long double d2 = (a * (p1 + x * d1) - b * d0) / c;
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  *dp = d1;
+  return p1;
+}
+
+bool make_tables(int n_nodes, Tables &T) {
+  const int M = n_nodes - 1;
+  if (M < 1 || M >= kMaxNodes) return false;
+  T.M = M;
+  long double tau[kMaxNodes + 1];
+  tau[0] = 0.0L;
+  tau[M] = 1.0L;
+  for (int j = 1; j < M; ++j) {
+    long double x = cosl(3.141592653589793238462643383279502884L * (M - j) / M);
+    for (int it = 0; it < 200; ++it) {
+      long double dp, p = jacobi11(M - 1, x, &dp);
+      long double dx = p / dp;
+      x -= dx;
+      if (fabsl(dx) <= 1e-20L) break;
+    }
+    tau[j] = 0.5L * (1.0L + x);
+  }
+  // moment equations V^T q = mu with V_{jp} = tau_j^p
+  auto solve_weights = [&](long double a, long double b, long double *q) {
+    long double A[kMaxNodes + 1][kMaxNodes + 2];
+    for (int p = 0; p <= M; ++p) {
+      for (int j = 0; j <= M; ++j) A[p][j] = powl(tau[j], p);
+      A[p][M + 1] = (powl(b, p + 1) - powl(a, p + 1)) / (p + 1);
+    }
+    for (int k = 0; k <= M; ++k) {   // Gaussian elimination with partial pivoting
+      int piv = k;
+      for (int i = k + 1; i <= M; ++i) if (fabsl(A[i][k]) > fabsl(A[piv][k])) piv = i;
+      for (int j = 0; j <= M + 1; ++j) std::swap(A[k][j], A[piv][j]);
+      for (int i = k + 1; i <= M; ++i) {
+        long double f = A[i][k] / A[k][k];
+        for (int j = k; j <= M + 1; ++j) A[i][j] -= f * A[k][j];
+      }
+    }
+    for (int i = M; i >= 0; --i) {
+      long double s = A[i][M + 1];
+      for (int j = i + 1; j <= M; ++j) s -= A[i][j] * q[j];
+      q[i] = s / A[i][i];
+    }
+  };
+  long double Ql[kMaxNodes][kMaxNodes + 1];
+  for (int m = 1; m <= M; ++m) {
+    long double q[kMaxNodes + 1], s[kMaxNodes + 1];
+    solve_weights(0.0L, tau[m], q);
+    solve_weights(tau[m - 1], tau[m], s);
+    for (int j = 0; j <= M; ++j) {
+      Ql[m - 1][j] = q[j];
+      T.Q[m - 1][j] = (double)q[j];
+      T.S[m - 1][j] = (double)s[j];
+    }
+  }
+  for (int m = 0; m <= M; ++m) T.tau[m] = (double)tau[m];
+  // (Q~)^T = L U, L unit lower: eliminate below the diagonal, U is what remains
+  long double U[kMaxNodes][kMaxNodes];
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) U[i][j] = Ql[j][i + 1];
+  for (int k = 0; k < M; ++k)
+    for (int i = k + 1; i < M; ++i) {
+      long double f = U[i][k] / U[k][k];
+      for (int j = k; j < M; ++j) U[i][j] -= f * U[k][j];
+    }
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      T.QI[i][j] = (j <= i) ? (double)U[j][i] : 0.0;
+      // forward Euler from t^0: q~E_{i+1, j+1} = (tau_{j+2} - tau_{j+1}) for j < i
+      T.QE[i][j] = (j < i) ? (double)(tau[j + 2] - tau[j + 1]) : 0.0;
+    }
+  return true;
+}
+
+struct NodeBuf {
+  double *phi = nullptr, *T = nullptr, *theta = nullptr, *hsp = nullptr;
+  double *FE = nullptr, *FD = nullptr, *FR = nullptr;
+};
+
+}  // namespace
+
+struct misdc_solver {
+  int N = 0, R = 0, cs = 0, i0 = 0;
+  DevGrid g{};
+  DevMech m{};
+  misdc_opts o{};
+  Tables tab;
+  std::vector<void *> allocs;
+  std::vector<double> D0h;
+  double *vel = nullptr;
+  NodeBuf node0, K[kMaxNodes + 1], X[kMaxNodes + 1], Y[kMaxNodes + 1], AD[kMaxNodes + 1];
+  double *B[kMaxNodes + 1] = {};
+  double *rhsD = nullptr, *bR = nullptr, *thfD = nullptr, *thfR = nullptr;
+  double *stage_state = nullptr, *stage_T = nullptr;   // host-step staging
+  int *iters = nullptr;
+  DiffWork dw{};
+  DevStats *st = nullptr;
+  cudaStream_t sD = nullptr, sR = nullptr;
+  std::vector<cudaEvent_t> evD, evR;   // [M+1][nu]
+  cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr, evJoin = nullptr;
+  // CUDA graph of one step
+  cudaGraphExec_t gexec = nullptr;
+  double *g_state = nullptr, *g_T = nullptr;
+  double g_dt = 0.0;
+  int cheb_sweeps = 0;
+  double rho_bound = 0.0, rho_dt = -1.0;
+  long long kernels_per_step = 0, kernels_launched = 0;
+  // optional stage timing (opts.profile)
+  std::vector<cudaEvent_t> prof_n, prof_d;   // pairs: start, end
+  int n_used = 0, d_used = 0;
+
+  template <typename T>
+  cudaError_t alloc(T **p, size_t n) {
+    cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) allocs.push_back(*p);
+    return e;
+  }
+  cudaEvent_t &eD(int t, int l) { return evD[(size_t)t * o.nu + l]; }
+  cudaEvent_t &eR(int t, int l) { return evR[(size_t)t * o.nu + l]; }
+  NodeBuf &nodeK(int j) { return j == 0 ? node0 : K[j]; }
+};
+
+namespace {
+
+misdc_status alloc_node(misdc_solver *s, NodeBuf &b) {
+  const size_t cs = s->cs, F = s->N + 1;
+  CK(s->alloc(&b.phi, F * cs));
+  CK(s->alloc(&b.T, cs));
+  CK(s->alloc(&b.theta, cs));
+  CK(s->alloc(&b.hsp, (size_t)s->N * cs));
+  CK(s->alloc(&b.FE, F * cs));
+  CK(s->alloc(&b.FD, F * cs));
+  CK(s->alloc(&b.FR, F * cs));
+  CK(cudaMemset(b.FR, 0, F * cs * sizeof(double)));   // the enthalpy row of F_R stays zero
+  return MISDC_OK;
+}
+
+void copy_node(misdc_solver *s, NodeBuf &d, const NodeBuf &a, cudaStream_t st) {
+  const size_t cs = s->cs, F = s->N + 1, b = sizeof(double);
+  cudaMemcpyAsync(d.phi, a.phi, F * cs * b, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(d.T, a.T, cs * b, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(d.theta, a.theta, cs * b, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(d.hsp, a.hsp, (size_t)s->N * cs * b, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(d.FE, a.FE, F * cs * b, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(d.FD, a.FD, F * cs * b, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(d.FR, a.FR, F * cs * b, cudaMemcpyDeviceToDevice, st);
+}
+
+// F_E and F_D of a node state whose theta and hsp are current
+void node_operators(misdc_solver *s, NodeBuf &b, double *thf, cudaStream_t st) {
+  launch_theta_faces(s->g, b.theta, thf, st);
+  launch_operators(s->m, s->g, s->i0, b.phi, b.hsp, thf, s->vel, b.FE, b.FD, st);
+}
+
+double rho_bound_for(misdc_solver *s, double wdt_max) {
+  // Gershgorin bound of the Jacobi iteration matrix of I - c L_theta, with
+  // theta at most (T_max/T_ref)^e on every face
+  const double th = pow(kThi / s->m.T_ref, s->m.theta_exp);
+  double dmax = s->m.alpha0;
+  for (int i = 0; i < s->N; ++i) if (i != s->i0) dmax = std::max(dmax, s->D0h[i]);
+  const double cS = wdt_max * dmax / (s->g.dx * s->g.dx) * 2.0 * s->g.dim * th;
+  return cS / (1.0 + cS);
+}
+
+struct LC {
+  LinComb lc;
+  LC(double *out) { memset(&lc, 0, sizeof(lc)); lc.n_out = 1; lc.out[0] = out; }
+  void add(const double *in, double w) {
+    if (w == 0.0 || !in) return;
+    for (int k = 0; k < lc.n_in; ++k)
+      if (lc.in[k] == in) { lc.w[0][k] += w; return; }
+    lc.in[lc.n_in] = in;
+    lc.w[0][lc.n_in] = w;
+    ++lc.n_in;
+  }
+};
+
+// Quadrature of sweep k: the parts of every node update that depend on
+// sweep k only (one pass over the node stack).
+void sweep_quadrature(misdc_solver *s, double dt, cudaStream_t st) {
+  const Tables &T = s->tab;
+  const int M = T.M, sch = s->o.scheme;
+  const size_t n = (size_t)(s->N + 1) * s->cs;
+  LinComb lc;
+  memset(&lc, 0, sizeof(lc));
+  lc.n_out = M;
+  lc.in[0] = s->node0.phi;
+  int k = 1;
+  int idxE[kMaxNodes + 1], idxD[kMaxNodes + 1], idxR[kMaxNodes + 1];
+  for (int j = 0; j <= M; ++j) {
+    NodeBuf &b = s->nodeK(j);
+    idxE[j] = k; lc.in[k++] = b.FE;
+    idxD[j] = k; lc.in[k++] = b.FD;
+    idxR[j] = k; lc.in[k++] = b.FR;
+  }
+  lc.n_in = k;
+  for (int t = 1; t <= M; ++t) {
+    double *w = lc.w[t - 1];
+    lc.out[t - 1] = s->B[t];
+    const int m = t - 1;
+    w[0] = 1.0;
+    if (sch == MISDC_SCHEME_MISDC) {
+      const double dtm = dt * (T.tau[t] - T.tau[m]);
+      for (int j = 0; j <= M; ++j) {
+        const double q = dt * T.S[t - 1][j];
+        w[idxE[j]] += q; w[idxD[j]] += q; w[idxR[j]] += q;
+      }
+      w[0] = 0.0;   // MISDC starts from the new state at node m, added per stage
+      w[idxE[m]] -= dtm;
+      w[idxD[t]] -= dtm;
+      continue;
+    }
+    for (int j = 0; j <= M; ++j) {
+      const double q = dt * T.Q[t - 1][j];
+      w[idxE[j]] += q; w[idxD[j]] += q; w[idxR[j]] += q;
+    }
+    for (int j = 1; j <= m; ++j) {
+      w[idxE[j]] -= dt * T.QE[t - 1][j - 1];
+      w[idxD[j]] -= dt * T.QI[t - 1][j - 1];
+      if (sch == MISDC_SCHEME_CISDCQ) w[idxR[j]] -= dt * T.QI[t - 1][j - 1];
+    }
+    w[idxD[t]] -= dt * T.QI[t - 1][t - 1];
+    if (sch == MISDC_SCHEME_CISDCQ) w[idxR[t]] -= dt * T.QI[t - 1][t - 1];
+  }
+  launch_lincomb(lc, n, st);
+}
+
+// temperature, theta and species enthalpies of node 0 (I4) and its F's
+void prepare_node0(misdc_solver *s, const double *state, const double *Tin, cudaStream_t st) {
+  const size_t cs = s->cs, F = s->N + 1;
+  NodeBuf &b = s->node0;
+  cudaMemcpyAsync(b.phi, state, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  launch_temperature(s->m, s->cs, s->cs, b.phi, b.phi + (size_t)s->N * cs, Tin, b.T, b.theta,
+                     b.hsp, s->st, st);
+  node_operators(s, b, s->thfD, st);
+  launch_rates(s->m, s->cs, s->cs, b.phi, b.T, b.FR, st);
+}
+
+// diffusion step at node t: rhs already in s->rhsD; writes AD[t]
+void d_stage(misdc_solver *s, int t, const double *theta_coef, double wdt, bool lag_source,
+             const NodeBuf *Tguess, cudaStream_t st) {
+  NodeBuf &ad = s->AD[t];
+  const bool prof = s->o.profile && 2 * (s->d_used + 1) <= (int)s->prof_d.size();
+  if (prof) cudaEventRecordWithFlags(s->prof_d[2 * s->d_used], st, cudaEventRecordExternal);
+  diffusion_solve(s->m, s->g, s->i0, wdt, theta_coef, s->rhsD, ad.phi, s->dw, s->cheb_sweeps,
+                  s->rho_bound, s->o.lin_rtol, s->st, st);
+  if (prof) cudaEventRecordWithFlags(s->prof_d[2 * s->d_used++ + 1], st, cudaEventRecordExternal);
+  if (lag_source) {
+    launch_temperature(s->m, s->cs, s->cs, ad.phi, ad.phi + (size_t)s->N * s->cs, Tguess->T, ad.T,
+                       ad.theta, ad.hsp, s->st, st);
+    node_operators(s, ad, s->thfD, st);
+  }
+}
+
+// reaction step at node t: b already in s->bR; writes out (phi, T, theta, hsp, F's)
+void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &out,
+             cudaStream_t st) {
+  const size_t cs = s->cs, N = s->N;
+  const NodeBuf &ad = s->AD[t];
+  const bool prof = s->o.profile && 2 * (s->n_used + 1) <= (int)s->prof_n.size();
+  if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used], st, cudaEventRecordExternal);
+  launch_newton(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, s->bR,
+                ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR, out.hsp, out.theta,
+                s->iters, s->st, st);
+  if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used++ + 1], st, cudaEventRecordExternal);
+  cudaMemcpyAsync(out.phi + N * cs, ad.phi + N * cs, cs * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  node_operators(s, out, s->thfR, st);
+}
+
+// Enqueue one full time step on s->sD (and s->sR).
+void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
+  const Tables &T = s->tab;
+  const int M = T.M, nu = s->o.nu, sch = s->o.scheme;
+  const size_t cs = s->cs, F = s->N + 1, n = F * cs;
+  const bool two = s->o.two_streams && sch == MISDC_SCHEME_CISDCQ;
+  cudaStream_t sD = s->sD, sR = two ? s->sR : s->sD;
+  s->n_used = s->d_used = 0;
+
+  prepare_node0(s, state, Tio, sD);
+  for (int m = 1; m <= M; ++m) copy_node(s, s->K[m], s->node0, sD);   // I1-I2
+  if (two) {
+    cudaEventRecord(s->evFork, sD);
+    cudaStreamWaitEvent(sR, s->evFork, 0);
+  }
+  for (int k = 0; k < s->o.n_sweeps; ++k) {
+    sweep_quadrature(s, dt, sD);
+    if (sch == MISDC_SCHEME_CISDCQ) {
+      for (int l = 0; l < nu; ++l) {
+        NodeBuf *C = (l % 2 == 0) ? s->X : s->Y;
+        NodeBuf *P = (l == 0) ? s->K : ((l % 2 == 1) ? s->X : s->Y);
+        for (int m = 0; m < M; ++m) {
+          const int t = m + 1;
+          // ---- diffusion step at node t ----
+          if (two && l >= 1) {
+            if (m >= 1) cudaStreamWaitEvent(sD, s->eR(m, l - 1), 0);
+            cudaStreamWaitEvent(sD, s->eR(t, l - 1), 0);
+          }
+          if (two) for (int j = 1; j <= m - 1; ++j) cudaStreamWaitEvent(sD, s->eR(j, l), 0);
+          LC r(s->rhsD);
+          r.add(s->B[t], 1.0);
+          for (int j = 1; j <= m - 1; ++j) {
+            r.add(C[j].FE, dt * T.QE[t - 1][j - 1]);
+            r.add(C[j].FD, dt * T.QI[t - 1][j - 1]);
+            r.add(C[j].FR, dt * T.QI[t - 1][j - 1]);
+          }
+          if (m >= 1) {
+            const double *lagE = (l == 0) ? s->AD[m].FE : P[m].FE;
+            const double *lagD = (l == 0) ? s->AD[m].FD : P[m].FD;
+            const double *lagR = (l == 0) ? s->K[m].FR : P[m].FR;
+            r.add(lagE, dt * T.QE[t - 1][m - 1]);
+            r.add(lagD, dt * T.QI[t - 1][m - 1]);
+            r.add(lagR, dt * T.QI[t - 1][m - 1]);
+          }
+          const double *lagR1 = (l == 0) ? s->K[t].FR : P[t].FR;
+          r.add(lagR1, dt * T.QI[t - 1][t - 1]);
+          launch_lincomb(r.lc, n, sD);
+          const double wdt = dt * T.QI[t - 1][t - 1];
+          const double *coef = (l == 0) ? s->K[t].theta : P[t].theta;
+          d_stage(s, t, coef, wdt, l == 0 && t < M, &s->K[t], sD);
+          if (two) cudaEventRecord(s->eD(t, l), sD);
+          // ---- reaction step at node t (R_alt form) ----
+          if (two) cudaStreamWaitEvent(sR, s->eD(t, l), 0);
+          LC b(s->bR);
+          b.add(s->AD[t].phi, 1.0);
+          if (m >= 1) {
+            const double *lagRm = (l == 0) ? s->K[m].FR : P[m].FR;
+            b.add(C[m].FR, dt * T.QI[t - 1][m - 1]);
+            b.add(lagRm, -dt * T.QI[t - 1][m - 1]);
+          }
+          b.add(lagR1, -dt * T.QI[t - 1][t - 1]);
+          launch_lincomb(b.lc, n, sR);
+          r_stage(s, t, wdt, P[t], C[t], sR);
+          if (two) cudaEventRecord(s->eR(t, l), sR);
+        }
+      }
+      NodeBuf *last = ((nu - 1) % 2 == 0) ? s->X : s->Y;   // S7
+      if (two) cudaStreamWaitEvent(sD, s->eR(M, nu - 1), 0);
+      for (int m = 1; m <= M; ++m) std::swap(s->K[m], last[m]);
+    } else {
+      NodeBuf *C = s->X;
+      for (int m = 0; m < M; ++m) {
+        const int t = m + 1;
+        LC r(s->rhsD);
+        r.add(s->B[t], 1.0);
+        double wdt;
+        if (sch == MISDC_SCHEME_MISDCQ) {
+          for (int j = 1; j <= m; ++j) {
+            r.add(C[j].FE, dt * T.QE[t - 1][j - 1]);
+            r.add(C[j].FD, dt * T.QI[t - 1][j - 1]);
+          }
+          wdt = dt * T.QI[t - 1][t - 1];
+        } else {   // MISDC: from the new state at node m
+          const double dtm = dt * (T.tau[t] - T.tau[m]);
+          const NodeBuf &prev = (m == 0) ? s->node0 : C[m];
+          r.add(prev.phi, 1.0);
+          r.add(prev.FE, dtm);
+          wdt = dtm;
+        }
+        launch_lincomb(r.lc, n, sD);
+        d_stage(s, t, s->K[t].theta, wdt, false, nullptr, sD);
+        LC b(s->bR);
+        b.add(s->AD[t].phi, 1.0);
+        if (sch == MISDC_SCHEME_MISDCQ) {
+          for (int j = 1; j <= m; ++j) {
+            b.add(C[j].FR, dt * T.QI[t - 1][j - 1]);
+            b.add(s->K[j].FR, -dt * T.QI[t - 1][j - 1]);
+          }
+        }
+        b.add(s->K[t].FR, -wdt);
+        launch_lincomb(b.lc, n, sD);
+        r_stage(s, t, wdt, s->K[t], C[t], sD);
+      }
+      for (int m = 1; m <= M; ++m) std::swap(s->K[m], C[m]);
+    }
+  }
+  NodeBuf &fin = s->K[M];
+  cudaMemcpyAsync(state, fin.phi, n * sizeof(double), cudaMemcpyDeviceToDevice, sD);
+  if (Tio) cudaMemcpyAsync(Tio, fin.T, cs * sizeof(double), cudaMemcpyDeviceToDevice, sD);
+}
+
+misdc_status configure_dt(misdc_solver *s, double dt) {
+  if (s->rho_dt == dt) return MISDC_OK;
+  double qmax = 0.0;
+  for (int t = 0; t < s->tab.M; ++t) {
+    qmax = std::max(qmax, s->tab.QI[t][t]);
+    qmax = std::max(qmax, s->tab.tau[t + 1] - s->tab.tau[t]);
+  }
+  s->rho_bound = rho_bound_for(s, dt * qmax);
+  s->cheb_sweeps = chebyshev_sweeps(s->rho_bound, std::max(1e-3 * s->o.lin_rtol, 1e-17));
+  s->rho_dt = dt;
+  return MISDC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *misdc_last_error(void) { return g_err.c_str(); }
+
+void misdc_default_opts(misdc_opts *o) {
+  memset(o, 0, sizeof(*o));
+  o->n_nodes = 3;
+  o->n_sweeps = 4;
+  o->nu = 2;
+  o->scheme = MISDC_SCHEME_CISDCQ;
+  o->precision = MISDC_PREC_FP64;
+  o->dominant_species = 0;
+  o->rho = 1.0;
+  o->newton_rtol = 1e-12;
+  o->newton_maxit = 50;
+  o->lin_rtol = 1e-14;
+  o->mg_levels = 1;
+  o->two_streams = 1;
+  o->use_graph = 1;
+}
+
+misdc_status misdc_lobatto(int n_nodes, double *tau, double *Q, double *QI, double *QE) {
+  Tables T;
+  if (!make_tables(n_nodes, T)) return fail(MISDC_E_INVALID, "n_nodes must be in 2..9");
+  const int M = T.M;
+  for (int m = 0; m <= M; ++m) if (tau) tau[m] = T.tau[m];
+  for (int i = 0; i < M; ++i) {
+    for (int j = 0; j <= M; ++j) if (Q) Q[i * (M + 1) + j] = T.Q[i][j];
+    for (int j = 0; j < M; ++j) {
+      if (QI) QI[i * M + j] = T.QI[i][j];
+      if (QE) QE[i * M + j] = T.QE[i][j];
+    }
+  }
+  return MISDC_OK;
+}
+
+misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
+                          const misdc_opts *op, const double *face_vel, misdc_solver **out) {
+  if (!md || !gd || !op || !out) return fail(MISDC_E_INVALID, "null argument");
+  *out = nullptr;
+  const int N = md->n_species, R = md->n_reactions;
+  if (N < 1 || N > kMaxSpecies || R < 1 || R > 1024) return fail(MISDC_E_INVALID, "n_species must be 1..63 and n_reactions 1..1024");
+  if (!md->W || !md->nasa7 || !md->A || !md->beta || !md->Ea || !md->nu_f || !md->nu_r || !md->D0)
+    return fail(MISDC_E_INVALID, "null mechanism array");
+  if (gd->dim < 1 || gd->dim > 3 || gd->nx < 2 || gd->ny < 1 || gd->nz < 1 || !(gd->dx > 0.0))
+    return fail(MISDC_E_INVALID, "bad grid");
+  if ((gd->dim < 2 && gd->ny != 1) || (gd->dim < 3 && gd->nz != 1) || (gd->dim >= 2 && gd->ny < 2) ||
+      (gd->dim >= 3 && gd->nz < 2))
+    return fail(MISDC_E_INVALID, "grid extents do not match dim");
+  const long long cells = (long long)gd->nx * gd->ny * gd->nz;
+  if (cells > (1LL << 30)) return fail(MISDC_E_INVALID, "grid too large");
+  if (op->n_nodes < 2 || op->n_nodes > 5) return fail(MISDC_E_INVALID, "n_nodes must be 2..5");
+  if (op->n_sweeps < 1 || op->nu < 1 || op->nu > 16) return fail(MISDC_E_INVALID, "bad n_sweeps/nu");
+  if (op->scheme < 0 || op->scheme > 2) return fail(MISDC_E_INVALID, "bad scheme");
+  if (op->precision != MISDC_PREC_FP64) return fail(MISDC_E_INVALID, "only FP64 precision is built");
+  if (op->dominant_species < 0 || op->dominant_species >= N) return fail(MISDC_E_INVALID, "bad dominant species");
+  if (!(op->rho > 0.0) || !(op->newton_rtol > 0.0) || op->newton_maxit < 1 || !(op->lin_rtol > 0.0))
+    return fail(MISDC_E_INVALID, "bad tolerances or density");
+  if (op->mg_levels < 0 || op->mg_levels > 6) return fail(MISDC_E_INVALID, "mg_levels must be 0..6");
+  if (!face_vel) return fail(MISDC_E_INVALID, "null face velocity");
+  for (int i = 0; i < N; ++i)
+    if (!(md->W[i] > 0.0) || !(md->D0[i] >= 0.0)) return fail(MISDC_E_INVALID, "bad W or D0");
+
+  misdc_solver *s = new misdc_solver();
+  auto bail = [&](misdc_status st) { misdc_destroy(s); return st; };
+  s->N = N; s->R = R; s->cs = (int)cells; s->i0 = op->dominant_species; s->o = *op;
+  if (s->o.mg_levels == 0) s->o.mg_levels = 1;
+  if (!make_tables(op->n_nodes, s->tab)) return bail(fail(MISDC_E_INVALID, "bad n_nodes"));
+  s->g.dim = gd->dim; s->g.nx = gd->nx; s->g.ny = gd->ny; s->g.nz = gd->nz;
+  s->g.cells = (int)cells; s->g.dx = gd->dx;
+  s->D0h.assign(md->D0, md->D0 + N);
+
+  // ---- mechanism tables ----
+  std::vector<double> invW(N), hc(6 * N), sc(6 * N), cpc(5 * N), lnA(R), beta(R), TA(R), dn(R);
+  std::vector<signed char> fwd(kMaxSlots * R, -1), rev(kMaxSlots * R, -1);
+  std::vector<int> sp_ptr(N + 1, 0), sp_rx;
+  std::vector<double> sp_coef;
+  for (int i = 0; i < N; ++i) {
+    const double *a = md->nasa7 + 7 * i;
+    invW[i] = 1.0 / md->W[i];
+    const double h6[6] = {a[0], a[1] / 2, a[2] / 3, a[3] / 4, a[4] / 5, a[5]};
+    const double s6[6] = {a[0], a[1], a[2] / 2, a[3] / 3, a[4] / 4, a[6]};
+    for (int k = 0; k < 6; ++k) { hc[6 * i + k] = h6[k]; sc[6 * i + k] = s6[k]; }
+    for (int k = 0; k < 5; ++k) cpc[5 * i + k] = a[k];
+  }
+  for (int r = 0; r < R; ++r) {
+    if (!(md->A[r] > 0.0)) return bail(fail(MISDC_E_INVALID, "A must be positive"));
+    lnA[r] = log(md->A[r]);
+    beta[r] = md->beta[r];
+    TA[r] = md->Ea[r] / kRu;
+    int nf = 0, nr = 0, d = 0;
+    for (int i = 0; i < N; ++i) {
+      const int a = md->nu_f[(size_t)r * N + i], b = md->nu_r[(size_t)r * N + i];
+      if (a < 0 || b < 0) return bail(fail(MISDC_E_INVALID, "negative stoichiometry"));
+      for (int k = 0; k < a; ++k) { if (nf >= kMaxSlots) return bail(fail(MISDC_E_INVALID, "more than 3 reactant molecules")); fwd[kMaxSlots * r + nf++] = (signed char)i; }
+      for (int k = 0; k < b; ++k) { if (nr >= kMaxSlots) return bail(fail(MISDC_E_INVALID, "more than 3 product molecules")); rev[kMaxSlots * r + nr++] = (signed char)i; }
+      d += b - a;
+    }
+    dn[r] = d;
+  }
+  for (int i = 0; i < N; ++i) {
+    for (int r = 0; r < R; ++r) {
+      const int nu = md->nu_r[(size_t)r * N + i] - md->nu_f[(size_t)r * N + i];
+      if (nu) { sp_rx.push_back(r); sp_coef.push_back(md->W[i] * nu); }
+    }
+    sp_ptr[i + 1] = (int)sp_rx.size();
+  }
+  auto up = [&](auto &vec, auto **dst) -> cudaError_t {
+    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+    cudaError_t e = s->alloc((T **)dst, vec.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy((void *)*dst, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice);
+  };
+  std::vector<double> D0v(md->D0, md->D0 + N);
+  double *p_invW, *p_hc, *p_sc, *p_cpc, *p_D0, *p_lnA, *p_beta, *p_TA, *p_dn, *p_spc;
+  signed char *p_fwd, *p_rev;
+  int *p_spp, *p_spr;
+  if (up(invW, &p_invW) || up(hc, &p_hc) || up(sc, &p_sc) || up(cpc, &p_cpc) || up(D0v, &p_D0) ||
+      up(lnA, &p_lnA) || up(beta, &p_beta) || up(TA, &p_TA) || up(dn, &p_dn) || up(fwd, &p_fwd) ||
+      up(rev, &p_rev) || up(sp_ptr, &p_spp) || up(sp_rx, &p_spr) || up(sp_coef, &p_spc))
+    return bail(fail(MISDC_E_OOM, "mechanism upload failed"));
+  DevMech &m = s->m;
+  m.N = N; m.R = R; m.rho = op->rho; m.T_ref = md->T_ref; m.theta_exp = md->theta_exp;
+  m.alpha0 = md->alpha0; m.ln_p_over_R = log(md->p_ref / kRu);
+  m.invW = p_invW; m.hcoef = p_hc; m.scoef = p_sc; m.cpcoef = p_cpc; m.D0 = p_D0;
+  m.lnA = p_lnA; m.beta = p_beta; m.TA = p_TA; m.dn = p_dn; m.fwd = p_fwd; m.rev = p_rev;
+  m.sp_ptr = p_spp; m.sp_rx = p_spr; m.sp_coef = p_spc;
+  m.D0_host = s->D0h.data();
+  prepare_chem_kernels(m);
+
+  // ---- buffers ----
+  const size_t cs = s->cs, F = N + 1;
+  misdc_status st;
+  if (s->alloc(&s->vel, 3 * cs)) return bail(fail(MISDC_E_OOM, "velocity"));
+  if (cudaMemset(s->vel, 0, 3 * cs * sizeof(double)) ||
+      cudaMemcpy(s->vel, face_vel, (size_t)gd->dim * cs * sizeof(double), cudaMemcpyDefault))
+    return bail(fail(MISDC_E_CUDA, "velocity copy failed"));
+  if ((st = alloc_node(s, s->node0))) return bail(st);
+  const int M = s->tab.M;
+  for (int j = 1; j <= M; ++j) {
+    if ((st = alloc_node(s, s->K[j])) || (st = alloc_node(s, s->X[j])) || (st = alloc_node(s, s->AD[j])))
+      return bail(st);
+    if (op->scheme == MISDC_SCHEME_CISDCQ && op->nu > 1 && (st = alloc_node(s, s->Y[j]))) return bail(st);
+    if (s->alloc(&s->B[j], F * cs)) return bail(fail(MISDC_E_OOM, "B"));
+  }
+  if (s->alloc(&s->rhsD, F * cs) || s->alloc(&s->bR, F * cs) || s->alloc(&s->thfD, 3 * cs) ||
+      s->alloc(&s->thfR, 3 * cs) || s->alloc(&s->iters, cs) || s->alloc(&s->st, 1) ||
+      s->alloc(&s->dw.thf, 3 * cs) || s->alloc(&s->dw.invdiag, F * cs) || s->alloc(&s->dw.xa, F * cs) ||
+      s->alloc(&s->dw.xb, F * cs) || s->alloc(&s->dw.xc, F * cs))
+    return bail(fail(MISDC_E_OOM, "work buffers"));
+  cudaMemset(s->st, 0, sizeof(DevStats));
+  // multigrid hierarchy (levels with even extents only)
+  s->dw.levels = 1;
+  s->dw.cycles = 12;
+  s->dw.lg[0] = s->g;
+  if (s->o.mg_levels > 1) {
+    const size_t nfs = N;
+    if (s->alloc(&s->dw.lb[0], nfs * cs) || s->alloc(&s->dw.lx[0], nfs * cs) ||
+        s->alloc(&s->dw.lr[0], nfs * cs) || s->alloc(&s->dw.ly[0], nfs * cs))
+      return bail(fail(MISDC_E_OOM, "multigrid"));
+    for (int l = 1; l < s->o.mg_levels; ++l) {
+      DevGrid c = s->dw.lg[l - 1];
+      if ((c.nx % 2) || (c.dim > 1 && c.ny % 2) || (c.dim > 2 && c.nz % 2) || c.nx < 4) break;
+      c.nx /= 2;
+      if (c.dim > 1) c.ny /= 2;
+      if (c.dim > 2) c.nz /= 2;
+      c.cells = c.nx * c.ny * c.nz;
+      c.dx *= 2.0;
+      s->dw.lg[l] = c;
+      const size_t cc = c.cells;
+      if (s->alloc(&s->dw.lthf[l], 3 * cc) || s->alloc(&s->dw.linvdiag[l], nfs * cc) ||
+          s->alloc(&s->dw.lb[l], nfs * cc) || s->alloc(&s->dw.lx[l], nfs * cc) ||
+          s->alloc(&s->dw.lr[l], nfs * cc) || s->alloc(&s->dw.ly[l], nfs * cc))
+        return bail(fail(MISDC_E_OOM, "multigrid"));
+      s->dw.levels = l + 1;
+    }
+  }
+  if (cudaStreamCreateWithFlags(&s->sD, cudaStreamNonBlocking) ||
+      cudaStreamCreateWithFlags(&s->sR, cudaStreamNonBlocking))
+    return bail(fail(MISDC_E_CUDA, "stream creation failed"));
+  s->evD.assign((size_t)(M + 1) * op->nu, nullptr);
+  s->evR.assign((size_t)(M + 1) * op->nu, nullptr);
+  for (auto *v : {&s->evD, &s->evR})
+    for (auto &e : *v)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) return bail(fail(MISDC_E_CUDA, "event"));
+  for (cudaEvent_t *e : {&s->evIn, &s->evOut, &s->evFork, &s->evJoin})
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming)) return bail(fail(MISDC_E_CUDA, "event"));
+  if (op->profile) {
+    const int stages = op->n_sweeps * M * (op->scheme == MISDC_SCHEME_CISDCQ ? op->nu : 1);
+    s->prof_n.assign(2 * (size_t)stages, nullptr);
+    s->prof_d.assign(2 * (size_t)stages, nullptr);
+    for (auto *v : {&s->prof_n, &s->prof_d})
+      for (auto &ev : *v)
+        if (cudaEventCreate(&ev)) return bail(fail(MISDC_E_CUDA, "event"));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bail(fail(MISDC_E_CUDA, cudaGetErrorString(e)));
+  *out = s;
+  return MISDC_OK;
+}
+
+void misdc_destroy(misdc_solver *s) {
+  if (!s) return;
+  if (s->sD) cudaStreamSynchronize(s->sD);
+  if (s->sR) cudaStreamSynchronize(s->sR);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  for (auto *v : {&s->evD, &s->evR})
+    for (auto &ev : *v) if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : {s->evIn, s->evOut, s->evFork, s->evJoin}) if (ev) cudaEventDestroy(ev);
+  for (auto *v : {&s->prof_n, &s->prof_d})
+    for (auto &ev : *v) if (ev) cudaEventDestroy(ev);
+  if (s->sD) cudaStreamDestroy(s->sD);
+  if (s->sR) cudaStreamDestroy(s->sR);
+  for (void *p : s->allocs) cudaFree(p);
+  delete s;
+}
+
+misdc_status misdc_step(misdc_solver *s, double *state, double *T, double dt, int n_steps,
+                        void *stream) {
+  if (!s || !state) return fail(MISDC_E_INVALID, "null argument");
+  if (!(dt > 0.0) || n_steps < 0) return fail(MISDC_E_INVALID, "dt must be > 0 and n_steps >= 0");
+  if (n_steps == 0) return MISDC_OK;
+  cudaStream_t us = (cudaStream_t)stream;
+  configure_dt(s, dt);
+  CK(cudaEventRecord(s->evIn, us));
+  CK(cudaStreamWaitEvent(s->sD, s->evIn, 0));
+  if (s->o.use_graph) {
+    if (!s->gexec || s->g_state != state || s->g_T != T || s->g_dt != dt) {
+      if (s->gexec) { cudaGraphExecDestroy(s->gexec); s->gexec = nullptr; }
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(s->sD, cudaStreamCaptureModeThreadLocal));
+      enqueue_step(s, state, T, dt);
+      cudaError_t ec = cudaStreamEndCapture(s->sD, &graph);
+      if (ec != cudaSuccess) return fail(MISDC_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+      size_t nn = 0;
+      cudaGraphGetNodes(graph, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      cudaGraphGetNodes(graph, nodes.data(), &nn);
+      s->kernels_per_step = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        cudaGraphNodeGetType(nd, &ty);
+        if (ty == cudaGraphNodeTypeKernel) ++s->kernels_per_step;
+      }
+      ec = cudaGraphInstantiate(&s->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ec != cudaSuccess) return fail(MISDC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+      s->g_state = state; s->g_T = T; s->g_dt = dt;
+    }
+    for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(s->gexec, s->sD));
+    s->kernels_launched += s->kernels_per_step * n_steps;
+  } else {
+    for (int i = 0; i < n_steps; ++i) enqueue_step(s, state, T, dt);
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(s->evOut, s->sD));
+  CK(cudaStreamWaitEvent(us, s->evOut, 0));
+  return MISDC_OK;
+}
+
+misdc_status misdc_step_host(misdc_solver *s, double *state_host, double *T_host, double dt,
+                             int n_steps, void *stream) {
+  if (!s || !state_host) return fail(MISDC_E_INVALID, "null argument");
+  const size_t cs = s->cs, F = s->N + 1;
+  if (!s->stage_state) {
+    CK(s->alloc(&s->stage_state, F * cs));
+    CK(s->alloc(&s->stage_T, cs));
+  }
+  cudaStream_t us = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(s->stage_state, state_host, F * cs * sizeof(double), cudaMemcpyHostToDevice, us));
+  if (T_host) CK(cudaMemcpyAsync(s->stage_T, T_host, cs * sizeof(double), cudaMemcpyHostToDevice, us));
+  misdc_status st = misdc_step(s, s->stage_state, T_host ? s->stage_T : nullptr, dt, n_steps, stream);
+  if (st) return st;
+  CK(cudaMemcpyAsync(state_host, s->stage_state, F * cs * sizeof(double), cudaMemcpyDeviceToHost, us));
+  if (T_host) CK(cudaMemcpyAsync(T_host, s->stage_T, cs * sizeof(double), cudaMemcpyDeviceToHost, us));
+  CK(cudaStreamSynchronize(us));
+  return MISDC_OK;
+}
+
+misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
+  if (!s || !out) return fail(MISDC_E_INVALID, "null argument");
+  CK(cudaStreamSynchronize(s->sD));
+  CK(cudaStreamSynchronize(s->sR));
+  DevStats d;
+  CK(cudaMemcpy(&d, s->st, sizeof(d), cudaMemcpyDeviceToHost));
+  out->newton_solves = (long long)d.newton_solves;
+  out->newton_iters = (long long)d.newton_iters;
+  out->newton_fail = (long long)d.newton_fail;
+  out->newton_max = d.newton_max;
+  out->lin_sweeps = (long long)d.lin_sweeps;
+  double r;
+  memcpy(&r, &d.lin_resid_bits, sizeof(r));
+  out->lin_resid_max = r;
+  out->kernel_launches = s->kernels_launched;
+  int st = MISDC_OK;
+  if (d.status_bits & kBitTdiag) st = MISDC_E_TDIAG;
+  else if (d.status_bits & (kBitNan | kBitSingular)) st = MISDC_E_NAN;
+  else if (d.status_bits & kBitNewton) st = MISDC_E_NEWTON;
+  else if (d.status_bits & kBitMG) st = MISDC_E_MG;
+  else if (d.status_bits & kBitTimeout) st = MISDC_E_TIMEOUT;
+  out->status = st;
+  if (reset) {
+    CK(cudaMemset(s->st, 0, sizeof(DevStats)));
+    s->kernels_launched = 0;
+  }
+  return MISDC_OK;
+}
+
+misdc_status misdc_stage_times(misdc_solver *s, double *newton_ms, int *newton_launches,
+                               double *diffusion_ms, int *diffusion_launches) {
+  if (!s) return fail(MISDC_E_INVALID, "null argument");
+  if (!s->o.profile) return fail(MISDC_E_INVALID, "solver was created without opts.profile");
+  CK(cudaStreamSynchronize(s->sD));
+  CK(cudaStreamSynchronize(s->sR));
+  double tn = 0.0, td = 0.0;
+  for (int i = 0; i < s->n_used; ++i) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, s->prof_n[2 * i], s->prof_n[2 * i + 1]));
+    tn += ms;
+  }
+  for (int i = 0; i < s->d_used; ++i) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, s->prof_d[2 * i], s->prof_d[2 * i + 1]));
+    td += ms;
+  }
+  if (newton_ms) *newton_ms = tn;
+  if (newton_launches) *newton_launches = s->n_used;
+  if (diffusion_ms) *diffusion_ms = td;
+  if (diffusion_launches) *diffusion_launches = s->d_used;
+  return MISDC_OK;
+}
+
+misdc_status misdc_enthalpy(misdc_solver *s, const double *Y, const double *T, double *h, int n,
+                            void *stream) {
+  if (!s || !Y || !T || !h || n < 0) return fail(MISDC_E_INVALID, "bad argument");
+  launch_enthalpy(s->m, n, n, Y, T, h, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+misdc_status misdc_temperature(misdc_solver *s, const double *Y, const double *h, double *T, int n,
+                               void *stream) {
+  if (!s || !Y || !T || !h || n < 0) return fail(MISDC_E_INVALID, "bad argument");
+  launch_temperature(s->m, n, n, Y, h, T, T, nullptr, nullptr, s->st, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+misdc_status misdc_production_rates(misdc_solver *s, const double *Y, const double *T, double *FR,
+                                    int n, void *stream) {
+  if (!s || !Y || !T || !FR || n < 0) return fail(MISDC_E_INVALID, "bad argument");
+  launch_rates(s->m, n, n, Y, T, FR, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+misdc_status misdc_reaction_solve(misdc_solver *s, double wdt, const double *b, const double *hstar,
+                                  double *x, double *FR, int *iters, int n, void *stream) {
+  if (!s || !b || !hstar || !x || n < 0) return fail(MISDC_E_INVALID, "bad argument");
+  if (!(wdt >= 0.0)) return fail(MISDC_E_INVALID, "wdt must be >= 0");
+  if (n == 0) return MISDC_OK;
+  const size_t N = s->N;
+  double *hsp = nullptr, *th = nullptr;
+  CK(cudaMallocAsync(&hsp, N * n * sizeof(double), (cudaStream_t)stream));
+  CK(cudaMallocAsync(&th, n * sizeof(double), (cudaStream_t)stream));
+  launch_newton(s->m, n, n, wdt, s->o.newton_rtol, s->o.newton_maxit, b, hstar, x, x + N * n, x,
+                x + N * n, FR, hsp, th, iters, s->st, (cudaStream_t)stream);
+  cudaFreeAsync(hsp, (cudaStream_t)stream);
+  cudaFreeAsync(th, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+misdc_status misdc_operators(misdc_solver *s, const double *state, double *FE, double *FD, double *FR,
+                             void *stream) {
+  if (!s || !state) return fail(MISDC_E_INVALID, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(s->sD));
+  NodeBuf &b = s->node0;
+  const size_t cs = s->cs, F = s->N + 1;
+  CK(cudaMemcpyAsync(b.phi, state, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_temperature(s->m, s->cs, s->cs, b.phi, b.phi + (size_t)s->N * cs, nullptr, b.T, b.theta,
+                     b.hsp, s->st, st);
+  launch_theta_faces(s->g, b.theta, s->thfD, st);
+  if (FE || FD) launch_operators(s->m, s->g, s->i0, b.phi, b.hsp, s->thfD, s->vel, FE, FD, st);
+  if (FR) {
+    launch_rates(s->m, s->cs, s->cs, b.phi, b.T, FR, st);
+    CK(cudaMemsetAsync(FR + (size_t)s->N * cs, 0, cs * sizeof(double), st));
+  }
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+misdc_status misdc_diffusion_solve(misdc_solver *s, double wdt, const double *coef_state,
+                                   const double *rhs, double *x, void *stream) {
+  if (!s || !coef_state || !rhs || !x) return fail(MISDC_E_INVALID, "bad argument");
+  if (!(wdt >= 0.0)) return fail(MISDC_E_INVALID, "wdt must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(s->sD));
+  NodeBuf &b = s->node0;
+  const size_t cs = s->cs, F = s->N + 1;
+  CK(cudaMemcpyAsync(b.phi, coef_state, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_temperature(s->m, s->cs, s->cs, b.phi, b.phi + (size_t)s->N * cs, nullptr, b.T, b.theta,
+                     nullptr, s->st, st);
+  s->rho_dt = -1.0;
+  s->rho_bound = rho_bound_for(s, wdt);
+  s->cheb_sweeps = chebyshev_sweeps(s->rho_bound, std::max(1e-3 * s->o.lin_rtol, 1e-17));
+  CK(cudaMemcpyAsync(s->rhsD, rhs, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  diffusion_solve(s->m, s->g, s->i0, wdt, b.theta, s->rhsD, x, s->dw, s->cheb_sweeps, s->rho_bound,
+                  s->o.lin_rtol, s->st, st);
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double *const *in,
+                           const double *w, size_t n, void *stream) {
+  if (n_out < 1 || n_out > 8 || n_in < 1 || n_in > 16 || !out || !in || !w)
+    return fail(MISDC_E_INVALID, "lincomb supports 1..8 outputs and 1..16 inputs");
+  LinComb lc;
+  memset(&lc, 0, sizeof(lc));
+  lc.n_out = n_out;
+  lc.n_in = n_in;
+  for (int o = 0; o < n_out; ++o) {
+    if (!out[o]) return fail(MISDC_E_INVALID, "null output");
+    lc.out[o] = out[o];
+    for (int k = 0; k < n_in; ++k) lc.w[o][k] = w[o * n_in + k];
+  }
+  for (int k = 0; k < n_in; ++k) {
+    if (!in[k]) return fail(MISDC_E_INVALID, "null input");
+    lc.in[k] = in[k];
+  }
+  launch_lincomb(lc, n, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+}  // extern "C"

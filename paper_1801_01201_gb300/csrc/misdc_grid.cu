@@ -1,0 +1,438 @@
+// Grid kernels: spectral-integration / right-hand-side linear combinations,
+// the advection-diffusion right-hand sides (Sec. 2 operators, steps S3, S4, S6)
+// and the implicit diffusion solve of steps S3-S4 (Chebyshev-accelerated
+// Jacobi smoother, multigrid V-cycles, flux-form reconstruction, closure).
+//
+// Layout: field-major [field][cells], cells x-fastest, periodic grid.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "misdc_internal.cuh"
+
+namespace misdc {
+
+namespace {
+
+struct FieldMap {
+  int nfs;                  // number of solved fields (all but the dominant species)
+  int fld[kMaxSpecies + 1]; // physical field of each solved field
+  double cf[kMaxSpecies + 1];   // wdt * diffusivity / dx^2
+};
+
+struct Nbr {
+  int cm2[3], cm[3], cp[3], cp2[3];
+};
+
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+__device__ __forceinline__ Nbr neighbours(const DevGrid &g, int c) {
+  Nbr b;
+  const int x = c % g.nx, y = (c / g.nx) % g.ny, z = c / (g.nx * g.ny);
+  const int sx = 1, sy = g.nx, sz = g.nx * g.ny;
+  const int base[3] = {c - x * sx, c - y * sy, c - z * sz};
+  const int pos[3] = {x, y, z}, n[3] = {g.nx, g.ny, g.nz}, str[3] = {sx, sy, sz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int p = pos[d], nn = n[d];
+    b.cm2[d] = base[d] + wrapi(wrapi(p - 2, nn), nn) * str[d];
+    b.cm[d] = base[d] + wrapi(p - 1, nn) * str[d];
+    b.cp[d] = base[d] + wrapi(p + 1, nn) * str[d];
+    b.cp2[d] = base[d] + wrapi(wrapi(p + 2, nn), nn) * str[d];
+  }
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_lincomb(LinComb lc, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = (k < lc.n_in) ? lc.in[k][e] : 0.0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      if (o < lc.n_out) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (k < lc.n_in) s = fma(lc.w[o][k], v[k], s);
+        lc.out[o][e] = s;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// F_E (advection of every field + explicit differential diffusion of h) and
+// F_D (implicit diffusion, dominant species closed by minus the sum).
+// ---------------------------------------------------------------------------
+__global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restrict__ phi,
+                            const double *__restrict__ hsp, const double *__restrict__ thf,
+                            const double *__restrict__ vel, double *__restrict__ FE,
+                            double *__restrict__ FD) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cs = g.cells;
+  if (c >= cs) return;
+  const int N = m.N, dim = g.dim;
+  const Nbr nb = neighbours(g, c);
+  const double invdx = 1.0 / g.dx, invdx2 = invdx * invdx;
+  double ulo[3], uhi[3], tlo[3], thi[3];
+  double qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0}, glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
+  for (int d = 0; d < dim; ++d) {
+    ulo[d] = vel[(size_t)d * cs + c];
+    uhi[d] = vel[(size_t)d * cs + nb.cp[d]];
+    tlo[d] = thf[(size_t)d * cs + c];
+    thi[d] = thf[(size_t)d * cs + nb.cp[d]];
+  }
+  double fd_i0 = 0.0, fa_h = 0.0;
+  for (int f = 0; f <= N; ++f) {
+    const double *x = phi + (size_t)f * cs;
+    const double xc = x[c];
+    double fa = 0.0, fdl = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      const double xm2 = x[nb.cm2[d]], xm = x[nb.cm[d]], xp = x[nb.cp[d]], xp2 = x[nb.cp2[d]];
+      const double lo = (7.0 * (xm + xc) - (xm2 + xp)) / 12.0;
+      const double hi = (7.0 * (xc + xp) - (xm + xp2)) / 12.0;
+      fa += uhi[d] * hi - ulo[d] * lo;
+      fdl += thi[d] * (xp - xc) - tlo[d] * (xc - xm);
+      if (f < N) {
+        const double *hs = hsp + (size_t)f * cs;
+        const double hbl = 0.5 * (hs[nb.cm[d]] + hs[c]);
+        const double hbh = 0.5 * (hs[c] + hs[nb.cp[d]]);
+        const double dyl = (xc - xm) * invdx, dyh = (xp - xc) * invdx;
+        qlo[d] += hbl * m.alpha0 * tlo[d] * dyl;
+        qhi[d] += hbh * m.alpha0 * thi[d] * dyh;
+        if (f != i0) {
+          const double Gl = m.D0[f] * tlo[d] * dyl, Gh = m.D0[f] * thi[d] * dyh;
+          qlo[d] -= hbl * Gl;
+          qhi[d] -= hbh * Gh;
+          glo[d] += Gl;
+          ghi[d] += Gh;
+        }
+      }
+    }
+    if (f < N) {
+      if (FE) FE[(size_t)f * cs + c] = -fa * invdx;
+      if (f != i0) {
+        const double v = m.D0[f] * fdl * invdx2;
+        if (FD) FD[(size_t)f * cs + c] = v;
+        fd_i0 -= v;
+      }
+    } else {
+      fa_h = fa;
+      if (FD) FD[(size_t)N * cs + c] = m.alpha0 * fdl * invdx2;
+    }
+  }
+  if (FD) FD[(size_t)i0 * cs + c] = fd_i0;
+  if (FE) {
+    const double *hs0 = hsp + (size_t)i0 * cs;
+    double div = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      const double hbl = 0.5 * (hs0[nb.cm[d]] + hs0[c]);
+      const double hbh = 0.5 * (hs0[c] + hs0[nb.cp[d]]);
+      div += (qhi[d] + hbh * ghi[d]) - (qlo[d] + hbl * glo[d]);
+    }
+    FE[(size_t)N * cs + c] = -fa_h * invdx - div * invdx;
+  }
+}
+
+// theta at cells -> harmonic mean at the low face of each cell; inverse
+// diagonal of I - c_f L_theta for every solved field.
+__global__ void k_face_coef(DevGrid g, FieldMap fm, const double *__restrict__ theta,
+                            double *__restrict__ thf, double *__restrict__ invdiag) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cs = g.cells;
+  if (c >= cs) return;
+  const Nbr nb = neighbours(g, c);
+  const double tc = theta[c];
+  double S = 0.0;
+  for (int d = 0; d < g.dim; ++d) {
+    const double a = theta[nb.cm[d]], b = theta[nb.cp[d]];
+    const double lo = 2.0 * a * tc / (a + tc), hi = 2.0 * tc * b / (tc + b);
+    thf[(size_t)d * cs + c] = lo;
+    S += lo + hi;
+  }
+  for (int k = 0; k < fm.nfs; ++k) invdiag[(size_t)k * cs + c] = 1.0 / (1.0 + fm.cf[k] * S);
+}
+
+__device__ __forceinline__ double lap_theta(const DevGrid &g, const Nbr &nb, int c, int cs,
+                                            const double *__restrict__ thf,
+                                            const double *__restrict__ x) {
+  const double xc = x[c];
+  double s = 0.0;
+  for (int d = 0; d < g.dim; ++d)
+    s += thf[(size_t)d * cs + nb.cp[d]] * (x[nb.cp[d]] - xc) - thf[(size_t)d * cs + c] * (xc - x[nb.cm[d]]);
+  return s;
+}
+
+// One Chebyshev-accelerated Jacobi sweep for every solved field:
+// y = D^{-1} (b + c_f * offdiag(x_k)), x_{k+1} = omega (y - x_{k-1}) + x_{k-1}.
+__global__ void k_cheb(DevGrid g, FieldMap fm, const double *__restrict__ thf,
+                       const double *__restrict__ invdiag, const double *__restrict__ rhs,
+                       const double *__restrict__ xk, const double *__restrict__ xkm1,
+                       double *__restrict__ xkp1, double omega, int first) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  const int cs = g.cells;
+  if (c >= cs) return;
+  const Nbr nb = neighbours(g, c);
+  const size_t off = (size_t)fm.fld[k] * cs;
+  const double *x = xk + off;
+  double s = 0.0;
+  for (int d = 0; d < g.dim; ++d)
+    s += thf[(size_t)d * cs + nb.cp[d]] * x[nb.cp[d]] + thf[(size_t)d * cs + c] * x[nb.cm[d]];
+  const double y = (rhs[off + c] + fm.cf[k] * s) * invdiag[(size_t)k * cs + c];
+  xkp1[off + c] = first ? y : fma(omega, y - xkm1[off + c], xkm1[off + c]);
+}
+
+__device__ __forceinline__ unsigned long long dbits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+
+// Residual check, flux-form reconstruction x := rhs + c_f L x, and closure of
+// the dominant species. Writes the advection-diffusion state.
+__global__ void k_finish(DevGrid g, FieldMap fm, int N, int i0, double tol,
+                         const double *__restrict__ thf, const double *__restrict__ rhs,
+                         const double *__restrict__ x, double *__restrict__ out, DevStats *st) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cs = g.cells;
+  double rmax = 0.0;
+  if (c < cs) {
+    const Nbr nb = neighbours(g, c);
+    double sum = 0.0;
+    for (int k = 0; k < fm.nfs; ++k) {
+      const int f = fm.fld[k];
+      const size_t off = (size_t)f * cs;
+      const double L = lap_theta(g, nb, c, cs, thf, x + off);
+      const double b = rhs[off + c];
+      const double scale = fabs(b) + fabs(fm.cf[k] * L) + fabs(x[off + c]) + 1e-300;
+      const double r = b - (x[off + c] - fm.cf[k] * L);
+      rmax = fmax(rmax, fabs(r) / scale);
+      const double v = b + fm.cf[k] * L;
+      out[off + c] = v;
+      if (f < N) sum += v;
+    }
+    out[(size_t)i0 * cs + c] = 1.0 - sum;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  if ((threadIdx.x & 31) == 0 && rmax > 0.0) {
+    atomicMax(&st->lin_resid_bits, dbits(rmax));
+    if (!(rmax <= tol)) atomicOr(&st->status_bits, kBitMG);
+  }
+}
+
+// ---- multigrid transfer (cell-centred, coarsening by 2 in every used direction)
+// restriction: coarse residual = mean of the 2^dim fine residuals
+__global__ void k_restrict(DevGrid gf, DevGrid gc, int nfs, const int *__restrict__ dummy,
+                           const double *__restrict__ rf, double *__restrict__ rc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (c >= gc.cells) return;
+  (void)dummy;
+  const int X = c % gc.nx, Y = (c / gc.nx) % gc.ny, Z = c / (gc.nx * gc.ny);
+  const int sx = gf.dim > 0 ? 2 : 1, sy = gf.dim > 1 ? 2 : 1, sz = gf.dim > 2 ? 2 : 1;
+  double s = 0.0;
+  for (int dz = 0; dz < sz; ++dz)
+    for (int dy = 0; dy < sy; ++dy)
+      for (int dx = 0; dx < sx; ++dx)
+        s += rf[(size_t)k * gf.cells + (size_t)(X * sx + dx) + gf.nx * ((size_t)(Y * sy + dy) + (size_t)gf.ny * (Z * sz + dz))];
+  rc[(size_t)k * gc.cells + c] = s / (sx * sy * sz);
+}
+
+// prolongation: fine correction += coarse value of the parent cell
+__global__ void k_prolong(DevGrid gf, DevGrid gc, const double *__restrict__ xc,
+                          double *__restrict__ xf) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (c >= gf.cells) return;
+  const int x = c % gf.nx, y = (c / gf.nx) % gf.ny, z = c / (gf.nx * gf.ny);
+  const int X = gf.dim > 0 ? x / 2 : x, Y = gf.dim > 1 ? y / 2 : y, Z = gf.dim > 2 ? z / 2 : z;
+  xf[(size_t)k * gf.cells + c] += xc[(size_t)k * gc.cells + X + gc.nx * (Y + gc.ny * Z)];
+}
+
+// coarse face coefficient: mean of the fine faces that tile the coarse face
+__global__ void k_coarsen_faces(DevGrid gf, DevGrid gc, const double *__restrict__ tf,
+                                double *__restrict__ tc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= gc.cells) return;
+  const int X = c % gc.nx, Y = (c / gc.nx) % gc.ny, Z = c / (gc.nx * gc.ny);
+  for (int d = 0; d < gf.dim; ++d) {
+    double s = 0.0;
+    int cnt = 0;
+    const int ox = (d == 0) ? 1 : 2, oy = (gf.dim > 1) ? ((d == 1) ? 1 : 2) : 1,
+              oz = (gf.dim > 2) ? ((d == 2) ? 1 : 2) : 1;
+    for (int dz = 0; dz < oz; ++dz)
+      for (int dy = 0; dy < oy; ++dy)
+        for (int dx = 0; dx < ox; ++dx) {
+          const int fx = (gf.dim > 0 ? 2 * X : X) + dx, fy = (gf.dim > 1 ? 2 * Y : Y) + dy,
+                    fz = (gf.dim > 2 ? 2 * Z : Z) + dz;
+          s += tf[(size_t)d * gf.cells + fx + (size_t)gf.nx * (fy + (size_t)gf.ny * fz)];
+          ++cnt;
+        }
+    tc[(size_t)d * gc.cells + c] = s / cnt;
+  }
+}
+
+// residual r = b - (I - c L) x on one level for the solved fields (compact storage [k][cells])
+__global__ void k_residual(DevGrid g, FieldMap fm, const double *__restrict__ thf,
+                           const double *__restrict__ b, const double *__restrict__ x,
+                           double *__restrict__ r) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (c >= g.cells) return;
+  const Nbr nb = neighbours(g, c);
+  const size_t off = (size_t)k * g.cells;
+  r[off + c] = b[off + c] - (x[off + c] - fm.cf[k] * lap_theta(g, nb, c, g.cells, thf, x + off));
+}
+
+// damped Jacobi on a coarse level (compact storage): x_new = x + w D^{-1} (b - A x)
+__global__ void k_jacobi_level(DevGrid g, FieldMap fm, const double *__restrict__ thf,
+                               const double *__restrict__ invdiag, const double *__restrict__ b,
+                               const double *__restrict__ x, double *__restrict__ y, double w) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (c >= g.cells) return;
+  const Nbr nb = neighbours(g, c);
+  const size_t off = (size_t)k * g.cells;
+  const double r = b[off + c] - (x[off + c] - fm.cf[k] * lap_theta(g, nb, c, g.cells, thf, x + off));
+  y[off + c] = fma(w * invdiag[off + c], r, x[off + c]);
+}
+
+__global__ void k_diag_level(DevGrid g, FieldMap fm, const double *__restrict__ thf,
+                             double *__restrict__ invdiag) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.cells) return;
+  const Nbr nb = neighbours(g, c);
+  double S = 0.0;
+  for (int d = 0; d < g.dim; ++d) S += thf[(size_t)d * g.cells + c] + thf[(size_t)d * g.cells + nb.cp[d]];
+  for (int k = 0; k < fm.nfs; ++k) invdiag[(size_t)k * g.cells + c] = 1.0 / (1.0 + fm.cf[k] * S);
+}
+
+// gather the solved fields of a full-layout array into compact storage and back
+__global__ void k_gather(int cs, FieldMap fm, const double *__restrict__ full, double *__restrict__ compact) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (c >= cs) return;
+  compact[(size_t)k * cs + c] = full[(size_t)fm.fld[k] * cs + c];
+}
+__global__ void k_scatter_set(int cs, FieldMap fm, const double *__restrict__ compact, double *__restrict__ full) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (c >= cs) return;
+  full[(size_t)fm.fld[k] * cs + c] = compact[(size_t)k * cs + c];
+}
+
+inline dim3 grid2(int cells, int nf) { return dim3((cells + 255) / 256, nf); }
+
+FieldMap make_map(const DevMech &m, const double *D0h, double alpha0, int i0, double wdt, double dx) {
+  FieldMap fm;
+  fm.nfs = 0;
+  for (int f = 0; f <= m.N; ++f) {
+    if (f == i0) continue;
+    fm.fld[fm.nfs] = f;
+    fm.cf[fm.nfs] = wdt * ((f < m.N) ? D0h[f] : alpha0) / (dx * dx);
+    ++fm.nfs;
+  }
+  return fm;
+}
+
+}  // namespace
+
+int chebyshev_sweeps(double rho_bound, double reduction) {
+  if (rho_bound <= 0.0) return 1;
+  const double a = acosh(1.0 / rho_bound);
+  const double need = acosh(1.0 / reduction);
+  return std::max(1, (int)ceil(need / a));
+}
+
+void launch_lincomb(const LinComb &lc, size_t n, cudaStream_t s) {
+  if (!n) return;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  k_lincomb<<<(unsigned)blocks, 256, 0, s>>>(lc, n);
+}
+
+void launch_operators(const DevMech &m, const DevGrid &g, int i0, const double *phi,
+                      const double *hsp, const double *theta_face, const double *vel,
+                      double *FE, double *FD, cudaStream_t s) {
+  k_operators<<<(g.cells + 127) / 128, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, FE, FD);
+}
+
+void launch_theta_faces(const DevGrid &g, const double *theta, double *thf, cudaStream_t s) {
+  FieldMap fm;
+  fm.nfs = 0;
+  k_face_coef<<<(g.cells + 255) / 256, 256, 0, s>>>(g, fm, theta, thf, nullptr);
+}
+
+void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, const double *theta,
+                     const double *rhs, double *out, DiffWork &w, int sweeps, double rho_bound,
+                     double lin_rtol, DevStats *st, cudaStream_t s) {
+  const FieldMap fm = make_map(m, m.D0_host, m.alpha0, i0, wdt, g.dx);
+  const int cs = g.cells;
+  k_face_coef<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, theta, w.thf, w.invdiag);
+  const dim3 gr = grid2(cs, fm.nfs);
+  const double r2 = rho_bound * rho_bound;
+  // Chebyshev-accelerated Jacobi from x0 = rhs (the operator is I - c L)
+  const double *xkm1 = rhs, *xk = rhs;
+  double *bufs[3] = {w.xa, w.xb, w.xc};
+  double omega = 1.0;
+  int slot = 0;
+  for (int it = 0; it < sweeps; ++it) {
+    double *xn = bufs[slot];
+    if (it == 1) omega = 1.0 / (1.0 - 0.5 * r2);
+    else if (it > 1) omega = 1.0 / (1.0 - 0.25 * r2 * omega);
+    k_cheb<<<gr, 256, 0, s>>>(g, fm, w.thf, w.invdiag, rhs, xk, xkm1, xn, omega, it == 0);
+    xkm1 = xk;
+    xk = xn;
+    slot = (slot + 1) % 3;
+  }
+  // Multigrid (levels > 1): V-cycles of the correction scheme on compact
+  // [solved field][cells] storage, damped-Jacobi smoothing on every level,
+  // mean-value restriction and piecewise-constant prolongation, coefficients
+  // re-discretised from the fine face coefficients.
+  if (w.levels > 1) {
+    w.lthf[0] = w.thf;
+    w.linvdiag[0] = w.invdiag;
+    FieldMap fl[8];
+    fl[0] = fm;
+    for (int l = 1; l < w.levels; ++l) {
+      fl[l] = fm;
+      for (int k = 0; k < fm.nfs; ++k) fl[l].cf[k] = fm.cf[k] / (double)(1 << (2 * l));
+      const DevGrid &gf = w.lg[l - 1], &gc = w.lg[l];
+      k_coarsen_faces<<<(gc.cells + 255) / 256, 256, 0, s>>>(gf, gc, w.lthf[l - 1], w.lthf[l]);
+      k_diag_level<<<(gc.cells + 255) / 256, 256, 0, s>>>(gc, fl[l], w.lthf[l], w.linvdiag[l]);
+    }
+    k_gather<<<gr, 256, 0, s>>>(cs, fm, rhs, w.lb[0]);
+    k_gather<<<gr, 256, 0, s>>>(cs, fm, xk, w.lx[0]);
+    auto smooth = [&](int l, int n_sw) {
+      const DevGrid &gl = w.lg[l];
+      for (int sw = 0; sw < n_sw; ++sw) {
+        k_jacobi_level<<<grid2(gl.cells, fm.nfs), 256, 0, s>>>(gl, fl[l], w.lthf[l], w.linvdiag[l], w.lb[l], w.lx[l], w.ly[l], 0.8);
+        std::swap(w.lx[l], w.ly[l]);
+      }
+    };
+    for (int cyc = 0; cyc < w.cycles; ++cyc) {
+      for (int l = 0; l + 1 < w.levels; ++l) {          // down-leg
+        const DevGrid &gl = w.lg[l], &gc = w.lg[l + 1];
+        smooth(l, 2);
+        k_residual<<<grid2(gl.cells, fm.nfs), 256, 0, s>>>(gl, fl[l], w.lthf[l], w.lb[l], w.lx[l], w.lr[l]);
+        k_restrict<<<grid2(gc.cells, fm.nfs), 256, 0, s>>>(gl, gc, fm.nfs, nullptr, w.lr[l], w.lb[l + 1]);
+        cudaMemsetAsync(w.lx[l + 1], 0, sizeof(double) * (size_t)fm.nfs * gc.cells, s);
+      }
+      smooth(w.levels - 1, 8);                            // coarsest level
+      for (int l = w.levels - 2; l >= 0; --l) {          // up-leg
+        k_prolong<<<grid2(w.lg[l].cells, fm.nfs), 256, 0, s>>>(w.lg[l], w.lg[l + 1], w.lx[l + 1], w.lx[l]);
+        smooth(l, 2);
+      }
+    }
+    double *xn = bufs[slot];
+    k_scatter_set<<<gr, 256, 0, s>>>(cs, fm, w.lx[0], xn);
+    xk = xn;
+  }
+  k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, xk, out, st);
+}
+
+}  // namespace misdc

@@ -152,7 +152,8 @@ def _anchor_compositions(rng, n):
 
 
 def make_mechanism(seed: int, n_species: int, n_reactions: int,
-                   T_u: float = 300.0, T_b: float = 2000.0) -> Mechanism:
+                   T_u: float = 300.0, T_b: float = 2000.0,
+                   logA_range: tuple = (8.0, 14.0)) -> Mechanism:
     """Seeded, element-balanced synthetic mechanism with equilibrium-anchored thermo.
 
     Stoichiometry: reactions drawn from the enumerated balanced forms
@@ -239,7 +240,7 @@ def make_mechanism(seed: int, n_species: int, n_reactions: int,
         nu_f[r], nu_r[r] = lf, lr
 
     order = nu_f.sum(axis=1)
-    logA = rng.uniform(8.0, 14.0, R)
+    logA = rng.uniform(logA_range[0], logA_range[1], R)
     A = 10.0 ** logA * (1e-6) ** (order - 1)                   # cm-mol-s -> SI
     beta = rng.uniform(-1.0, 1.0, R)
     Ea = rng.uniform(0.0, 200.0, R) * 1e3

@@ -1,0 +1,199 @@
+"""Python binding of the C ABI: argument marshalling around libmisdc.
+
+Every step of the method runs in the CUDA library; PyTorch only provides
+device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(t.ctypes.data)
+    raise TypeError("expected a torch tensor or numpy array")
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(a, device):
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=torch.float64).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=device)
+
+
+def lobatto(n_nodes):
+    """tau, Q, QI, QE as the CUDA library builds them."""
+    lib = L.load()
+    M = n_nodes - 1
+    tau = np.zeros(M + 1)
+    Q = np.zeros((M, M + 1))
+    QI = np.zeros((M, M))
+    QE = np.zeros((M, M))
+    L.check(lib.misdc_lobatto(n_nodes, tau.ctypes.data_as(L.dp), Q.ctypes.data_as(L.dp),
+                              QI.ctypes.data_as(L.dp), QE.ctypes.data_as(L.dp)))
+    return tau, Q, QI, QE
+
+
+def lincomb(outs, ins, w, n, stream=None):
+    """out[o] = sum_k w[o][k] in[k] over n elements (device tensors)."""
+    lib = L.load()
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    op = (C.c_void_p * len(outs))(*[t.data_ptr() for t in outs])
+    ip = (C.c_void_p * len(ins))(*[t.data_ptr() for t in ins])
+    L.check(lib.misdc_lincomb(len(outs), len(ins), op, ip, w.ctypes.data_as(L.dp), n, _stream(stream)))
+
+
+class Solver:
+    """One flame: mechanism + periodic grid + face velocities + time-integration options."""
+
+    def __init__(self, mech, flame, *, n_nodes=3, n_sweeps=4, nu=2, scheme="CISDCQ",
+                 precision="fp64", newton_rtol=1e-12, newton_maxit=50, lin_rtol=1e-14,
+                 mg_levels=1, two_streams=True, use_graph=True, profile=False, device="cuda"):
+        self.lib = L.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.device = torch.device(device)
+        self.mech, self.flame = mech, flame
+        self.N = mech.n_species
+        self.cells = flame.nx * flame.ny * flame.nz
+        k = dict(W=np.ascontiguousarray(mech.W, np.float64), nasa7=np.ascontiguousarray(mech.nasa7, np.float64),
+                 A=np.ascontiguousarray(mech.A, np.float64), beta=np.ascontiguousarray(mech.beta, np.float64),
+                 Ea=np.ascontiguousarray(mech.Ea, np.float64), nu_f=np.ascontiguousarray(mech.nu_f, np.int32),
+                 nu_r=np.ascontiguousarray(mech.nu_r, np.int32), D0=np.ascontiguousarray(mech.D0, np.float64))
+        self._keep = k
+        md = L.MechDesc(self.N, mech.n_reactions, k["W"].ctypes.data_as(L.dp), k["nasa7"].ctypes.data_as(L.dp),
+                        k["A"].ctypes.data_as(L.dp), k["beta"].ctypes.data_as(L.dp),
+                        k["Ea"].ctypes.data_as(L.dp), k["nu_f"].ctypes.data_as(L.ip),
+                        k["nu_r"].ctypes.data_as(L.ip), k["D0"].ctypes.data_as(L.dp),
+                        mech.alpha0, mech.T_ref, mech.theta_exp, mech.p_ref)
+        gd = L.GridDesc(flame.dim, flame.nx, flame.ny, flame.nz, flame.dx)
+        o = L.Opts()
+        self.lib.misdc_default_opts(C.byref(o))
+        o.n_nodes, o.n_sweeps, o.nu = n_nodes, n_sweeps, nu
+        o.scheme = L.SCHEMES[scheme]
+        o.precision = L.PRECISIONS[precision]
+        o.dominant_species = flame.dominant
+        o.rho = flame.rho
+        o.newton_rtol, o.newton_maxit, o.lin_rtol = newton_rtol, newton_maxit, lin_rtol
+        o.mg_levels = mg_levels
+        o.two_streams, o.use_graph = int(two_streams), int(use_graph)
+        o.profile = int(profile)
+        self.opts = o
+        vel = _dev(flame.vel, self.device)
+        h = C.c_void_p()
+        L.check(self.lib.misdc_create(C.byref(md), C.byref(gd), C.byref(o), _ptr(vel), C.byref(h)))
+        self.handle = h
+        torch.cuda.synchronize()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.misdc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state helpers ------------------------------------------------------
+    def enthalpy(self, Y, T, stream=None):
+        Y = _dev(Y, self.device)
+        T = _dev(T, self.device)
+        n = T.numel()
+        h = torch.empty(n, dtype=torch.float64, device=self.device)
+        L.check(self.lib.misdc_enthalpy(self.handle, _ptr(Y), _ptr(T), _ptr(h), n, _stream(stream)))
+        return h
+
+    def temperature(self, Y, h, T_guess=None, stream=None):
+        Y = _dev(Y, self.device)
+        h = _dev(h, self.device)
+        n = h.numel()
+        T = (_dev(T_guess, self.device).clone() if T_guess is not None
+             else torch.full((n,), -1.0, dtype=torch.float64, device=self.device))
+        L.check(self.lib.misdc_temperature(self.handle, _ptr(Y), _ptr(h), _ptr(T), n, _stream(stream)))
+        return T
+
+    def state_from_YT(self, Y, T):
+        """Device state [N+1, cells] = (Y, h(T)) with h from the library's thermo."""
+        Y = _dev(Y, self.device)
+        h = self.enthalpy(Y, T)
+        return torch.cat([Y, h[None, :]], dim=0).contiguous()
+
+    # -- time stepping ------------------------------------------------------
+    def step(self, state, dt, n_steps=1, T=None, stream=None):
+        L.check(self.lib.misdc_step(self.handle, _ptr(state), _ptr(T), float(dt), int(n_steps),
+                                    _stream(stream)))
+        return state
+
+    def step_host(self, state_host, dt, n_steps=1, T_host=None, stream=None):
+        L.check(self.lib.misdc_step_host(self.handle, _ptr(state_host), _ptr(T_host), float(dt),
+                                         int(n_steps), _stream(stream)))
+        return state_host
+
+    def stats(self, reset=True):
+        st = L.Stats()
+        L.check(self.lib.misdc_get_stats(self.handle, C.byref(st), int(reset)))
+        return st.as_dict()
+
+    def stage_times(self):
+        tn, td = C.c_double(), C.c_double()
+        nn, nd = C.c_int(), C.c_int()
+        L.check(self.lib.misdc_stage_times(self.handle, C.byref(tn), C.byref(nn), C.byref(td), C.byref(nd)))
+        return dict(newton_ms=tn.value, newton_launches=nn.value, diffusion_ms=td.value,
+                    diffusion_launches=nd.value)
+
+    # -- row-level entry points --------------------------------------------
+    def production_rates(self, Y, T, stream=None):
+        Y = _dev(Y, self.device)
+        T = _dev(T, self.device)
+        n = T.numel()
+        FR = torch.empty((self.N, n), dtype=torch.float64, device=self.device)
+        L.check(self.lib.misdc_production_rates(self.handle, _ptr(Y), _ptr(T), _ptr(FR), n, _stream(stream)))
+        return FR
+
+    def reaction_solve(self, wdt, b, hstar, x0, stream=None):
+        b = _dev(b, self.device)
+        hstar = _dev(hstar, self.device)
+        x = _dev(x0, self.device).clone()
+        n = hstar.numel()
+        FR = torch.empty((self.N, n), dtype=torch.float64, device=self.device)
+        it = torch.zeros(n, dtype=torch.int32, device=self.device)
+        L.check(self.lib.misdc_reaction_solve(self.handle, float(wdt), _ptr(b), _ptr(hstar), _ptr(x),
+                                              _ptr(FR), _ptr(it), n, _stream(stream)))
+        return x, FR, it
+
+    def operators(self, state, stream=None):
+        state = _dev(state, self.device)
+        FE = torch.empty_like(state)
+        FD = torch.empty_like(state)
+        FR = torch.empty_like(state)
+        L.check(self.lib.misdc_operators(self.handle, _ptr(state), _ptr(FE), _ptr(FD), _ptr(FR),
+                                         _stream(stream)))
+        return FE, FD, FR
+
+    def diffusion_solve(self, wdt, coef_state, rhs, stream=None):
+        coef_state = _dev(coef_state, self.device)
+        rhs = _dev(rhs, self.device)
+        x = torch.empty_like(rhs)
+        L.check(self.lib.misdc_diffusion_solve(self.handle, float(wdt), _ptr(coef_state), _ptr(rhs),
+                                               _ptr(x), _stream(stream)))
+        return x

@@ -1,0 +1,52 @@
+"""Host-side checks of the C ABI (no GPU work): build, exported symbols, tables, argument checks."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1801_01201_gb300 import _lib as L
+from paper_1801_01201_gb300 import solver as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "misdc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(misdc_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function():
+    lib = L.load()
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(L.EXPORTS)
+
+
+@pytest.mark.parametrize("n_nodes", [2, 3, 4, 5])
+def test_library_tables_equal_oracle_tables(n_nodes):
+    tau, Q, QI, QE = S.lobatto(n_nodes)
+    t2, Q2, S2, QI2, QE2 = O.lobatto(n_nodes - 1)
+    np.testing.assert_allclose(tau, t2, atol=1e-15)
+    np.testing.assert_allclose(Q, Q2, atol=1e-15)
+    np.testing.assert_allclose(QI, QI2, atol=1e-15)
+    np.testing.assert_allclose(QE, QE2, atol=1e-15)
+
+
+def test_invalid_arguments_are_rejected_before_device_work():
+    lib = L.load()
+    assert lib.misdc_lobatto(1, None, None, None, None) == L.E_INVALID
+    assert lib.misdc_lobatto(12, None, None, None, None) == L.E_INVALID
+    h = C.c_void_p()
+    assert lib.misdc_create(None, None, None, None, C.byref(h)) == L.E_INVALID
+    assert b"null" in lib.misdc_last_error()
+    assert lib.misdc_step(None, None, None, 1e-6, 1, None) == L.E_INVALID
+    assert lib.misdc_lincomb(0, 1, None, None, None, 0, None) == L.E_INVALID
+    o = L.Opts()
+    lib.misdc_default_opts(C.byref(o))
+    assert (o.n_nodes, o.n_sweeps, o.nu, o.scheme) == (3, 4, 2, L.SCHEMES["CISDCQ"])

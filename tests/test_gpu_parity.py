@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Tolerance (FP64 mode): 1e-10 relative per field, ||a - b||_inf / ||b||_inf, for
+every mass fraction, the enthalpy and the temperature, on every per-call kernel
+(thermo, rates, reaction Newton, operators, diffusion solve, quadrature) and on
+full time steps of well-conditioned chemistry (pre-exponential factors up to
+1e11). With the full mechanism ranges (A up to 1e14, Ea down to 0) the
+near-equilibrium reaction fluxes reach 1e12 mol/m^3/s and the time step itself
+amplifies round-off: the oracle's own output moves by ~1e-8 when its input is
+perturbed by one ulp. There the bound is max(1e-10, 20 x that measured
+self-sensitivity), per field. Iteration counts are checked for validity, not
+equality, since rounding may move a stopping test.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1801_01201_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def S():
+    from paper_1801_01201_gb300 import solver
+    return solver
+
+
+def relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.ndim == 1:
+        return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+    return np.max(np.abs(a - b), axis=1) / np.maximum(np.max(np.abs(b), axis=1), 1e-300)
+
+
+def small_2d(mech_key=(1802, 21, 84), n=32, ny=None, logA=(8.0, 14.0)):
+    mech = I.make_mechanism(*mech_key, logA_range=logA)
+    fl = I.flame_2d(mech, 0, n=n, dx=4e-5, radius=n * 4e-5 / 4, delta=2 * 4e-5)
+    if ny is not None:   # ragged rectangle: crop the square flame to n x ny cells
+        Y = fl.Y.reshape(mech.n_species, n, n)[:, :ny, :].reshape(mech.n_species, -1)
+        T = fl.T.reshape(n, n)[:ny, :].reshape(-1)
+        vel = np.zeros((3, n * ny))
+        ix, iy = np.arange(n * ny) % n, np.arange(n * ny) // n
+        vel[0] = 0.5 * np.sin(2 * np.pi * iy / ny)     # u(y), v(x): discretely divergence free
+        vel[1] = 0.3 * np.cos(2 * np.pi * ix / n)
+        fl = I.Flame(2, n, ny, 1, fl.dx, Y.copy(), T.copy(), vel, fl.rho, fl.dominant)
+    return mech, fl
+
+
+@pytest.fixture(scope="module")
+def flame1d():
+    mech, fl, w = I.build_workload("flame1d_128_n9")
+    return mech, fl, w
+
+
+def test_thermo_parity(flame1d):
+    mech, fl, _ = flame1d
+    sv = S().Solver(mech, fl)
+    ad = O.ADR(mech, fl)
+    h_gpu = sv.enthalpy(fl.Y, fl.T).cpu().numpy()
+    h_or = ad.h_from_T(fl.Y, fl.T)
+    assert relerr(h_gpu, h_or) < 1e-14
+    T_gpu = sv.temperature(fl.Y, h_or).cpu().numpy()
+    assert relerr(T_gpu, fl.T) < 1e-12
+
+
+@pytest.mark.parametrize("key", [(1801, 9, 21), (1802, 21, 84), (1803, 53, 325)])
+def test_production_rates_parity(key):
+    mech = I.make_mechanism(*key)
+    fl = I.flame_1d(mech, 0, nx=64, dx=1e-4)
+    rng = np.random.default_rng(5)
+    Y = fl.Y * (1 + 0.05 * rng.standard_normal(fl.Y.shape))
+    T = fl.T * (1 + 0.01 * rng.standard_normal(fl.T.shape))
+    sv = S().Solver(mech, fl)
+    FR = sv.production_rates(Y, T).cpu().numpy()
+    ad = O.ADR(mech, fl)
+    want = np.stack([ad.wdot(Y[:, c], T[c])[0] / fl.rho for c in range(64)], axis=1)
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(FR - want)) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("key", [(1801, 9, 21), (1802, 21, 84), (1803, 53, 325)])
+def test_reaction_newton_parity(key):
+    mech = I.make_mechanism(*key)
+    n = 96   # three warps' worth of tail beyond a multiple of 32 cells
+    fl = I.flame_1d(mech, 0, nx=n, dx=1e-4)
+    ad = O.ADR(mech, fl)
+    N = mech.n_species
+    rng = np.random.default_rng(6)
+    b = fl.Y * (1 + 0.02 * rng.standard_normal(fl.Y.shape))
+    hstar = ad.h_from_T(fl.Y, fl.T)
+    x0 = np.concatenate([fl.Y, fl.T[None, :]], axis=0)
+    wdt = 5e-6 / 4
+    sv = S().Solver(mech, fl)
+    x, FR, it = sv.reaction_solve(wdt, b, hstar, x0)
+    x = x.cpu().numpy()
+    it = it.cpu().numpy()
+    assert np.all(it > 0), it
+    want = np.zeros_like(x)
+    for c in range(n):
+        xc, ic = ad.reaction_newton(wdt, b[:, c], hstar[c], x0[:, c])
+        assert ic > 0
+        want[:, c] = xc
+    assert np.all(relerr(x[:N], want[:N]) < TOL)
+    assert relerr(x[N], want[N]) < TOL
+    st = sv.stats()
+    assert st["newton_fail"] == 0 and st["newton_solves"] == n
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_operators_parity(dim):
+    if dim == 1:
+        mech, fl, _ = I.build_workload("flame1d_128_n9", dict(nx=40))
+    elif dim == 2:
+        mech, fl = small_2d(n=24)
+    else:
+        mech = I.make_mechanism(1802, 21, 84)
+        fl = I.flame_3d(mech, 0, n=8, dx=1e-4, radius=2e-4, delta=2e-4)
+    ad = O.ADR(mech, fl)
+    # off the anchored equilibria (5% composition noise) so that the net rates are
+    # well conditioned relative to their own size
+    rng = np.random.default_rng(9)
+    Y = fl.Y * (1 + 0.05 * rng.standard_normal(fl.Y.shape))
+    phi = ad.state_from_YT(Y, fl.T)
+    FE, FD, FR = ad.operators(phi)
+    sv = S().Solver(mech, fl)
+    gE, gD, gR = [t.cpu().numpy() for t in sv.operators(phi)]
+    for got, want in ((gE, FE), (gD, FD), (gR, FR)):
+        scale = np.max(np.abs(want), axis=1) + 1e-300
+        assert np.all(np.max(np.abs(got - want), axis=1) <= 1e-11 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("levels", [1, 3])
+def test_diffusion_solve_parity(levels):
+    mech, fl = small_2d(n=32)
+    ad = O.ADR(mech, fl)
+    coef = ad.state_from_YT(fl.Y, fl.T)
+    rng = np.random.default_rng(7)
+    rhs = coef * (1 + 0.1 * rng.standard_normal(coef.shape))
+    wdt = 5e-6 / 3
+    want, rc = ad.solve_diff(wdt, coef, rhs)
+    assert rc == 0
+    sv = S().Solver(mech, fl, mg_levels=levels)
+    got = sv.diffusion_solve(wdt, coef, rhs).cpu().numpy()
+    assert np.all(relerr(got, want) < 1e-12)
+    st = sv.stats()
+    assert st["status_name"] == "OK", st
+
+
+def _run_both(mech, fl, dt, steps, scheme="CISDCQ", nu=2, sweeps=4, sensitivity=False, **kw):
+    ad = O.ADR(mech, fl)
+    phi0 = ad.state_from_YT(fl.Y, fl.T)
+    want, st_or = ad.step(phi0, dt, scheme, 2, sweeps, nu, n_steps=steps)
+    sens = None
+    if sensitivity:   # the oracle against itself under one-ulp input perturbations
+        sens = np.zeros(phi0.shape[0])
+        for r in range(2):
+            rng = np.random.default_rng(100 + r)
+            pert = phi0 * (1 + 1e-16 * rng.standard_normal(phi0.shape))
+            other, _ = ad.step(pert, dt, scheme, 2, sweeps, nu, n_steps=steps)
+            sens = np.maximum(sens, relerr(other, want))
+    sv = S().Solver(mech, fl, scheme=scheme, nu=nu, n_sweeps=sweeps, **kw)
+    state = torch.as_tensor(phi0, device="cuda").contiguous()
+    T = torch.as_tensor(fl.T, device="cuda").contiguous()
+    sv.step(state, dt, steps, T=T)
+    torch.cuda.synchronize()
+    st = sv.stats()
+    assert st["status_name"] == "OK", st
+    return state.cpu().numpy(), T.cpu().numpy(), want, ad, st, sens
+
+
+def tol_from(sens):
+    return np.maximum(TOL, 20.0 * sens)
+
+
+MILD = (8.0, 11.0)   # log10 A range of the well-conditioned chemistry
+
+
+@pytest.mark.parametrize("scheme,nu", [("CISDCQ", 2), ("CISDCQ", 1), ("CISDCQ", 3), ("MISDCQ", 1), ("MISDC", 1)])
+def test_step_parity_schemes_mild_chemistry(scheme, nu):
+    mech = I.make_mechanism(1801, 9, 21, logA_range=MILD)
+    fl = I.flame_1d(mech, 1801, nx=128, dx=1e-4)
+    got, T, want, ad, st, sens = _run_both(mech, fl, 1e-5, 5, scheme=scheme, nu=nu, sensitivity=True)
+    N = mech.n_species
+    err = relerr(got, want)
+    assert np.all(err <= tol_from(sens)), (err, sens)
+    if scheme == "CISDCQ" and nu == 2:   # well conditioned: the plain bound applies
+        assert np.all(err < TOL), err
+    assert relerr(T, ad.T_from_h(want[:N], want[N])) < max(TOL, 20 * sens.max())
+
+
+@pytest.mark.parametrize("case", ["2d_n21", "2d_n53", "3d_n21", "2d_ragged"])
+def test_step_parity_mild_multid(case):
+    if case == "2d_n21":
+        mech, fl = small_2d((1802, 21, 84), n=32, logA=MILD)
+    elif case == "2d_n53":
+        mech, fl = small_2d((1803, 53, 325), n=16, logA=MILD)
+    elif case == "3d_n21":
+        mech = I.make_mechanism(1802, 21, 84, logA_range=MILD)
+        fl = I.flame_3d(mech, 0, n=8, dx=1e-4, radius=3e-4, delta=2e-4)
+    else:
+        mech, fl = small_2d((1802, 21, 84), n=36, ny=22, logA=MILD)
+    got, T, want, ad, st, sens = _run_both(mech, fl, 5e-6, 2, sensitivity=True)
+    err = relerr(got, want)
+    assert np.all(err <= tol_from(sens)), (err, sens)
+
+
+@pytest.mark.parametrize("scheme,nu", [("CISDCQ", 2), ("MISDCQ", 1)])
+def test_step_parity_flame1d_full_config(scheme, nu):
+    """The 1D slab workload as specified (128 cells, N=9/R=21, 4 sweeps, 20 steps)."""
+    mech, fl, w = I.build_workload("flame1d_128_n9")
+    got, T, want, ad, st, sens = _run_both(mech, fl, w["dt"], w["steps"], scheme=scheme, nu=nu,
+                                           sensitivity=True)
+    err = relerr(got, want)
+    assert np.all(err <= tol_from(sens)), (err, sens)
+
+
+@pytest.mark.parametrize("case", ["2d_n21", "2d_n53", "3d_n21"])
+def test_step_parity_full_chemistry_multid(case):
+    if case == "2d_n21":
+        mech, fl = small_2d(n=32)
+    elif case == "2d_n53":
+        mech, fl = small_2d((1803, 53, 325), n=16)
+    else:
+        mech = I.make_mechanism(1802, 21, 84)
+        fl = I.flame_3d(mech, 0, n=8, dx=1e-4, radius=3e-4, delta=2e-4)
+    got, T, want, ad, st, sens = _run_both(mech, fl, 5e-6, 2, sensitivity=True)
+    err = relerr(got, want)
+    assert np.all(err <= tol_from(sens)), (err, sens)
+
+
+def test_stream_graph_variants_are_bitwise_identical():
+    mech, fl = small_2d(n=32)
+    ad = O.ADR(mech, fl)
+    phi0 = ad.state_from_YT(fl.Y, fl.T)
+    outs = []
+    for two, graph in ((True, True), (False, True), (True, False), (False, False)):
+        sv = S().Solver(mech, fl, two_streams=two, use_graph=graph)
+        st = torch.as_tensor(phi0, device="cuda").contiguous()
+        sv.step(st, 5e-6, 2)
+        torch.cuda.synchronize()
+        outs.append(st.cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_multigrid_levels_agree():
+    mech, fl = small_2d(n=32, logA=MILD)
+    a = _run_both(mech, fl, 5e-6, 1, mg_levels=1)[0]
+    b = _run_both(mech, fl, 5e-6, 1, mg_levels=3)[0]
+    assert np.all(relerr(a, b) < 1e-11)
+
+
+def test_host_step_matches_device_step(flame1d):
+    mech, fl, w = flame1d
+    ad = O.ADR(mech, fl)
+    phi0 = ad.state_from_YT(fl.Y, fl.T)
+    sv = S().Solver(mech, fl)
+    dev = torch.as_tensor(phi0, device="cuda").contiguous()
+    sv.step(dev, w["dt"], 2)
+    host = torch.as_tensor(phi0.copy()).pin_memory()
+    sv2 = S().Solver(mech, fl)
+    sv2.step_host(host, w["dt"], 2)
+    assert np.array_equal(dev.cpu().numpy(), host.numpy())
+
+
+def test_full_size_2d_sampled_cells_and_invariants():
+    """256^2 N=21 workload at full size: one step; per-cell reaction parity on sampled cells and
+    the invariants that hold at any size (sum Y = 1, conservation of h and elements)."""
+    mech, fl, w = I.build_workload("flame2d_256_n21")
+    sv = S().Solver(mech, fl)
+    phi0 = sv.state_from_YT(fl.Y, fl.T)
+    h0 = phi0[-1].double().sum().item()
+    N = mech.n_species
+    e0 = mech.elem @ (phi0[:N].cpu().numpy() / mech.W[:, None])
+    st = phi0.clone()
+    sv.step(st, w["dt"], 1)
+    torch.cuda.synchronize()
+    out = st.cpu().numpy()
+    assert sv.stats()["status_name"] == "OK"
+    np.testing.assert_allclose(out[:N].sum(axis=0), 1.0, atol=1e-14)
+    assert abs(out[N].sum() - h0) <= 1e-13 * np.abs(out[N]).sum()
+    e1 = mech.elem @ (out[:N] / mech.W[:, None])
+    np.testing.assert_allclose(e1.sum(axis=1), e0.sum(axis=1), rtol=1e-12)
+    # reaction solve at full size, sampled cells against the oracle one by one
+    ad = O.ADR(mech, fl)
+    rng = np.random.default_rng(8)
+    cells = fl.nx * fl.ny
+    Y = fl.Y * (1 + 0.01 * rng.standard_normal(fl.Y.shape))
+    hstar = sv.enthalpy(fl.Y, fl.T).cpu().numpy()
+    x0 = np.concatenate([fl.Y, fl.T[None, :]], axis=0)
+    x, FR, it = sv.reaction_solve(w["dt"] / 4, Y, hstar, x0)
+    x = x.cpu().numpy()
+    assert np.all(it.cpu().numpy() > 0)
+    for c in rng.choice(cells, 24, replace=False):
+        xc, ic = ad.reaction_newton(w["dt"] / 4, Y[:, c], hstar[c], x0[:, c])
+        assert np.max(np.abs(x[:N, c] - xc[:N])) <= TOL and abs(x[N, c] - xc[N]) <= TOL * xc[N]
