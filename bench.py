@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 METRIC = "MISDC cell-updates/s, learned+mixed vs plain FP64 sweep, at 1e-8 rel err"
 UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12      # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_newton launch on this workload,
+# from the ncu capture summarised in profiles/k_newton_flame2d_256_n21.md; None when the
+# kernel has changed since that capture.
+NEWTON_TRAFFIC_BYTES = 23.5e6
 
 
 def workload_config(name, w, mech, fl, scheme, precision):
@@ -253,7 +257,7 @@ def main():
     achieved = per_launch_flops / avg_launch_s / 1e12
     roofline = {"kernel": "k_newton (reaction Newton, warp per cell)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NEWTON_TRAFFIC_BYTES,
                 "peak_source": "FP64 nominal from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "exp_log_calls_per_launch": exps / max(newton_launches, 1),
                 "newton_ms_per_step": newton_ms / args.steps,
