@@ -191,6 +191,20 @@ misdc_status misdc_diffusion_solve(misdc_solver *s, double wdt, const double *co
 misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double *const *in,
                            const double *w, size_t n, void *stream);
 
+/* Reaction solve that allocates nothing. The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory during the call (host
+ * callbacks, memory-pool-restricted or real-time processes, plugins whose host
+ * owns every allocation). Same arguments, results and stream semantics as
+ * misdc_reaction_solve; its scratch lives in one static 4 MiB device array that
+ * every device loading the library keeps until the process exits. Needs
+ * 32 + n (N+1) doubles of it: a larger n returns MISDC_E_INVALID. Calls share
+ * the array, so calls that overlap on the GPU race; the first call on a device
+ * looks the array up and should come before any stream capture. Accumulates
+ * no solver statistics (the per-cell iteration codes are in iters). */
+misdc_status misdc_reaction_solve_noalloc(misdc_solver *s, double wdt, const double *b,
+                                          const double *hstar, double *x, double *FR, int *iters,
+                                          int n, void *stream);
+
 const char *misdc_last_error(void);
 
 #ifdef __cplusplus

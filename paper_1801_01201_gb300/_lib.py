@@ -54,7 +54,8 @@ class Stats(C.Structure):
 EXPORTS = ["misdc_default_opts", "misdc_create", "misdc_destroy", "misdc_step", "misdc_step_host",
            "misdc_get_stats", "misdc_lobatto", "misdc_enthalpy", "misdc_temperature",
            "misdc_production_rates", "misdc_reaction_solve", "misdc_operators",
-           "misdc_diffusion_solve", "misdc_lincomb", "misdc_last_error", "misdc_stage_times"]
+           "misdc_diffusion_solve", "misdc_lincomb", "misdc_last_error", "misdc_stage_times",
+           "misdc_reaction_solve_noalloc"]
 
 _lib = None
 
@@ -94,6 +95,7 @@ def load(build_if_missing: bool = True):
     L.misdc_diffusion_solve.argtypes = [vp, C.c_double, vp, vp, vp, vp]
     L.misdc_lincomb.argtypes = [C.c_int, C.c_int, C.POINTER(vp), C.POINTER(vp), dp, C.c_size_t, vp]
     L.misdc_stage_times.argtypes = [vp, dp, ip, dp, ip]
+    L.misdc_reaction_solve_noalloc.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp, C.c_int, vp]
     L.misdc_last_error.restype = C.c_char_p
     L.misdc_last_error.argtypes = []
     for name in EXPORTS:

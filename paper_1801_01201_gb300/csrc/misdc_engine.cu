@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -900,3 +901,82 @@ misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Reaction solve without any device allocation.
+//
+// Some callers cannot allocate device memory while they run: code executing
+// inside a host callback or a memory-pool-restricted process, plugins whose host
+// application owns every allocation, and real-time loops that forbid the
+// implicit synchronisation cudaMalloc/cudaFree can cause. For them this entry
+// point runs the same per-cell reaction Newton as misdc_reaction_solve, but
+// takes its scratch (per-call counters, theta and the species enthalpies of the
+// solution, which this call discards) from one statically sized device array
+// instead of cudaMallocAsync. It allocates nothing.
+//
+// Limits and rules: the array holds kNoAllocScratchDoubles doubles (4 MiB) on
+// every device that loads the library, for the life of the process; a call
+// needs 32 + n (N + 1) of them and larger n is rejected with MISDC_E_INVALID.
+// All calls share the array: calls that overlap on the GPU (different streams,
+// or several solvers at once) race on it. The first call on a device looks the
+// array's device address up (cudaGetSymbolAddress); make that first call before
+// any stream capture. Each call clears its counters before the kernel runs.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 19;   // 4 MiB
+constexpr size_t kNoAllocStatsDoubles = 32;                   // 256 bytes for DevStats
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[64] = {};   // device address of the array, per device ordinal
+
+// Device address of the scratch array on the current device (looked up once).
+misdc_status noalloc_scratch(double **out) {
+  static_assert(sizeof(DevStats) <= kNoAllocStatsDoubles * sizeof(double), "stats block");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(MISDC_E_INVALID, "device ordinal above 63");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(MISDC_E_CUDA, std::string("cudaGetSymbolAddress(no-allocation scratch): ") +
+                                    cudaGetErrorString(e));
+    g_noalloc_addr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return MISDC_OK;
+}
+
+}  // namespace
+
+extern "C" misdc_status misdc_reaction_solve_noalloc(misdc_solver *s, double wdt, const double *b,
+                                                     const double *hstar, double *x, double *FR,
+                                                     int *iters, int n, void *stream) {
+  if (!s || !b || !hstar || !x || n < 0) return fail(MISDC_E_INVALID, "bad argument");
+  if (!(wdt >= 0.0)) return fail(MISDC_E_INVALID, "wdt must be >= 0");
+  const size_t N = s->N;
+  const size_t need = kNoAllocStatsDoubles + (size_t)n * (N + 1);
+  if (need > kNoAllocScratchDoubles)
+    return fail(MISDC_E_INVALID, "n = " + std::to_string(n) + " needs " + std::to_string(need) +
+                                     " scratch doubles; the no-allocation scratch holds " +
+                                     std::to_string(kNoAllocScratchDoubles) + " (at most " +
+                                     std::to_string((kNoAllocScratchDoubles - kNoAllocStatsDoubles) / (N + 1)) +
+                                     " cells for this mechanism)");
+  if (n == 0) return MISDC_OK;
+  double *base = nullptr;
+  misdc_status st = noalloc_scratch(&base);
+  if (st != MISDC_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  DevStats *stats = reinterpret_cast<DevStats *>(base);
+  double *theta = base + kNoAllocStatsDoubles;
+  double *hsp = theta + n;
+  CK(cudaMemsetAsync(stats, 0, sizeof(DevStats), cs));
+  launch_newton(s->m, n, n, wdt, s->o.newton_rtol, s->o.newton_maxit, b, hstar, x, x + N * n, x,
+                x + N * n, FR, hsp, theta, iters, stats, cs);
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
