@@ -23,11 +23,6 @@ __device__ __forceinline__ void species_thermo(const DevMech &m, int i, double T
   cpR = c[0] + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4])));
 }
 
-template <int RPL>
-__device__ __forceinline__ double pick(const double (&a)[RPL], int q) {
-  return (RPL == 1 || q == 0) ? a[0] : a[RPL - 1];
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -186,206 +181,232 @@ __global__ void __launch_bounds__(128) k_rates(DevMech m, int n, int cs,
 }
 
 // ---------------------------------------------------------------------------
-// Reaction Newton: one warp per cell, rows of the augmented (N+1)x(N+2)
-// Jacobian in shared memory, lane i owns rows i, i+32, ...; partial pivoting
-// by a warp argmax; dense LU by rank-1 row updates.
-// Unknowns x = (Y_1..Y_N, T); residual r_i = Y_i - wdt wdot_i/rho - b_i,
-// r_T = sum_i Y_i h_i(T) - h*.
+// Reaction Newton, lane-balanced form: one warp per cell; the iterate, the
+// augmented Jacobian and the per-reaction quantities live in shared memory and
+// every phase spreads its work over all 32 lanes:
+//  * thermo over species, rates and slot derivatives over reactions;
+//  * Jacobian and residual assembly from a host-built list of contributions
+//    (target entry, source value, weight) sorted by target and cut into 32
+//    segments of whole targets, so each lane owns its targets (deterministic,
+//    no atomics) and the lanes carry equal work;
+//  * partial pivoting by a warp argmax on the integer bit patterns of |J_ik|;
+//    elimination of the trailing block spread element-wise over the lanes.
+// The temperature row is scaled by 1/(c_p T) (the solution is unchanged).
 // ---------------------------------------------------------------------------
-template <int RPL>
-__global__ void __launch_bounds__(128) k_newton(DevMech m, int n, int cs, double wdt, double rtol,
-                                                int maxit, int ld, const double *__restrict__ b,
-                                                const double *__restrict__ hstar,
-                                                const double *Yg, const double *Tg,
-                                                double *Yout, double *Tout,
-                                                double *__restrict__ FR,
-                                                double *__restrict__ hsp,
-                                                double *__restrict__ theta,
-                                                int *__restrict__ iters, DevStats *st) {
+struct NW {
+  double *J, *src, *xs, *bs, *c, *g, *hRT, *hm, *cpm, *piv, *dx;
+};
+
+__device__ __forceinline__ NW carve2(double *p, int N, int R, int ld) {
+  const int nn = N + 1;
+  NW w;
+  w.J = p; p += (size_t)nn * ld;
+  w.src = p; p += 8 * R;
+  w.xs = p; p += nn;
+  w.bs = p; p += N;
+  w.c = p; p += N;
+  w.g = p; p += N;
+  w.hRT = p; p += N;
+  w.hm = p; p += N;
+  w.cpm = p; p += N;
+  w.piv = p; p += nn;
+  w.dx = p;
+  return w;
+}
+
+__global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, double wdt, double rtol,
+                                                 int maxit, int ld, const double *__restrict__ b,
+                                                 const double *__restrict__ hstar,
+                                                 const double *Yg, const double *Tg, double *Yout,
+                                                 double *Tout, double *__restrict__ FR,
+                                                 double *__restrict__ hsp,
+                                                 double *__restrict__ theta,
+                                                 int *__restrict__ iters, DevStats *st) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int N = m.N, R = m.R, nn = N + 1;
-  const size_t per_warp = (size_t)nn * ld + 5 * N + 4 * R;
-  double *J = smem + (size_t)wib * per_warp;
-  WarpChem w = carve(J + (size_t)nn * ld, N, R);
-  const double invrho = 1.0 / m.rho, wr = wdt * invrho;
-  const int qT = N >> 5, lT = N & 31;   // owner of the temperature row
+  const int N = m.N, R = m.R, nn = N + 1, na = nn + 1;   // na: columns of the augmented matrix
+  const size_t per_warp = (size_t)nn * ld + 8 * R + 6 * N + 3 * nn;
+  NW w = carve2(smem + (size_t)wib * per_warp, N, R, ld);
+  double *J = w.J;
+  const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
   unsigned long long my_solves = 0, my_iters = 0, my_fail = 0;
   int my_max = 0;
   unsigned bits = 0;
 
   for (int cell = blockIdx.x * wpb + wib; cell < n; cell += gridDim.x * wpb) {
-    double x[RPL], bb[RPL];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      int i = lane + 32 * q;
-      x[q] = (i < N) ? Yg[(size_t)i * cs + cell] : (i == N ? Tg[cell] : 0.0);
-      bb[q] = (i < N) ? b[(size_t)i * cs + cell] : 0.0;
+    for (int i = lane; i < N; i += 32) {
+      w.xs[i] = Yg[(size_t)i * cs + cell];
+      w.bs[i] = b[(size_t)i * cs + cell];
     }
+    if (lane == 0) w.xs[N] = Tg[cell];
     const double hst = hstar[cell];
-    double T = __shfl_sync(0xffffffffu, pick<RPL>(x, qT), lT);
+    __syncwarp();
+    double T = w.xs[N];
     double dprev = INFINITY;
     int it, code = 0;
     for (it = 1; it <= maxit; ++it) {
-      // concentrations, thermo and rates at the current iterate
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) {
-        int i = lane + 32 * q;
-        if (i < N) w.c[i] = m.rho * x[q] * m.invW[i];
-      }
-      __syncwarp();
-      eval_chem(m, w, lane, T, true);
-      // species rows of the augmented Jacobian
+      // ---- thermo and concentrations (species over lanes)
+      const double lnT = log(T), invT = 1.0 / T;
       double sh = 0.0, scp = 0.0;
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) {
-        int i = lane + 32 * q;
-        if (i < N) {
-          double *row = J + (size_t)i * ld;
-          for (int j = 0; j <= nn; ++j) row[j] = 0.0;
-          row[i] = 1.0;
-          double wd = 0.0, jT = 0.0;
-          for (int p = m.sp_ptr[i]; p < m.sp_ptr[i + 1]; ++p) {
-            const int r = m.sp_rx[p];
-            const double co = m.sp_coef[p];
-            wd = fma(co, w.q[r], wd);
-            const double a = -wdt * co;
-            const signed char *fs = m.fwd + kMaxSlots * r, *rs = m.rev + kMaxSlots * r;
-#pragma unroll
-            for (int s0 = 0; s0 < kMaxSlots; ++s0) {
-              int sp = fs[s0];
-              if (sp >= 0) {
-                double prod = w.kf[r];
-#pragma unroll
-                for (int s1 = 0; s1 < kMaxSlots; ++s1)
-                  if (s1 != s0 && fs[s1] >= 0) prod *= w.c[fs[s1]];
-                row[sp] = fma(a * m.invW[sp], prod, row[sp]);
-              }
-              sp = rs[s0];
-              if (sp >= 0) {
-                double prod = w.kr[r];
-#pragma unroll
-                for (int s1 = 0; s1 < kMaxSlots; ++s1)
-                  if (s1 != s0 && rs[s1] >= 0) prod *= w.c[rs[s1]];
-                row[sp] = fma(-a * m.invW[sp], prod, row[sp]);
-              }
-            }
-            jT = fma(co, w.dqdT[r], jT);
-          }
-          row[N] -= wr * jT;
-          row[nn] = -(x[q] - wr * wd - bb[q]);
-          sh = fma(x[q], w.hm[i], sh);
-          scp = fma(x[q], w.cpm[i], scp);
-        }
+      for (int i = lane; i < N; i += 32) {
+        double hRT, gRT, cpR;
+        species_thermo(m, i, T, lnT, invT, hRT, gRT, cpR);
+        const double y = w.xs[i];
+        w.c[i] = m.rho * y * m.invW[i];
+        w.g[i] = gRT;
+        w.hRT[i] = hRT;
+        const double hm = kRu * m.invW[i] * T * hRT, cpm = kRu * m.invW[i] * cpR;
+        w.hm[i] = hm;
+        sh = fma(y, hm, sh);
+        scp = fma(y, cpm, scp);
       }
       sh = warp_sum(sh);
       scp = warp_sum(scp);
-      // temperature row: d/dY_j = h_j, d/dT = cp
-      double *rowT = J + (size_t)N * ld;
-      for (int j = lane; j < N; j += 32) rowT[j] = w.hm[j];
-      if (lane == 0) { rowT[N] = scp; rowT[nn] = -(sh - hst); }
       __syncwarp();
-
-      // LU with partial pivoting on the augmented matrix
+      // ---- rates of progress, dq/dT and slot derivatives (reactions over lanes)
+      for (int r = lane; r < R; r += 32) {
+        const signed char *fs = m.fwd + kMaxSlots * r, *rs = m.rev + kMaxSlots * r;
+        double cf[kMaxSlots], cr[kMaxSlots];
+        double dg = 0.0, dh = 0.0;
+#pragma unroll
+        for (int p = 0; p < kMaxSlots; ++p) {
+          const int sf = fs[p], sr = rs[p];
+          cf[p] = 1.0;
+          cr[p] = 1.0;
+          if (sf >= 0) { dg -= w.g[sf]; dh -= w.hRT[sf]; cf[p] = w.c[sf]; }
+          if (sr >= 0) { dg += w.g[sr]; dh += w.hRT[sr]; cr[p] = w.c[sr]; }
+        }
+        const double beta = m.beta[r], TA = m.TA[r], dn = m.dn[r];
+        const double lnkf = m.lnA[r] + beta * lnT - TA * invT;
+        const double lnKc = -dg + dn * (m.ln_p_over_R - lnT);
+        const double kf = exp(lnkf);
+        const double kr = exp(lnkf - lnKc);
+        const double Ff = cf[0] * cf[1] * cf[2], Fr = cr[0] * cr[1] * cr[2];
+        const double dlnkf = (beta + TA * invT) * invT;
+        const double dlnKc = (dh - dn) * invT;
+        w.src[r] = kf * Ff - kr * Fr;
+        w.src[R + r] = kf * Ff * dlnkf - kr * Fr * (dlnkf - dlnKc);
+        double *sd = w.src + 2 * R + 6 * r;
+        sd[0] = kf * (cf[1] * cf[2]);
+        sd[1] = kf * (cf[0] * cf[2]);
+        sd[2] = kf * (cf[0] * cf[1]);
+        sd[3] = -kr * (cr[1] * cr[2]);
+        sd[4] = -kr * (cr[0] * cr[2]);
+        sd[5] = -kr * (cr[0] * cr[1]);
+      }
+      // ---- augmented matrix: identity species rows with b - Y, scaled T row
+      for (int i = 0; i < N; ++i)
+        for (int j = lane; j < na; j += 32)
+          J[(size_t)i * ld + j] = (j == i) ? 1.0 : (j == nn ? w.bs[i] - w.xs[i] : 0.0);
+      const double sT = 1.0 / (scp * T);
+      for (int j = lane; j < N; j += 32) J[(size_t)N * ld + j] = w.hm[j] * sT;
+      if (lane == 0) {
+        J[(size_t)N * ld + N] = scp * sT;
+        J[(size_t)N * ld + nn] = -(sh - hst) * sT;
+      }
+      __syncwarp();
+      // ---- Jacobian and residual contributions: J[t] -= wdt * sum w * src
+      {
+        int cur = -1;
+        double acc = 0.0;
+        for (int p = seg0; p < seg1; ++p) {
+          const int pk = m.jc_pack[p];
+          const int t = pk >> 16;
+          if (t != cur) {
+            if (cur >= 0) J[cur] = fma(-wdt, acc, J[cur]);
+            cur = t;
+            acc = 0.0;
+          }
+          acc = fma(m.jc_w[p], w.src[pk & 0xffff], acc);
+        }
+        if (cur >= 0) J[cur] = fma(-wdt, acc, J[cur]);
+      }
+      __syncwarp();
+      // ---- LU with partial pivoting
       bool singular = false;
       for (int k = 0; k < nn; ++k) {
-        double best = -1.0;
+        unsigned long long best = 0ull;
         int bi = nn;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          int i = lane + 32 * q;
-          if (i >= k && i < nn) {
-            double v = fabs(J[(size_t)i * ld + k]);
-            if (v > best) { best = v; bi = i; }
-          }
+        for (int i = k + lane; i < nn; i += 32) {
+          const unsigned long long v =
+              (unsigned long long)__double_as_longlong(J[(size_t)i * ld + k]) & 0x7fffffffffffffffull;
+          if (v > best) { best = v; bi = i; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          double ob = __shfl_xor_sync(0xffffffffu, best, o);
-          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (!(best > 0.0) || !isfinite(best)) { singular = true; break; }
+        if (best == 0ull || best >= 0x7ff0000000000000ull) { singular = true; break; }
         if (bi != k) {
-          for (int j = lane; j <= nn; j += 32) {
-            double t = J[(size_t)k * ld + j];
+          for (int j = lane; j < na; j += 32) {
+            const double t = J[(size_t)k * ld + j];
             J[(size_t)k * ld + j] = J[(size_t)bi * ld + j];
             J[(size_t)bi * ld + j] = t;
           }
+          __syncwarp();
         }
+        const double pinv = 1.0 / J[(size_t)k * ld + k];
+        if (lane == 0) w.piv[k] = pinv;
+        for (int i = k + 1 + lane; i < nn; i += 32) J[(size_t)i * ld + k] *= pinv;
         __syncwarp();
-        const double *rk = J + (size_t)k * ld;
-        const double pinv = 1.0 / rk[k];
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          int i = lane + 32 * q;
-          if (i > k && i < nn) {
-            double *ri = J + (size_t)i * ld;
-            const double l = ri[k] * pinv;
-            for (int j = k + 1; j <= nn; ++j) ri[j] = fma(-l, rk[j], ri[j]);
+        const int rows = nn - 1 - k, cols = na - 1 - k;   // trailing block (k, nn) x (k, na)
+        const int total = rows * cols;
+        if (total > 0) {
+          int i = lane / cols, j = lane - i * cols;
+          const int qs = 32 / cols, rsd = 32 - qs * cols;
+          for (int e = lane; e < total; e += 32) {
+            const size_t ri = (size_t)(k + 1 + i) * ld;
+            J[ri + k + 1 + j] = fma(-J[ri + k], J[(size_t)k * ld + k + 1 + j], J[ri + k + 1 + j]);
+            i += qs;
+            j += rsd;
+            if (j >= cols) { j -= cols; ++i; }
           }
         }
         __syncwarp();
       }
       if (singular) { code = -2; break; }
-      double dx[RPL];
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) dx[q] = 0.0;
       for (int k = nn - 1; k >= 0; --k) {
-        const double xk = J[(size_t)k * ld + nn] / J[(size_t)k * ld + k];
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          int i = lane + 32 * q;
-          if (i < k) J[(size_t)i * ld + nn] = fma(-J[(size_t)i * ld + k], xk, J[(size_t)i * ld + nn]);
-          if (i == k) dx[q] = xk;
-        }
+        const double xk = J[(size_t)k * ld + nn] * w.piv[k];
+        if (lane == 0) w.dx[k] = xk;
+        for (int i = lane; i < k; i += 32)
+          J[(size_t)i * ld + nn] = fma(-J[(size_t)i * ld + k], xk, J[(size_t)i * ld + nn]);
         __syncwarp();
       }
-      // update and convergence on d = max(max|dY|, |dT|/T): d <= rtol, or d <= 1e-8
-      // no longer halving (the round-off floor of very stiff cells)
-      bool fin = true;
+      // ---- update and convergence on d = max(max|dY|, |dT|/T)
       double dmax = 0.0;
-      const double dT = __shfl_sync(0xffffffffu, pick<RPL>(dx, qT), lT);
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) {
-        int i = lane + 32 * q;
-        if (i < nn) {
-          x[q] += dx[q];
-          if (!isfinite(x[q])) fin = false;
-          if (i < N) dmax = fmax(dmax, fabs(dx[q]));
-        }
+      bool fin = true;
+      for (int i = lane; i < nn; i += 32) {
+        const double v = w.xs[i] + w.dx[i];
+        w.xs[i] = v;
+        if (!isfinite(v)) fin = false;
+        if (i < N) dmax = fmax(dmax, fabs(w.dx[i]));
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-      T = __shfl_sync(0xffffffffu, pick<RPL>(x, qT), lT);
       fin = __all_sync(0xffffffffu, fin);
+      __syncwarp();
+      T = w.xs[N];
       if (!fin || !(T > 0.0)) { code = -3; break; }
-      const double d = fmax(dmax, fabs(dT) / T);
+      const double d = fmax(dmax, fabs(w.dx[N]) / T);
       if (!isfinite(d)) { code = -3; break; }
       if (d <= rtol || (d <= 1e-8 && d >= 0.5 * dprev)) break;
       dprev = d;
     }
     if (code == 0 && it > maxit) code = -1;
-    // species enthalpies and theta at the solution; the reaction term of the new
-    // state is the one the implicit equation assigns to it, (Y - b)/wdt
+    // species enthalpies and theta at the solution; reaction term (Y - b)/wdt
     const double Tf = (code == -3) ? 1000.0 : T;
+    const double invw = (wdt > 0.0) ? 1.0 / wdt : 0.0;
     {
       const double lnT = log(Tf), invT = 1.0 / Tf;
       for (int i = lane; i < N; i += 32) {
         double hRT, gRT, cpR;
         species_thermo(m, i, Tf, lnT, invT, hRT, gRT, cpR);
-        w.hm[i] = kRu * m.invW[i] * Tf * hRT;
-      }
-    }
-    __syncwarp();
-    const double invw = (wdt > 0.0) ? 1.0 / wdt : 0.0;
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      int i = lane + 32 * q;
-      if (i < N) {
-        Yout[(size_t)i * cs + cell] = x[q];
-        if (FR) FR[(size_t)i * cs + cell] = (x[q] - bb[q]) * invw;
-        if (hsp) hsp[(size_t)i * cs + cell] = w.hm[i];
+        const double y = w.xs[i];
+        Yout[(size_t)i * cs + cell] = y;
+        if (FR) FR[(size_t)i * cs + cell] = (y - w.bs[i]) * invw;
+        if (hsp) hsp[(size_t)i * cs + cell] = kRu * m.invW[i] * Tf * hRT;
       }
     }
     if (lane == 0) {
@@ -427,9 +448,8 @@ int sm_count() {
 
 static size_t newton_smem(const DevMech &m, int &ld, int &wpb) {
   const int nn = m.N + 1;
-  ld = nn + 1;
-  if ((ld & 1) == 0) ld += 1;   // odd leading dimension spreads rows over banks
-  const size_t per_warp = (size_t)nn * ld + 5 * m.N + 4 * m.R;
+  ld = newton_ld(m.N);
+  const size_t per_warp = (size_t)nn * ld + 8 * m.R + 6 * m.N + 3 * nn;
   wpb = (per_warp * 8 * 4 <= 200 * 1024) ? 4 : 2;
   return (size_t)wpb * per_warp * sizeof(double);
 }
@@ -437,8 +457,7 @@ static size_t newton_smem(const DevMech &m, int &ld, int &wpb) {
 void prepare_chem_kernels(const DevMech &m) {
   int ld, wpb;
   const size_t sm = newton_smem(m, ld, wpb);
-  cudaFuncSetAttribute(k_newton<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(k_newton<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_newton2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const size_t smr = (size_t)4 * (5 * m.N + 4 * m.R) * sizeof(double);
   cudaFuncSetAttribute(k_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
 }
@@ -471,19 +490,13 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
                    DevStats *st, cudaStream_t s) {
   if (n <= 0) return;
-  const int nn = m.N + 1;
   int ld, wpb;
   const size_t sm = newton_smem(m, ld, wpb);
   int grid = (n + wpb - 1) / wpb;
   const int cap = sm_count() * (wpb == 4 ? 8 : 12);
   grid = grid < cap ? grid : cap;
-  if (nn <= 32) {
-    k_newton<1><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
-                                           FR, hsp, theta, iters, st);
-  } else {
-    k_newton<2><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
-                                           FR, hsp, theta, iters, st);
-  }
+  k_newton2<<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T, FR,
+                                       hsp, theta, iters, st);
 }
 
 }  // namespace misdc

@@ -200,6 +200,7 @@ misdc_status alloc_node(misdc_solver *s, NodeBuf &b) {
   CK(s->alloc(&b.FD, F * cs));
   CK(s->alloc(&b.FR, F * cs));
   CK(cudaMemset(b.FR, 0, F * cs * sizeof(double)));   // the enthalpy row of F_R stays zero
+  CK(cudaMemset(b.T, 0, cs * sizeof(double)));         // "no guess" until a step writes it
   return MISDC_OK;
 }
 
@@ -298,7 +299,9 @@ void prepare_node0(misdc_solver *s, const double *state, const double *Tin, cuda
   const size_t cs = s->cs, F = s->N + 1;
   NodeBuf &b = s->node0;
   cudaMemcpyAsync(b.phi, state, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  launch_temperature(s->m, s->cs, s->cs, b.phi, b.phi + (size_t)s->N * cs, Tin, b.T, b.theta,
+  // first guess of the temperature: the caller's T, else the last step's final T
+  const double *guess = Tin ? Tin : s->K[s->tab.M].T;
+  launch_temperature(s->m, s->cs, s->cs, b.phi, b.phi + (size_t)s->N * cs, guess, b.T, b.theta,
                      b.hsp, s->st, st);
   node_operators(s, b, s->thfD, st);
   launch_rates(s->m, s->cs, s->cs, b.phi, b.T, b.FR, st);
@@ -571,6 +574,42 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     }
     sp_ptr[i + 1] = (int)sp_rx.size();
   }
+  // Newton assembly list (see DevMech::jc_pack): for every species row i and every
+  // reaction r it takes part in, with c = W_i nu_ri: the residual term (-c/rho, q_r),
+  // the temperature column (c/rho, dq_r/dT) and one entry per molecule slot s of r,
+  // (c/W_s, slot derivative of q_r). Sorted by target, cut into 32 lane segments.
+  const int ldn = newton_ld(N), nnn = N + 1;
+  struct Contrib { int t, s; double w; };
+  std::vector<Contrib> cl;
+  for (int i = 0; i < N; ++i)
+    for (int r = 0; r < R; ++r) {
+      const int nu = md->nu_r[(size_t)r * N + i] - md->nu_f[(size_t)r * N + i];
+      if (!nu) continue;
+      const double c = md->W[i] * nu;
+      cl.push_back({i * ldn + nnn, r, -c / op->rho});
+      cl.push_back({i * ldn + N, R + r, c / op->rho});
+      for (int p = 0; p < kMaxSlots; ++p) {
+        const int sf = fwd[kMaxSlots * r + p], sr = rev[kMaxSlots * r + p];
+        if (sf >= 0) cl.push_back({i * ldn + sf, 2 * R + 6 * r + p, c / md->W[sf]});
+        if (sr >= 0) cl.push_back({i * ldn + sr, 2 * R + 6 * r + 3 + p, c / md->W[sr]});
+      }
+    }
+  std::stable_sort(cl.begin(), cl.end(), [](const Contrib &a, const Contrib &b) {
+    return a.t != b.t ? a.t < b.t : a.s < b.s;
+  });
+  std::vector<int> jc_pack(cl.size()), jc_seg(33, (int)cl.size());
+  std::vector<double> jc_w(cl.size());
+  for (size_t k = 0; k < cl.size(); ++k) {
+    jc_pack[k] = (cl[k].t << 16) | cl[k].s;
+    jc_w[k] = cl[k].w;
+  }
+  jc_seg[0] = 0;
+  {
+    int lanes = 1;
+    const double per = (double)cl.size() / 32.0;
+    for (size_t k = 1; k < cl.size() && lanes < 32; ++k)
+      if (cl[k].t != cl[k - 1].t && (double)k >= per * lanes) jc_seg[lanes++] = (int)k;
+  }
   auto up = [&](auto &vec, auto **dst) -> cudaError_t {
     using T = typename std::remove_reference<decltype(vec)>::type::value_type;
     cudaError_t e = s->alloc((T **)dst, vec.size());
@@ -578,12 +617,13 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     return cudaMemcpy((void *)*dst, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice);
   };
   std::vector<double> D0v(md->D0, md->D0 + N);
-  double *p_invW, *p_hc, *p_sc, *p_cpc, *p_D0, *p_lnA, *p_beta, *p_TA, *p_dn, *p_spc;
+  double *p_invW, *p_hc, *p_sc, *p_cpc, *p_D0, *p_lnA, *p_beta, *p_TA, *p_dn, *p_spc, *p_jcw;
   signed char *p_fwd, *p_rev;
-  int *p_spp, *p_spr;
+  int *p_spp, *p_spr, *p_jcp, *p_jcs;
   if (up(invW, &p_invW) || up(hc, &p_hc) || up(sc, &p_sc) || up(cpc, &p_cpc) || up(D0v, &p_D0) ||
       up(lnA, &p_lnA) || up(beta, &p_beta) || up(TA, &p_TA) || up(dn, &p_dn) || up(fwd, &p_fwd) ||
-      up(rev, &p_rev) || up(sp_ptr, &p_spp) || up(sp_rx, &p_spr) || up(sp_coef, &p_spc))
+      up(rev, &p_rev) || up(sp_ptr, &p_spp) || up(sp_rx, &p_spr) || up(sp_coef, &p_spc) ||
+      up(jc_pack, &p_jcp) || up(jc_w, &p_jcw) || up(jc_seg, &p_jcs))
     return bail(fail(MISDC_E_OOM, "mechanism upload failed"));
   DevMech &m = s->m;
   m.N = N; m.R = R; m.rho = op->rho; m.T_ref = md->T_ref; m.theta_exp = md->theta_exp;
@@ -592,6 +632,7 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   m.lnA = p_lnA; m.beta = p_beta; m.TA = p_TA; m.dn = p_dn; m.fwd = p_fwd; m.rev = p_rev;
   m.sp_ptr = p_spp; m.sp_rx = p_spr; m.sp_coef = p_spc;
   m.D0_host = s->D0h.data();
+  m.jc_pack = p_jcp; m.jc_w = p_jcw; m.jc_seg = p_jcs;
   prepare_chem_kernels(m);
 
   // ---- buffers ----

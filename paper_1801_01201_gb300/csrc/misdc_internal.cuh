@@ -45,7 +45,18 @@ struct DevMech {
   const int *sp_rx;        // [nnz]
   const double *sp_coef;   // [nnz]  W_i * nu_ri
   const double *D0_host;   // [N] host copy (launch parameters)
+  // reaction-Newton assembly list: entry p adds -wdt * jc_w[p] * src[jc_pack[p] & 0xffff] to
+  // J[jc_pack[p] >> 16]; entries sorted by target and cut into 32 lane segments jc_seg[0..32]
+  const int *jc_pack;
+  const double *jc_w;
+  const int *jc_seg;
 };
+
+// leading dimension of the augmented (N+1) x (N+2) Newton matrix in shared memory (odd)
+__host__ __device__ inline int newton_ld(int N) {
+  int ld = N + 2;
+  return (ld & 1) ? ld : ld + 1;
+}
 
 struct DevGrid {
   int dim, nx, ny, nz, cells;
