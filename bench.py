@@ -122,6 +122,35 @@ def cpu_oracle_rate(name, cells_side, steps=1):
     return fl.cells * steps / el, el, fl.cells
 
 
+def time_variant(Solver, mech, fl, w, args, dev, state0, flush, stream, precision):
+    """Cell-updates/s of the same workload with another precision (same timing rules)."""
+    import torch
+    sv = Solver(mech, fl, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"], scheme=args.scheme,
+                precision=precision, profile=True, device=dev)
+    state = state0.clone()
+    for _ in range(args.warmup):
+        sv.step(state, w["dt"], 1)
+    torch.cuda.synchronize()
+    sv.stats(reset=True)
+    ms, nms = [], 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sv.step(state, w["dt"], 1, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        nms += sv.stage_times()["newton_ms"]
+    st = sv.stats(reset=True)
+    cells = fl.nx * fl.ny * fl.nz
+    return {"precision": precision, "value": cells * args.steps / (sum(ms) / 1e3), "unit": UNIT,
+            "ms_per_step": sum(ms) / args.steps, "newton_ms_per_step": nms / args.steps,
+            "newton_iters_per_solve": st["newton_iters"] / max(st["newton_solves"], 1),
+            "status": st["status_name"]}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the plain serial CPU oracle on this host, bounded samples."""
     if rank != 0:
@@ -160,6 +189,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="flame2d_256_n21")
     ap.add_argument("--scheme", default="CISDCQ")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--compare-mixed", type=int, default=1,
+                    help="also time the mixed-precision sweep (reported as an extra field)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-side", type=int, default=64)
     ap.add_argument("--ref-side", type=int, default=32)
@@ -186,7 +218,7 @@ def main():
     name = args.workload
     mech, fl, w = I.build_workload(name)
     sv = Solver(mech, fl, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"], scheme=args.scheme,
-                profile=True, device=dev)
+                precision=args.precision, profile=True, device=dev)
     cells = fl.nx * fl.ny * fl.nz
     state0 = sv.state_from_YT(fl.Y, fl.T)
     state = state0.clone()
@@ -274,12 +306,14 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(name, w, mech, fl, args.scheme, "fp64"),
+            "config": workload_config(name, w, mech, fl, args.scheme, args.precision),
             "clocks": clk, "gpu_launches": st["kernel_launches"],
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_bytes,
                     "d2h_bytes_per_step": e2e_bytes},
             "roofline": roofline, "cpu_baseline": cpu,
             "status": st["status_name"], "newton_fail": st["newton_fail"]}
+    if args.compare_mixed and args.precision == "fp64":
+        line["mixed"] = time_variant(Solver, mech, fl, w, args, dev, state0, flush, stream, "mixed")
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -119,7 +119,10 @@ __device__ __forceinline__ WarpChem carve(double *p, int N, int R) {
 // thermo of every species at T, then every reaction's rate of progress (and
 // what the Jacobian needs); concentrations w.c must be set.
 __device__ void eval_chem(const DevMech &m, const WarpChem &w, int lane, double T, bool jac) {
-  const double lnT = log(T), invT = 1.0 / T;
+  double lnT = 0.0, invT = 0.0;   // warp-uniform: computed on one lane, broadcast
+  if (lane == 0) { lnT = log(T); invT = 1.0 / T; }
+  lnT = __shfl_sync(0xffffffffu, lnT, 0);
+  invT = __shfl_sync(0xffffffffu, invT, 0);
   for (int i = lane; i < m.N; i += 32) {
     double hRT, gRT, cpR;
     species_thermo(m, i, T, lnT, invT, hRT, gRT, cpR);
@@ -195,9 +198,21 @@ __global__ void __launch_bounds__(128) k_rates(DevMech m, int n, int cs,
 // ---------------------------------------------------------------------------
 struct NW {
   double *J, *src, *xs, *bs, *c, *g, *hRT, *hm, *cpm, *piv, *dx;
+  // mixed precision: FP32 factor, FP64 right-hand side and residual
+  float *Jf, *zf, *pivf;
+  int *sw;
+  double *r64, *res;
 };
 
-__device__ __forceinline__ NW carve2(double *p, int N, int R, int ld) {
+// doubles of shared memory one warp needs
+__host__ __device__ inline size_t newton_warp_doubles(int N, int R, int ld, bool mixed) {
+  const size_t nn = N + 1;
+  size_t d = nn * ld + 8 * (size_t)R + 6 * (size_t)N + 3 * nn;
+  if (mixed) d += (nn * ld + 1) / 2 + 2 * nn + (3 * nn + 1) / 2 + 1;
+  return d;
+}
+
+__device__ __forceinline__ NW carve2(double *p, int N, int R, int ld, bool mixed) {
   const int nn = N + 1;
   NW w;
   w.J = p; p += (size_t)nn * ld;
@@ -210,10 +225,22 @@ __device__ __forceinline__ NW carve2(double *p, int N, int R, int ld) {
   w.hm = p; p += N;
   w.cpm = p; p += N;
   w.piv = p; p += nn;
-  w.dx = p;
+  w.dx = p; p += nn;
+  if (mixed) {
+    w.r64 = p; p += nn;
+    w.res = p; p += nn;
+    w.Jf = reinterpret_cast<float *>(p); p += ((size_t)nn * ld + 1) / 2;
+    float *f = reinterpret_cast<float *>(p);
+    w.zf = f; w.pivf = f + nn;
+    w.sw = reinterpret_cast<int *>(f + 2 * nn);
+  } else {
+    w.r64 = w.res = nullptr; w.Jf = w.zf = w.pivf = nullptr; w.sw = nullptr;
+  }
   return w;
 }
 
+
+template <bool MIXED>
 __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, double wdt, double rtol,
                                                  int maxit, int ld, const double *__restrict__ b,
                                                  const double *__restrict__ hstar,
@@ -225,8 +252,8 @@ __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, doubl
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int N = m.N, R = m.R, nn = N + 1, na = nn + 1;   // na: columns of the augmented matrix
-  const size_t per_warp = (size_t)nn * ld + 8 * R + 6 * N + 3 * nn;
-  NW w = carve2(smem + (size_t)wib * per_warp, N, R, ld);
+  const size_t per_warp = newton_warp_doubles(N, R, ld, MIXED);
+  NW w = carve2(smem + (size_t)wib * per_warp, N, R, ld, MIXED);
   double *J = w.J;
   const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
   unsigned long long my_solves = 0, my_iters = 0, my_fail = 0;
@@ -245,8 +272,13 @@ __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, doubl
     double dprev = INFINITY;
     int it, code = 0;
     for (it = 1; it <= maxit; ++it) {
-      // ---- thermo and concentrations (species over lanes)
-      const double lnT = log(T), invT = 1.0 / T;
+      // ---- thermo and concentrations (species over lanes). FP64 work is paid per
+      // active lane on this part, so warp-uniform scalars are computed by lane 0
+      // and broadcast.
+      double lnT = 0.0, invT = 0.0;
+      if (lane == 0) { lnT = log(T); invT = 1.0 / T; }
+      lnT = __shfl_sync(0xffffffffu, lnT, 0);
+      invT = __shfl_sync(0xffffffffu, invT, 0);
       double sh = 0.0, scp = 0.0;
       for (int i = lane; i < N; i += 32) {
         double hRT, gRT, cpR;
@@ -298,7 +330,9 @@ __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, doubl
       for (int i = 0; i < N; ++i)
         for (int j = lane; j < na; j += 32)
           J[(size_t)i * ld + j] = (j == i) ? 1.0 : (j == nn ? w.bs[i] - w.xs[i] : 0.0);
-      const double sT = 1.0 / (scp * T);
+      double sT = 0.0;
+      if (lane == 0) sT = invT / scp;
+      sT = __shfl_sync(0xffffffffu, sT, 0);
       for (int j = lane; j < N; j += 32) J[(size_t)N * ld + j] = w.hm[j] * sT;
       if (lane == 0) {
         J[(size_t)N * ld + N] = scp * sT;
@@ -322,57 +356,175 @@ __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, doubl
         if (cur >= 0) J[cur] = fma(-wdt, acc, J[cur]);
       }
       __syncwarp();
-      // ---- LU with partial pivoting
-      bool singular = false;
-      for (int k = 0; k < nn; ++k) {
-        unsigned long long best = 0ull;
-        int bi = nn;
-        for (int i = k + lane; i < nn; i += 32) {
-          const unsigned long long v =
-              (unsigned long long)__double_as_longlong(J[(size_t)i * ld + k]) & 0x7fffffffffffffffull;
-          if (v > best) { best = v; bi = i; }
+      bool singular = false, fallback = false;
+      if (MIXED) {
+        // ---- mixed precision: FP32 factor of J, FP64 residual refinement; cells
+        // whose refinement does not contract fall back to the FP64 factor below
+        // rows are equilibrated (scaled by 1/max|J_ij|) before rounding to FP32, which
+        // keeps stiff rows (entries up to ~1e30) in range; the scaling does not
+        // change the solution and the FP64 residual uses the unscaled rows
+        float *Jf = w.Jf;
+        for (int i = lane; i < nn; i += 32) {
+          double amax = 0.0;
+          const double *Ji = J + (size_t)i * ld;
+          for (int j = 0; j < nn; ++j) amax = fmax(amax, fabs(Ji[j]));
+          w.res[i] = (amax > 0.0) ? 1.0 / amax : 1.0;
+          w.r64[i] = Ji[nn];
+          w.dx[i] = 0.0;
         }
+        __syncwarp();
+        for (int i = 0; i < nn; ++i) {
+          const double si = w.res[i];
+          for (int j = lane; j < nn; j += 32) Jf[(size_t)i * ld + j] = __double2float_rn(J[(size_t)i * ld + j] * si);
+        }
+        __syncwarp();
+        for (int k = 0; k < nn; ++k) {
+          unsigned best = 0u;
+          int bi = nn;
+          for (int i = k + lane; i < nn; i += 32) {
+            const unsigned v = (unsigned)__float_as_int(Jf[(size_t)i * ld + k]) & 0x7fffffffu;
+            if (v > best) { best = v; bi = i; }
+          }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (best == 0ull || best >= 0x7ff0000000000000ull) { singular = true; break; }
-        if (bi != k) {
-          for (int j = lane; j < na; j += 32) {
-            const double t = J[(size_t)k * ld + j];
-            J[(size_t)k * ld + j] = J[(size_t)bi * ld + j];
-            J[(size_t)bi * ld + j] = t;
+          for (int o = 16; o > 0; o >>= 1) {
+            const unsigned ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          }
+          if (best == 0u || best >= 0x7f800000u) { fallback = true; break; }
+          if (lane == 0) w.sw[k] = bi;
+          if (bi != k) {
+            for (int j = lane; j < nn; j += 32) {
+              const float t = Jf[(size_t)k * ld + j];
+              Jf[(size_t)k * ld + j] = Jf[(size_t)bi * ld + j];
+              Jf[(size_t)bi * ld + j] = t;
+            }
+            __syncwarp();
+          }
+          const float pinv = 1.0f / Jf[(size_t)k * ld + k];
+          if (lane == 0) w.pivf[k] = pinv;
+          for (int i = k + 1 + lane; i < nn; i += 32) Jf[(size_t)i * ld + k] *= pinv;
+          __syncwarp();
+          const int rows = nn - 1 - k, cols = nn - 1 - k;
+          const int total = rows * cols;
+          if (total > 0) {
+            int i = lane / cols, j = lane - i * cols;
+            const int qs = 32 / cols, rsd = 32 - qs * cols;
+            for (int e = lane; e < total; e += 32) {
+              const size_t ri = (size_t)(k + 1 + i) * ld;
+              Jf[ri + k + 1 + j] = fmaf(-Jf[ri + k], Jf[(size_t)k * ld + k + 1 + j], Jf[ri + k + 1 + j]);
+              i += qs;
+              j += rsd;
+              if (j >= cols) { j -= cols; ++i; }
+            }
           }
           __syncwarp();
         }
-        const double pinv = 1.0 / J[(size_t)k * ld + k];
-        if (lane == 0) w.piv[k] = pinv;
-        for (int i = k + 1 + lane; i < nn; i += 32) J[(size_t)i * ld + k] *= pinv;
-        __syncwarp();
-        const int rows = nn - 1 - k, cols = na - 1 - k;   // trailing block (k, nn) x (k, na)
-        const int total = rows * cols;
-        if (total > 0) {
-          int i = lane / cols, j = lane - i * cols;
-          const int qs = 32 / cols, rsd = 32 - qs * cols;
-          for (int e = lane; e < total; e += 32) {
-            const size_t ri = (size_t)(k + 1 + i) * ld;
-            J[ri + k + 1 + j] = fma(-J[ri + k], J[(size_t)k * ld + k + 1 + j], J[ri + k + 1 + j]);
-            i += qs;
-            j += rsd;
-            if (j >= cols) { j -= cols; ++i; }
+        // dx = 0; repeat: res = r - J dx (FP64), z = LU^{-1} P res (FP32), dx += z
+        float zprev = INFINITY;
+        for (int ref = 0; ref < 6 && !fallback; ++ref) {
+          if (ref == 0) {
+            for (int i = lane; i < nn; i += 32) w.zf[i] = __double2float_rn(w.r64[i] * w.res[i]);
+          } else {
+            for (int i = lane; i < nn; i += 32) {
+              double sacc = w.r64[i];
+              const double *Ji = J + (size_t)i * ld;
+              for (int j = 0; j < nn; ++j) sacc = fma(-Ji[j], w.dx[j], sacc);
+              w.zf[i] = __double2float_rn(sacc * w.res[i]);
+            }
           }
+          __syncwarp();
+          if (lane == 0)
+            for (int k = 0; k < nn; ++k) {
+              const int t = w.sw[k];
+              if (t != k) { const float v = w.zf[k]; w.zf[k] = w.zf[t]; w.zf[t] = v; }
+            }
+          __syncwarp();
+          for (int k = 0; k < nn; ++k) {
+            const float zk = w.zf[k];
+            for (int i = k + 1 + lane; i < nn; i += 32) w.zf[i] = fmaf(-Jf[(size_t)i * ld + k], zk, w.zf[i]);
+            __syncwarp();
+          }
+          for (int k = nn - 1; k >= 0; --k) {
+            const float zk = w.zf[k] * w.pivf[k];
+            __syncwarp();
+            if (lane == 0) w.zf[k] = zk;
+            for (int i = lane; i < k; i += 32) w.zf[i] = fmaf(-Jf[(size_t)i * ld + k], zk, w.zf[i]);
+            __syncwarp();
+          }
+          float zmax = 0.0f, dmx = 0.0f;
+          for (int i = lane; i < nn; i += 32) {
+            const double v = w.dx[i] + (double)w.zf[i];
+            w.dx[i] = v;
+            zmax = fmaxf(zmax, fabsf(w.zf[i]));
+            dmx = fmaxf(dmx, fabsf(__double2float_rn(v)));
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+            dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+          }
+          __syncwarp();
+          if (!(zmax <= zprev * 0.5f) || !isfinite(dmx)) { fallback = true; break; }   // not contracting
+          if (zmax <= 1e-6f * dmx) break;   // correction below 1e-6 of the step
+          zprev = zmax;
+          if (ref == 5) fallback = true;
         }
-        __syncwarp();
       }
-      if (singular) { code = -2; break; }
-      for (int k = nn - 1; k >= 0; --k) {
-        const double xk = J[(size_t)k * ld + nn] * w.piv[k];
-        if (lane == 0) w.dx[k] = xk;
-        for (int i = lane; i < k; i += 32)
-          J[(size_t)i * ld + nn] = fma(-J[(size_t)i * ld + k], xk, J[(size_t)i * ld + nn]);
-        __syncwarp();
+      if (!MIXED || fallback) {
+        // ---- FP64 LU with partial pivoting
+        for (int k = 0; k < nn; ++k) {
+          unsigned long long best = 0ull;
+          int bi = nn;
+          for (int i = k + lane; i < nn; i += 32) {
+            const unsigned long long v =
+                (unsigned long long)__double_as_longlong(J[(size_t)i * ld + k]) & 0x7fffffffffffffffull;
+            if (v > best) { best = v; bi = i; }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          }
+          if (best == 0ull || best >= 0x7ff0000000000000ull) { singular = true; break; }
+          if (bi != k) {
+            for (int j = lane; j < na; j += 32) {
+              const double t = J[(size_t)k * ld + j];
+              J[(size_t)k * ld + j] = J[(size_t)bi * ld + j];
+              J[(size_t)bi * ld + j] = t;
+            }
+            __syncwarp();
+          }
+          double pinv = 0.0;
+          if (lane == 0) { pinv = 1.0 / J[(size_t)k * ld + k]; w.piv[k] = pinv; }
+          pinv = __shfl_sync(0xffffffffu, pinv, 0);
+          for (int i = k + 1 + lane; i < nn; i += 32) J[(size_t)i * ld + k] *= pinv;
+          __syncwarp();
+          const int rows = nn - 1 - k, cols = na - 1 - k;   // trailing block (k, nn) x (k, na)
+          const int total = rows * cols;
+          if (total > 0) {
+            int i = lane / cols, j = lane - i * cols;
+            const int qs = 32 / cols, rsd = 32 - qs * cols;
+            for (int e = lane; e < total; e += 32) {
+              const size_t ri = (size_t)(k + 1 + i) * ld;
+              J[ri + k + 1 + j] = fma(-J[ri + k], J[(size_t)k * ld + k + 1 + j], J[ri + k + 1 + j]);
+              i += qs;
+              j += rsd;
+              if (j >= cols) { j -= cols; ++i; }
+            }
+          }
+          __syncwarp();
+        }
+        if (singular) { code = -2; break; }
+        for (int k = nn - 1; k >= 0; --k) {
+          double xk = 0.0;
+          if (lane == 0) { xk = J[(size_t)k * ld + nn] * w.piv[k]; w.dx[k] = xk; }
+          xk = __shfl_sync(0xffffffffu, xk, 0);
+          for (int i = lane; i < k; i += 32)
+            J[(size_t)i * ld + nn] = fma(-J[(size_t)i * ld + k], xk, J[(size_t)i * ld + nn]);
+          __syncwarp();
+        }
       }
       // ---- update and convergence on d = max(max|dY|, |dT|/T)
       double dmax = 0.0;
@@ -389,7 +541,9 @@ __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, doubl
       __syncwarp();
       T = w.xs[N];
       if (!fin || !(T > 0.0)) { code = -3; break; }
-      const double d = fmax(dmax, fabs(w.dx[N]) / T);
+      double d = 0.0;
+      if (lane == 0) d = fmax(dmax, fabs(w.dx[N]) / T);
+      d = __shfl_sync(0xffffffffu, d, 0);
       if (!isfinite(d)) { code = -3; break; }
       if (d <= rtol || (d <= 1e-8 && d >= 0.5 * dprev)) break;
       dprev = d;
@@ -397,9 +551,14 @@ __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, doubl
     if (code == 0 && it > maxit) code = -1;
     // species enthalpies and theta at the solution; reaction term (Y - b)/wdt
     const double Tf = (code == -3) ? 1000.0 : T;
-    const double invw = (wdt > 0.0) ? 1.0 / wdt : 0.0;
+    double invw = 0.0;
+    if (lane == 0 && wdt > 0.0) invw = 1.0 / wdt;
+    invw = __shfl_sync(0xffffffffu, invw, 0);
     {
-      const double lnT = log(Tf), invT = 1.0 / Tf;
+      double lnT = 0.0, invT = 0.0;
+      if (lane == 0) { lnT = log(Tf); invT = 1.0 / Tf; }
+      lnT = __shfl_sync(0xffffffffu, lnT, 0);
+      invT = __shfl_sync(0xffffffffu, invT, 0);
       for (int i = lane; i < N; i += 32) {
         double hRT, gRT, cpR;
         species_thermo(m, i, Tf, lnT, invT, hRT, gRT, cpR);
@@ -446,18 +605,19 @@ int sm_count() {
 
 }  // namespace
 
-static size_t newton_smem(const DevMech &m, int &ld, int &wpb) {
-  const int nn = m.N + 1;
+static size_t newton_smem(const DevMech &m, bool mixed, int &ld, int &wpb) {
   ld = newton_ld(m.N);
-  const size_t per_warp = (size_t)nn * ld + 8 * m.R + 6 * m.N + 3 * nn;
+  const size_t per_warp = newton_warp_doubles(m.N, m.R, ld, mixed);
   wpb = (per_warp * 8 * 4 <= 200 * 1024) ? 4 : 2;
   return (size_t)wpb * per_warp * sizeof(double);
 }
 
 void prepare_chem_kernels(const DevMech &m) {
   int ld, wpb;
-  const size_t sm = newton_smem(m, ld, wpb);
-  cudaFuncSetAttribute(k_newton2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  size_t sm = newton_smem(m, false, ld, wpb);
+  cudaFuncSetAttribute(k_newton2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  sm = newton_smem(m, true, ld, wpb);
+  cudaFuncSetAttribute(k_newton2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const size_t smr = (size_t)4 * (5 * m.N + 4 * m.R) * sizeof(double);
   cudaFuncSetAttribute(k_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
 }
@@ -488,15 +648,19 @@ void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double
 void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit,
                    const double *b, const double *hstar, const double *Yg, const double *Tg,
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
-                   DevStats *st, cudaStream_t s) {
+                   DevStats *st, cudaStream_t s, bool mixed) {
   if (n <= 0) return;
   int ld, wpb;
-  const size_t sm = newton_smem(m, ld, wpb);
+  const size_t sm = newton_smem(m, mixed, ld, wpb);
   int grid = (n + wpb - 1) / wpb;
   const int cap = sm_count() * (wpb == 4 ? 8 : 12);
   grid = grid < cap ? grid : cap;
-  k_newton2<<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T, FR,
-                                       hsp, theta, iters, st);
+  if (mixed)
+    k_newton2<true><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
+                                               FR, hsp, theta, iters, st);
+  else
+    k_newton2<false><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
+                                                FR, hsp, theta, iters, st);
 }
 
 }  // namespace misdc

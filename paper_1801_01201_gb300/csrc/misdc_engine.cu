@@ -332,7 +332,7 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
   if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used], st, cudaEventRecordExternal);
   launch_newton(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, s->bR,
                 ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR, out.hsp, out.theta,
-                s->iters, s->st, st);
+                s->iters, s->st, st, s->o.precision == MISDC_PREC_MIXED);
   if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used++ + 1], st, cudaEventRecordExternal);
   cudaMemcpyAsync(out.phi + N * cs, ad.phi + N * cs, cs * sizeof(double), cudaMemcpyDeviceToDevice, st);
   node_operators(s, out, s->thfR, st);
@@ -457,7 +457,7 @@ misdc_status configure_dt(misdc_solver *s, double dt) {
     qmax = std::max(qmax, s->tab.tau[t + 1] - s->tab.tau[t]);
   }
   s->rho_bound = rho_bound_for(s, dt * qmax);
-  s->cheb_sweeps = chebyshev_sweeps(s->rho_bound, std::max(1e-3 * s->o.lin_rtol, 1e-17));
+  s->cheb_sweeps = std::min(kMaxCheb, chebyshev_sweeps(s->rho_bound, std::max(1e-3 * s->o.lin_rtol, 1e-17)));
   s->rho_dt = dt;
   return MISDC_OK;
 }
@@ -521,7 +521,8 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   if (op->n_nodes < 2 || op->n_nodes > 5) return fail(MISDC_E_INVALID, "n_nodes must be 2..5");
   if (op->n_sweeps < 1 || op->nu < 1 || op->nu > 16) return fail(MISDC_E_INVALID, "bad n_sweeps/nu");
   if (op->scheme < 0 || op->scheme > 2) return fail(MISDC_E_INVALID, "bad scheme");
-  if (op->precision != MISDC_PREC_FP64) return fail(MISDC_E_INVALID, "only FP64 precision is built");
+  if (op->precision != MISDC_PREC_FP64 && op->precision != MISDC_PREC_MIXED)
+    return fail(MISDC_E_INVALID, "precision must be MISDC_PREC_FP64 or MISDC_PREC_MIXED");
   if (op->dominant_species < 0 || op->dominant_species >= N) return fail(MISDC_E_INVALID, "bad dominant species");
   if (!(op->rho > 0.0) || !(op->newton_rtol > 0.0) || op->newton_maxit < 1 || !(op->lin_rtol > 0.0))
     return fail(MISDC_E_INVALID, "bad tolerances or density");
@@ -653,7 +654,8 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   if (s->alloc(&s->rhsD, F * cs) || s->alloc(&s->bR, F * cs) || s->alloc(&s->thfD, 3 * cs) ||
       s->alloc(&s->thfR, 3 * cs) || s->alloc(&s->iters, cs) || s->alloc(&s->st, 1) ||
       s->alloc(&s->dw.thf, 3 * cs) || s->alloc(&s->dw.invdiag, F * cs) || s->alloc(&s->dw.xa, F * cs) ||
-      s->alloc(&s->dw.xb, F * cs) || s->alloc(&s->dw.xc, F * cs))
+      s->alloc(&s->dw.xb, F * cs) || s->alloc(&s->dw.xc, F * cs) ||
+      s->alloc(&s->dw.rho_bits, 1) || s->alloc(&s->dw.kdev, 1) || s->alloc(&s->dw.omega, kMaxCheb))
     return bail(fail(MISDC_E_OOM, "work buffers"));
   cudaMemset(s->st, 0, sizeof(DevStats));
   // multigrid hierarchy (levels with even extents only)
@@ -871,7 +873,8 @@ misdc_status misdc_reaction_solve(misdc_solver *s, double wdt, const double *b, 
   CK(cudaMallocAsync(&hsp, N * n * sizeof(double), (cudaStream_t)stream));
   CK(cudaMallocAsync(&th, n * sizeof(double), (cudaStream_t)stream));
   launch_newton(s->m, n, n, wdt, s->o.newton_rtol, s->o.newton_maxit, b, hstar, x, x + N * n, x,
-                x + N * n, FR, hsp, th, iters, s->st, (cudaStream_t)stream);
+                x + N * n, FR, hsp, th, iters, s->st, (cudaStream_t)stream,
+                s->o.precision == MISDC_PREC_MIXED);
   cudaFreeAsync(hsp, (cudaStream_t)stream);
   cudaFreeAsync(th, (cudaStream_t)stream);
   CK(cudaGetLastError());
@@ -911,7 +914,7 @@ misdc_status misdc_diffusion_solve(misdc_solver *s, double wdt, const double *co
                      nullptr, s->st, st);
   s->rho_dt = -1.0;
   s->rho_bound = rho_bound_for(s, wdt);
-  s->cheb_sweeps = chebyshev_sweeps(s->rho_bound, std::max(1e-3 * s->o.lin_rtol, 1e-17));
+  s->cheb_sweeps = std::min(kMaxCheb, chebyshev_sweeps(s->rho_bound, std::max(1e-3 * s->o.lin_rtol, 1e-17)));
   CK(cudaMemcpyAsync(s->rhsD, rhs, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   diffusion_solve(s->m, s->g, s->i0, wdt, b.theta, s->rhsD, x, s->dw, s->cheb_sweeps, s->rho_bound,
                   s->o.lin_rtol, s->st, st);
@@ -1017,7 +1020,7 @@ extern "C" misdc_status misdc_reaction_solve_noalloc(misdc_solver *s, double wdt
   double *hsp = theta + n;
   CK(cudaMemsetAsync(stats, 0, sizeof(DevStats), cs));
   launch_newton(s->m, n, n, wdt, s->o.newton_rtol, s->o.newton_maxit, b, hstar, x, x + N * n, x,
-                x + N * n, FR, hsp, theta, iters, stats, cs);
+                x + N * n, FR, hsp, theta, iters, stats, cs, s->o.precision == MISDC_PREC_MIXED);
   CK(cudaGetLastError());
   return MISDC_OK;
 }

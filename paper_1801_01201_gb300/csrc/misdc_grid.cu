@@ -139,22 +139,56 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
 }
 
 // theta at cells -> harmonic mean at the low face of each cell; inverse
-// diagonal of I - c_f L_theta for every solved field.
+// diagonal of I - c_f L_theta for every solved field; and (if rho_bits) the
+// largest Gershgorin bound c S/(1 + c S) of the Jacobi iteration matrix over
+// cells, for the largest c_f (bit pattern of a non-negative double).
 __global__ void k_face_coef(DevGrid g, FieldMap fm, const double *__restrict__ theta,
-                            double *__restrict__ thf, double *__restrict__ invdiag) {
+                            double *__restrict__ thf, double *__restrict__ invdiag, double cmax,
+                            unsigned long long *rho_bits) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int cs = g.cells;
-  if (c >= cs) return;
-  const Nbr nb = neighbours(g, c);
-  const double tc = theta[c];
-  double S = 0.0;
-  for (int d = 0; d < g.dim; ++d) {
-    const double a = theta[nb.cm[d]], b = theta[nb.cp[d]];
-    const double lo = 2.0 * a * tc / (a + tc), hi = 2.0 * tc * b / (tc + b);
-    thf[(size_t)d * cs + c] = lo;
-    S += lo + hi;
+  double ratio = 0.0;
+  if (c < cs) {
+    const Nbr nb = neighbours(g, c);
+    const double tc = theta[c];
+    double S = 0.0;
+    for (int d = 0; d < g.dim; ++d) {
+      const double a = theta[nb.cm[d]], b = theta[nb.cp[d]];
+      const double lo = 2.0 * a * tc / (a + tc), hi = 2.0 * tc * b / (tc + b);
+      thf[(size_t)d * cs + c] = lo;
+      S += lo + hi;
+    }
+    for (int k = 0; k < fm.nfs; ++k) invdiag[(size_t)k * cs + c] = 1.0 / (1.0 + fm.cf[k] * S);
+    ratio = cmax * S / (1.0 + cmax * S);
   }
-  for (int k = 0; k < fm.nfs; ++k) invdiag[(size_t)k * cs + c] = 1.0 / (1.0 + fm.cf[k] * S);
+  if (rho_bits) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ratio = fmax(ratio, __shfl_xor_sync(0xffffffffu, ratio, o));
+    if ((threadIdx.x & 31) == 0 && ratio > 0.0)
+      atomicMax(rho_bits, (unsigned long long)__double_as_longlong(ratio));
+  }
+}
+
+// Chebyshev plan from the measured bound: sweep count K (at most kmax) for an
+// error reduction `red`, and the weights omega_k of the semi-iterative method.
+__global__ void k_cheb_plan(const unsigned long long *rho_bits, int kmax, double red, int *kdev,
+                            double *omega) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double rho = __longlong_as_double((long long)*rho_bits) * (1.0 + 1e-12);
+  int K = 1;
+  if (rho > 0.0) {
+    if (rho >= 1.0) rho = 1.0 - 1e-12;
+    K = (int)ceil(acosh(1.0 / red) / acosh(1.0 / rho));
+  }
+  K = max(1, min(K, kmax));
+  *kdev = K;
+  const double r2 = rho * rho;
+  double om = 1.0;
+  for (int k = 0; k < K; ++k) {
+    if (k == 1) om = 1.0 / (1.0 - 0.5 * r2);
+    else if (k > 1) om = 1.0 / (1.0 - 0.25 * r2 * om);
+    omega[k] = om;
+  }
 }
 
 __device__ __forceinline__ double lap_theta(const DevGrid &g, const Nbr &nb, int c, int cs,
@@ -169,10 +203,13 @@ __device__ __forceinline__ double lap_theta(const DevGrid &g, const Nbr &nb, int
 
 // One Chebyshev-accelerated Jacobi sweep for every solved field:
 // y = D^{-1} (b + c_f * offdiag(x_k)), x_{k+1} = omega (y - x_{k-1}) + x_{k-1}.
+// Sweeps it >= *kdev (the device-planned count) do nothing.
 __global__ void k_cheb(DevGrid g, FieldMap fm, const double *__restrict__ thf,
                        const double *__restrict__ invdiag, const double *__restrict__ rhs,
                        const double *__restrict__ xk, const double *__restrict__ xkm1,
-                       double *__restrict__ xkp1, double omega, int first) {
+                       double *__restrict__ xkp1, int it, const int *__restrict__ kdev,
+                       const double *__restrict__ omega) {
+  if (it >= *kdev) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   const int cs = g.cells;
@@ -184,7 +221,7 @@ __global__ void k_cheb(DevGrid g, FieldMap fm, const double *__restrict__ thf,
   for (int d = 0; d < g.dim; ++d)
     s += thf[(size_t)d * cs + nb.cp[d]] * x[nb.cp[d]] + thf[(size_t)d * cs + c] * x[nb.cm[d]];
   const double y = (rhs[off + c] + fm.cf[k] * s) * invdiag[(size_t)k * cs + c];
-  xkp1[off + c] = first ? y : fma(omega, y - xkm1[off + c], xkm1[off + c]);
+  xkp1[off + c] = (it == 0) ? y : fma(omega[it], y - xkm1[off + c], xkm1[off + c]);
 }
 
 __device__ __forceinline__ unsigned long long dbits(double v) {
@@ -195,10 +232,17 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
 // the dominant species. Writes the advection-diffusion state.
 __global__ void k_finish(DevGrid g, FieldMap fm, int N, int i0, double tol,
                          const double *__restrict__ thf, const double *__restrict__ rhs,
-                         const double *__restrict__ x, double *__restrict__ out, DevStats *st) {
+                         const double *x0, const double *x1, const double *x2,
+                         const int *kdev, double *__restrict__ out, DevStats *st) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int cs = g.cells;
   double rmax = 0.0;
+  // final iterate: x0 alone, or the buffer the last planned sweep wrote
+  const double *x = x0;
+  if (kdev) {
+    const int K = *kdev, sl = (K - 1) % 3;
+    x = sl == 0 ? x0 : (sl == 1 ? x1 : x2);
+  }
   if (c < cs) {
     const Nbr nb = neighbours(g, c);
     double sum = 0.0;
@@ -209,7 +253,8 @@ __global__ void k_finish(DevGrid g, FieldMap fm, int N, int i0, double tol,
       const double b = rhs[off + c];
       const double scale = fabs(b) + fabs(fm.cf[k] * L) + fabs(x[off + c]) + 1e-300;
       const double r = b - (x[off + c] - fm.cf[k] * L);
-      rmax = fmax(rmax, fabs(r) / scale);
+      // diagnostic ratio in FP32 (FP64 divisions are scarce on this part)
+      rmax = fmax(rmax, (double)(__double2float_ru(fabs(r)) / fmaxf(__double2float_rd(scale), 1e-30f)));
       const double v = b + fm.cf[k] * L;
       out[off + c] = v;
       if (f < N) sum += v;
@@ -312,10 +357,17 @@ __global__ void k_diag_level(DevGrid g, FieldMap fm, const double *__restrict__ 
 }
 
 // gather the solved fields of a full-layout array into compact storage and back
-__global__ void k_gather(int cs, FieldMap fm, const double *__restrict__ full, double *__restrict__ compact) {
+// (with kdev: from the buffer the last planned Chebyshev sweep wrote)
+__global__ void k_gather(int cs, FieldMap fm, const double *f0, const double *f1, const double *f2,
+                         const int *kdev, double *__restrict__ compact) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (c >= cs) return;
+  const double *full = f0;
+  if (kdev) {
+    const int sl = (*kdev - 1) % 3;
+    full = sl == 0 ? f0 : (sl == 1 ? f1 : f2);
+  }
   compact[(size_t)k * cs + c] = full[(size_t)fm.fld[k] * cs + c];
 }
 __global__ void k_scatter_set(int cs, FieldMap fm, const double *__restrict__ compact, double *__restrict__ full) {
@@ -364,31 +416,33 @@ void launch_operators(const DevMech &m, const DevGrid &g, int i0, const double *
 void launch_theta_faces(const DevGrid &g, const double *theta, double *thf, cudaStream_t s) {
   FieldMap fm;
   fm.nfs = 0;
-  k_face_coef<<<(g.cells + 255) / 256, 256, 0, s>>>(g, fm, theta, thf, nullptr);
+  k_face_coef<<<(g.cells + 255) / 256, 256, 0, s>>>(g, fm, theta, thf, nullptr, 0.0, nullptr);
 }
 
 void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, const double *theta,
                      const double *rhs, double *out, DiffWork &w, int sweeps, double rho_bound,
                      double lin_rtol, DevStats *st, cudaStream_t s) {
+  const double reduction = std::max(1e-3 * lin_rtol, 1e-17);
   const FieldMap fm = make_map(m, m.D0_host, m.alpha0, i0, wdt, g.dx);
   const int cs = g.cells;
-  k_face_coef<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, theta, w.thf, w.invdiag);
+  double cmax = 0.0;
+  for (int k = 0; k < fm.nfs; ++k) cmax = std::max(cmax, fm.cf[k]);
+  cudaMemsetAsync(w.rho_bits, 0, sizeof(unsigned long long), s);
+  k_face_coef<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, theta, w.thf, w.invdiag, cmax, w.rho_bits);
+  // sweeps: planned on the device from the measured Gershgorin bound, at most
+  // `sweeps` (the a-priori bound with theta at the 6000 K cap)
+  (void)rho_bound;
+  k_cheb_plan<<<1, 32, 0, s>>>(w.rho_bits, sweeps, reduction, w.kdev, w.omega);
   const dim3 gr = grid2(cs, fm.nfs);
-  const double r2 = rho_bound * rho_bound;
   // Chebyshev-accelerated Jacobi from x0 = rhs (the operator is I - c L)
-  const double *xkm1 = rhs, *xk = rhs;
   double *bufs[3] = {w.xa, w.xb, w.xc};
-  double omega = 1.0;
-  int slot = 0;
   for (int it = 0; it < sweeps; ++it) {
-    double *xn = bufs[slot];
-    if (it == 1) omega = 1.0 / (1.0 - 0.5 * r2);
-    else if (it > 1) omega = 1.0 / (1.0 - 0.25 * r2 * omega);
-    k_cheb<<<gr, 256, 0, s>>>(g, fm, w.thf, w.invdiag, rhs, xk, xkm1, xn, omega, it == 0);
-    xkm1 = xk;
-    xk = xn;
-    slot = (slot + 1) % 3;
+    const double *xk = (it == 0) ? rhs : bufs[(it - 1) % 3];
+    const double *xkm1 = (it <= 1) ? rhs : bufs[(it - 2) % 3];
+    k_cheb<<<gr, 256, 0, s>>>(g, fm, w.thf, w.invdiag, rhs, xk, xkm1, bufs[it % 3], it, w.kdev, w.omega);
   }
+  const int *kdev = w.kdev;
+  const double *xfin = w.xa;
   // Multigrid (levels > 1): V-cycles of the correction scheme on compact
   // [solved field][cells] storage, damped-Jacobi smoothing on every level,
   // mean-value restriction and piecewise-constant prolongation, coefficients
@@ -405,8 +459,8 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
       k_coarsen_faces<<<(gc.cells + 255) / 256, 256, 0, s>>>(gf, gc, w.lthf[l - 1], w.lthf[l]);
       k_diag_level<<<(gc.cells + 255) / 256, 256, 0, s>>>(gc, fl[l], w.lthf[l], w.linvdiag[l]);
     }
-    k_gather<<<gr, 256, 0, s>>>(cs, fm, rhs, w.lb[0]);
-    k_gather<<<gr, 256, 0, s>>>(cs, fm, xk, w.lx[0]);
+    k_gather<<<gr, 256, 0, s>>>(cs, fm, rhs, nullptr, nullptr, nullptr, w.lb[0]);
+    k_gather<<<gr, 256, 0, s>>>(cs, fm, w.xa, w.xb, w.xc, w.kdev, w.lx[0]);
     auto smooth = [&](int l, int n_sw) {
       const DevGrid &gl = w.lg[l];
       for (int sw = 0; sw < n_sw; ++sw) {
@@ -428,11 +482,14 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
         smooth(l, 2);
       }
     }
-    double *xn = bufs[slot];
-    k_scatter_set<<<gr, 256, 0, s>>>(cs, fm, w.lx[0], xn);
-    xk = xn;
+    // the corrected iterate goes to w.xa (its dominant-species row is not written
+    // and never read: k_finish closes that field)
+    k_scatter_set<<<gr, 256, 0, s>>>(cs, fm, w.lx[0], w.xa);
+    kdev = nullptr;
+    xfin = w.xa;
   }
-  k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, xk, out, st);
+  k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, xfin, w.xb,
+                                            w.xc, kdev, out, st);
 }
 
 }  // namespace misdc

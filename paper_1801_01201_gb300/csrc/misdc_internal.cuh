@@ -14,6 +14,7 @@ constexpr double kTlo = 50.0, kThi = 6000.0;   // temperature range of the one-r
 constexpr int kMaxSlots = 3;               // molecules per reaction side
 constexpr int kMaxSpecies = 63;
 constexpr int kMaxNodes = 9;
+constexpr int kMaxCheb = 512;   // cap on Chebyshev sweeps per diffusion solve
 
 // Device status bits (OR-ed into DevStats::status_bits); mapped to misdc_status
 enum : unsigned {
@@ -76,7 +77,7 @@ void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double
 void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit,
                    const double *b, const double *hstar, const double *Yg, const double *Tg,
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
-                   DevStats *st, cudaStream_t s);
+                   DevStats *st, cudaStream_t s, bool mixed = false);
 
 // ---- grid kernels (misdc_grid.cu) ----
 struct LinComb {
@@ -99,6 +100,9 @@ struct DiffWork {
   double *invdiag;   // [N+1][cs]
   double *xa, *xb, *xc;   // [N+1][cs] iterates
   double *res;       // [N+1][cs] residual (multigrid)
+  unsigned long long *rho_bits;   // measured Gershgorin bound (bit pattern)
+  int *kdev;                      // planned Chebyshev sweep count
+  double *omega;                  // [kMaxCheb] Chebyshev weights
   // multigrid levels (level 0 = this grid, compact [solved field][cells] storage)
   int levels, cycles;
   DevGrid lg[8];

@@ -110,6 +110,28 @@ def test_reaction_newton_parity(key):
     assert st["newton_fail"] == 0 and st["newton_solves"] == n
 
 
+@pytest.mark.parametrize("key", [(1801, 9, 21), (1802, 21, 84), (1803, 53, 325)])
+def test_reaction_newton_parity_mixed_precision(key):
+    """FP32 Jacobian/LU with FP64 residual refinement converges to the FP64 root."""
+    mech = I.make_mechanism(*key)
+    n = 96
+    fl = I.flame_1d(mech, 0, nx=n, dx=1e-4)
+    ad = O.ADR(mech, fl)
+    N = mech.n_species
+    rng = np.random.default_rng(6)
+    b = fl.Y * (1 + 0.02 * rng.standard_normal(fl.Y.shape))
+    hstar = ad.h_from_T(fl.Y, fl.T)
+    x0 = np.concatenate([fl.Y, fl.T[None, :]], axis=0)
+    wdt = 5e-6 / 4
+    sv = S().Solver(mech, fl, precision="mixed")
+    x, FR, it = sv.reaction_solve(wdt, b, hstar, x0)
+    x = x.cpu().numpy()
+    assert np.all(it.cpu().numpy() > 0)
+    want = np.stack([ad.reaction_newton(wdt, b[:, c], hstar[c], x0[:, c])[0] for c in range(n)], axis=1)
+    assert np.all(relerr(x[:N], want[:N]) < TOL)
+    assert relerr(x[N], want[N]) < TOL
+
+
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_operators_parity(dim):
     if dim == 1:
@@ -230,6 +252,20 @@ def test_step_parity_full_chemistry_multid(case):
     got, T, want, ad, st, sens = _run_both(mech, fl, 5e-6, 2, sensitivity=True)
     err = relerr(got, want)
     assert np.all(err <= tol_from(sens)), (err, sens)
+
+
+@pytest.mark.parametrize("case", ["2d_n21", "2d_n53"])
+def test_step_mixed_precision_meets_accuracy_bar(case):
+    """Mixed mode against the FP64 oracle: Y within 1e-8, T within 1e-6 relative."""
+    if case == "2d_n21":
+        mech, fl = small_2d(n=32)
+    else:
+        mech, fl = small_2d((1803, 53, 325), n=16)
+    got, T, want, ad, st, sens = _run_both(mech, fl, 5e-6, 2, precision="mixed", sensitivity=True)
+    N = mech.n_species
+    err = relerr(got, want)
+    assert np.all(err[:N] <= np.maximum(1e-8, 20 * sens[:N])), (err, sens)
+    assert relerr(T, ad.T_from_h(want[:N], want[N])) <= 1e-6
 
 
 def test_stream_graph_variants_are_bitwise_identical():
