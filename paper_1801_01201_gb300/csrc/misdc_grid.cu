@@ -203,7 +203,9 @@ __device__ __forceinline__ double lap_theta(const DevGrid &g, const Nbr &nb, int
 
 // One Chebyshev-accelerated Jacobi sweep for every solved field:
 // y = D^{-1} (b + c_f * offdiag(x_k)), x_{k+1} = omega (y - x_{k-1}) + x_{k-1}.
-// Sweeps it >= *kdev (the device-planned count) do nothing.
+// A thread takes one cell and kChebFields fields (neighbour indices and face
+// coefficients loaded once). Sweeps it >= *kdev (the device-planned count) do nothing.
+constexpr int kChebFields = 4;
 __global__ void k_cheb(DevGrid g, FieldMap fm, const double *__restrict__ thf,
                        const double *__restrict__ invdiag, const double *__restrict__ rhs,
                        const double *__restrict__ xk, const double *__restrict__ xkm1,
@@ -211,17 +213,27 @@ __global__ void k_cheb(DevGrid g, FieldMap fm, const double *__restrict__ thf,
                        const double *__restrict__ omega) {
   if (it >= *kdev) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y;
   const int cs = g.cells;
   if (c >= cs) return;
   const Nbr nb = neighbours(g, c);
-  const size_t off = (size_t)fm.fld[k] * cs;
-  const double *x = xk + off;
-  double s = 0.0;
-  for (int d = 0; d < g.dim; ++d)
-    s += thf[(size_t)d * cs + nb.cp[d]] * x[nb.cp[d]] + thf[(size_t)d * cs + c] * x[nb.cm[d]];
-  const double y = (rhs[off + c] + fm.cf[k] * s) * invdiag[(size_t)k * cs + c];
-  xkp1[off + c] = (it == 0) ? y : fma(omega[it], y - xkm1[off + c], xkm1[off + c]);
+  double tlo[3], thi[3];
+  int cm[3], cp[3];
+  for (int d = 0; d < g.dim; ++d) {
+    cm[d] = nb.cm[d];
+    cp[d] = nb.cp[d];
+    tlo[d] = thf[(size_t)d * cs + c];
+    thi[d] = thf[(size_t)d * cs + cp[d]];
+  }
+  const double om = omega[it];
+  const int k0 = blockIdx.y * kChebFields, k1 = min(fm.nfs, k0 + kChebFields);
+  for (int k = k0; k < k1; ++k) {
+    const size_t off = (size_t)fm.fld[k] * cs;
+    const double *x = xk + off;
+    double s = 0.0;
+    for (int d = 0; d < g.dim; ++d) s += thi[d] * x[cp[d]] + tlo[d] * x[cm[d]];
+    const double y = (rhs[off + c] + fm.cf[k] * s) * invdiag[(size_t)k * cs + c];
+    xkp1[off + c] = (it == 0) ? y : fma(om, y - xkm1[off + c], xkm1[off + c]);
+  }
 }
 
 __device__ __forceinline__ unsigned long long dbits(double v) {
@@ -439,7 +451,8 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
   for (int it = 0; it < sweeps; ++it) {
     const double *xk = (it == 0) ? rhs : bufs[(it - 1) % 3];
     const double *xkm1 = (it <= 1) ? rhs : bufs[(it - 2) % 3];
-    k_cheb<<<gr, 256, 0, s>>>(g, fm, w.thf, w.invdiag, rhs, xk, xkm1, bufs[it % 3], it, w.kdev, w.omega);
+    k_cheb<<<dim3((cs + 255) / 256, (fm.nfs + kChebFields - 1) / kChebFields), 256, 0, s>>>(
+        g, fm, w.thf, w.invdiag, rhs, xk, xkm1, bufs[it % 3], it, w.kdev, w.omega);
   }
   const int *kdev = w.kdev;
   const double *xfin = w.xa;
