@@ -110,6 +110,8 @@ typedef struct misdc_stats {
   long long lin_sweeps;         /* smoother sweeps per field, summed     */
   double lin_resid_max;         /* largest relative residual seen        */
   long long kernel_launches;    /* library kernels launched by misdc_step */
+  long long surrogate_used;     /* cells whose Newton started from the learned guess */
+  long long surrogate_rejected; /* learned guesses the residual judge rejected */
 } misdc_stats;
 
 typedef struct misdc_solver misdc_solver;
@@ -204,6 +206,70 @@ misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double
 misdc_status misdc_reaction_solve_noalloc(misdc_solver *s, double wdt, const double *b,
                                           const double *hstar, double *x, double *FR, int *iters,
                                           int n, void *stream);
+
+/* ---- learned initial guess of the reaction Newton ------------------------
+ * The paper has no counterpart: this is the learned form of the reaction step
+ * S5 (Sec. 3.3), whose Newton otherwise starts from the previous iterate
+ * x_p = (Y_p, T_p) of the same node. A per-solver MLP
+ * n_in -> 256 -> 256 -> 256 -> n_out (GELU, BF16 weights and activations,
+ * FP32 accumulation, tensor-core kernels) maps the features of a cell
+ *   r_i = b_i - Y_p,i + wdt F_p,i,  r_T = (h* - h_p)/(cp(x_p) T_p),
+ *   s = max(max_i |r_i|, |r_T|),
+ *   f = [Y_p (N), (T_p - 1150)/850, log10(wdt) + 6, r/s (N), r_T/s]   (n_in = 2N+3)
+ * to p (n_out = N+1); Newton starts from Y_p + s p_Y, T_p (1 + s p_T) (the T
+ * factor clamped to [0.5, 1.5]) when s > s_min, and keeps that start only if
+ * the scaled residual max-norm there is below s; otherwise it starts from x_p.
+ * Training targets are [(Y* - Y_p)/s, (T* - T_p)/(T_p s)] clipped to [-8, 8],
+ * recorded from the solver's own reaction steps. BF16 feature rows have
+ * ldx = n_in rounded up to 8 columns; target and output rows have ldo = n_out
+ * rounded up to 16 columns (padding zero). The FP32 parameter vector is
+ * W1 [256][ldx], W2 [256][256], W3 [256][256], W4 [ldo][256], b1, b2, b3 [256],
+ * b4 [ldo] (row-major, y = W x + b); padded entries must be zero.
+ * The network state lives in the solver and is created on first use. Calls that
+ * change what misdc_step does (enable, collect) drop its captured graph. */
+misdc_status misdc_surrogate_dims(misdc_solver *s, int *n_in, int *ldx, int *n_hidden, int *n_out,
+                                  int *ldo, size_t *n_params);
+/* Random initial parameters (seeded; output layer scaled by 0.1), Adam state reset. */
+misdc_status misdc_surrogate_init(misdc_solver *s, unsigned long long seed);
+/* Load / save the FP32 parameter vector (host arrays of n_params floats; synchronous). */
+misdc_status misdc_surrogate_load(misdc_solver *s, const float *params, size_t n_params);
+misdc_status misdc_surrogate_save(misdc_solver *s, float *params, size_t n_params);
+/* on = 1: later misdc_step calls start each reaction Newton from the learned guess
+ * (needs parameters). s_min: cells with s <= s_min keep x_p. */
+misdc_status misdc_surrogate_enable(misdc_solver *s, int on, double s_min);
+/* capacity > 0: later misdc_step calls record (features, target) rows of every
+ * reaction solve with s > s_min (plain Newton from x_p) until capacity rows are
+ * held; a larger capacity starts a new, empty dataset. 0 stops recording. */
+misdc_status misdc_surrogate_collect(misdc_solver *s, long long capacity);
+/* Rows recorded so far and the library-owned device arrays holding them
+ * (X: BF16 [rows][ldx], targets: FP32 [rows][ldo]); synchronises the solver. */
+misdc_status misdc_surrogate_dataset(misdc_solver *s, long long *rows, const void **X,
+                                     const float **targets);
+/* Train on the recorded rows: steps AdamW steps (beta 0.9/0.999, eps 1e-8,
+ * decoupled weight decay on the weights only, learning rate lr with cosine decay
+ * to 0.05 lr) on minibatches of `batch` rows drawn with a counter-based
+ * generator from `seed`; mean-squared loss over the n_out outputs. loss_curve:
+ * host [steps] (may be NULL). Synchronous. */
+misdc_status misdc_surrogate_train(misdc_solver *s, int steps, int batch, double lr,
+                                   double weight_decay, unsigned long long seed,
+                                   float *loss_curve);
+/* Row-level entry points (device arrays, stream-ordered):
+ * features of n cells: b, Yp, FRp [N][n]; hstar, Tp, hp [n]; X out BF16 [n][ldx];
+ * scale out [n] (= s). */
+misdc_status misdc_surrogate_features(misdc_solver *s, double wdt, const double *b,
+                                      const double *hstar, const double *Yp, const double *Tp,
+                                      const double *FRp, const double *hp, int n, void *X,
+                                      double *scale, void *stream);
+/* out FP32 [n][ldo] = MLP(X BF16 [n][ldx]). */
+misdc_status misdc_surrogate_forward(misdc_solver *s, const void *X, int n, float *out,
+                                     void *stream);
+/* Gradient of the mean-squared loss (mean over n rows and n_out outputs) against
+ * targets FP32 [n][ldo]: grad [n_params] and loss [1] (device, may be NULL). */
+misdc_status misdc_surrogate_gradient(misdc_solver *s, const void *X, const float *targets, int n,
+                                      float *grad, float *loss, void *stream);
+/* misdc_surrogate_gradient followed by one AdamW step with learning rate lr. */
+misdc_status misdc_surrogate_train_batch(misdc_solver *s, const void *X, const float *targets, int n,
+                                         double lr, double weight_decay, float *loss, void *stream);
 
 const char *misdc_last_error(void);
 

@@ -43,7 +43,8 @@ class Stats(C.Structure):
     _fields_ = [("newton_solves", C.c_longlong), ("newton_iters", C.c_longlong),
                 ("newton_fail", C.c_longlong), ("newton_max", C.c_int), ("status", C.c_int),
                 ("lin_sweeps", C.c_longlong), ("lin_resid_max", C.c_double),
-                ("kernel_launches", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("surrogate_used", C.c_longlong),
+                ("surrogate_rejected", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -55,7 +56,11 @@ EXPORTS = ["misdc_default_opts", "misdc_create", "misdc_destroy", "misdc_step", 
            "misdc_get_stats", "misdc_lobatto", "misdc_enthalpy", "misdc_temperature",
            "misdc_production_rates", "misdc_reaction_solve", "misdc_operators",
            "misdc_diffusion_solve", "misdc_lincomb", "misdc_last_error", "misdc_stage_times",
-           "misdc_reaction_solve_noalloc"]
+           "misdc_reaction_solve_noalloc", "misdc_surrogate_dims", "misdc_surrogate_init",
+           "misdc_surrogate_load", "misdc_surrogate_save", "misdc_surrogate_enable",
+           "misdc_surrogate_collect", "misdc_surrogate_dataset", "misdc_surrogate_train",
+           "misdc_surrogate_features", "misdc_surrogate_forward", "misdc_surrogate_gradient",
+           "misdc_surrogate_train_batch"]
 
 _lib = None
 
@@ -96,6 +101,19 @@ def load(build_if_missing: bool = True):
     L.misdc_lincomb.argtypes = [C.c_int, C.c_int, C.POINTER(vp), C.POINTER(vp), dp, C.c_size_t, vp]
     L.misdc_stage_times.argtypes = [vp, dp, ip, dp, ip]
     L.misdc_reaction_solve_noalloc.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp, C.c_int, vp]
+    fp = C.POINTER(C.c_float)
+    L.misdc_surrogate_dims.argtypes = [vp, ip, ip, ip, ip, ip, C.POINTER(C.c_size_t)]
+    L.misdc_surrogate_init.argtypes = [vp, C.c_ulonglong]
+    L.misdc_surrogate_load.argtypes = [vp, fp, C.c_size_t]
+    L.misdc_surrogate_save.argtypes = [vp, fp, C.c_size_t]
+    L.misdc_surrogate_enable.argtypes = [vp, C.c_int, C.c_double]
+    L.misdc_surrogate_collect.argtypes = [vp, C.c_longlong]
+    L.misdc_surrogate_dataset.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(vp), C.POINTER(vp)]
+    L.misdc_surrogate_train.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_ulonglong, fp]
+    L.misdc_surrogate_features.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp, vp, C.c_int, vp, vp, vp]
+    L.misdc_surrogate_forward.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.misdc_surrogate_gradient.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp]
+    L.misdc_surrogate_train_batch.argtypes = [vp, vp, vp, C.c_int, C.c_double, C.c_double, vp, vp]
     L.misdc_last_error.restype = C.c_char_p
     L.misdc_last_error.argtypes = []
     for name in EXPORTS:

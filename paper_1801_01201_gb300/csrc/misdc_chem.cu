@@ -241,14 +241,17 @@ __device__ __forceinline__ NW carve2(double *p, int N, int R, int ld, bool mixed
 
 
 template <bool MIXED>
-__global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, double wdt, double rtol,
+__global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, double wdt, double rtol,
                                                  int maxit, int ld, const double *__restrict__ b,
                                                  const double *__restrict__ hstar,
                                                  const double *Yg, const double *Tg, double *Yout,
                                                  double *Tout, double *__restrict__ FR,
                                                  double *__restrict__ hsp,
                                                  double *__restrict__ theta,
-                                                 int *__restrict__ iters, DevStats *st) {
+                                                 int *__restrict__ iters, DevStats *st,
+                                                 const float *__restrict__ pred, int ldp,
+                                                 const double *__restrict__ sc, double s_min,
+                                                 int *__restrict__ work) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int N = m.N, R = m.R, nn = N + 1, na = nn + 1;   // na: columns of the augmented matrix
@@ -256,18 +259,44 @@ __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, doubl
   NW w = carve2(smem + (size_t)wib * per_warp, N, R, ld, MIXED);
   double *J = w.J;
   const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
-  unsigned long long my_solves = 0, my_iters = 0, my_fail = 0;
+  unsigned long long my_solves = 0, my_iters = 0, my_fail = 0, my_sg = 0, my_rej = 0;
   int my_max = 0;
   unsigned bits = 0;
 
-  for (int cell = blockIdx.x * wpb + wib; cell < n; cell += gridDim.x * wpb) {
+  // cells: a fixed grid-stride share per warp, or (work != NULL) the next free cell
+  // from a global counter, which balances the per-cell iteration counts
+  auto next_cell = [&](int cur) -> int {
+    if (!work) return cur < 0 ? blockIdx.x * wpb + wib : cur + gridDim.x * wpb;
+    int c = 0;
+    if (lane == 0) c = atomicAdd(work, 1);
+    return __shfl_sync(0xffffffffu, c, 0);
+  };
+  for (int cell = next_cell(-1); cell < n; cell = next_cell(cell)) {
     for (int i = lane; i < N; i += 32) {
       w.xs[i] = Yg[(size_t)i * cs + cell];
       w.bs[i] = b[(size_t)i * cs + cell];
     }
     if (lane == 0) w.xs[N] = Tg[cell];
     const double hst = hstar[cell];
+    // learned guess: x0 = x_p + s p, judged below by its residual against the
+    // residual at x_p (whose scaled max-norm is s); x_p is kept in dx until then
+    bool judge = false;
+    double s0 = 0.0;
+    if (pred) {
+      s0 = sc[cell];
+      judge = s0 > s_min && isfinite(s0);
+    }
     __syncwarp();
+    if (judge) {
+      const float *pc = pred + (size_t)cell * ldp;
+      for (int i = lane; i < nn; i += 32) {
+        const double xp = w.xs[i];
+        w.dx[i] = xp;
+        const double f = s0 * (double)pc[i];
+        w.xs[i] = (i < N) ? xp + f : xp * (1.0 + fmin(fmax(f, -0.5), 0.5));
+      }
+      __syncwarp();
+    }
     double T = w.xs[N];
     double dprev = INFINITY;
     int it, code = 0;
@@ -356,6 +385,23 @@ __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, doubl
         if (cur >= 0) J[cur] = fma(-wdt, acc, J[cur]);
       }
       __syncwarp();
+      if (judge) {
+        // accept the learned guess only if the scaled residual max-norm drops
+        judge = false;
+        double rm = 0.0;
+        for (int i = lane; i < nn; i += 32) rm = fmax(rm, fabs(J[(size_t)i * ld + nn]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+        if (!(rm < s0)) {
+          for (int i = lane; i < nn; i += 32) w.xs[i] = w.dx[i];
+          __syncwarp();
+          T = w.xs[N];
+          ++my_rej;
+          --it;   // evaluate again at x_p; the rejected evaluation is not an iteration
+          continue;
+        }
+        ++my_sg;
+      }
       bool singular = false, fallback = false;
       if (MIXED) {
         // ---- mixed precision: FP32 factor of J, FP64 residual refinement; cells
@@ -589,6 +635,8 @@ __global__ void __launch_bounds__(128) k_newton2(DevMech m, int n, int cs, doubl
     if (my_fail) atomicAdd(&st->newton_fail, my_fail);
     atomicMax(&st->newton_max, my_max);
     if (bits) atomicOr(&st->status_bits, bits);
+    if (my_sg) atomicAdd(&st->sg_used, my_sg);
+    if (my_rej) atomicAdd(&st->sg_rejected, my_rej);
   }
 }
 
@@ -605,11 +653,20 @@ int sm_count() {
 
 }  // namespace
 
-static size_t newton_smem(const DevMech &m, bool mixed, int &ld, int &wpb) {
+// warps per block: the requested count if its shared memory fits, else 4, 2 or 1
+static size_t newton_smem(const DevMech &m, bool mixed, int &ld, int &wpb, int want = 0) {
   ld = newton_ld(m.N);
-  const size_t per_warp = newton_warp_doubles(m.N, m.R, ld, mixed);
-  wpb = (per_warp * 8 * 4 <= 200 * 1024) ? 4 : 2;
-  return (size_t)wpb * per_warp * sizeof(double);
+  const size_t per_warp = newton_warp_doubles(m.N, m.R, ld, mixed) * sizeof(double);
+  const size_t cap = 200 * 1024;
+  if (want < 1 || want > 4 || want * per_warp > cap) want = 0;
+  wpb = want ? want : (4 * per_warp <= cap ? 4 : (2 * per_warp <= cap ? 2 : 1));
+  return (size_t)wpb * per_warp;
+}
+
+int newton_max_wpb(const DevMech &m, bool mixed) {
+  int ld, wpb;
+  newton_smem(m, mixed, ld, wpb);
+  return wpb;
 }
 
 void prepare_chem_kernels(const DevMech &m) {
@@ -648,19 +705,25 @@ void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double
 void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit,
                    const double *b, const double *hstar, const double *Yg, const double *Tg,
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
-                   DevStats *st, cudaStream_t s, bool mixed) {
+                   DevStats *st, cudaStream_t s, bool mixed, const float *pred, int ldp,
+                   const double *sc, double s_min, const NewtonLaunch *cfg) {
   if (n <= 0) return;
   int ld, wpb;
-  const size_t sm = newton_smem(m, mixed, ld, wpb);
+  const size_t sm = newton_smem(m, mixed, ld, wpb, cfg ? cfg->wpb : 0);
   int grid = (n + wpb - 1) / wpb;
-  const int cap = sm_count() * (wpb == 4 ? 8 : 12);
+  const int per_sm = (cfg && cfg->blocks_per_sm > 0) ? cfg->blocks_per_sm : (wpb == 4 ? 8 : 12);
+  const int cap = sm_count() * per_sm;
   grid = grid < cap ? grid : cap;
+  int *work = (cfg && cfg->dynamic) ? cfg->work : nullptr;
+  if (work) cudaMemsetAsync(work, 0, sizeof(int), s);
   if (mixed)
     k_newton2<true><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
-                                               FR, hsp, theta, iters, st);
+                                               FR, hsp, theta, iters, st, pred, ldp, sc,
+                                               s_min, work);
   else
     k_newton2<false><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
-                                                FR, hsp, theta, iters, st);
+                                                FR, hsp, theta, iters, st, pred, ldp, sc,
+                                                s_min, work);
 }
 
 }  // namespace misdc

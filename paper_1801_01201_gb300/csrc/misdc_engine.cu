@@ -161,6 +161,10 @@ struct misdc_solver {
   double *rhsD = nullptr, *bR = nullptr, *thfD = nullptr, *thfR = nullptr;
   double *stage_state = nullptr, *stage_T = nullptr;   // host-step staging
   int *iters = nullptr;
+  // learned Newton guess (created on first use)
+  Surrogate *sg = nullptr;
+  bool sg_on = false, sg_collect = false;
+  double sg_smin = 1e-8;
   DiffWork dw{};
   DevStats *st = nullptr;
   cudaStream_t sD = nullptr, sR = nullptr;
@@ -330,9 +334,26 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
   const NodeBuf &ad = s->AD[t];
   const bool prof = s->o.profile && 2 * (s->n_used + 1) <= (int)s->prof_n.size();
   if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used], st, cudaEventRecordExternal);
+  Surrogate *sg = s->sg;
+  const float *pred = nullptr;
+  if (sg && (s->sg_on || s->sg_collect)) {
+    // features of the guess (both uses) and, for the learned guess, the forward pass
+    const bool rec = s->sg_collect;
+    mlp_features(s->m, s->cs, s->cs, wdt, s->bR, ad.phi + N * cs, guess.phi, guess.T, guess.FR,
+                 guess.phi + N * cs, sg->ldx, rec ? sg->DX : sg->Xi, sg->scale, s->sg_smin,
+                 rec ? sg->ds_count : nullptr, sg->ds_cap, sg->rowmap, st);
+    if (s->sg_on && !rec) {
+      sg->forward(sg->Xi, s->cs, sg->Oi, false, st);
+      pred = sg->Oi;
+    }
+  }
   launch_newton(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, s->bR,
                 ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR, out.hsp, out.theta,
-                s->iters, s->st, st, s->o.precision == MISDC_PREC_MIXED);
+                s->iters, s->st, st, s->o.precision == MISDC_PREC_MIXED, pred, sg ? sg->ldo : 0,
+                sg ? sg->scale : nullptr, s->sg_smin);
+  if (sg && s->sg_collect)
+    mlp_targets(s->N, s->cs, s->cs, guess.phi, guess.T, out.phi, out.T, sg->scale, sg->rowmap,
+                sg->ldo, sg->DT, st);
   if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used++ + 1], st, cudaEventRecordExternal);
   cudaMemcpyAsync(out.phi + N * cs, ad.phi + N * cs, cs * sizeof(double), cudaMemcpyDeviceToDevice, st);
   node_operators(s, out, s->thfR, st);
@@ -721,6 +742,7 @@ void misdc_destroy(misdc_solver *s) {
   if (s->sD) cudaStreamDestroy(s->sD);
   if (s->sR) cudaStreamDestroy(s->sR);
   for (void *p : s->allocs) cudaFree(p);
+  delete s->sg;
   delete s;
 }
 
@@ -801,6 +823,8 @@ misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
   memcpy(&r, &d.lin_resid_bits, sizeof(r));
   out->lin_resid_max = r;
   out->kernel_launches = s->kernels_launched;
+  out->surrogate_used = (long long)d.sg_used;
+  out->surrogate_rejected = (long long)d.sg_rejected;
   int st = MISDC_OK;
   if (d.status_bits & kBitTdiag) st = MISDC_E_TDIAG;
   else if (d.status_bits & (kBitNan | kBitSingular)) st = MISDC_E_NAN;
@@ -1024,3 +1048,229 @@ extern "C" misdc_status misdc_reaction_solve_noalloc(misdc_solver *s, double wdt
   CK(cudaGetLastError());
   return MISDC_OK;
 }
+
+// ===========================================================================
+// Learned initial guess of the reaction Newton
+// ===========================================================================
+namespace {
+
+misdc_status sg_ready(misdc_solver *s, bool need_params) {
+  if (!s) return fail(MISDC_E_INVALID, "null solver");
+  if (!s->sg) {
+    Surrogate *g = new Surrogate();
+    cudaError_t e = g->setup(s->N);
+    if (e != cudaSuccess) {
+      delete g;
+      return fail(e == cudaErrorMemoryAllocation ? MISDC_E_OOM : MISDC_E_CUDA,
+                  std::string("surrogate setup: ") + cudaGetErrorString(e));
+    }
+    mlp_prepare();
+    s->sg = g;
+  }
+  if (need_params && !s->sg->ready)
+    return fail(MISDC_E_INVALID, "surrogate parameters are not initialised or loaded");
+  return MISDC_OK;
+}
+
+// a changed step program must be captured again
+void drop_graph(misdc_solver *s) {
+  if (s->gexec) {
+    cudaStreamSynchronize(s->sD);
+    cudaGraphExecDestroy(s->gexec);
+    s->gexec = nullptr;
+  }
+}
+
+misdc_status sg_check_err(misdc_solver *s, cudaStream_t st) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, s->sg->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (e) {
+    CK(cudaMemset(s->sg->err, 0, sizeof(int)));
+    return fail(MISDC_E_TIMEOUT, "a tensor-core MMA wait gave up");
+  }
+  return MISDC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+misdc_status misdc_surrogate_dims(misdc_solver *s, int *n_in, int *ldx, int *n_hidden, int *n_out,
+                                  int *ldo, size_t *n_params) {
+  misdc_status st = sg_ready(s, false);
+  if (st) return st;
+  const Surrogate &g = *s->sg;
+  if (n_in) *n_in = g.n_in;
+  if (ldx) *ldx = g.ldx;
+  if (n_hidden) *n_hidden = g.H;
+  if (n_out) *n_out = g.n_out;
+  if (ldo) *ldo = g.ldo;
+  if (n_params) *n_params = g.n_params;
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_init(misdc_solver *s, unsigned long long seed) {
+  misdc_status st = sg_ready(s, false);
+  if (st) return st;
+  std::vector<float> h;
+  s->sg->init_params(seed, h);
+  CK(s->sg->upload(h.data(), s->sD));
+  CK(cudaStreamSynchronize(s->sD));
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_load(misdc_solver *s, const float *params, size_t n_params) {
+  misdc_status st = sg_ready(s, false);
+  if (st) return st;
+  if (!params || n_params != s->sg->n_params) return fail(MISDC_E_INVALID, "parameter count mismatch");
+  CK(s->sg->upload(params, s->sD));
+  CK(cudaStreamSynchronize(s->sD));
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_save(misdc_solver *s, float *params, size_t n_params) {
+  misdc_status st = sg_ready(s, true);
+  if (st) return st;
+  if (!params || n_params != s->sg->n_params) return fail(MISDC_E_INVALID, "parameter count mismatch");
+  CK(cudaStreamSynchronize(s->sD));
+  CK(cudaStreamSynchronize(s->sR));
+  CK(cudaMemcpy(params, s->sg->P, n_params * sizeof(float), cudaMemcpyDeviceToHost));
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_enable(misdc_solver *s, int on, double s_min) {
+  misdc_status st = sg_ready(s, on != 0);
+  if (st) return st;
+  if (!(s_min >= 0.0)) return fail(MISDC_E_INVALID, "s_min must be >= 0");
+  if (on) {
+    cudaError_t e = s->sg->ensure_inference(s->cs);
+    if (e != cudaSuccess) return fail(MISDC_E_OOM, cudaGetErrorString(e));
+  }
+  drop_graph(s);
+  s->sg_on = on != 0;
+  s->sg_smin = s_min;
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_collect(misdc_solver *s, long long capacity) {
+  misdc_status st = sg_ready(s, false);
+  if (st) return st;
+  if (capacity < 0) return fail(MISDC_E_INVALID, "capacity must be >= 0");
+  drop_graph(s);
+  if (capacity == 0) {
+    s->sg_collect = false;
+    return MISDC_OK;
+  }
+  cudaError_t e = s->sg->ensure_inference(s->cs);
+  if (e == cudaSuccess) e = s->sg->ensure_dataset(capacity);
+  if (e != cudaSuccess) return fail(MISDC_E_OOM, cudaGetErrorString(e));
+  s->sg_collect = true;
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_dataset(misdc_solver *s, long long *rows, const void **X,
+                                     const float **targets) {
+  misdc_status st = sg_ready(s, false);
+  if (st) return st;
+  long long r = 0;
+  if (s->sg->ds_count) {
+    CK(cudaStreamSynchronize(s->sD));
+    CK(cudaStreamSynchronize(s->sR));
+    unsigned long long c = 0;
+    CK(cudaMemcpy(&c, s->sg->ds_count, sizeof(c), cudaMemcpyDeviceToHost));
+    r = (long long)std::min<unsigned long long>(c, (unsigned long long)s->sg->ds_cap);
+  }
+  if (rows) *rows = r;
+  if (X) *X = s->sg->DX;
+  if (targets) *targets = s->sg->DT;
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_features(misdc_solver *s, double wdt, const double *b,
+                                      const double *hstar, const double *Yp, const double *Tp,
+                                      const double *FRp, const double *hp, int n, void *X,
+                                      double *scale, void *stream) {
+  misdc_status st = sg_ready(s, false);
+  if (st) return st;
+  if (!b || !hstar || !Yp || !Tp || !FRp || !hp || !X || !scale || n < 0 || !(wdt > 0.0))
+    return fail(MISDC_E_INVALID, "bad argument");
+  mlp_features(s->m, n, n, wdt, b, hstar, Yp, Tp, FRp, hp, s->sg->ldx, (__nv_bfloat16 *)X, scale,
+               0.0, nullptr, 0, nullptr, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_forward(misdc_solver *s, const void *X, int n, float *out,
+                                     void *stream) {
+  misdc_status st = sg_ready(s, true);
+  if (st) return st;
+  if (!X || !out || n < 0) return fail(MISDC_E_INVALID, "bad argument");
+  if (n == 0) return MISDC_OK;
+  cudaError_t e = s->sg->ensure_inference(n);
+  if (e != cudaSuccess) return fail(MISDC_E_OOM, cudaGetErrorString(e));
+  cudaStream_t us = (cudaStream_t)stream;
+  s->sg->forward((const __nv_bfloat16 *)X, n, out, false, us);
+  CK(cudaGetLastError());
+  return sg_check_err(s, us);
+}
+
+misdc_status misdc_surrogate_gradient(misdc_solver *s, const void *X, const float *targets, int n,
+                                      float *grad, float *loss, void *stream) {
+  misdc_status st = sg_ready(s, true);
+  if (st) return st;
+  if (!X || !targets || n <= 0) return fail(MISDC_E_INVALID, "bad argument");
+  Surrogate &g = *s->sg;
+  cudaError_t e = g.ensure_training(n, 1);
+  if (e != cudaSuccess) return fail(MISDC_E_OOM, cudaGetErrorString(e));
+  cudaStream_t us = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(g.Yt, targets, (size_t)n * g.ldo * sizeof(float), cudaMemcpyDeviceToDevice, us));
+  CK(cudaMemsetAsync(g.loss, 0, sizeof(float), us));
+  g.forward((const __nv_bfloat16 *)X, n, g.Ot, true, us);
+  g.backward((const __nv_bfloat16 *)X, n, g.loss, us);
+  if (grad) CK(cudaMemcpyAsync(grad, g.G, g.n_params * sizeof(float), cudaMemcpyDeviceToDevice, us));
+  if (loss) CK(cudaMemcpyAsync(loss, g.loss, sizeof(float), cudaMemcpyDeviceToDevice, us));
+  CK(cudaGetLastError());
+  return sg_check_err(s, us);
+}
+
+misdc_status misdc_surrogate_train_batch(misdc_solver *s, const void *X, const float *targets, int n,
+                                         double lr, double weight_decay, float *loss, void *stream) {
+  misdc_status st = misdc_surrogate_gradient(s, X, targets, n, nullptr, loss, stream);
+  if (st) return st;
+  s->sg->adamw((float)lr, (float)weight_decay, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_train(misdc_solver *s, int steps, int batch, double lr,
+                                   double weight_decay, unsigned long long seed,
+                                   float *loss_curve) {
+  misdc_status st = sg_ready(s, true);
+  if (st) return st;
+  if (steps <= 0 || batch <= 0 || !(lr > 0.0) || !(weight_decay >= 0.0))
+    return fail(MISDC_E_INVALID, "bad argument");
+  long long rows = 0;
+  if ((st = misdc_surrogate_dataset(s, &rows, nullptr, nullptr))) return st;
+  if (rows <= 0) return fail(MISDC_E_INVALID, "no recorded solves to train on");
+  Surrogate &g = *s->sg;
+  cudaError_t e = g.ensure_training(batch, steps);
+  if (e != cudaSuccess) return fail(MISDC_E_OOM, cudaGetErrorString(e));
+  cudaStream_t us = s->sD;
+  CK(cudaMemsetAsync(g.loss, 0, (size_t)steps * sizeof(float), us));
+  for (int t = 0; t < steps; ++t) {
+    // cosine decay of the learning rate to 5% of lr
+    const double lrt = lr * std::max(0.05, 0.5 * (1.0 + cos(M_PI * t / steps)));
+    mlp_gather(batch, rows, seed + (unsigned long long)t * (unsigned long long)batch, g.ldx, g.ldo,
+               g.DX, g.DT, g.Xt, g.Yt, us);
+    g.forward(g.Xt, batch, g.Ot, true, us);
+    g.backward(g.Xt, batch, g.loss + t, us);
+    g.adamw((float)lrt, (float)weight_decay, us);
+  }
+  CK(cudaGetLastError());
+  if (loss_curve)
+    CK(cudaMemcpyAsync(loss_curve, g.loss, (size_t)steps * sizeof(float), cudaMemcpyDeviceToHost, us));
+  return sg_check_err(s, us);
+}
+
+}  // extern "C"

@@ -2,8 +2,11 @@
 // Not part of the C ABI (see include/misdc.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <vector>
 
 #include "../../include/misdc.h"
 
@@ -29,6 +32,8 @@ struct DevStats {
   int newton_max;
   unsigned status_bits;
   unsigned long long lin_resid_bits;   // bit pattern of the largest relative residual (>= 0)
+  unsigned long long sg_used;          // cells that started Newton from the learned guess
+  unsigned long long sg_rejected;      // learned guesses rejected by the residual judge
 };
 
 // Mechanism tables in device memory (built by the engine from misdc_mech_desc).
@@ -74,10 +79,22 @@ void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double
                   double *FR, cudaStream_t s);
 // Reaction Newton (S5). b [N][cs], hstar [cs], guess Yg [N][cs], Tg [cs];
 // outputs Y, T, FR (wdot/rho at the solution), hsp [N][cs] and theta at the solution.
+// pred [n][ldp] (optional): learned correction, applied to cells with sc[c] > s_min as
+// x0 = x_p + sc p (T scaled by T_p) and kept only if the residual drops below sc[c].
+// Launch shape of the reaction Newton (chosen by the autotuner): warps per block
+// (0: largest that fits), resident-block cap per SM (0: default), and dynamic
+// cell scheduling through the device counter `work`.
+struct NewtonLaunch {
+  int wpb = 0, blocks_per_sm = 0, dynamic = 0;
+  int *work = nullptr;
+};
 void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit,
                    const double *b, const double *hstar, const double *Yg, const double *Tg,
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
-                   DevStats *st, cudaStream_t s, bool mixed = false);
+                   DevStats *st, cudaStream_t s, bool mixed = false,
+                   const float *pred = nullptr, int ldp = 0, const double *sc = nullptr,
+                   double s_min = 0.0, const NewtonLaunch *cfg = nullptr);
+int newton_max_wpb(const DevMech &m, bool mixed);
 
 // ---- grid kernels (misdc_grid.cu) ----
 struct LinComb {
@@ -112,5 +129,103 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
                      const double *rhs, double *out, DiffWork &w, int sweeps, double rho_bound,
                      double lin_rtol, DevStats *st, cudaStream_t s);
 int chebyshev_sweeps(double rho_bound, double reduction);
+
+// ---- learned Newton guess: MLP kernels (misdc_mlp.cu) ----
+namespace mlp {
+// BF16 operand: element (r, k) at p[r * sm + k * sk]; rows >= rows read as zero
+struct Operand {
+  const __nv_bfloat16 *p;
+  long long sm, sk;
+  int rows;
+};
+enum : int { kEpiStore = 0, kEpiBiasGelu = 1, kEpiGeluGrad = 2, kEpiAtomic = 3 };
+// Epilogue of the tensor-core GEMM, per output element (row, col < n_store) at row*ldo + col:
+//  kEpiStore:    out_f32 = C (+ bias)
+//  kEpiBiasGelu: z = C + bias; out_f32 = z (optional); out_bf16 = gelu(z)
+//  kEpiGeluGrad: g = C * gelu'(zsaved); out_f32 = g (optional); out_bf16 = g
+//  kEpiAtomic:   out_f32 += C (split-K)
+struct Epi {
+  int mode, n_store, ldo;
+  const float *bias;
+  float *out_f32;
+  __nv_bfloat16 *out_bf16;
+  const float *zsaved;
+};
+constexpr int kGemmSmemLaunch = 100 * 1024;
+}  // namespace mlp
+void mlp_prepare();
+// C[M x N] (+)= A[M x K] Bt^T; splits > 1 splits K over CTAs (use kEpiAtomic). err: device flag
+// set to 1 when an MMA wait gave up.
+void mlp_gemm(const mlp::Operand &A, const mlp::Operand &Bt, int M, int N, int K, int splits,
+              const mlp::Epi &ep, int *err, cudaStream_t s);
+void mlp_features(const DevMech &m, int n, int cs, double wdt, const double *b,
+                  const double *hstar, const double *Yp, const double *Tp, const double *FRp,
+                  const double *hp, int ldx, __nv_bfloat16 *X, double *scale, double s_min,
+                  unsigned long long *counter, long long cap, int *rowmap, cudaStream_t s);
+void mlp_targets(int N, int n, int cs, const double *Yp, const double *Tp, const double *Ys,
+                 const double *Ts, const double *scale, const int *rowmap, int ldt, float *tgt,
+                 cudaStream_t s);
+void mlp_mse(int B, int n_out, int ld, const float *O, const float *Yt, float *dO,
+             __nv_bfloat16 *dOb, float *loss, cudaStream_t s);
+void mlp_colsum(int rows, int n, int ld, const float *in, float *out, cudaStream_t s);
+void mlp_adamw(size_t n, size_t n_decay, float *P, const float *G, float *Mm, float *Vm,
+               __nv_bfloat16 *Pb, float lr, float beta1, float beta2, float eps, float wd,
+               float bc1, float bc2, cudaStream_t s);
+void mlp_to_bf16(size_t n, const float *in, __nv_bfloat16 *out, cudaStream_t s);
+void mlp_gather(int B, long long rows, unsigned long long seed, int ldx, int ldt,
+                const __nv_bfloat16 *DX, const float *DT, __nv_bfloat16 *X, float *Yt,
+                cudaStream_t s);
+
+// The learned-guess network of one solver: parameters, Adam moments, activation
+// buffers, and the dataset of recorded solves. Parameter vector (FP32, with a
+// BF16 copy at the same offsets): W1 [H][ldx], W2 [H][H], W3 [H][H],
+// W4 [ldo][H], then b1 [H], b2 [H], b3 [H], b4 [ldo]; W1 columns >= n_in and
+// W4 rows / b4 entries >= n_out stay zero.
+struct Surrogate {
+  int N = 0, n_in = 0, ldx = 0, H = 256, n_out = 0, ldo = 0;
+  size_t off[8] = {};
+  size_t n_params = 0, n_weights = 0;
+  float *P = nullptr, *G = nullptr, *Mm = nullptr, *Vm = nullptr;
+  __nv_bfloat16 *Pb = nullptr;
+  int *err = nullptr;
+  long long adam_t = 0;
+  bool ready = false;   // parameters initialised or loaded
+  // inference over the cells of a reaction step
+  int cap_inf = 0;
+  __nv_bfloat16 *Xi = nullptr, *Ha = nullptr, *Hb = nullptr;
+  float *Oi = nullptr;
+  double *scale = nullptr;
+  int *rowmap = nullptr;
+  // training batch
+  int cap_tr = 0;
+  __nv_bfloat16 *Xt = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *dOb = nullptr,
+                *dZa = nullptr, *dZb = nullptr;
+  float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *Ot = nullptr, *dO = nullptr, *dZf = nullptr,
+        *Yt = nullptr, *loss = nullptr;
+  int loss_cap = 0;
+  // dataset of recorded solves
+  long long ds_cap = 0;
+  unsigned long long *ds_count = nullptr;
+  __nv_bfloat16 *DX = nullptr;
+  float *DT = nullptr;
+  std::vector<void *> allocs;
+
+  ~Surrogate();
+  cudaError_t setup(int n_species);                       // sizes and parameter storage
+  void init_params(unsigned long long seed, std::vector<float> &host) const;
+  cudaError_t upload(const float *host, cudaStream_t s);   // parameters (FP32) -> device + BF16
+  cudaError_t ensure_inference(int cells);
+  cudaError_t ensure_training(int batch, int steps);
+  cudaError_t ensure_dataset(long long cap);
+  // O [n][ldo] = MLP(X [n][ldx]); train: keep pre-activations in the training buffers
+  void forward(const __nv_bfloat16 *X, int n, float *O, bool train, cudaStream_t s);
+  // gradient of the mean-squared loss of the training forward pass against Yt into G
+  void backward(const __nv_bfloat16 *X, int B, float *loss_slot, cudaStream_t s);
+  void adamw(float lr, float wd, cudaStream_t s);
+
+ private:
+  template <typename T>
+  cudaError_t alloc(T **p, size_t n);
+};
 
 }  // namespace misdc

@@ -197,3 +197,99 @@ class Solver:
         L.check(self.lib.misdc_diffusion_solve(self.handle, float(wdt), _ptr(coef_state), _ptr(rhs),
                                                _ptr(x), _stream(stream)))
         return x
+
+    # -- learned initial guess of the reaction Newton ------------------------
+    def surrogate_dims(self):
+        v = [C.c_int() for _ in range(5)]
+        n = C.c_size_t()
+        L.check(self.lib.misdc_surrogate_dims(self.handle, *[C.byref(x) for x in v], C.byref(n)))
+        n_in, ldx, hid, n_out, ldo = (x.value for x in v)
+        return dict(n_in=n_in, ldx=ldx, n_hidden=hid, n_out=n_out, ldo=ldo, n_params=n.value)
+
+    def surrogate_init(self, seed=0):
+        L.check(self.lib.misdc_surrogate_init(self.handle, int(seed)))
+
+    def surrogate_load(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        L.check(self.lib.misdc_surrogate_load(self.handle, p.ctypes.data_as(C.POINTER(C.c_float)), p.size))
+
+    def surrogate_save(self):
+        p = np.zeros(self.surrogate_dims()["n_params"], dtype=np.float32)
+        L.check(self.lib.misdc_surrogate_save(self.handle, p.ctypes.data_as(C.POINTER(C.c_float)), p.size))
+        return p
+
+    def surrogate_enable(self, on=True, s_min=1e-8):
+        L.check(self.lib.misdc_surrogate_enable(self.handle, int(bool(on)), float(s_min)))
+
+    def surrogate_collect(self, capacity):
+        L.check(self.lib.misdc_surrogate_collect(self.handle, int(capacity)))
+
+    def surrogate_dataset(self):
+        """(rows, X bf16 [rows, ldx] as int16 bits, targets f32 [rows, ldo]) copied to torch."""
+        rows = C.c_longlong()
+        xp, tp = C.c_void_p(), C.c_void_p()
+        L.check(self.lib.misdc_surrogate_dataset(self.handle, C.byref(rows), C.byref(xp), C.byref(tp)))
+        d = self.surrogate_dims()
+        r = rows.value
+        if r == 0:
+            return 0, None, None
+        X = _wrap_device(xp.value, (r, d["ldx"]), "<i2").clone().view(torch.bfloat16)
+        T = _wrap_device(tp.value, (r, d["ldo"]), "<f4").clone()
+        return r, X, T
+
+    def surrogate_train(self, steps, batch=4096, lr=1e-3, weight_decay=1e-4, seed=0):
+        curve = np.zeros(int(steps), dtype=np.float32)
+        L.check(self.lib.misdc_surrogate_train(self.handle, int(steps), int(batch), float(lr),
+                                               float(weight_decay), int(seed),
+                                               curve.ctypes.data_as(C.POINTER(C.c_float))))
+        return curve
+
+    def surrogate_features(self, wdt, b, hstar, Yp, Tp, FRp, hp, stream=None):
+        d = self.surrogate_dims()
+        b, hstar, Yp, Tp, FRp, hp = (_dev(a, self.device) for a in (b, hstar, Yp, Tp, FRp, hp))
+        n = hstar.numel()
+        X = torch.empty((n, d["ldx"]), dtype=torch.bfloat16, device=self.device)
+        sc = torch.empty(n, dtype=torch.float64, device=self.device)
+        L.check(self.lib.misdc_surrogate_features(self.handle, float(wdt), _ptr(b), _ptr(hstar), _ptr(Yp),
+                                                  _ptr(Tp), _ptr(FRp), _ptr(hp), n, _ptr(X), _ptr(sc),
+                                                  _stream(stream)))
+        return X, sc
+
+    def surrogate_forward(self, X, stream=None):
+        d = self.surrogate_dims()
+        X = X.to(device=self.device, dtype=torch.bfloat16).contiguous()
+        out = torch.empty((X.shape[0], d["ldo"]), dtype=torch.float32, device=self.device)
+        L.check(self.lib.misdc_surrogate_forward(self.handle, _ptr(X), X.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def surrogate_gradient(self, X, targets, stream=None):
+        d = self.surrogate_dims()
+        X = X.to(device=self.device, dtype=torch.bfloat16).contiguous()
+        t = targets.to(device=self.device, dtype=torch.float32).contiguous()
+        g = torch.empty(d["n_params"], dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        L.check(self.lib.misdc_surrogate_gradient(self.handle, _ptr(X), _ptr(t), X.shape[0], _ptr(g),
+                                                  _ptr(loss), _stream(stream)))
+        return g, loss
+
+    def surrogate_train_batch(self, X, targets, lr, weight_decay=0.0, stream=None):
+        X = X.to(device=self.device, dtype=torch.bfloat16).contiguous()
+        t = targets.to(device=self.device, dtype=torch.float32).contiguous()
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        L.check(self.lib.misdc_surrogate_train_batch(self.handle, _ptr(X), _ptr(t), X.shape[0], float(lr),
+                                                     float(weight_decay), _ptr(loss), _stream(stream)))
+        return loss
+
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ view of library-owned device memory (no copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 3}
+
+
+def _wrap_device(ptr, shape, typestr):
+    torch.cuda.synchronize()
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")

@@ -1,0 +1,256 @@
+"""GPU parity of the learned Newton guess: the library's tensor-core MLP
+kernels, features and AdamW (through the C ABI) against the FP64 numpy oracle
+(oracle/mlp_oracle.py), and the learned guess inside full time steps.
+
+Tolerances. The kernels store weights, inputs and hidden activations in BF16
+and accumulate in FP32; the oracle rounds the same operands to BF16 at the same
+points and accumulates exactly. What remains is the FP32 accumulation order
+(~K 2^-24 relative per dot product, K <= 256) and BF16 ties that the two sides
+round to different neighbours (one BF16 ulp, 2^-8 relative, on isolated
+elements). Outputs and gradients are compared normwise per layer,
+||a - b||_inf / ||b||_inf <= 2e-2; features elementwise within one BF16 ulp.
+The learned guess never changes the converged answer beyond the Newton
+tolerance: steps with it match steps without it within 1e-10 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp_oracle as MO
+from paper_1801_01201_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NORM_TOL = 2e-2
+
+
+def S():
+    from paper_1801_01201_gb300 import solver
+    return solver
+
+
+def nrel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def bf16_np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def setup21():
+    mech = I.make_mechanism(1802, 21, 84)
+    fl = I.flame_2d(mech, 0, n=32, dx=4e-5, radius=32 * 4e-5 / 4, delta=2 * 4e-5)
+    sv = S().Solver(mech, fl, n_sweeps=2, nu=2)
+    sv.surrogate_init(seed=11)
+    return mech, fl, sv
+
+
+def _data(lay, n, seed):
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, lay.ldx))
+    X[:, : lay.n_in] = rng.standard_normal((n, lay.n_in))
+    t = np.zeros((n, lay.ldo))
+    t[:, : lay.n_out] = rng.standard_normal((n, lay.n_out))
+    return MO.round_bf16(X), t
+
+
+@pytest.mark.parametrize("n", [1, 200, 1000])
+def test_forward_parity(setup21, n):
+    mech, fl, sv = setup21
+    d = sv.surrogate_dims()
+    lay = MO.Layout(mech.n_species)
+    assert (d["n_in"], d["ldx"], d["n_out"], d["ldo"], d["n_params"]) == (
+        lay.n_in, lay.ldx, lay.n_out, lay.ldo, lay.n_params)
+    p = sv.surrogate_save().astype(np.float64)
+    X, _ = _data(lay, n, n)
+    y_gpu = sv.surrogate_forward(torch.as_tensor(X, dtype=torch.bfloat16)).cpu().numpy()
+    y_ref, _ = MO.forward(lay, p, X, bf16=True)
+    assert np.all(y_gpu[:, lay.n_out:] == 0.0)
+    assert nrel(y_gpu[:, : lay.n_out], y_ref[:, : lay.n_out]) < NORM_TOL
+
+
+def test_forward_parity_small_mechanism():
+    mech = I.make_mechanism(1801, 9, 21)
+    fl = I.flame_1d(mech, 0, nx=64, dx=1e-4, u=1.0)
+    sv = S().Solver(mech, fl)
+    sv.surrogate_init(seed=3)
+    lay = MO.Layout(9)
+    assert sv.surrogate_dims()["ldx"] == 24
+    p = sv.surrogate_save().astype(np.float64)
+    X, _ = _data(lay, 333, 1)
+    y_gpu = sv.surrogate_forward(torch.as_tensor(X, dtype=torch.bfloat16)).cpu().numpy()
+    y_ref, _ = MO.forward(lay, p, X, bf16=True)
+    assert nrel(y_gpu[:, : lay.n_out], y_ref[:, : lay.n_out]) < NORM_TOL
+
+
+@pytest.mark.parametrize("n", [128, 1000])
+def test_gradient_parity(setup21, n):
+    mech, fl, sv = setup21
+    lay = MO.Layout(mech.n_species)
+    p = sv.surrogate_save().astype(np.float64)
+    X, t = _data(lay, n, 100 + n)
+    g_gpu, loss = sv.surrogate_gradient(torch.as_tensor(X, dtype=torch.bfloat16),
+                                        torch.as_tensor(t, dtype=torch.float32))
+    g_gpu = g_gpu.cpu().numpy().astype(np.float64)
+    g_ref, loss_ref = MO.gradient(lay, p, X, t, bf16=True)
+    assert abs(float(loss.item()) - loss_ref) <= 1e-3 * loss_ref
+    G, R = lay.unpack(g_gpu), lay.unpack(g_ref)
+    for k in ("W1", "W2", "W3", "W4", "b1", "b2", "b3", "b4"):
+        assert nrel(G[k], R[k]) < NORM_TOL, k
+    # padded entries stay exactly zero
+    assert np.all(G["W1"][:, lay.n_in:] == 0.0)
+    assert np.all(G["W4"][lay.n_out:, :] == 0.0) and np.all(G["b4"][lay.n_out:] == 0.0)
+
+
+def test_adamw_parity(setup21):
+    mech, fl, sv = setup21
+    lay = MO.Layout(mech.n_species)
+    sv.surrogate_init(seed=21)
+    X, t = _data(lay, 512, 7)
+    Xt = torch.as_tensor(X, dtype=torch.bfloat16)
+    tt = torch.as_tensor(t, dtype=torch.float32)
+    p = sv.surrogate_save().astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    lr, wd = 1e-3, 0.05
+    for step in (1, 2):
+        g, _ = sv.surrogate_gradient(Xt, tt)
+        g = g.cpu().numpy().astype(np.float64)
+        sv.surrogate_train_batch(Xt, tt, lr, wd)
+        p_gpu = sv.surrogate_save().astype(np.float64)
+        p, m, v = MO.adamw_step(lay, p, g, m, v, step, lr, wd)
+        # FP32 arithmetic of the update: a few ulp of |p| plus lr eps-level terms
+        assert np.max(np.abs(p_gpu - p)) <= 1e-6 * max(1.0, np.max(np.abs(p))), step
+        p = p_gpu
+    sv.surrogate_init(seed=11)
+
+
+def test_features_parity(setup21):
+    mech, fl, sv = setup21
+    N = mech.n_species
+    lay = MO.Layout(N)
+    adr = O.ADR(mech, fl)
+    rng = np.random.default_rng(4)
+    n = 300
+    Yp = np.abs(fl.Y[:, :n] * (1 + 0.01 * rng.standard_normal((N, n))))
+    Tp = fl.T[:n] * (1 + 0.01 * rng.standard_normal(n))
+    hp = adr.h_from_T(Yp, Tp)
+    FRp = rng.standard_normal((N, n)) * 1e2
+    wdt = 1.7e-6
+    b = Yp - wdt * FRp + 1e-5 * rng.standard_normal((N, n))
+    b[:, :10] = Yp[:, :10] - wdt * FRp[:, :10]         # nearly converged cells
+    hstar = hp + 50.0 * rng.standard_normal(n)
+    cp = np.array([sum(Yp[i, c] * adr.species_cp(i, Tp[c]) for i in range(N)) for c in range(n)])
+    f_ref, s_ref = MO.features(lay, cp, wdt, b, hstar, Yp, Tp, FRp, hp)
+    X, sc = sv.surrogate_features(wdt, b, hstar, Yp, Tp, FRp, hp)
+    np.testing.assert_allclose(sc.cpu().numpy(), s_ref, rtol=1e-12, atol=1e-300)
+    fx = bf16_np(X)
+    fr = MO.round_bf16(f_ref)
+    ulp = np.maximum(np.abs(fr), 2.0 ** -126) * 2.0 ** -7
+    bad = np.abs(fx - fr) > ulp * 1.0001
+    # the scaled forcing of the ten converged cells is round-off over round-off:
+    # only its range is fixed
+    assert np.all(np.abs(fx[:10, N + 2: 2 * N + 3]) <= 1.0)
+    bad[:10, N + 2: 2 * N + 3] = False
+    assert not bad.any(), [(int(r), int(c), fx[r, c], fr[r, c]) for r, c in zip(*np.nonzero(bad))][:8]
+    assert np.all(fx[:, lay.n_in:] == 0.0)
+
+
+def _mild_flame(n=32):
+    mech = I.make_mechanism(1802, 21, 84, logA_range=(8.0, 11.0))
+    fl = I.flame_2d(mech, 0, n=n, dx=4e-5, radius=n * 4e-5 / 4, delta=2 * 4e-5)
+    return mech, fl
+
+
+def test_dataset_rows_valid():
+    """Rows recorded during a step: features and targets of real solves."""
+    mech, fl = _mild_flame()
+    sv = S().Solver(mech, fl, n_sweeps=1, nu=1, use_graph=False)
+    sv.surrogate_collect(100000)
+    st = sv.state_from_YT(fl.Y, fl.T)
+    sv.step(st, 5e-6, 1)
+    rows, X, T = sv.surrogate_dataset()
+    lay = MO.Layout(mech.n_species)
+    assert 0 < rows <= 2 * fl.nx * fl.ny
+    x = bf16_np(X)
+    t = T.cpu().numpy()
+    assert np.all(np.isfinite(x)) and np.all(np.isfinite(t))
+    N = mech.n_species
+    sf = x[:, N + 2: 2 * N + 3]                     # scaled forcing: max-norm one
+    assert np.allclose(np.max(np.abs(sf), axis=1), 1.0, rtol=2 ** -7)
+    assert np.all(np.abs(t[:, : lay.n_out]) <= 8.0) and np.all(t[:, lay.n_out:] == 0.0)
+
+
+def test_learned_guess_fallback_and_agreement():
+    """A useless network (huge random output layer) is rejected by the residual
+    judge on every cell: the steps equal plain Newton's and take the same number
+    of iterations. A trained network leaves the answer unchanged too."""
+    mech, fl = _mild_flame()
+    dt = 5e-6
+    base = S().Solver(mech, fl)
+    s0 = base.state_from_YT(fl.Y, fl.T)
+    ref = s0.clone()
+    base.stats(reset=True)
+    base.step(ref, dt, 2)
+    st_ref = base.stats(reset=True)
+
+    bad = S().Solver(mech, fl)
+    bad.surrogate_init(seed=5)
+    lay = MO.Layout(mech.n_species)
+    p = bad.surrogate_save()
+    P = lay.unpack(p.astype(np.float64))
+    P["W4"][: lay.n_out, :] *= 1e4
+    bad.surrogate_load(lay.pack(P).astype(np.float32))
+    bad.surrogate_enable(True, s_min=0.0)
+    out = s0.clone()
+    bad.step(out, dt, 2)
+    st_bad = bad.stats(reset=True)
+    assert st_bad["status"] == 0
+    assert st_bad["surrogate_rejected"] > 0
+    assert st_bad["surrogate_used"] <= 0.01 * st_bad["surrogate_rejected"]
+    a, b_ = out.cpu().numpy(), ref.cpu().numpy()
+    for f in range(a.shape[0]):
+        assert nrel(a[f], b_[f]) < 1e-10, f
+    assert abs(st_bad["newton_iters"] - st_ref["newton_iters"]) <= 0.01 * st_ref["newton_iters"]
+
+
+def test_trained_guess_gain():
+    """Record solves, train on them with the library's kernels, and compare the
+    Newton iterations of the same steps with and without the learned guess. The
+    converged state is the same; the iteration counts are reported."""
+    mech, fl = _mild_flame(48)
+    dt = 5e-6
+    sv = S().Solver(mech, fl, use_graph=False)
+    sv.surrogate_init(seed=1)
+    s0 = sv.state_from_YT(fl.Y, fl.T)
+    warm = s0.clone()
+    sv.surrogate_collect(400000)
+    sv.step(warm, dt, 3)
+    rows, _, _ = sv.surrogate_dataset()
+    assert rows > 1000
+    sv.surrogate_collect(0)
+    curve = sv.surrogate_train(600, batch=2048, lr=2e-3, weight_decay=1e-4, seed=9)
+    assert np.all(np.isfinite(curve))
+    assert curve[-50:].mean() < 0.5 * curve[:10].mean()
+    a = warm.clone()
+    sv.stats(reset=True)
+    sv.step(a, dt, 2)
+    plain = sv.stats(reset=True)
+    sv.surrogate_enable(True, s_min=1e-8)
+    b = warm.clone()
+    sv.step(b, dt, 2)
+    learned = sv.stats(reset=True)
+    sv.surrogate_enable(False, 0.0)
+    A, B = a.cpu().numpy(), b.cpu().numpy()
+    for f in range(A.shape[0]):
+        assert nrel(B[f], A[f]) < 1e-10, f
+    assert learned["status"] == 0 and plain["status"] == 0
+    print("\nplain iters/solve %.4f  learned iters/solve %.4f  used %d rejected %d  loss %.3g -> %.3g"
+          % (plain["newton_iters"] / plain["newton_solves"],
+             learned["newton_iters"] / learned["newton_solves"], learned["surrogate_used"],
+             learned["surrogate_rejected"], curve[:10].mean(), curve[-50:].mean()))
+    assert learned["surrogate_used"] > 0
