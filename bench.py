@@ -1,13 +1,24 @@
-"""Benchmark: MISDC cell-updates/s of the concurrent MISDC sweep (CISDCQ-2, FP64).
+"""Benchmark: MISDC cell-updates/s, learned + mixed-precision concurrent MISDC
+against the plain FP64 sweep, at 1e-8 relative error.
 
 Workload (default): 2D periodic 256x256 flame, synthetic 21-species/84-reaction
 mechanism, Taylor-Green velocity (2 m/s), circular tanh kernel of radius 2 mm,
 3 Gauss-Lobatto nodes, 4 sweeps, nu = 2, dt = 5e-6 s. One "step" = one time
 step of every cell (all nodes, sweeps and nested iterations).
 
+Three variants of the same workload are timed back to back, each from the same
+initial state: the plain FP64 sweep, the mixed-precision sweep, and the learned
++ mixed sweep (the headline `value`). The learned guess is trained first, with
+the library's own kernels, on solves recorded from a different flame of the
+same mechanism; training is setup, outside the timed region. The headline's
+error against the FP64 sweep after the same steps is reported per field.
+
+Other workloads: --workload flame2d_512_n53 | flame3d_128_n21 | flame1d_128_n9 |
+batch64_2d (64 independent flames, one graph launch per step, autotuned).
+
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank advances its own flame (weak scaling, no collective
-on the data path); rank 0 prints one JSON line.
+Under torchrun each rank advances its own copy of the workload (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -28,31 +39,28 @@ sys.path.insert(0, ROOT)
 METRIC = "MISDC cell-updates/s, learned+mixed vs plain FP64 sweep, at 1e-8 rel err"
 UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12      # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_newton launch on this workload,
-# from the ncu capture summarised in profiles/k_newton_flame2d_256_n21.md; None when the
-# kernel has changed since that capture.
-NEWTON_TRAFFIC_BYTES = 23.5e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one reaction-Newton launch, per
+# (workload, variant), from the ncu captures summarised under profiles/; a variant
+# missing here has changed since its capture (traffic reported as null).
+NEWTON_TRAFFIC_BYTES = {}
 
 
-def workload_config(name, w, mech, fl, scheme, precision):
-    return {"workload": name, "grid": [fl.nx, fl.ny, fl.nz], "cells": fl.nx * fl.ny * fl.nz,
-            "species": mech.n_species, "reactions": mech.n_reactions, "nodes": w["nodes"],
-            "sweeps": w["sweeps"], "nu": w["nu"], "dt": w["dt"], "scheme": scheme,
-            "precision": precision, "l2": "flushed between steps (256 MB write)"}
-
-
-def newton_flops(N, R, nnz):
-    """FP64 flops (FMA = 2) of one Newton iteration and of the final rate evaluation
-    per cell, exp/log calls counted separately."""
+def newton_flops(N, R, nnz, mixed=False):
+    """Flops (FMA = 2) of one Newton iteration and of the final evaluation per cell,
+    split into FP64 and FP32 parts; exp/log calls counted separately."""
     n = N + 1
     thermo = N * 34                       # h, s, cp polynomials + scalings
     rates = R * 30                        # ln k_f, Delta g, ln K_c, products, q, dq/dT
     jac = nnz * 22 + 4 * N                # Jacobian rows + temperature row
-    lu = (2 * n ** 3) // 3 + 2 * n * n    # augmented elimination + back substitution
-    it = thermo + rates + jac + lu + 6 * n
+    lu = (2 * n ** 3) // 3 + 2 * n * n    # elimination + substitutions
     fin = thermo + R * 14 + 2 * nnz
-    return it, fin, 2 * R + 1, 2 * R + 1   # flops/iter, flops/final, exp+log per iter, per final
-
+    if mixed:   # FP32 factor and solves; FP64 residual refinement (about two rounds)
+        f64 = thermo + rates + jac + 2 * (2 * n * n) + 6 * n
+        f32 = lu + 2 * (2 * n * n)
+    else:
+        f64 = thermo + rates + jac + lu + 6 * n
+        f32 = 0
+    return f64, f32, fin, 2 * R + 1, 2 * R + 1
 
 class ClockSampler:
     def __init__(self, gpu_index=0):
@@ -98,11 +106,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def cpu_oracle_rate(name, cells_side, steps=1):
-    """Time the CPU oracle on a bounded sample of the workload (same mechanism, dt,
-    sweeps, nu; a cells_side^2 flame). Returns (cell-updates/s, seconds, cells)."""
-    import oracle as O
+def oracle_sample(name, cells_side):
+    """Mechanism, flame, dt and time-integration settings of a bounded CPU sample of
+    the workload: a cells_side^2 (cells_side^3 in 3D) flame of the same mechanism."""
     from paper_1801_01201_gb300 import inputs as I
+    if name in I.BATCHES:
+        b = I.BATCHES[name]
+        mech = I.make_mechanism(*b["mechs"][1])
+        n = cells_side
+        fl = I.flame_2d(mech, b["seed"], n=n, dx=b["dx"], amp=b["amp"], radius=n * b["dx"] / 4,
+                        delta=4 * b["dx"])
+        return mech, fl, 0.5 * sum(b["dt"]), b
     w = I.WORKLOADS[name]
     mech = I.make_mechanism(w["seed"], *w["mech"])
     g = dict(w["grid"])
@@ -111,74 +125,216 @@ def cpu_oracle_rate(name, cells_side, steps=1):
         fl = I.flame_2d(mech, w["seed"], n=n, dx=g["dx"], amp=g["amp"], radius=n * g["dx"] / 4,
                         delta=4 * g["dx"])
     elif w["dim"] == 3:
-        fl = I.flame_3d(mech, w["seed"], n=cells_side, dx=g["dx"], radius=cells_side * g["dx"] / 4)
+        n = max(4, round(cells_side ** (2.0 / 3.0)))
+        fl = I.flame_3d(mech, w["seed"], n=n, dx=g["dx"], radius=n * g["dx"] / 4)
     else:
-        fl = I.flame_1d(mech, w["seed"], nx=cells_side, dx=g["dx"])
+        fl = I.flame_1d(mech, w["seed"], nx=cells_side * cells_side, dx=g["dx"])
+    return mech, fl, w["dt"], w
+
+
+def cpu_oracle_rate(name, cells_side, steps=1):
+    """Time the CPU oracle on a bounded sample of the workload. Returns
+    (cell-updates/s, seconds, cells, description)."""
+    import oracle as O
+    mech, fl, dt, w = oracle_sample(name, cells_side)
     ad = O.ADR(mech, fl)
     phi = ad.state_from_YT(fl.Y, fl.T)
     t0 = time.perf_counter()
-    ad.step(phi, w["dt"], "CISDCQ", w["nodes"] - 1, w["sweeps"], w["nu"], n_steps=steps)
+    ad.step(phi, dt, "CISDCQ", w["nodes"] - 1, w["sweeps"], w["nu"], n_steps=steps)
     el = time.perf_counter() - t0
-    return fl.cells * steps / el, el, fl.cells
-
-
-def time_variant(Solver, mech, fl, w, args, dev, state0, flush, stream, precision):
-    """Cell-updates/s of the same workload with another precision (same timing rules)."""
-    import torch
-    sv = Solver(mech, fl, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"], scheme=args.scheme,
-                precision=precision, profile=True, device=dev)
-    state = state0.clone()
-    for _ in range(args.warmup):
-        sv.step(state, w["dt"], 1)
-    torch.cuda.synchronize()
-    sv.stats(reset=True)
-    ms, nms = [], 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sv.step(state, w["dt"], 1, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        nms += sv.stage_times()["newton_ms"]
-    st = sv.stats(reset=True)
-    cells = fl.nx * fl.ny * fl.nz
-    return {"precision": precision, "value": cells * args.steps / (sum(ms) / 1e3), "unit": UNIT,
-            "ms_per_step": sum(ms) / args.steps, "newton_ms_per_step": nms / args.steps,
-            "newton_iters_per_solve": st["newton_iters"] / max(st["newton_solves"], 1),
-            "status": st["status_name"]}
+    desc = "%d-cell %dD flame, mechanism %d/%d, dt %.3g, %d sweeps, nu %d" % (
+        fl.cells, fl.dim, mech.n_species, mech.n_reactions, dt, w["sweeps"], w["nu"])
+    return fl.cells * steps / el, el, fl.cells, desc
 
 
 def run_reference(args, rank, world):
     """Reference arm: the plain serial CPU oracle on this host, bounded samples."""
     if rank != 0:
         return 0
-    from paper_1801_01201_gb300 import inputs as I
     name = args.workload
-    w = I.WORKLOADS[name]
     side = args.ref_side
     for _ in range(args.warmup):
         cpu_oracle_rate(name, side, 1)
-    times, cells = [], 0
+    times, cells, desc = [], 0, ""
     for _ in range(args.steps):
-        r, el, cells = cpu_oracle_rate(name, side, 1)
+        r, el, cells, desc = cpu_oracle_rate(name, side, 1)
         times.append(el)
     tot = sum(times)
     value = cells * args.steps / tot
-    mech = I.make_mechanism(w["seed"], *w["mech"])
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": name, "species": mech.n_species, "reactions": mech.n_reactions,
-                       "sweeps": w["sweeps"], "nu": w["nu"], "dt": w["dt"], "scheme": "CISDCQ"},
+            "data": "synthetic", "config": {"workload": name, "scheme": "CISDCQ"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%dx%d-cell flame of the same mechanism, dt, sweeps and nu per step" % (side, side)},
+                             "sample": "one time step per step of a " + desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def entries_for(name):
+    """[(mechanism, flame, dt)] and the time-integration settings of a workload."""
+    from paper_1801_01201_gb300 import inputs as I
+    if name in I.BATCHES:
+        b = I.BATCHES[name]
+        return I.build_batch(name), b
+    mech, fl, w = I.build_workload(name)
+    return [(mech, fl, w["dt"])], w
+
+
+def training_flame(mech, fl):
+    """A different flame of the same mechanism for recording training solves:
+    another seed and kernel, at most 128^2 (48^3) cells."""
+    from paper_1801_01201_gb300 import inputs as I
+    if fl.dim == 2:
+        n = min(fl.nx, 128)
+        L = n * fl.dx
+        return I.flame_2d(mech, 4242, n=n, dx=fl.dx, amp=2.0, radius=0.28 * L,
+                          delta=min(2e-4, L / 16), centre=(0.41 * L, 0.57 * L))
+    if fl.dim == 3:
+        n = min(fl.nx, 48)
+        return I.flame_3d(mech, 4242, n=n, dx=fl.dx, urms=3.0, radius=0.28 * n * fl.dx)
+    return I.flame_1d(mech, 4242, nx=fl.nx, dx=fl.dx)
+
+
+def train_params(Solver, mech, fl, dt, w, dev, args):
+    """Record solves on a training flame, train the MLP, return (params, info)."""
+    import torch
+    tf = training_flame(mech, fl)
+    sv = Solver(mech, tf, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"], scheme=args.scheme,
+                precision="fp64", device=dev)
+    sv.surrogate_init(seed=args.seed)
+    x = sv.state_from_YT(tf.Y, tf.T)
+    sv.surrogate_collect(args.train_rows)
+    t0 = time.perf_counter()
+    sv.step(x, dt, args.collect_steps)
+    rows, _, _ = sv.surrogate_dataset()
+    sv.surrogate_collect(0)
+    curve = sv.surrogate_train(args.train_steps, batch=args.train_batch, lr=args.train_lr,
+                               weight_decay=1e-4, seed=args.seed)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    p = sv.surrogate_save()
+    info = {"rows": rows, "train_steps": args.train_steps, "batch": args.train_batch,
+            "loss_first": float(curve[:10].mean()), "loss_last": float(curve[-50:].mean()),
+            "seconds": el, "flame_cells": tf.cells}
+    sv.close()
+    return p, info
+
+
+class Runner:
+    """One variant of the workload: a solver per flame (and a batch for several)."""
+
+    def __init__(self, entries, w, args, dev, precision, params=None, tune=False):
+        import torch
+        from paper_1801_01201_gb300.solver import Solver, Batch
+        self.entries = entries
+        self.solvers = []
+        self.states0 = []
+        for mech, fl, dt in entries:
+            sv = Solver(mech, fl, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"],
+                        scheme=args.scheme, precision=precision, profile=len(entries) == 1, device=dev)
+            st = sv.state_from_YT(fl.Y, fl.T)
+            if params is not None:
+                sv.surrogate_load(params[id(mech)])
+                sv.surrogate_enable(True, s_min=args.s_min)
+            if tune:
+                T = torch.as_tensor(fl.T, device=dev).contiguous()
+                sv.autotune(st, T, dt)
+            self.solvers.append(sv)
+            self.states0.append(st)
+        self.dts = [dt for _, _, dt in entries]
+        self.batch = Batch(self.solvers) if len(entries) > 1 else None
+        self.states = [x.clone() for x in self.states0]
+        self.cells = sum(fl.cells for _, fl, _ in entries)
+
+    def step(self, stream=None):
+        if self.batch is not None:
+            self.batch.step(self.states, self.dts, 1, stream=stream)
+        else:
+            self.solvers[0].step(self.states[0], self.dts[0], 1, stream=stream)
+
+    def stats(self):
+        if self.batch is not None:
+            return self.batch.stats(reset=True)
+        return self.solvers[0].stats(reset=True)
+
+    def stage_times(self):
+        if self.batch is not None:
+            return None
+        return self.solvers[0].stage_times()
+
+
+def max_over_ranks(total_ms, dist=None, device=None):
+    """The slowest rank's timed-region length (ms): the whole job ends with it."""
+    if not dist:
+        return total_ms
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, cells, steps, total_ms):
+    """Cell-updates/s of the whole job: every rank advances its own copy of the
+    workload (weak scaling), so the units are world x cells x steps."""
+    return world * cells * steps / (total_ms / 1e3)
+
+
+def timed(runner, args, flush, stream, dist=None, clocks=None):
+    """W untimed steps, then K steps timed with CUDA events (L2 flushed between)."""
+    import torch
+    for _ in range(args.warmup):
+        runner.step()
+    torch.cuda.synchronize()
+    runner.stats()
+    if dist:
+        dist.barrier()
+    if clocks:
+        clocks.start()
+    torch.cuda.synchronize()
+    ms, newton_ms, newton_n, diff_ms = [], 0.0, 0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        runner.step(stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        t = runner.stage_times()
+        if t:
+            newton_ms += t["newton_ms"]
+            newton_n += t["newton_launches"]
+            diff_ms += t["diffusion_ms"]
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    if dist:
+        dist.barrier()
+    st = runner.stats()
+    total = max_over_ranks(sum(ms), dist, flush.device)
+    return dict(total_ms=total, ms=ms, newton_ms=newton_ms, newton_launches=newton_n,
+                diffusion_ms=diff_ms, stats=st, clocks=clk)
+
+
+def field_errors(solver, a, b):
+    """Relative error of state a against b: mass fractions max|dY| / max|Y| over all
+    species and cells (the Newton tolerance is absolute in Y, so trace species
+    are converged to ~1e-12 absolute in either precision; the worst per-species
+    ratio ||dY_i|| / ||Y_i|| is reported beside it), the temperature and h."""
+    N = solver.N
+    A, B = a.cpu().numpy(), b.cpu().numpy()
+    den = np.maximum(np.max(np.abs(B), axis=1), 1e-300)
+    e = np.max(np.abs(A - B), axis=1) / den
+    Ta = solver.temperature(a[:N], a[N]).cpu().numpy()
+    Tb = solver.temperature(b[:N], b[N]).cpu().numpy()
+    return {"Y": float(np.max(np.abs(A[:N] - B[:N])) / np.max(np.abs(B[:N]))),
+            "Y_species_worst": float(e[:N].max()), "h": float(e[N]),
+            "T": float(np.max(np.abs(Ta - Tb)) / np.max(np.abs(Tb)))}
 
 
 def main():
@@ -189,15 +345,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="flame2d_256_n21")
     ap.add_argument("--scheme", default="CISDCQ")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--compare-mixed", type=int, default=1,
-                    help="also time the mixed-precision sweep (reported as an extra field)")
+    ap.add_argument("--headline", default="learned_mixed", choices=["learned_mixed", "mixed", "fp64"])
+    ap.add_argument("--autotune", type=int, default=-1, help="1/0; default: on for batches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-side", type=int, default=64)
     ap.add_argument("--ref-side", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--collect-steps", type=int, default=3)
+    ap.add_argument("--train-rows", type=int, default=4_000_000)
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--train-batch", type=int, default=8192)
+    ap.add_argument("--train-lr", type=float, default=2e-3)
+    ap.add_argument("--s-min", type=float, default=1e-8)
+    ap.add_argument("--seed", type=int, default=7)
     args = ap.parse_args()
-
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -211,109 +372,160 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    from paper_1801_01201_gb300 import inputs as I
     from paper_1801_01201_gb300.solver import Solver
 
     name = args.workload
-    mech, fl, w = I.build_workload(name)
-    sv = Solver(mech, fl, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"], scheme=args.scheme,
-                precision=args.precision, profile=True, device=dev)
-    cells = fl.nx * fl.ny * fl.nz
-    state0 = sv.state_from_YT(fl.Y, fl.T)
-    state = state0.clone()
+    entries, w = entries_for(name)
+    tune = (len(entries) > 1) if args.autotune < 0 else bool(args.autotune)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    for _ in range(args.warmup):
-        sv.step(state, w["dt"], 1)
-    torch.cuda.synchronize()
-    sv.stats(reset=True)
-    clocks = ClockSampler(local)
-    if rank == 0:
-        clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    step_ms, newton_ms, newton_launches, diff_ms, diff_launches = [], 0.0, 0, 0.0, 0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sv.step(state, w["dt"], 1, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        t = sv.stage_times()
-        newton_ms += t["newton_ms"]
-        newton_launches += t["newton_launches"]
-        diff_ms += t["diffusion_ms"]
-        diff_launches += t["diffusion_launches"]
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop() if rank == 0 else None
-    st = sv.stats(reset=True)
-    total_ms = sum(step_ms)
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = tt.item()
-    value = world * cells * args.steps / (total_ms / 1e3)
+    # plain FP64 sweep
+    plain = Runner(entries, w, args, dev, "fp64", tune=tune)
+    r_plain = timed(plain, args, flush, stream, dist)
+    variants = {"fp64": (plain, r_plain)}
+    # mixed precision
+    if args.headline in ("mixed", "learned_mixed"):
+        mixed = Runner(entries, w, args, dev, "mixed", tune=tune)
+        variants["mixed"] = (mixed, timed(mixed, args, flush, stream, dist))
+    # learned + mixed: train one network per mechanism, then time
+    train_info = None
+    if args.headline == "learned_mixed":
+        params, train_info = {}, {}
+        for mech, fl, dt in entries:
+            if id(mech) not in params:
+                p, info = train_params(Solver, mech, fl, dt, w, dev, args)
+                params[id(mech)] = p
+                train_info["%d/%d" % (mech.n_species, mech.n_reactions)] = info
+        lm = Runner(entries, w, args, dev, "mixed", params=params, tune=tune)
+        variants["learned_mixed"] = (lm, timed(lm, args, flush, stream, dist))
+    head, r_head = variants[args.headline]
+    # the headline again with the clock sampler running (its own timed region)
+    clocks = ClockSampler(local) if rank == 0 else None
+    head.states = [x.clone() for x in head.states0]
+    r_head = timed(head, args, flush, stream, dist, clocks)
+    cells = head.cells
+    value = whole_job_rate(world, cells, args.steps, r_head["total_ms"])
 
-    # end to end through the host-buffer entry point (H2D + step + D2H per step)
-    host = state0.cpu().pin_memory()
-    e2e_times = []
-    for _ in range(args.e2e_steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sv.step_host(host, w["dt"], 1)
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times)
-    e2e_bytes = state0.numel() * 8
-    e2e_value = world * cells * len(e2e_times) / e2e_s if e2e_times else None
+    # accuracy of each variant against the FP64 sweep after the same steps
+    errs = {}
+    for k, (rn, _) in variants.items():
+        if k == "fp64":
+            continue
+        errs[k] = [field_errors(rn.solvers[i], rn.states[i], plain.states[i]) for i in range(len(entries))]
+        errs[k] = {f: max(e[f] for e in errs[k]) for f in ("Y", "Y_species_worst", "h", "T")}
+
+    # end to end through the host-buffer entry point (single-flame workloads)
+    e2e = None
+    if len(entries) == 1:
+        sv = head.solvers[0]
+        host = head.states0[0].cpu().pin_memory()
+        tms = []
+        for _ in range(args.e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sv.step_host(host, head.dts[0], 1)
+            tms.append(time.perf_counter() - t0)
+        nbytes = head.states0[0].numel() * 8
+        e2e = {"value": world * cells * len(tms) / sum(tms) if tms else None, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    else:
+        # batches: copy every flame's state in and out around the device step
+        hosts = [x.cpu().pin_memory() for x in head.states0]
+        tms = []
+        for _ in range(args.e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for h, d in zip(hosts, head.states):
+                d.copy_(h, non_blocking=True)
+            head.step()
+            for h, d in zip(hosts, head.states):
+                h.copy_(d, non_blocking=True)
+            torch.cuda.synchronize()
+            tms.append(time.perf_counter() - t0)
+        nbytes = sum(x.numel() * 8 for x in head.states0)
+        e2e = {"value": world * cells * len(tms) / sum(tms) if tms else None, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
 
-    nnz = int(np.count_nonzero(mech.nu_r - mech.nu_f))
-    f_it, f_fin, x_it, x_fin = newton_flops(mech.n_species, mech.n_reactions, nnz)
-    flops = st["newton_iters"] * f_it + st["newton_solves"] * f_fin
-    exps = st["newton_iters"] * x_it + st["newton_solves"] * x_fin
-    per_launch_flops = flops / max(newton_launches, 1)
-    avg_launch_s = newton_ms / 1e3 / max(newton_launches, 1)
-    achieved = per_launch_flops / avg_launch_s / 1e12
-    roofline = {"kernel": "k_newton (reaction Newton, warp per cell)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NEWTON_TRAFFIC_BYTES,
-                "peak_source": "FP64 nominal from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                "exp_log_calls_per_launch": exps / max(newton_launches, 1),
-                "newton_ms_per_step": newton_ms / args.steps,
-                "diffusion_ms_per_step": diff_ms / args.steps,
-                "newton_iters_per_solve": st["newton_iters"] / max(st["newton_solves"], 1)}
+    st = r_head["stats"]
+    roofline = None
+    if len(entries) == 1 and r_head["newton_launches"]:
+        mech = entries[0][0]
+        nnz = int(np.count_nonzero(mech.nu_r - mech.nu_f))
+        mixedk = args.headline != "fp64"
+        f64, f32, fin, x_it, x_fin = newton_flops(mech.n_species, mech.n_reactions, nnz, mixedk)
+        flops64 = st["newton_iters"] * f64 + st["newton_solves"] * fin
+        per_launch = flops64 / r_head["newton_launches"]
+        avg_s = r_head["newton_ms"] / 1e3 / r_head["newton_launches"]
+        achieved = per_launch / avg_s / 1e12
+        roofline = {"kernel": "k_newton2<%s> (reaction Newton, warp per cell)" % ("mixed" if mixedk else "fp64"),
+                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NEWTON_TRAFFIC_BYTES.get(
+                        (name, args.headline)),
+                    "peak_source": "FP64 nominal from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                    "flops_counted": "FP64 only (FP32 LU work of the mixed kernel excluded)",
+                    "newton_ms_per_step": r_head["newton_ms"] / args.steps,
+                    "diffusion_ms_per_step": r_head["diffusion_ms"] / args.steps,
+                    "newton_launch_ms": avg_s * 1e3,
+                    "exp_log_calls_per_launch": (st["newton_iters"] * x_it + st["newton_solves"] * x_fin)
+                    / r_head["newton_launches"]}
     cpu = None
-    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
+    if not args.no_cpu_baseline:
         try:
-            r, el, c = cpu_oracle_rate(name, args.cpu_side, 1)
+            r, el, c, desc = cpu_oracle_rate(name, args.cpu_side, 1)
             cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "one time step of a %dx%d-cell flame, same mechanism/dt/sweeps/nu (%.1f s)" % (args.cpu_side, args.cpu_side, el)}
+                   "sample": "one time step of a %s (%.1f s)" % (desc, el)}
         except Exception as e:   # the baseline is informative, never fatal
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % e}
+
+    def summary(k):
+        rn, r = variants[k]
+        s_ = r["stats"]
+        d = {"value": whole_job_rate(world, rn.cells, args.steps, r["total_ms"]), "unit": UNIT,
+             "ms_per_step": r["total_ms"] / args.steps,
+             "newton_iters_per_solve": s_["newton_iters"] / max(s_["newton_solves"], 1),
+             "status": s_["status_name"]}
+        if r["newton_launches"]:
+            d["newton_ms_per_step"] = r["newton_ms"] / args.steps
+        if k == "learned_mixed":
+            d["surrogate_used"] = s_["surrogate_used"]
+            d["surrogate_rejected"] = s_["surrogate_rejected"]
+        if k in errs:
+            d["rel_err_vs_fp64"] = errs[k]
+        return d
+
+    dtype = {"fp64": "f64", "mixed": "f64+f32", "learned_mixed": "f64+f32, bf16 MLP"}[args.headline]
+    cfg = {"workload": name, "flames": len(entries), "cells": cells, "nodes": w["nodes"],
+           "sweeps": w["sweeps"], "nu": w["nu"], "scheme": args.scheme, "variant": args.headline,
+           "autotuned": tune, "l2": "flushed between steps (256 MB write)"}
+    if len(entries) == 1:
+        mech, fl, dt = entries[0]
+        cfg.update({"grid": [fl.nx, fl.ny, fl.nz], "species": mech.n_species,
+                    "reactions": mech.n_reactions, "dt": dt})
+    else:
+        cfg["mechanisms"] = sorted({"%d/%d" % (m.n_species, m.n_reactions) for m, _, _ in entries})
+    acc_ok = None
+    if args.headline in errs:
+        e = errs[args.headline]
+        acc_ok = e["Y"] <= 1e-8 and e["T"] <= 1e-6
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(name, w, mech, fl, args.scheme, args.precision),
-            "clocks": clk, "gpu_launches": st["kernel_launches"],
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_bytes,
-                    "d2h_bytes_per_step": e2e_bytes},
-            "roofline": roofline, "cpu_baseline": cpu,
-            "status": st["status_name"], "newton_fail": st["newton_fail"]}
-    if args.compare_mixed and args.precision == "fp64":
-        line["mixed"] = time_variant(Solver, mech, fl, w, args, dev, state0, flush, stream, "mixed")
+            "warmup": args.warmup, "ms_per_step": r_head["total_ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": cfg, "clocks": r_head["clocks"],
+            "gpu_launches": st["kernel_launches"], "e2e": e2e, "roofline": roofline,
+            "cpu_baseline": cpu, "status": st["status_name"],
+            "accuracy_vs_fp64_ok": acc_ok,
+            "variants": {k: summary(k) for k in variants},
+            "speedup_vs_plain_fp64": value / summary("fp64")["value"] / world}
+    if train_info:
+        line["training"] = train_info
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -112,6 +112,8 @@ typedef struct misdc_stats {
   long long kernel_launches;    /* library kernels launched by misdc_step */
   long long surrogate_used;     /* cells whose Newton started from the learned guess */
   long long surrogate_rejected; /* learned guesses the residual judge rejected */
+  long long newton_fp64_fallbacks; /* mixed precision: iterations whose FP32 factor
+                                      was replaced by the FP64 one */
 } misdc_stats;
 
 typedef struct misdc_solver misdc_solver;
@@ -260,9 +262,19 @@ misdc_status misdc_surrogate_features(misdc_solver *s, double wdt, const double 
                                       const double *hstar, const double *Yp, const double *Tp,
                                       const double *FRp, const double *hp, int n, void *X,
                                       double *scale, void *stream);
-/* out FP32 [n][ldo] = MLP(X BF16 [n][ldx]). */
+/* out FP32 [n][ldo] = MLP(X BF16 [n][ldx]): the fused inference kernel (all
+ * four layers per 128-row tile on chip). */
 misdc_status misdc_surrogate_forward(misdc_solver *s, const void *X, int n, float *out,
                                      void *stream);
+/* Same result from one tensor-core GEMM launch per layer (the training kernels). */
+misdc_status misdc_surrogate_forward_layers(misdc_solver *s, const void *X, int n, float *out,
+                                            void *stream);
+/* What a reaction step uses: features of n cells computed from the state (as in
+ * misdc_surrogate_features) and the network's output, in one fused launch.
+ * out FP32 [n][ldo], scale [n] (= s). */
+misdc_status misdc_surrogate_guess(misdc_solver *s, double wdt, const double *b, const double *hstar,
+                                   const double *Yp, const double *Tp, const double *FRp,
+                                   const double *hp, int n, float *out, double *scale, void *stream);
 /* Gradient of the mean-squared loss (mean over n rows and n_out outputs) against
  * targets FP32 [n][ldo]: grad [n_params] and loss [1] (device, may be NULL). */
 misdc_status misdc_surrogate_gradient(misdc_solver *s, const void *X, const float *targets, int n,
@@ -270,6 +282,42 @@ misdc_status misdc_surrogate_gradient(misdc_solver *s, const void *X, const floa
 /* misdc_surrogate_gradient followed by one AdamW step with learning rate lr. */
 misdc_status misdc_surrogate_train_batch(misdc_solver *s, const void *X, const float *targets, int n,
                                          double lr, double weight_decay, float *loss, void *stream);
+
+/* ---- launch-shape autotuner -------------------------------------------------
+ * Launch shapes of the two hot kernels. The paper has no counterpart (it runs
+ * on CPU cores); these are GPU scheduling choices that leave results unchanged. */
+typedef struct misdc_tuning {
+  int newton_warps_per_block;   /* cells (one warp each) per block, 1..4; 0 = largest that fits */
+  int newton_blocks_per_sm;     /* cap on resident blocks per SM; 0 = default */
+  int newton_dynamic;           /* 1: warps take the next cell from a global counter */
+  int cheb_block;               /* threads per block of the smoother sweep; 0 = 256 */
+  double newton_ms;             /* autotune: best time of the probe reaction solve */
+  double cheb_ms;               /* autotune: best time of the probe diffusion solve */
+} misdc_tuning;
+/* Time candidate shapes on this solver's grid and mechanism (a reaction step of
+ * weight max_m dt q~I_mm from `state` with temperature T, and a diffusion solve
+ * of the same weight; device arrays) and keep the fastest. Synchronous; resets
+ * the statistics. */
+misdc_status misdc_autotune(misdc_solver *s, const double *state, const double *T, double dt,
+                            misdc_tuning *out);
+misdc_status misdc_get_tuning(misdc_solver *s, misdc_tuning *out);
+misdc_status misdc_set_tuning(misdc_solver *s, const misdc_tuning *t);
+
+/* ---- batched stepping of independent flames ----------------------------------
+ * A batch holds n solvers (each with its own mechanism, grid and options) and
+ * advances all of them with one CUDA graph launch per time step: the flames'
+ * step programs run concurrently, each on its own pair of streams, so that many
+ * small grids fill the GPU together. The graph is captured on the first call and
+ * again whenever a state or T pointer or a dt changes. states[i] / T[i]
+ * (T may be NULL, or hold NULL entries) are device arrays of solver i; dts[i]
+ * its time step. The solvers must not record solves while batched. */
+typedef struct misdc_batch misdc_batch;
+misdc_status misdc_batch_create(misdc_solver *const *solvers, int n, misdc_batch **out);
+void misdc_batch_destroy(misdc_batch *b);
+misdc_status misdc_batch_step(misdc_batch *b, double *const *states, double *const *T,
+                              const double *dts, int n_steps, void *stream);
+/* Statistics summed over the batch's solvers (synchronises). */
+misdc_status misdc_batch_stats(misdc_batch *b, misdc_stats *out, int reset);
 
 const char *misdc_last_error(void);
 

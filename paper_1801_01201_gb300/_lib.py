@@ -44,12 +44,21 @@ class Stats(C.Structure):
                 ("newton_fail", C.c_longlong), ("newton_max", C.c_int), ("status", C.c_int),
                 ("lin_sweeps", C.c_longlong), ("lin_resid_max", C.c_double),
                 ("kernel_launches", C.c_longlong), ("surrogate_used", C.c_longlong),
-                ("surrogate_rejected", C.c_longlong)]
+                ("surrogate_rejected", C.c_longlong), ("newton_fp64_fallbacks", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
         return d
+
+
+class Tuning(C.Structure):
+    _fields_ = [("newton_warps_per_block", C.c_int), ("newton_blocks_per_sm", C.c_int),
+                ("newton_dynamic", C.c_int), ("cheb_block", C.c_int), ("newton_ms", C.c_double),
+                ("cheb_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 EXPORTS = ["misdc_default_opts", "misdc_create", "misdc_destroy", "misdc_step", "misdc_step_host",
@@ -60,7 +69,8 @@ EXPORTS = ["misdc_default_opts", "misdc_create", "misdc_destroy", "misdc_step", 
            "misdc_surrogate_load", "misdc_surrogate_save", "misdc_surrogate_enable",
            "misdc_surrogate_collect", "misdc_surrogate_dataset", "misdc_surrogate_train",
            "misdc_surrogate_features", "misdc_surrogate_forward", "misdc_surrogate_gradient",
-           "misdc_surrogate_train_batch"]
+           "misdc_surrogate_train_batch", "misdc_surrogate_forward_layers", "misdc_surrogate_guess", "misdc_autotune", "misdc_get_tuning", "misdc_set_tuning",
+           "misdc_batch_create", "misdc_batch_destroy", "misdc_batch_step", "misdc_batch_stats"]
 
 _lib = None
 
@@ -113,11 +123,21 @@ def load(build_if_missing: bool = True):
     L.misdc_surrogate_features.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp, vp, C.c_int, vp, vp, vp]
     L.misdc_surrogate_forward.argtypes = [vp, vp, C.c_int, vp, vp]
     L.misdc_surrogate_gradient.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp]
+    L.misdc_surrogate_forward_layers.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.misdc_surrogate_guess.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp, vp, C.c_int, vp, vp, vp]
     L.misdc_surrogate_train_batch.argtypes = [vp, vp, vp, C.c_int, C.c_double, C.c_double, vp, vp]
+    L.misdc_autotune.argtypes = [vp, vp, vp, C.c_double, C.POINTER(Tuning)]
+    L.misdc_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.misdc_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.misdc_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
+    L.misdc_batch_destroy.argtypes = [vp]
+    L.misdc_batch_destroy.restype = None
+    L.misdc_batch_step.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), dp, C.c_int, vp]
+    L.misdc_batch_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
     L.misdc_last_error.restype = C.c_char_p
     L.misdc_last_error.argtypes = []
     for name in EXPORTS:
-        if name not in ("misdc_default_opts", "misdc_destroy", "misdc_last_error"):
+        if name not in ("misdc_default_opts", "misdc_destroy", "misdc_last_error", "misdc_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

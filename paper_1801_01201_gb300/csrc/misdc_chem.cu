@@ -5,6 +5,8 @@
 // Layout: every per-cell array is field-major, [field][cs] with a cell stride cs.
 #include <math.h>
 
+#include <mutex>
+
 #include "misdc_internal.cuh"
 
 namespace misdc {
@@ -251,6 +253,8 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
                                                  int *__restrict__ iters, DevStats *st,
                                                  const float *__restrict__ pred, int ldp,
                                                  const double *__restrict__ sc, double s_min,
+                                                 const double *__restrict__ FRp,
+                                                 const double *__restrict__ hp,
                                                  int *__restrict__ work) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
   NW w = carve2(smem + (size_t)wib * per_warp, N, R, ld, MIXED);
   double *J = w.J;
   const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
-  unsigned long long my_solves = 0, my_iters = 0, my_fail = 0, my_sg = 0, my_rej = 0;
+  unsigned long long my_solves = 0, my_iters = 0, my_fail = 0, my_sg = 0, my_rej = 0, my_fb = 0;
   int my_max = 0;
   unsigned bits = 0;
 
@@ -386,13 +390,28 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       }
       __syncwarp();
       if (judge) {
-        // accept the learned guess only if the scaled residual max-norm drops
+        // Accept the learned guess only if the residual drops, measured in the
+        // Jacobi-scaled max-norm max_i |r_i / J_ii| (species rows; the temperature
+        // row as the relative temperature change) with the Jacobian at the guess
+        // (a diagonal stand-in for the natural norm |J^{-1} r| of Newton's method,
+        // which a plain residual norm would overweight along stiff directions).
+        // The residual at x_p comes from the stored reaction term of x_p.
         judge = false;
-        double rm = 0.0;
-        for (int i = lane; i < nn; i += 32) rm = fmax(rm, fabs(J[(size_t)i * ld + nn]));
+        double rm = 0.0, rp = 0.0;
+        for (int i = lane; i < nn; i += 32) {
+          // the temperature row is already in units of dT/T
+          const double dinv = (i < N) ? 1.0 / fabs(J[(size_t)i * ld + i]) : 1.0;
+          rm = fmax(rm, fabs(J[(size_t)i * ld + nn]) * dinv);
+          const double r0 = (i < N) ? w.bs[i] - w.dx[i] + wdt * FRp[(size_t)i * cs + cell]
+                                    : (hst - hp[cell]) * sT;
+          rp = fmax(rp, fabs(r0) * dinv);
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
-        if (!(rm < s0)) {
+        for (int o = 16; o > 0; o >>= 1) {
+          rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+          rp = fmax(rp, __shfl_xor_sync(0xffffffffu, rp, o));
+        }
+        if (!(rm < rp)) {
           for (int i = lane; i < nn; i += 32) w.xs[i] = w.dx[i];
           __syncwarp();
           T = w.xs[N];
@@ -517,6 +536,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           if (ref == 5) fallback = true;
         }
       }
+      if (MIXED && fallback) ++my_fb;
       if (!MIXED || fallback) {
         // ---- FP64 LU with partial pivoting
         for (int k = 0; k < nn; ++k) {
@@ -637,6 +657,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     if (bits) atomicOr(&st->status_bits, bits);
     if (my_sg) atomicAdd(&st->sg_used, my_sg);
     if (my_rej) atomicAdd(&st->sg_rejected, my_rej);
+    if (my_fb) atomicAdd(&st->fp64_fallbacks, my_fb);
   }
 }
 
@@ -669,14 +690,22 @@ int newton_max_wpb(const DevMech &m, bool mixed) {
   return wpb;
 }
 
+// The shared-memory limit is an attribute of the kernel, not of a launch: every
+// solver in the process shares it, so it only ever grows to the largest need.
 void prepare_chem_kernels(const DevMech &m) {
+  static std::mutex mu;
+  static size_t have[3] = {0, 0, 0};
+  std::lock_guard<std::mutex> lock(mu);
   int ld, wpb;
-  size_t sm = newton_smem(m, false, ld, wpb);
-  cudaFuncSetAttribute(k_newton2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  sm = newton_smem(m, true, ld, wpb);
-  cudaFuncSetAttribute(k_newton2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const size_t smr = (size_t)4 * (5 * m.N + 4 * m.R) * sizeof(double);
-  cudaFuncSetAttribute(k_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  const size_t need[3] = {newton_smem(m, false, ld, wpb), newton_smem(m, true, ld, wpb),
+                          (size_t)4 * (5 * m.N + 4 * m.R) * sizeof(double)};
+  const void *fn[3] = {(const void *)k_newton2<false>, (const void *)k_newton2<true>,
+                       (const void *)k_rates};
+  for (int k = 0; k < 3; ++k)
+    if (need[k] > have[k]) {
+      cudaFuncSetAttribute(fn[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need[k]);
+      have[k] = need[k];
+    }
 }
 
 void launch_temperature(const DevMech &m, int n, int cs, const double *Y, const double *h,
@@ -706,7 +735,8 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                    const double *b, const double *hstar, const double *Yg, const double *Tg,
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
                    DevStats *st, cudaStream_t s, bool mixed, const float *pred, int ldp,
-                   const double *sc, double s_min, const NewtonLaunch *cfg) {
+                   const double *sc, double s_min, const double *FRp, const double *hp,
+                   const NewtonLaunch *cfg) {
   if (n <= 0) return;
   int ld, wpb;
   const size_t sm = newton_smem(m, mixed, ld, wpb, cfg ? cfg->wpb : 0);
@@ -719,11 +749,11 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
   if (mixed)
     k_newton2<true><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
                                                FR, hsp, theta, iters, st, pred, ldp, sc,
-                                               s_min, work);
+                                               s_min, FRp, hp, work);
   else
     k_newton2<false><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
                                                 FR, hsp, theta, iters, st, pred, ldp, sc,
-                                                s_min, work);
+                                                s_min, FRp, hp, work);
 }
 
 }  // namespace misdc

@@ -165,6 +165,8 @@ struct misdc_solver {
   Surrogate *sg = nullptr;
   bool sg_on = false, sg_collect = false;
   double sg_smin = 1e-8;
+  // reaction-Newton launch shape (autotuned)
+  NewtonLaunch nl{};
   DiffWork dw{};
   DevStats *st = nullptr;
   cudaStream_t sD = nullptr, sR = nullptr;
@@ -336,21 +338,21 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
   if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used], st, cudaEventRecordExternal);
   Surrogate *sg = s->sg;
   const float *pred = nullptr;
-  if (sg && (s->sg_on || s->sg_collect)) {
-    // features of the guess (both uses) and, for the learned guess, the forward pass
-    const bool rec = s->sg_collect;
+  if (sg && s->sg_collect) {
+    // record the features of every solve worth learning (plain Newton follows)
     mlp_features(s->m, s->cs, s->cs, wdt, s->bR, ad.phi + N * cs, guess.phi, guess.T, guess.FR,
-                 guess.phi + N * cs, sg->ldx, rec ? sg->DX : sg->Xi, sg->scale, s->sg_smin,
-                 rec ? sg->ds_count : nullptr, sg->ds_cap, sg->rowmap, st);
-    if (s->sg_on && !rec) {
-      sg->forward(sg->Xi, s->cs, sg->Oi, false, st);
-      pred = sg->Oi;
-    }
+                 guess.phi + N * cs, sg->ldx, sg->DX, sg->scale, s->sg_smin, sg->ds_count,
+                 sg->ds_cap, sg->rowmap, st);
+  } else if (sg && s->sg_on) {
+    // learned guess: features and the four layers in one fused kernel
+    mlp_fused_forward(*sg, &s->m, s->cs, wdt, s->bR, ad.phi + N * cs, guess.phi, guess.T,
+                      guess.FR, guess.phi + N * cs, sg->scale, nullptr, s->cs, sg->Oi, st);
+    pred = sg->Oi;
   }
   launch_newton(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, s->bR,
                 ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR, out.hsp, out.theta,
                 s->iters, s->st, st, s->o.precision == MISDC_PREC_MIXED, pred, sg ? sg->ldo : 0,
-                sg ? sg->scale : nullptr, s->sg_smin);
+                sg ? sg->scale : nullptr, s->sg_smin, guess.FR, guess.phi + N * cs, &s->nl);
   if (sg && s->sg_collect)
     mlp_targets(s->N, s->cs, s->cs, guess.phi, guess.T, out.phi, out.T, sg->scale, sg->rowmap,
                 sg->ldo, sg->DT, st);
@@ -674,6 +676,7 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   }
   if (s->alloc(&s->rhsD, F * cs) || s->alloc(&s->bR, F * cs) || s->alloc(&s->thfD, 3 * cs) ||
       s->alloc(&s->thfR, 3 * cs) || s->alloc(&s->iters, cs) || s->alloc(&s->st, 1) ||
+      s->alloc(&s->nl.work, 1) ||
       s->alloc(&s->dw.thf, 3 * cs) || s->alloc(&s->dw.invdiag, F * cs) || s->alloc(&s->dw.xa, F * cs) ||
       s->alloc(&s->dw.xb, F * cs) || s->alloc(&s->dw.xc, F * cs) ||
       s->alloc(&s->dw.rho_bits, 1) || s->alloc(&s->dw.kdev, 1) || s->alloc(&s->dw.omega, kMaxCheb))
@@ -825,6 +828,7 @@ misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
   out->kernel_launches = s->kernels_launched;
   out->surrogate_used = (long long)d.sg_used;
   out->surrogate_rejected = (long long)d.sg_rejected;
+  out->newton_fp64_fallbacks = (long long)d.fp64_fallbacks;
   int st = MISDC_OK;
   if (d.status_bits & kBitTdiag) st = MISDC_E_TDIAG;
   else if (d.status_bits & (kBitNan | kBitSingular)) st = MISDC_E_NAN;
@@ -896,9 +900,11 @@ misdc_status misdc_reaction_solve(misdc_solver *s, double wdt, const double *b, 
   double *hsp = nullptr, *th = nullptr;
   CK(cudaMallocAsync(&hsp, N * n * sizeof(double), (cudaStream_t)stream));
   CK(cudaMallocAsync(&th, n * sizeof(double), (cudaStream_t)stream));
+  NewtonLaunch nl = s->nl;
+  nl.dynamic = 0;   // the counter belongs to the step's stream
   launch_newton(s->m, n, n, wdt, s->o.newton_rtol, s->o.newton_maxit, b, hstar, x, x + N * n, x,
                 x + N * n, FR, hsp, th, iters, s->st, (cudaStream_t)stream,
-                s->o.precision == MISDC_PREC_MIXED);
+                s->o.precision == MISDC_PREC_MIXED, nullptr, 0, nullptr, 0.0, nullptr, nullptr, &nl);
   cudaFreeAsync(hsp, (cudaStream_t)stream);
   cudaFreeAsync(th, (cudaStream_t)stream);
   CK(cudaGetLastError());
@@ -1210,7 +1216,36 @@ misdc_status misdc_surrogate_forward(misdc_solver *s, const void *X, int n, floa
   cudaError_t e = s->sg->ensure_inference(n);
   if (e != cudaSuccess) return fail(MISDC_E_OOM, cudaGetErrorString(e));
   cudaStream_t us = (cudaStream_t)stream;
+  mlp_fused_forward(*s->sg, nullptr, 0, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, (const __nv_bfloat16 *)X, n, out, us);
+  CK(cudaGetLastError());
+  return sg_check_err(s, us);
+}
+
+misdc_status misdc_surrogate_forward_layers(misdc_solver *s, const void *X, int n, float *out,
+                                            void *stream) {
+  misdc_status st = sg_ready(s, true);
+  if (st) return st;
+  if (!X || !out || n < 0) return fail(MISDC_E_INVALID, "bad argument");
+  if (n == 0) return MISDC_OK;
+  cudaError_t e = s->sg->ensure_inference(n);
+  if (e != cudaSuccess) return fail(MISDC_E_OOM, cudaGetErrorString(e));
+  cudaStream_t us = (cudaStream_t)stream;
   s->sg->forward((const __nv_bfloat16 *)X, n, out, false, us);
+  CK(cudaGetLastError());
+  return sg_check_err(s, us);
+}
+
+misdc_status misdc_surrogate_guess(misdc_solver *s, double wdt, const double *b, const double *hstar,
+                                   const double *Yp, const double *Tp, const double *FRp,
+                                   const double *hp, int n, float *out, double *scale, void *stream) {
+  misdc_status st = sg_ready(s, true);
+  if (st) return st;
+  if (!b || !hstar || !Yp || !Tp || !FRp || !hp || !out || !scale || n < 0 || !(wdt > 0.0))
+    return fail(MISDC_E_INVALID, "bad argument");
+  if (n == 0) return MISDC_OK;
+  cudaStream_t us = (cudaStream_t)stream;
+  mlp_fused_forward(*s->sg, &s->m, n, wdt, b, hstar, Yp, Tp, FRp, hp, scale, nullptr, n, out, us);
   CK(cudaGetLastError());
   return sg_check_err(s, us);
 }
@@ -1271,6 +1306,268 @@ misdc_status misdc_surrogate_train(misdc_solver *s, int steps, int batch, double
   if (loss_curve)
     CK(cudaMemcpyAsync(loss_curve, g.loss, (size_t)steps * sizeof(float), cudaMemcpyDeviceToHost, us));
   return sg_check_err(s, us);
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Autotuner of the launch shapes, and batched stepping of many flames
+// ===========================================================================
+namespace {
+
+// time one enqueue (ms) with events on the stream
+template <typename F>
+float time_ms(cudaStream_t st, cudaEvent_t a, cudaEvent_t b, F &&f) {
+  cudaEventRecord(a, st);
+  f();
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+}  // namespace
+
+struct misdc_batch {
+  std::vector<misdc_solver *> sv;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr;
+  std::vector<cudaEvent_t> evDone;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<double *> g_state, g_T;
+  std::vector<double> g_dt;
+  long long kernels_per_step = 0, kernels_launched = 0;
+};
+
+extern "C" {
+
+misdc_status misdc_get_tuning(misdc_solver *s, misdc_tuning *t) {
+  if (!s || !t) return fail(MISDC_E_INVALID, "null argument");
+  memset(t, 0, sizeof(*t));
+  t->newton_warps_per_block = s->nl.wpb;
+  t->newton_blocks_per_sm = s->nl.blocks_per_sm;
+  t->newton_dynamic = s->nl.dynamic;
+  t->cheb_block = s->dw.cheb_block;
+  return MISDC_OK;
+}
+
+misdc_status misdc_set_tuning(misdc_solver *s, const misdc_tuning *t) {
+  if (!s || !t) return fail(MISDC_E_INVALID, "null argument");
+  if (t->newton_warps_per_block < 0 || t->newton_warps_per_block > 4 || t->newton_blocks_per_sm < 0 ||
+      t->newton_blocks_per_sm > 32 || (t->cheb_block && (t->cheb_block < 32 || t->cheb_block > 1024 ||
+                                                         t->cheb_block % 32)))
+    return fail(MISDC_E_INVALID, "tuning out of range");
+  drop_graph(s);
+  s->nl.wpb = t->newton_warps_per_block;
+  s->nl.blocks_per_sm = t->newton_blocks_per_sm;
+  s->nl.dynamic = t->newton_dynamic ? 1 : 0;
+  s->dw.cheb_block = t->cheb_block;
+  return MISDC_OK;
+}
+
+misdc_status misdc_autotune(misdc_solver *s, const double *state, const double *T, double dt,
+                            misdc_tuning *out) {
+  if (!s || !state || !T) return fail(MISDC_E_INVALID, "null argument");
+  if (!(dt > 0.0)) return fail(MISDC_E_INVALID, "dt must be > 0");
+  configure_dt(s, dt);
+  const size_t cs = s->cs, N = s->N, F = N + 1;
+  cudaStream_t st = s->sD;
+  CK(cudaStreamSynchronize(s->sD));
+  CK(cudaStreamSynchronize(s->sR));
+  double *x = nullptr, *x0 = nullptr, *FR = nullptr, *hsp = nullptr, *th = nullptr, *out_s = nullptr;
+  double *Ts = nullptr, *theta = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  auto cleanup = [&]() {
+    for (double *p : {x, x0, FR, hsp, th, out_s, Ts, theta}) if (p) cudaFree(p);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  };
+  if (cudaMalloc(&x, F * cs * 8) || cudaMalloc(&x0, F * cs * 8) || cudaMalloc(&FR, N * cs * 8) ||
+      cudaMalloc(&hsp, N * cs * 8) || cudaMalloc(&th, cs * 8) || cudaMalloc(&out_s, F * cs * 8) ||
+      cudaMalloc(&Ts, cs * 8) || cudaMalloc(&theta, cs * 8) || cudaEventCreate(&a) ||
+      cudaEventCreate(&b)) {
+    cleanup();
+    return fail(MISDC_E_OOM, "autotune scratch");
+  }
+  // the reaction step of the largest implicit weight from the given state:
+  // b = Y, h* = h, guess (Y, T)
+  double wdt = 0.0;
+  for (int t = 0; t < s->tab.M; ++t) wdt = std::max(wdt, dt * s->tab.QI[t][t]);
+  cudaMemcpyAsync(x0, state, N * cs * 8, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(x0 + N * cs, T, cs * 8, cudaMemcpyDeviceToDevice, st);
+  const bool mixed = s->o.precision == MISDC_PREC_MIXED;
+  const int wmax = newton_max_wpb(s->m, mixed);
+  NewtonLaunch best = s->nl;
+  float best_ms = 1e30f;
+  auto run = [&](const NewtonLaunch &c) {
+    cudaMemcpyAsync(x, x0, F * cs * 8, cudaMemcpyDeviceToDevice, st);
+    return time_ms(st, a, b, [&] {
+      launch_newton(s->m, (int)cs, (int)cs, wdt, s->o.newton_rtol, s->o.newton_maxit, state,
+                    state + N * cs, x, x + N * cs, x, x + N * cs, FR, hsp, th, nullptr, s->st, st,
+                    mixed, nullptr, 0, nullptr, 0.0, nullptr, nullptr, &c);
+    });
+  };
+  // candidates (warps per block, blocks per SM, dynamic): the default shape, then
+  // dynamic scheduling at 16 resident warps per SM in blocks of 4, 2 and 1 warps
+  const int cand[][3] = {{0, 0, 0}, {4, 4, 1}, {2, 8, 1}, {1, 16, 1}, {2, 8, 0}, {1, 16, 0}};
+  {
+    NewtonLaunch c = s->nl;
+    c.wpb = 0; c.blocks_per_sm = 0; c.dynamic = 0;
+    run(c);   // warm-up
+  }
+  for (const auto &cd : cand) {
+    if (cd[0] > wmax) continue;
+    NewtonLaunch c = s->nl;
+    c.wpb = cd[0]; c.blocks_per_sm = cd[1]; c.dynamic = cd[2];
+    const float ms = run(c);
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  // smoother block size on a diffusion solve of the same size, coefficients at the state
+  launch_temperature(s->m, (int)cs, (int)cs, state, state + N * cs, T, Ts, theta, hsp, s->st, st);
+  int best_tb = 256;
+  float best_d = 1e30f;
+  for (int tb : {128, 256, 512}) {
+    s->dw.cheb_block = tb;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2; ++rep) {
+      const float t1 = time_ms(st, a, b, [&] {
+        diffusion_solve(s->m, s->g, s->i0, wdt, theta, state, out_s, s->dw, s->cheb_sweeps,
+                        s->rho_bound, s->o.lin_rtol, s->st, st);
+      });
+      if (rep) ms += t1;
+    }
+    if (ms < best_d) { best_d = ms; best_tb = tb; }
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return fail(MISDC_E_CUDA, cudaGetErrorString(e));
+  CK(cudaMemset(s->st, 0, sizeof(DevStats)));
+  drop_graph(s);
+  s->nl = best;
+  s->dw.cheb_block = best_tb;
+  if (out) {
+    misdc_get_tuning(s, out);
+    out->newton_ms = best_ms;
+    out->cheb_ms = best_d;
+  }
+  return MISDC_OK;
+}
+
+misdc_status misdc_batch_create(misdc_solver *const *solvers, int n, misdc_batch **out) {
+  if (!solvers || n <= 0 || !out) return fail(MISDC_E_INVALID, "bad argument");
+  for (int i = 0; i < n; ++i) {
+    if (!solvers[i]) return fail(MISDC_E_INVALID, "null solver");
+    for (int j = 0; j < i; ++j)
+      if (solvers[j] == solvers[i]) return fail(MISDC_E_INVALID, "a solver appears twice");
+  }
+  misdc_batch *b = new misdc_batch();
+  b->sv.assign(solvers, solvers + n);
+  b->evDone.assign(n, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->evIn, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->evOut, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->evFork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < n; ++i)
+    ok = cudaEventCreateWithFlags(&b->evDone[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    misdc_batch_destroy(b);
+    return fail(MISDC_E_CUDA, "batch streams/events");
+  }
+  *out = b;
+  return MISDC_OK;
+}
+
+void misdc_batch_destroy(misdc_batch *b) {
+  if (!b) return;
+  if (b->cs) cudaStreamSynchronize(b->cs);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (cudaEvent_t e : b->evDone) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {b->evIn, b->evOut, b->evFork}) if (e) cudaEventDestroy(e);
+  if (b->cs) cudaStreamDestroy(b->cs);
+  delete b;
+}
+
+misdc_status misdc_batch_step(misdc_batch *b, double *const *states, double *const *T,
+                              const double *dts, int n_steps, void *stream) {
+  if (!b || !states || !dts || n_steps < 0) return fail(MISDC_E_INVALID, "bad argument");
+  const int n = (int)b->sv.size();
+  for (int i = 0; i < n; ++i) {
+    if (!states[i] || !(dts[i] > 0.0)) return fail(MISDC_E_INVALID, "bad state or dt");
+    if (b->sv[i]->sg_collect) return fail(MISDC_E_INVALID, "batched steps do not record solves");
+  }
+  if (n_steps == 0) return MISDC_OK;
+  bool stale = !b->gexec;
+  for (int i = 0; i < n && !stale; ++i)
+    stale = b->g_state[i] != states[i] || b->g_T[i] != (T ? T[i] : nullptr) || b->g_dt[i] != dts[i];
+  if (stale) {
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    for (int i = 0; i < n; ++i) configure_dt(b->sv[i], dts[i]);
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(b->evFork, b->cs);
+    for (int i = 0; i < n; ++i) {
+      misdc_solver *s = b->sv[i];
+      s->n_used = s->d_used = 0;
+      cudaStreamWaitEvent(s->sD, b->evFork, 0);
+      enqueue_step(s, states[i], T ? T[i] : nullptr, dts[i]);
+      cudaEventRecord(b->evDone[i], s->sD);
+      cudaStreamWaitEvent(b->cs, b->evDone[i], 0);
+    }
+    cudaError_t ec = cudaStreamEndCapture(b->cs, &graph);
+    if (ec != cudaSuccess) return fail(MISDC_E_CUDA, std::string("batch capture: ") + cudaGetErrorString(ec));
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    b->kernels_per_step = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      cudaGraphNodeGetType(nd, &ty);
+      if (ty == cudaGraphNodeTypeKernel) ++b->kernels_per_step;
+    }
+    ec = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) return fail(MISDC_E_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(ec));
+    b->g_state.assign(states, states + n);
+    b->g_T.assign(n, nullptr);
+    if (T) b->g_T.assign(T, T + n);
+    b->g_dt.assign(dts, dts + n);
+  }
+  cudaStream_t us = (cudaStream_t)stream;
+  CK(cudaEventRecord(b->evIn, us));
+  CK(cudaStreamWaitEvent(b->cs, b->evIn, 0));
+  for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(b->gexec, b->cs));
+  b->kernels_launched += b->kernels_per_step * n_steps;
+  CK(cudaEventRecord(b->evOut, b->cs));
+  CK(cudaStreamWaitEvent(us, b->evOut, 0));
+  return MISDC_OK;
+}
+
+misdc_status misdc_batch_stats(misdc_batch *b, misdc_stats *out, int reset) {
+  if (!b || !out) return fail(MISDC_E_INVALID, "null argument");
+  CK(cudaStreamSynchronize(b->cs));
+  misdc_stats sum;
+  memset(&sum, 0, sizeof(sum));
+  for (misdc_solver *s : b->sv) {
+    misdc_stats t;
+    misdc_status st = misdc_get_stats(s, &t, reset);
+    if (st) return st;
+    sum.newton_solves += t.newton_solves;
+    sum.newton_iters += t.newton_iters;
+    sum.newton_fail += t.newton_fail;
+    sum.newton_max = std::max(sum.newton_max, t.newton_max);
+    if (!sum.status) sum.status = t.status;
+    sum.lin_sweeps += t.lin_sweeps;
+    sum.lin_resid_max = std::max(sum.lin_resid_max, t.lin_resid_max);
+    sum.surrogate_used += t.surrogate_used;
+    sum.surrogate_rejected += t.surrogate_rejected;
+    sum.newton_fp64_fallbacks += t.newton_fp64_fallbacks;
+  }
+  sum.kernel_launches = b->kernels_launched;
+  if (reset) b->kernels_launched = 0;
+  *out = sum;
+  return MISDC_OK;
 }
 
 }  // extern "C"

@@ -451,7 +451,8 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
   for (int it = 0; it < sweeps; ++it) {
     const double *xk = (it == 0) ? rhs : bufs[(it - 1) % 3];
     const double *xkm1 = (it <= 1) ? rhs : bufs[(it - 2) % 3];
-    k_cheb<<<dim3((cs + 255) / 256, (fm.nfs + kChebFields - 1) / kChebFields), 256, 0, s>>>(
+    const int tb = (w.cheb_block >= 32 && w.cheb_block <= 1024) ? w.cheb_block : 256;
+    k_cheb<<<dim3((cs + tb - 1) / tb, (fm.nfs + kChebFields - 1) / kChebFields), tb, 0, s>>>(
         g, fm, w.thf, w.invdiag, rhs, xk, xkm1, bufs[it % 3], it, w.kdev, w.omega);
   }
   const int *kdev = w.kdev;

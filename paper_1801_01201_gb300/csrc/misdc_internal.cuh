@@ -34,6 +34,7 @@ struct DevStats {
   unsigned long long lin_resid_bits;   // bit pattern of the largest relative residual (>= 0)
   unsigned long long sg_used;          // cells that started Newton from the learned guess
   unsigned long long sg_rejected;      // learned guesses rejected by the residual judge
+  unsigned long long fp64_fallbacks;   // mixed-precision iterations that fell back to FP64 LU
 };
 
 // Mechanism tables in device memory (built by the engine from misdc_mech_desc).
@@ -80,7 +81,9 @@ void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double
 // Reaction Newton (S5). b [N][cs], hstar [cs], guess Yg [N][cs], Tg [cs];
 // outputs Y, T, FR (wdot/rho at the solution), hsp [N][cs] and theta at the solution.
 // pred [n][ldp] (optional): learned correction, applied to cells with sc[c] > s_min as
-// x0 = x_p + sc p (T scaled by T_p) and kept only if the residual drops below sc[c].
+// x0 = x_p + sc p (T scaled by T_p) and kept only if the Jacobi-scaled residual at x0 is
+// below that at the guess x_p, whose reaction term FRp [N][cs] and enthalpy hp [cs] give
+// its residual without a rate evaluation.
 // Launch shape of the reaction Newton (chosen by the autotuner): warps per block
 // (0: largest that fits), resident-block cap per SM (0: default), and dynamic
 // cell scheduling through the device counter `work`.
@@ -93,7 +96,8 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
                    DevStats *st, cudaStream_t s, bool mixed = false,
                    const float *pred = nullptr, int ldp = 0, const double *sc = nullptr,
-                   double s_min = 0.0, const NewtonLaunch *cfg = nullptr);
+                   double s_min = 0.0, const double *FRp = nullptr, const double *hp = nullptr,
+                   const NewtonLaunch *cfg = nullptr);
 int newton_max_wpb(const DevMech &m, bool mixed);
 
 // ---- grid kernels (misdc_grid.cu) ----
@@ -122,6 +126,7 @@ struct DiffWork {
   double *omega;                  // [kMaxCheb] Chebyshev weights
   // multigrid levels (level 0 = this grid, compact [solved field][cells] storage)
   int levels, cycles;
+  int cheb_block;   // threads per block of the Chebyshev sweep (autotuned; 0 = 256)
   DevGrid lg[8];
   double *lthf[8], *linvdiag[8], *lb[8], *lx[8], *lr[8], *ly[8];
 };
@@ -158,6 +163,14 @@ void mlp_prepare();
 // set to 1 when an MMA wait gave up.
 void mlp_gemm(const mlp::Operand &A, const mlp::Operand &Bt, int M, int N, int K, int splits,
               const mlp::Epi &ep, int *err, cudaStream_t s);
+struct Surrogate;
+// Fused inference over n rows: with m != NULL the features of cells [0, n) are
+// computed from the reaction step's state (scale s written to `scale`),
+// otherwise the BF16 rows X [n][ldx] are the input; out [n][ldo] FP32.
+void mlp_fused_forward(const Surrogate &g, const DevMech *m, int cs, double wdt, const double *b,
+                       const double *hstar, const double *Yp, const double *Tp, const double *FRp,
+                       const double *hp, double *scale, const __nv_bfloat16 *X, int n, float *out,
+                       cudaStream_t s);
 void mlp_features(const DevMech &m, int n, int cs, double wdt, const double *b,
                   const double *hstar, const double *Yp, const double *Tp, const double *FRp,
                   const double *hp, int ldx, __nv_bfloat16 *X, double *scale, double s_min,

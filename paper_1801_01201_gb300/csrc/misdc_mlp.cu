@@ -415,6 +415,193 @@ __global__ void k_gather(int B, long long rows, unsigned long long seed, int ldx
   for (int j = threadIdx.x; j < ldt; j += blockDim.x) Yt[(size_t)bi * ldt + j] = DT[(size_t)r * ldt + j];
 }
 
+// ---------------------------------------------------------------------------
+// Fused inference: features (or given BF16 rows) -> four layers -> outputs, one
+// CTA per 128 rows. Activations never leave the SM: each layer's FP32
+// accumulator lives in tensor memory, its GELU epilogue writes the BF16 result
+// back into shared memory as the next layer's A operand. Weights stream through
+// a two-stage shared-memory ring in K chunks of 64, the copy of chunk k+1
+// overlapping the MMAs of chunk k.
+// ---------------------------------------------------------------------------
+constexpr int kFThreads = 256;               // 8 warps: 2 per TMEM lane quadrant
+constexpr int kFKmax = 256;                  // widest layer input
+constexpr int kFSmemA = kTileM * kFKmax * 2; // 64 KB, A operand, core-matrix layout
+constexpr int kFSmemB = kMaxN * kTileK * 2;  // 32 KB per weight stage
+constexpr int kFSmem = kFSmemA + 2 * kFSmemB + 64;
+
+struct FusedArgs {
+  // features from the state (FEAT) ...
+  DevMech m;
+  int cs;
+  double wdt;
+  const double *b, *hstar, *Yp, *Tp, *FRp, *hp;
+  double *scale;
+  // ... or BF16 rows X [n][ldx]
+  const __nv_bfloat16 *X;
+  int n, ldx, k1;          // rows, feature row length, layer-1 K (ldx rounded up to 64)
+  const __nv_bfloat16 *W[4];
+  const float *bias[4];
+  int ldo;                 // output width (layer-4 N, multiple of 16)
+  float *out;              // [n][ldo]
+  int *err;
+};
+
+// element (r, k) of the 128 x 256 A buffer: ((r/8)*32 + k/8)*64 + (r%8)*8 + k%8
+__device__ __forceinline__ int a_index(int r, int k) {
+  return (((r >> 3) << 5) + (k >> 3)) * 64 + ((r & 7) << 3) + (k & 7);
+}
+
+template <bool FEAT>
+__global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(FusedArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smraw);
+  __nv_bfloat16 *sB0 = reinterpret_cast<__nv_bfloat16 *>(smraw + kFSmemA);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smraw + kFSmemA + 2 * kFSmemB);   // [2]
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r0 = blockIdx.x * kTileM;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+  }
+  // ---- layer-1 input rows into the A buffer
+  if (FEAT) {
+    if (tid < kTileM) {
+      const int r = tid, c = r0 + r;
+      const int N = a.m.N;
+      if (c < a.n) {
+        const int cs = a.cs;
+        const double T = a.Tp[c];
+        double cp = 0.0, rmax = 0.0;
+        for (int i = 0; i < N; ++i) {
+          const double *q = a.m.cpcoef + 5 * i;
+          const double cpR = q[0] + T * (q[1] + T * (q[2] + T * (q[3] + T * q[4])));
+          const double y = a.Yp[(size_t)i * cs + c];
+          cp = fma(y, kRu * a.m.invW[i] * cpR, cp);
+          rmax = fmax(rmax, fabs(a.b[(size_t)i * cs + c] - y + a.wdt * a.FRp[(size_t)i * cs + c]));
+        }
+        const double rT = (a.hstar[c] - a.hp[c]) / (cp * T);
+        const double sc = fmax(rmax, fabs(rT));
+        const double inv = (sc > 0.0) ? 1.0 / sc : 0.0;
+        a.scale[c] = sc;
+        // features straight into the A buffer (columns beyond n_in stay zero)
+        for (int i = 0; i < N; ++i) {
+          const double y = a.Yp[(size_t)i * cs + c];
+          sA[a_index(r, i)] = __double2bfloat16(y);
+          sA[a_index(r, N + 2 + i)] =
+              __double2bfloat16((a.b[(size_t)i * cs + c] - y + a.wdt * a.FRp[(size_t)i * cs + c]) * inv);
+        }
+        sA[a_index(r, N)] = __double2bfloat16((T - 1150.0) / 850.0);
+        sA[a_index(r, N + 1)] = __double2bfloat16(log10(a.wdt) + 6.0);
+        sA[a_index(r, 2 * N + 2)] = __double2bfloat16(rT * inv);
+        for (int j = 2 * N + 3; j < a.k1; ++j) sA[a_index(r, j)] = __float2bfloat16(0.0f);
+      } else {
+        for (int j = 0; j < a.k1; ++j) sA[a_index(r, j)] = __float2bfloat16(0.0f);
+      }
+    }
+  } else {
+    for (int e = tid; e < kTileM * a.k1; e += kFThreads) {
+      const int r = e / a.k1, k = e - r * a.k1, c = r0 + r;
+      __nv_bfloat16 v = __float2bfloat16(0.0f);
+      if (c < a.n && k < a.ldx) v = a.X[(size_t)c * a.ldx + k];
+      sA[a_index(r, k)] = v;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  uint32_t phase[2] = {0u, 0u};
+  bool ok = true;
+
+  for (int L = 0; L < 4; ++L) {
+    const int K = (L == 0) ? a.k1 : kFKmax;
+    const int N = (L == 3) ? a.ldo : kMaxN;
+    const int ldw = (L == 0) ? a.ldx : kFKmax;   // weight row length (K of the stored matrix)
+    const int kvalid = (L == 0) ? a.ldx : kFKmax;
+    const __nv_bfloat16 *W = a.W[L];
+    const uint32_t idesc = instr_desc(kTileM, N);
+    const int nch = K / kTileK;
+    for (int kc = 0; kc < nch; ++kc) {
+      const int st = kc & 1;
+      __nv_bfloat16 *sB = sB0 + st * (kFSmemB / 2);
+      if (kc >= 2) {   // the MMAs of chunk kc-2 read this stage
+        if (!mbar_wait(bar + st, phase[st])) ok = false;
+        phase[st] ^= 1u;
+      }
+      // weight chunk: rows n < N, K columns [64 kc, 64 kc + 64), 16-byte pieces
+      for (int e = tid; e < N * 8; e += kFThreads) {
+        const int r7 = e & 7, q = (e >> 3) & 7, rg = e >> 6;
+        const int nrow = rg * 8 + r7, k = kc * kTileK + q * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (k < kvalid) v = *reinterpret_cast<const uint4 *>(W + (size_t)nrow * ldw + k);
+        reinterpret_cast<uint4 *>(sB)[e] = v;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = smem_u32(sA) + kc * 1024, b0 = smem_u32(sB);
+#pragma unroll
+        for (int kk = 0; kk < kTileK / 16; ++kk) {
+          const uint64_t da = smem_desc(a0 + kk * 256, 128, 4096);
+          const uint64_t db = smem_desc(b0 + kk * 256, 128, 1024);
+          umma_bf16(tmem, da, db, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+        }
+        umma_commit(bar + st);
+      }
+      __syncwarp();
+    }
+    // wait for the outstanding commits in order: all MMAs of the layer are done
+    for (int kc = (nch >= 2 ? nch - 2 : 0); kc < nch; ++kc) {
+      const int st = kc & 1;
+      if (!mbar_wait(bar + st, phase[st])) ok = false;
+      phase[st] ^= 1u;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    // epilogue: warp w reads lanes 32 (w % 4) .. + 31; the N/16 column chunks are
+    // split between the two warps of a lane quadrant (the first takes the odd one)
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = quad * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+    const int nck = N / 16, first = (nck + 1) / 2;
+    const int cbeg = half ? first * 16 : 0, cend = half ? N : first * 16;
+    const float *bias = a.bias[L];
+    for (int c0 = cbeg; c0 < cend; c0 += 16) {
+      float v[16];
+      tmem_ld16(trow + (uint32_t)c0, v);
+      if (L < 3) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sA[a_index(row, c0 + i)] = __float2bfloat16(gelu(v[i] + bias[c0 + i]));
+      } else if (r0 + row < a.n) {
+        float *o = a.out + (size_t)(r0 + row) * a.ldo;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[c0 + i] = v[i] + bias[c0 + i];
+      }
+    }
+    // the next layer's MMAs read sA and overwrite tensor memory
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  if (!ok && tid == 0) atomicExch(a.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
+
 }  // namespace mlp
 
 // ---------------------------------------------------------------------------
@@ -426,8 +613,40 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 void mlp_prepare() {
   // 100 KB of shared memory keeps at most two CTAs (2 x 256 TMEM columns) per SM,
-  // so tcgen05.alloc never waits for another CTA's columns
+  // so tcgen05.alloc never waits for another CTA's columns; the fused kernel
+  // (160 KB) runs one CTA per SM
   cudaFuncSetAttribute(k_umma_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmemLaunch);
+  cudaFuncSetAttribute(k_mlp_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem);
+  cudaFuncSetAttribute(k_mlp_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem);
+}
+
+void mlp_fused_forward(const Surrogate &g, const DevMech *m, int cs, double wdt, const double *b,
+                       const double *hstar, const double *Yp, const double *Tp, const double *FRp,
+                       const double *hp, double *scale, const __nv_bfloat16 *X, int n, float *out,
+                       cudaStream_t s) {
+  if (n <= 0) return;
+  FusedArgs a;
+  memset(&a, 0, sizeof(a));
+  if (m) a.m = *m;
+  a.cs = cs;
+  a.wdt = wdt;
+  a.b = b; a.hstar = hstar; a.Yp = Yp; a.Tp = Tp; a.FRp = FRp; a.hp = hp; a.scale = scale;
+  a.X = X;
+  a.n = n;
+  a.ldx = g.ldx;
+  a.k1 = (g.ldx + kTileK - 1) / kTileK * kTileK;
+  for (int L = 0; L < 4; ++L) {
+    a.W[L] = g.Pb + g.off[L];
+    a.bias[L] = g.P + g.off[4 + L];
+  }
+  a.ldo = g.ldo;
+  a.out = out;
+  a.err = g.err;
+  const unsigned grid = (unsigned)((n + kTileM - 1) / kTileM);
+  if (m)
+    k_mlp_fused<true><<<grid, kFThreads, kFSmem, s>>>(a);
+  else
+    k_mlp_fused<false><<<grid, kFThreads, kFSmem, s>>>(a);
 }
 
 void mlp_gemm(const Operand &A, const Operand &Bt, int M, int N, int K, int splits, const Epi &ep,

@@ -322,7 +322,10 @@ def flame_2d(mech: Mechanism, seed: int, n=256, dx=4e-5, amp=2.0, radius=2e-3,
     c = (L / 2, L / 2) if centre is None else centre
     xc = _centres(n, dx)
     X, Yg = np.meshgrid(xc, xc)
-    r = np.sqrt((X - c[0]) ** 2 + (Yg - c[1]) ** 2).reshape(-1)
+    ddx, ddy = X - c[0], Yg - c[1]
+    ddx -= L * np.round(ddx / L)          # nearest periodic image
+    ddy -= L * np.round(ddy / L)
+    r = np.sqrt(ddx ** 2 + ddy ** 2).reshape(-1)
     s = 0.5 * (1.0 - np.tanh((r - radius) / delta))
     Y, T = _profile(mech, s)
     vel = _taylor_green_faces(n, n, dx, amp)
@@ -389,6 +392,39 @@ WORKLOADS = {
     "flame3d_128_n21": dict(mech=(21, 84), seed=1802, dim=3, grid=dict(n=128, dx=1e-4, urms=3.0),
                             dt=5e-6, steps=10, sweeps=4, nodes=3, nu=2),
 }
+
+
+# Batched form: independent 2D flames of uneven size and mechanism.
+BATCHES = {
+    "batch64_2d": dict(n_flames=64, seed=1804, side_log2=(5.0, 8.0), dx=4e-5, amp=2.0,
+                       mechs=((1801, 9, 21), (1802, 21, 84), (1803, 53, 325)),
+                       dt=(1e-6, 1e-5), radius=(1e-3, 3e-3), steps=10, sweeps=4, nodes=3, nu=2),
+}
+
+
+def build_batch(name: str = "batch64_2d", n_flames: int | None = None):
+    """List of (mechanism, flame, dt) of a batched workload.
+
+    Grid side n = round(2^U[5,8]) (cells 32^2..256^2, log-uniform side), mechanism
+    drawn uniformly from the three, dt ~ U[1e-6, 1e-5] s, kernel centre uniform in
+    the periodic box and radius ~ U[1, 3] mm clipped to 0.3 L (so that every
+    flame keeps a front), front width min(0.2 mm, L/16).
+    """
+    b = BATCHES[name]
+    rng = np.random.default_rng(b["seed"])
+    mechs = [make_mechanism(*m) for m in b["mechs"]]
+    out = []
+    for f in range(b["n_flames"] if n_flames is None else n_flames):
+        side = int(round(2.0 ** rng.uniform(*b["side_log2"])))
+        mech = mechs[int(rng.integers(len(mechs)))]
+        dt = float(rng.uniform(*b["dt"]))
+        L = side * b["dx"]
+        radius = min(float(rng.uniform(*b["radius"])), 0.3 * L)
+        centre = (float(rng.uniform(0, L)), float(rng.uniform(0, L)))
+        fl = flame_2d(mech, b["seed"] + f, n=side, dx=b["dx"], amp=b["amp"], radius=radius,
+                      delta=min(2e-4, L / 16), centre=centre)
+        out.append((mech, fl, dt))
+    return out
 
 
 def build_workload(name: str, grid_override: dict | None = None):

@@ -198,6 +198,24 @@ class Solver:
                                                _ptr(x), _stream(stream)))
         return x
 
+    # -- launch shapes ------------------------------------------------------
+    def autotune(self, state, T, dt):
+        t = L.Tuning()
+        L.check(self.lib.misdc_autotune(self.handle, _ptr(state), _ptr(T), float(dt), C.byref(t)))
+        return t.as_dict()
+
+    def get_tuning(self):
+        t = L.Tuning()
+        L.check(self.lib.misdc_get_tuning(self.handle, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = L.Tuning()
+        L.check(self.lib.misdc_get_tuning(self.handle, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        L.check(self.lib.misdc_set_tuning(self.handle, C.byref(t)))
+
     # -- learned initial guess of the reaction Newton ------------------------
     def surrogate_dims(self):
         v = [C.c_int() for _ in range(5)]
@@ -262,6 +280,25 @@ class Solver:
         L.check(self.lib.misdc_surrogate_forward(self.handle, _ptr(X), X.shape[0], _ptr(out), _stream(stream)))
         return out
 
+    def surrogate_forward_layers(self, X, stream=None):
+        d = self.surrogate_dims()
+        X = X.to(device=self.device, dtype=torch.bfloat16).contiguous()
+        out = torch.empty((X.shape[0], d["ldo"]), dtype=torch.float32, device=self.device)
+        L.check(self.lib.misdc_surrogate_forward_layers(self.handle, _ptr(X), X.shape[0], _ptr(out),
+                                                        _stream(stream)))
+        return out
+
+    def surrogate_guess(self, wdt, b, hstar, Yp, Tp, FRp, hp, stream=None):
+        d = self.surrogate_dims()
+        b, hstar, Yp, Tp, FRp, hp = (_dev(a, self.device) for a in (b, hstar, Yp, Tp, FRp, hp))
+        n = hstar.numel()
+        out = torch.empty((n, d["ldo"]), dtype=torch.float32, device=self.device)
+        sc = torch.empty(n, dtype=torch.float64, device=self.device)
+        L.check(self.lib.misdc_surrogate_guess(self.handle, float(wdt), _ptr(b), _ptr(hstar), _ptr(Yp),
+                                               _ptr(Tp), _ptr(FRp), _ptr(hp), n, _ptr(out), _ptr(sc),
+                                               _stream(stream)))
+        return out, sc
+
     def surrogate_gradient(self, X, targets, stream=None):
         d = self.surrogate_dims()
         X = X.to(device=self.device, dtype=torch.bfloat16).contiguous()
@@ -280,6 +317,43 @@ class Solver:
                                                      float(weight_decay), _ptr(loss), _stream(stream)))
         return loss
 
+
+
+class Batch:
+    """Independent flames advanced together, one CUDA graph launch per step."""
+
+    def __init__(self, solvers):
+        self.lib = L.load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s.handle.value for s in self.solvers])
+        h = C.c_void_p()
+        L.check(self.lib.misdc_batch_create(arr, len(self.solvers), C.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.misdc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, states, dts, n_steps=1, Ts=None, stream=None):
+        n = len(self.solvers)
+        sp = (C.c_void_p * n)(*[t.data_ptr() for t in states])
+        tp = None if Ts is None else (C.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in Ts])
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        L.check(self.lib.misdc_batch_step(self.handle, sp, tp, d.ctypes.data_as(L.dp), int(n_steps),
+                                          _stream(stream)))
+        return states
+
+    def stats(self, reset=True):
+        st = L.Stats()
+        L.check(self.lib.misdc_batch_stats(self.handle, C.byref(st), int(reset)))
+        return st.as_dict()
 
 
 class _DeviceArray:

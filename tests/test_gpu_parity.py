@@ -172,19 +172,19 @@ def test_diffusion_solve_parity(levels):
     assert st["status_name"] == "OK", st
 
 
-def _run_both(mech, fl, dt, steps, scheme="CISDCQ", nu=2, sweeps=4, sensitivity=False, **kw):
+def _run_both(mech, fl, dt, steps, scheme="CISDCQ", nu=2, sweeps=4, sensitivity=False, M=2, **kw):
     ad = O.ADR(mech, fl)
     phi0 = ad.state_from_YT(fl.Y, fl.T)
-    want, st_or = ad.step(phi0, dt, scheme, 2, sweeps, nu, n_steps=steps)
+    want, st_or = ad.step(phi0, dt, scheme, M, sweeps, nu, n_steps=steps)
     sens = None
     if sensitivity:   # the oracle against itself under one-ulp input perturbations
         sens = np.zeros(phi0.shape[0])
         for r in range(2):
             rng = np.random.default_rng(100 + r)
             pert = phi0 * (1 + 1e-16 * rng.standard_normal(phi0.shape))
-            other, _ = ad.step(pert, dt, scheme, 2, sweeps, nu, n_steps=steps)
+            other, _ = ad.step(pert, dt, scheme, M, sweeps, nu, n_steps=steps)
             sens = np.maximum(sens, relerr(other, want))
-    sv = S().Solver(mech, fl, scheme=scheme, nu=nu, n_sweeps=sweeps, **kw)
+    sv = S().Solver(mech, fl, scheme=scheme, nu=nu, n_sweeps=sweeps, n_nodes=M + 1, **kw)
     state = torch.as_tensor(phi0, device="cuda").contiguous()
     T = torch.as_tensor(fl.T, device="cuda").contiguous()
     sv.step(state, dt, steps, T=T)
@@ -212,6 +212,17 @@ def test_step_parity_schemes_mild_chemistry(scheme, nu):
     if scheme == "CISDCQ" and nu == 2:   # well conditioned: the plain bound applies
         assert np.all(err < TOL), err
     assert relerr(T, ad.T_from_h(want[:N], want[N])) < max(TOL, 20 * sens.max())
+
+
+@pytest.mark.parametrize("scheme,nu", [("CISDCQ", 2), ("CISDCQ", 3), ("MISDCQ", 1), ("MISDC", 1)])
+def test_step_parity_five_nodes(scheme, nu):
+    """Five Gauss-Lobatto nodes (M = 4): the paper's Sec. 4 node count."""
+    mech = I.make_mechanism(1801, 9, 21, logA_range=MILD)
+    fl = I.flame_1d(mech, 1801, nx=64, dx=1e-4)
+    got, T, want, ad, st, sens = _run_both(mech, fl, 1e-5, 3, scheme=scheme, nu=nu, sweeps=6, M=4,
+                                           sensitivity=True)
+    err = relerr(got, want)
+    assert np.all(err <= tol_from(sens)), (err, sens)
 
 
 @pytest.mark.parametrize("case", ["2d_n21", "2d_n53", "3d_n21", "2d_ragged"])

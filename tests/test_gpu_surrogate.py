@@ -73,6 +73,44 @@ def test_forward_parity(setup21, n):
     assert nrel(y_gpu[:, : lay.n_out], y_ref[:, : lay.n_out]) < NORM_TOL
 
 
+def test_fused_and_layered_forward_agree(setup21):
+    """The fused inference kernel and the per-layer GEMM kernels round at the same
+    points; only FP32 accumulation order and BF16 ties differ."""
+    mech, fl, sv = setup21
+    lay = MO.Layout(mech.n_species)
+    X, _ = _data(lay, 777, 3)
+    Xt = torch.as_tensor(X, dtype=torch.bfloat16)
+    a = sv.surrogate_forward(Xt).cpu().numpy()
+    b = sv.surrogate_forward_layers(Xt).cpu().numpy()
+    assert nrel(a[:, : lay.n_out], b[:, : lay.n_out]) < NORM_TOL
+    assert np.all(b[:, lay.n_out:] == 0.0)
+
+
+def test_guess_parity(setup21):
+    """Fused features + network against the oracle's features and network."""
+    mech, fl, sv = setup21
+    N = mech.n_species
+    lay = MO.Layout(N)
+    adr = O.ADR(mech, fl)
+    rng = np.random.default_rng(8)
+    n = 333
+    Yp = np.abs(fl.Y[:, :n] * (1 + 0.01 * rng.standard_normal((N, n))))
+    Tp = fl.T[:n] * (1 + 0.01 * rng.standard_normal(n))
+    hp = adr.h_from_T(Yp, Tp)
+    FRp = rng.standard_normal((N, n)) * 1e2
+    wdt = 1.7e-6
+    b = Yp - wdt * FRp + 1e-5 * rng.standard_normal((N, n))
+    hstar = hp + 50.0 * rng.standard_normal(n)
+    cp = np.array([sum(Yp[i, c] * adr.species_cp(i, Tp[c]) for i in range(N)) for c in range(n)])
+    f_ref, s_ref = MO.features(lay, cp, wdt, b, hstar, Yp, Tp, FRp, hp)
+    p = sv.surrogate_save().astype(np.float64)
+    y_ref, _ = MO.forward(lay, p, MO.round_bf16(f_ref), bf16=True)
+    out, sc = sv.surrogate_guess(wdt, b, hstar, Yp, Tp, FRp, hp)
+    np.testing.assert_allclose(sc.cpu().numpy(), s_ref, rtol=1e-12)
+    y = out.cpu().numpy()
+    assert nrel(y[:, : lay.n_out], y_ref[:, : lay.n_out]) < NORM_TOL
+
+
 def test_forward_parity_small_mechanism():
     mech = I.make_mechanism(1801, 9, 21)
     fl = I.flame_1d(mech, 0, nx=64, dx=1e-4, u=1.0)
@@ -85,6 +123,29 @@ def test_forward_parity_small_mechanism():
     y_gpu = sv.surrogate_forward(torch.as_tensor(X, dtype=torch.bfloat16)).cpu().numpy()
     y_ref, _ = MO.forward(lay, p, X, bf16=True)
     assert nrel(y_gpu[:, : lay.n_out], y_ref[:, : lay.n_out]) < NORM_TOL
+    y_l = sv.surrogate_forward_layers(torch.as_tensor(X, dtype=torch.bfloat16)).cpu().numpy()
+    assert nrel(y_l[:, : lay.n_out], y_ref[:, : lay.n_out]) < NORM_TOL
+
+
+def test_forward_parity_large_mechanism():
+    """53 species: 109 inputs (two K chunks in layer 1), 54 outputs (64 columns)."""
+    mech = I.make_mechanism(1803, 53, 325)
+    fl = I.flame_1d(mech, 0, nx=64, dx=1e-4, u=1.0)
+    sv = S().Solver(mech, fl)
+    sv.surrogate_init(seed=4)
+    lay = MO.Layout(53)
+    assert (sv.surrogate_dims()["ldx"], sv.surrogate_dims()["ldo"]) == (112, 64)
+    p = sv.surrogate_save().astype(np.float64)
+    X, t = _data(lay, 300, 2)
+    y_gpu = sv.surrogate_forward(torch.as_tensor(X, dtype=torch.bfloat16)).cpu().numpy()
+    y_ref, _ = MO.forward(lay, p, X, bf16=True)
+    assert nrel(y_gpu[:, : lay.n_out], y_ref[:, : lay.n_out]) < NORM_TOL
+    g_gpu, _ = sv.surrogate_gradient(torch.as_tensor(X, dtype=torch.bfloat16),
+                                     torch.as_tensor(t, dtype=torch.float32))
+    g_ref, _ = MO.gradient(lay, p, X, t, bf16=True)
+    G, R = lay.unpack(g_gpu.cpu().numpy().astype(np.float64)), lay.unpack(g_ref)
+    for k in ("W1", "W2", "W3", "W4", "b1", "b4"):
+        assert nrel(G[k], R[k]) < NORM_TOL, k
 
 
 @pytest.mark.parametrize("n", [128, 1000])
