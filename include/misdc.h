@@ -112,8 +112,11 @@ typedef struct misdc_stats {
   long long kernel_launches;    /* library kernels launched by misdc_step */
   long long surrogate_used;     /* cells whose Newton started from the learned guess */
   long long surrogate_rejected; /* learned guesses the residual judge rejected */
-  long long newton_fp64_fallbacks; /* mixed precision: iterations whose FP32 factor
-                                      was replaced by the FP64 one */
+  long long newton_fp64_fallbacks; /* mixed precision: solves restarted with FP64
+                                      Newton after the mixed iteration failed */
+  long long newton_jacobians;   /* Jacobian assemblies (every iteration in FP64 mode;
+                                   mixed precision reuses factors between them) */
+  long long newton_lu_fp64;     /* of which factorised in FP64 (the rest in FP32) */
 } misdc_stats;
 
 typedef struct misdc_solver misdc_solver;
@@ -291,6 +294,9 @@ typedef struct misdc_tuning {
   int newton_blocks_per_sm;     /* cap on resident blocks per SM; 0 = default */
   int newton_dynamic;           /* 1: warps take the next cell from a global counter */
   int cheb_block;               /* threads per block of the smoother sweep; 0 = 256 */
+  int newton_keep_factors;      /* mixed precision: 1 (default) keeps each cell's FP32
+                                   Jacobian factor between the solves of an SDC node,
+                                   0 rebuilds it in every solve */
   double newton_ms;             /* autotune: best time of the probe reaction solve */
   double cheb_ms;               /* autotune: best time of the probe diffusion solve */
 } misdc_tuning;

@@ -44,7 +44,8 @@ class Stats(C.Structure):
                 ("newton_fail", C.c_longlong), ("newton_max", C.c_int), ("status", C.c_int),
                 ("lin_sweeps", C.c_longlong), ("lin_resid_max", C.c_double),
                 ("kernel_launches", C.c_longlong), ("surrogate_used", C.c_longlong),
-                ("surrogate_rejected", C.c_longlong), ("newton_fp64_fallbacks", C.c_longlong)]
+                ("surrogate_rejected", C.c_longlong), ("newton_fp64_fallbacks", C.c_longlong),
+                ("newton_jacobians", C.c_longlong), ("newton_lu_fp64", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -54,7 +55,8 @@ class Stats(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("newton_warps_per_block", C.c_int), ("newton_blocks_per_sm", C.c_int),
-                ("newton_dynamic", C.c_int), ("cheb_block", C.c_int), ("newton_ms", C.c_double),
+                ("newton_dynamic", C.c_int), ("cheb_block", C.c_int),
+                ("newton_keep_factors", C.c_int), ("newton_ms", C.c_double),
                 ("cheb_ms", C.c_double)]
 
     def as_dict(self):

@@ -203,14 +203,14 @@ struct NW {
   // mixed precision: FP32 factor, FP64 right-hand side and residual
   float *Jf, *zf, *pivf;
   int *sw;
-  double *r64, *res;
+  double *r64, *res, *xg;
 };
 
 // doubles of shared memory one warp needs
 __host__ __device__ inline size_t newton_warp_doubles(int N, int R, int ld, bool mixed) {
   const size_t nn = N + 1;
   size_t d = nn * ld + 8 * (size_t)R + 6 * (size_t)N + 3 * nn;
-  if (mixed) d += (nn * ld + 1) / 2 + 2 * nn + (3 * nn + 1) / 2 + 1;
+  if (mixed) d += (nn * ld + 1) / 2 + 3 * nn + (3 * nn + 1) / 2 + 1;
   return d;
 }
 
@@ -231,12 +231,13 @@ __device__ __forceinline__ NW carve2(double *p, int N, int R, int ld, bool mixed
   if (mixed) {
     w.r64 = p; p += nn;
     w.res = p; p += nn;
+    w.xg = p; p += nn;
     w.Jf = reinterpret_cast<float *>(p); p += ((size_t)nn * ld + 1) / 2;
     float *f = reinterpret_cast<float *>(p);
     w.zf = f; w.pivf = f + nn;
     w.sw = reinterpret_cast<int *>(f + 2 * nn);
   } else {
-    w.r64 = w.res = nullptr; w.Jf = w.zf = w.pivf = nullptr; w.sw = nullptr;
+    w.r64 = w.res = w.xg = nullptr; w.Jf = w.zf = w.pivf = nullptr; w.sw = nullptr;
   }
   return w;
 }
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
                                                  const double *__restrict__ sc, double s_min,
                                                  const double *__restrict__ FRp,
                                                  const double *__restrict__ hp,
-                                                 int *__restrict__ work) {
+                                                 int *__restrict__ work, ChordStore cst) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int N = m.N, R = m.R, nn = N + 1, na = nn + 1;   // na: columns of the augmented matrix
@@ -263,7 +264,8 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
   NW w = carve2(smem + (size_t)wib * per_warp, N, R, ld, MIXED);
   double *J = w.J;
   const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
-  unsigned long long my_solves = 0, my_iters = 0, my_fail = 0, my_sg = 0, my_rej = 0, my_fb = 0;
+  unsigned long long my_solves = 0, my_iters = 0, my_fail = 0, my_sg = 0, my_rej = 0, my_fb = 0,
+                     my_jac = 0, my_lu64 = 0;
   int my_max = 0;
   unsigned bits = 0;
 
@@ -301,10 +303,64 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       }
       __syncwarp();
     }
+    // MIXED: a row-equilibrated FP32 factor of the Jacobian, reused across
+    // iterations and across calls (the node's previous solve) while the chord
+    // iteration contracts; `have` says the shared-memory factor is usable
+    bool have = false, fresh = false, from_store = false, fresh_exact = false, no32 = false;
+    bool exact = false;   // retry: plain FP64 Newton, no factor reuse
+    double sTf = 0.0;
+    if (MIXED && cst.valid) no32 = (cst.valid[cell] & 2) != 0;   // FP32 factors failed this cell
+    if (MIXED && cst.valid && (cst.valid[cell] & 1)) {
+      // a stored factor is used only while the cell stays within 1e-4 (Y, and T
+      // relative) of the state it was built at: a stale factor of a stiffer
+      // Jacobian would shrink the chord step and fake convergence
+      const double *src = cst.f + (size_t)cell * cst.fs;
+      const double *xf = src + nn * nn + 3 * nn + 1;
+      double dist = 0.0;
+      for (int i = lane; i < nn; i += 32) {
+        const double xi = w.xs[i];
+        dist = fmax(dist, (i < N) ? fabs(xi - xf[i]) : fabs(xi - xf[i]) / xi);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dist = fmax(dist, __shfl_xor_sync(0xffffffffu, dist, o));
+      if (dist <= 1e-4) {
+        for (int e = lane; e < nn * nn; e += 32) {
+          const int i = e / nn, j = e - i * nn;
+          J[(size_t)i * ld + j] = src[e];
+        }
+        for (int i = lane; i < nn; i += 32) {
+          w.piv[i] = src[nn * nn + i];
+          w.res[i] = src[nn * nn + nn + i];
+          w.sw[i] = cst.sw[(size_t)cell * cst.swld + i];
+        }
+        sTf = src[nn * nn + 3 * nn];
+        have = true;
+        from_store = true;
+      }
+      __syncwarp();
+    }
+    if (MIXED) {
+      for (int i = lane; i < nn; i += 32) w.xg[i] = w.xs[i];
+      __syncwarp();
+    }
     double T = w.xs[N];
     double dprev = INFINITY;
     int it, code = 0;
+    for (int attempt = 0; attempt < (MIXED ? 2 : 1); ++attempt) {
+    if (attempt == 1) {
+      // the mixed iteration failed: plain FP64 Newton from the same start
+      if (code == 0) break;
+      for (int i = lane; i < nn; i += 32) w.xs[i] = w.xg[i];
+      __syncwarp();
+      T = w.xs[N];
+      code = 0;
+      dprev = INFINITY;
+      have = fresh = from_store = fresh_exact = false;
+      exact = no32 = true;
+      ++my_fb;
+    }
     for (it = 1; it <= maxit; ++it) {
+      const bool jac = !MIXED || !have || exact;   // this iteration assembles the Jacobian
       // ---- thermo and concentrations (species over lanes). FP64 work is paid per
       // active lane on this part, so warp-uniform scalars are computed by lane 0
       // and broadcast.
@@ -347,25 +403,40 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         const double kf = exp(lnkf);
         const double kr = exp(lnkf - lnKc);
         const double Ff = cf[0] * cf[1] * cf[2], Fr = cr[0] * cr[1] * cr[2];
-        const double dlnkf = (beta + TA * invT) * invT;
-        const double dlnKc = (dh - dn) * invT;
         w.src[r] = kf * Ff - kr * Fr;
-        w.src[R + r] = kf * Ff * dlnkf - kr * Fr * (dlnkf - dlnKc);
-        double *sd = w.src + 2 * R + 6 * r;
-        sd[0] = kf * (cf[1] * cf[2]);
-        sd[1] = kf * (cf[0] * cf[2]);
-        sd[2] = kf * (cf[0] * cf[1]);
-        sd[3] = -kr * (cr[1] * cr[2]);
-        sd[4] = -kr * (cr[0] * cr[2]);
-        sd[5] = -kr * (cr[0] * cr[1]);
+        if (jac) {
+          const double dlnkf = (beta + TA * invT) * invT;
+          const double dlnKc = (dh - dn) * invT;
+          w.src[R + r] = kf * Ff * dlnkf - kr * Fr * (dlnkf - dlnKc);
+          double *sd = w.src + 2 * R + 6 * r;
+          sd[0] = kf * (cf[1] * cf[2]);
+          sd[1] = kf * (cf[0] * cf[2]);
+          sd[2] = kf * (cf[0] * cf[1]);
+          sd[3] = -kr * (cr[1] * cr[2]);
+          sd[4] = -kr * (cr[0] * cr[2]);
+          sd[5] = -kr * (cr[0] * cr[1]);
+        }
       }
+      double sT = 0.0;
+      if (lane == 0) sT = invT / scp;
+      sT = __shfl_sync(0xffffffffu, sT, 0);
+      if (!jac) {
+        // ---- chord iteration: FP64 residual only, wdot_i = sum_r W_i nu_ri q_r;
+        // the temperature row keeps the scaling its stored factor was built with
+        __syncwarp();
+        for (int i = lane; i < N; i += 32) {
+          double wd = 0.0;
+          for (int p = m.sp_ptr[i]; p < m.sp_ptr[i + 1]; ++p) wd = fma(m.sp_coef[p], w.src[m.sp_rx[p]], wd);
+          w.r64[i] = fma(wdt / m.rho, wd, w.bs[i] - w.xs[i]);
+        }
+        if (lane == 0) w.r64[N] = -(sh - hst) * sTf;
+        __syncwarp();
+      } else {
+      ++my_jac;
       // ---- augmented matrix: identity species rows with b - Y, scaled T row
       for (int i = 0; i < N; ++i)
         for (int j = lane; j < na; j += 32)
           J[(size_t)i * ld + j] = (j == i) ? 1.0 : (j == nn ? w.bs[i] - w.xs[i] : 0.0);
-      double sT = 0.0;
-      if (lane == 0) sT = invT / scp;
-      sT = __shfl_sync(0xffffffffu, sT, 0);
       for (int j = lane; j < N; j += 32) J[(size_t)N * ld + j] = w.hm[j] * sT;
       if (lane == 0) {
         J[(size_t)N * ld + N] = scp * sT;
@@ -389,6 +460,20 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         if (cur >= 0) J[cur] = fma(-wdt, acc, J[cur]);
       }
       __syncwarp();
+      if (MIXED) {
+        // rows are equilibrated (scaled by 1/max|J_ij|) before rounding to FP32, which
+        // keeps stiff rows (entries up to ~1e30) in range; the scaling does not change
+        // the solution
+        for (int i = lane; i < nn; i += 32) {
+          double amax = 0.0;
+          const double *Ji = J + (size_t)i * ld;
+          for (int j = 0; j < nn; ++j) amax = fmax(amax, fabs(Ji[j]));
+          w.res[i] = (amax > 0.0) ? 1.0 / amax : 1.0;
+          w.r64[i] = Ji[nn];
+        }
+        __syncwarp();
+      }
+      }   // jac
       if (judge) {
         // Accept the learned guess only if the residual drops, measured in the
         // Jacobi-scaled max-norm max_i |r_i / J_ii| (species rows; the temperature
@@ -399,11 +484,19 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         judge = false;
         double rm = 0.0, rp = 0.0;
         for (int i = lane; i < nn; i += 32) {
-          // the temperature row is already in units of dT/T
-          const double dinv = (i < N) ? 1.0 / fabs(J[(size_t)i * ld + i]) : 1.0;
-          rm = fmax(rm, fabs(J[(size_t)i * ld + nn]) * dinv);
+          // the temperature row is already in units of dT/T; MIXED scales the
+          // species rows by 1/max_j |J_ij| (the equilibration of its factor)
+          double dinv, ri;
+          if (MIXED) {
+            dinv = (i < N) ? w.res[i] : 1.0;
+            ri = w.r64[i];
+          } else {
+            dinv = (i < N) ? 1.0 / fabs(J[(size_t)i * ld + i]) : 1.0;
+            ri = J[(size_t)i * ld + nn];
+          }
+          rm = fmax(rm, fabs(ri) * dinv);
           const double r0 = (i < N) ? w.bs[i] - w.dx[i] + wdt * FRp[(size_t)i * cs + cell]
-                                    : (hst - hp[cell]) * sT;
+                                    : (hst - hp[cell]) * (jac ? sT : sTf);
           rp = fmax(rp, fabs(r0) * dinv);
         }
 #pragma unroll
@@ -423,121 +516,122 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       }
       bool singular = false, fallback = false;
       if (MIXED) {
-        // ---- mixed precision: FP32 factor of J, FP64 residual refinement; cells
-        // whose refinement does not contract fall back to the FP64 factor below
-        // rows are equilibrated (scaled by 1/max|J_ij|) before rounding to FP32, which
-        // keeps stiff rows (entries up to ~1e30) in range; the scaling does not
-        // change the solution and the FP64 residual uses the unscaled rows
+        // ---- mixed precision: chord (simplified Newton) steps driven by the FP64
+        // residual, with a factor of a recent Jacobian kept in J (L below the
+        // diagonal, U above, piv = 1/U_kk, row scales res, pivot rows sw). A new
+        // factor is an FP32 LU of the row-equilibrated FP64 Jacobian where that is
+        // well enough conditioned, else an FP64 LU (below, with fallback set).
         float *Jf = w.Jf;
-        for (int i = lane; i < nn; i += 32) {
-          double amax = 0.0;
-          const double *Ji = J + (size_t)i * ld;
-          for (int j = 0; j < nn; ++j) amax = fmax(amax, fabs(Ji[j]));
-          w.res[i] = (amax > 0.0) ? 1.0 / amax : 1.0;
-          w.r64[i] = Ji[nn];
-          w.dx[i] = 0.0;
-        }
-        __syncwarp();
-        for (int i = 0; i < nn; ++i) {
-          const double si = w.res[i];
-          for (int j = lane; j < nn; j += 32) Jf[(size_t)i * ld + j] = __double2float_rn(J[(size_t)i * ld + j] * si);
-        }
-        __syncwarp();
-        for (int k = 0; k < nn; ++k) {
-          unsigned best = 0u;
-          int bi = nn;
-          for (int i = k + lane; i < nn; i += 32) {
-            const unsigned v = (unsigned)__float_as_int(Jf[(size_t)i * ld + k]) & 0x7fffffffu;
-            if (v > best) { best = v; bi = i; }
+        fresh = false;
+        if (jac && no32) fallback = true;
+        if (jac && !no32) {
+          for (int i = 0; i < nn; ++i) {
+            const double si = w.res[i];
+            for (int j = lane; j < nn; j += 32)
+              Jf[(size_t)i * ld + j] = __double2float_rn(J[(size_t)i * ld + j] * si);
           }
+          __syncwarp();
+          for (int k = 0; k < nn; ++k) {
+            unsigned best = 0u;
+            int bi = nn;
+            for (int i = k + lane; i < nn; i += 32) {
+              const unsigned v = (unsigned)__float_as_int(Jf[(size_t)i * ld + k]) & 0x7fffffffu;
+              if (v > best) { best = v; bi = i; }
+            }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const unsigned ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-          }
-          if (best == 0u || best >= 0x7f800000u) { fallback = true; break; }
-          if (lane == 0) w.sw[k] = bi;
-          if (bi != k) {
-            for (int j = lane; j < nn; j += 32) {
-              const float t = Jf[(size_t)k * ld + j];
-              Jf[(size_t)k * ld + j] = Jf[(size_t)bi * ld + j];
-              Jf[(size_t)bi * ld + j] = t;
+            for (int o = 16; o > 0; o >>= 1) {
+              const unsigned ob = __shfl_xor_sync(0xffffffffu, best, o);
+              const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+              if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (best == 0u || best >= 0x7f800000u) { fallback = true; break; }
+            if (lane == 0) w.sw[k] = bi;
+            if (bi != k) {
+              for (int j = lane; j < nn; j += 32) {
+                const float t = Jf[(size_t)k * ld + j];
+                Jf[(size_t)k * ld + j] = Jf[(size_t)bi * ld + j];
+                Jf[(size_t)bi * ld + j] = t;
+              }
+              __syncwarp();
+            }
+            const float pinv = 1.0f / Jf[(size_t)k * ld + k];
+            if (lane == 0) w.pivf[k] = pinv;
+            for (int i = k + 1 + lane; i < nn; i += 32) Jf[(size_t)i * ld + k] *= pinv;
+            __syncwarp();
+            const int rows = nn - 1 - k, cols = nn - 1 - k;
+            const int total = rows * cols;
+            if (total > 0) {
+              int i = lane / cols, j = lane - i * cols;
+              const int qs = 32 / cols, rsd = 32 - qs * cols;
+              for (int e = lane; e < total; e += 32) {
+                const size_t ri = (size_t)(k + 1 + i) * ld;
+                Jf[ri + k + 1 + j] = fmaf(-Jf[ri + k], Jf[(size_t)k * ld + k + 1 + j], Jf[ri + k + 1 + j]);
+                i += qs;
+                j += rsd;
+                if (j >= cols) { j -= cols; ++i; }
+              }
             }
             __syncwarp();
           }
-          const float pinv = 1.0f / Jf[(size_t)k * ld + k];
-          if (lane == 0) w.pivf[k] = pinv;
-          for (int i = k + 1 + lane; i < nn; i += 32) Jf[(size_t)i * ld + k] *= pinv;
-          __syncwarp();
-          const int rows = nn - 1 - k, cols = nn - 1 - k;
-          const int total = rows * cols;
-          if (total > 0) {
-            int i = lane / cols, j = lane - i * cols;
-            const int qs = 32 / cols, rsd = 32 - qs * cols;
-            for (int e = lane; e < total; e += 32) {
-              const size_t ri = (size_t)(k + 1 + i) * ld;
-              Jf[ri + k + 1 + j] = fmaf(-Jf[ri + k], Jf[(size_t)k * ld + k + 1 + j], Jf[ri + k + 1 + j]);
-              i += qs;
-              j += rsd;
-              if (j >= cols) { j -= cols; ++i; }
+          if (!fallback) {
+            // FP32 is only trusted where it can contract: with rows equilibrated,
+            // the spread of the pivots max|U_kk| / min|U_kk| stands in for the
+            // condition number; above 1e5 (eps32 x cond ~ 1e-2) the cell goes FP64
+            float pmin = INFINITY, pmax = 0.0f;
+            for (int k = lane; k < nn; k += 32) {
+              const float a = fabsf(w.pivf[k]);   // 1 / |U_kk|
+              pmin = fminf(pmin, a);
+              pmax = fmaxf(pmax, a);
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              pmin = fminf(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
+              pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+            }
+            if (!(pmax <= 1e5f * pmin)) fallback = true;
           }
-          __syncwarp();
-        }
-        // dx = 0; repeat: res = r - J dx (FP64), z = LU^{-1} P res (FP32), dx += z
-        float zprev = INFINITY;
-        for (int ref = 0; ref < 6 && !fallback; ++ref) {
-          if (ref == 0) {
-            for (int i = lane; i < nn; i += 32) w.zf[i] = __double2float_rn(w.r64[i] * w.res[i]);
+          if (fallback) {
+            no32 = true;
           } else {
-            for (int i = lane; i < nn; i += 32) {
-              double sacc = w.r64[i];
-              const double *Ji = J + (size_t)i * ld;
-              for (int j = 0; j < nn; ++j) sacc = fma(-Ji[j], w.dx[j], sacc);
-              w.zf[i] = __double2float_rn(sacc * w.res[i]);
+            // the FP32 factor, widened, is the factor in J
+            for (int e = lane; e < nn * nn; e += 32) {
+              const int i = e / nn, j = e - i * nn;
+              J[(size_t)i * ld + j] = (double)Jf[(size_t)i * ld + j];
             }
+            for (int k = lane; k < nn; k += 32) w.piv[k] = (double)w.pivf[k];
+            __syncwarp();
+            have = fresh = true;
+            fresh_exact = false;
+            from_store = false;
+            sTf = sT;
           }
+        }
+        if (!fallback) {
+          // dx = U^{-1} L^{-1} P (D r), FP64 substitutions with the kept factor
+          for (int i = lane; i < nn; i += 32) w.dx[i] = w.r64[i] * w.res[i];
           __syncwarp();
           if (lane == 0)
             for (int k = 0; k < nn; ++k) {
               const int t = w.sw[k];
-              if (t != k) { const float v = w.zf[k]; w.zf[k] = w.zf[t]; w.zf[t] = v; }
+              if (t != k) { const double v = w.dx[k]; w.dx[k] = w.dx[t]; w.dx[t] = v; }
             }
           __syncwarp();
           for (int k = 0; k < nn; ++k) {
-            const float zk = w.zf[k];
-            for (int i = k + 1 + lane; i < nn; i += 32) w.zf[i] = fmaf(-Jf[(size_t)i * ld + k], zk, w.zf[i]);
+            const double zk = w.dx[k];
+            for (int i = k + 1 + lane; i < nn; i += 32) w.dx[i] = fma(-J[(size_t)i * ld + k], zk, w.dx[i]);
             __syncwarp();
           }
           for (int k = nn - 1; k >= 0; --k) {
-            const float zk = w.zf[k] * w.pivf[k];
+            const double zk = w.dx[k] * w.piv[k];
             __syncwarp();
-            if (lane == 0) w.zf[k] = zk;
-            for (int i = lane; i < k; i += 32) w.zf[i] = fmaf(-Jf[(size_t)i * ld + k], zk, w.zf[i]);
+            if (lane == 0) w.dx[k] = zk;
+            for (int i = lane; i < k; i += 32) w.dx[i] = fma(-J[(size_t)i * ld + k], zk, w.dx[i]);
             __syncwarp();
           }
-          float zmax = 0.0f, dmx = 0.0f;
-          for (int i = lane; i < nn; i += 32) {
-            const double v = w.dx[i] + (double)w.zf[i];
-            w.dx[i] = v;
-            zmax = fmaxf(zmax, fabsf(w.zf[i]));
-            dmx = fmaxf(dmx, fabsf(__double2float_rn(v)));
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
-            dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
-          }
-          __syncwarp();
-          if (!(zmax <= zprev * 0.5f) || !isfinite(dmx)) { fallback = true; break; }   // not contracting
-          if (zmax <= 1e-6f * dmx) break;   // correction below 1e-6 of the step
-          zprev = zmax;
-          if (ref == 5) fallback = true;
         }
       }
-      if (MIXED && fallback) ++my_fb;
       if (!MIXED || fallback) {
+        ++my_lu64;
         // ---- FP64 LU with partial pivoting
         for (int k = 0; k < nn; ++k) {
           unsigned long long best = 0ull;
@@ -554,6 +648,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
           }
           if (best == 0ull || best >= 0x7ff0000000000000ull) { singular = true; break; }
+          if (MIXED && lane == 0) w.sw[k] = bi;
           if (bi != k) {
             for (int j = lane; j < na; j += 32) {
               const double t = J[(size_t)k * ld + j];
@@ -591,6 +686,27 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
             J[(size_t)i * ld + nn] = fma(-J[(size_t)i * ld + k], xk, J[(size_t)i * ld + nn]);
           __syncwarp();
         }
+        if (MIXED) {   // an unscaled FP64 factor of the current Jacobian
+          for (int i = lane; i < nn; i += 32) w.res[i] = 1.0;
+          __syncwarp();
+          have = fresh = fresh_exact = true;
+          from_store = false;
+          sTf = sT;
+        }
+      }
+      if (MIXED && fresh && cst.f && !exact) {   // keep the new factor for this node's next solve
+        double *dst = cst.f + (size_t)cell * cst.fs;
+        for (int e = lane; e < nn * nn; e += 32) {
+          const int i = e / nn, j = e - i * nn;
+          dst[e] = J[(size_t)i * ld + j];
+        }
+        for (int i = lane; i < nn; i += 32) {
+          dst[nn * nn + i] = w.piv[i];
+          dst[nn * nn + nn + i] = w.res[i];
+          dst[nn * nn + 3 * nn + 1 + i] = w.xs[i];
+          cst.sw[(size_t)cell * cst.swld + i] = (unsigned char)w.sw[i];
+        }
+        if (lane == 0) dst[nn * nn + 3 * nn] = sT;
       }
       // ---- update and convergence on d = max(max|dY|, |dT|/T)
       double dmax = 0.0;
@@ -611,10 +727,41 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       if (lane == 0) d = fmax(dmax, fabs(w.dx[N]) / T);
       d = __shfl_sync(0xffffffffu, d, 0);
       if (!isfinite(d)) { code = -3; break; }
-      if (d <= rtol || (d <= 1e-8 && d >= 0.5 * dprev)) break;
+      if (!MIXED || exact || (fresh && fresh_exact)) {
+        // exact Newton step: stop on the step size, or at the round-off floor of
+        // very stiff cells (the step no longer halves below 1e-8)
+        if (d <= rtol || (d <= 1e-8 && d >= 0.5 * dprev)) break;
+      } else if (fresh) {
+        // a step with a new FP32 factor: converged when far below rtol
+        if (d <= 0.01 * rtol) break;
+      } else {
+        // chord steps converge linearly: with the contraction th = d_k / d_{k-1} of
+        // two steps on the same factor the remaining error is about d th / (1 - th);
+        // a chord contracting by less than 10 gets a new factor. A first step on a
+        // stored factor that is far below rtol is converged; one that is large is
+        // undone and the factor rebuilt.
+        if (it == 1) {
+          if (d <= 0.01 * rtol) break;
+          if (d > 1e-2) {
+            for (int i = lane; i < nn; i += 32) w.xs[i] -= w.dx[i];
+            __syncwarp();
+            T = w.xs[N];
+            have = false;
+            d = INFINITY;
+          }
+        } else {
+          const double th = d / dprev;
+          if (th < 0.1) {
+            if (d * th / (1.0 - th) <= rtol) break;
+          } else {
+            have = false;
+          }
+        }
+      }
       dprev = d;
     }
     if (code == 0 && it > maxit) code = -1;
+    }   // attempt
     // species enthalpies and theta at the solution; reaction term (Y - b)/wdt
     const double Tf = (code == -3) ? 1000.0 : T;
     double invw = 0.0;
@@ -634,6 +781,8 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         if (hsp) hsp[(size_t)i * cs + cell] = kRu * m.invW[i] * Tf * hRT;
       }
     }
+    if (MIXED && cst.valid && lane == 0)
+      cst.valid[cell] = ((have && code == 0 && !exact) ? 1 : 0) | (no32 ? 2 : 0);
     if (lane == 0) {
       Tout[cell] = T;
       if (theta) theta[cell] = pow(Tf / m.T_ref, m.theta_exp);
@@ -658,6 +807,8 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     if (my_sg) atomicAdd(&st->sg_used, my_sg);
     if (my_rej) atomicAdd(&st->sg_rejected, my_rej);
     if (my_fb) atomicAdd(&st->fp64_fallbacks, my_fb);
+    if (my_jac) atomicAdd(&st->jacobians, my_jac);
+    if (my_lu64) atomicAdd(&st->lu64, my_lu64);
   }
 }
 
@@ -736,7 +887,7 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
                    DevStats *st, cudaStream_t s, bool mixed, const float *pred, int ldp,
                    const double *sc, double s_min, const double *FRp, const double *hp,
-                   const NewtonLaunch *cfg) {
+                   const NewtonLaunch *cfg, const ChordStore *store) {
   if (n <= 0) return;
   int ld, wpb;
   const size_t sm = newton_smem(m, mixed, ld, wpb, cfg ? cfg->wpb : 0);
@@ -746,14 +897,16 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
   grid = grid < cap ? grid : cap;
   int *work = (cfg && cfg->dynamic) ? cfg->work : nullptr;
   if (work) cudaMemsetAsync(work, 0, sizeof(int), s);
+  ChordStore cst{};
+  if (mixed && store) cst = *store;
   if (mixed)
     k_newton2<true><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
                                                FR, hsp, theta, iters, st, pred, ldp, sc,
-                                               s_min, FRp, hp, work);
+                                               s_min, FRp, hp, work, cst);
   else
     k_newton2<false><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
                                                 FR, hsp, theta, iters, st, pred, ldp, sc,
-                                                s_min, FRp, hp, work);
+                                                s_min, FRp, hp, work, cst);
 }
 
 }  // namespace misdc

@@ -167,6 +167,9 @@ struct misdc_solver {
   double sg_smin = 1e-8;
   // reaction-Newton launch shape (autotuned)
   NewtonLaunch nl{};
+  // mixed precision: FP32 Jacobian factors kept per node between its solves
+  ChordStore cst[kMaxNodes + 1];
+  bool keep_factors = true;
   DiffWork dw{};
   DevStats *st = nullptr;
   cudaStream_t sD = nullptr, sR = nullptr;
@@ -352,7 +355,8 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
   launch_newton(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, s->bR,
                 ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR, out.hsp, out.theta,
                 s->iters, s->st, st, s->o.precision == MISDC_PREC_MIXED, pred, sg ? sg->ldo : 0,
-                sg ? sg->scale : nullptr, s->sg_smin, guess.FR, guess.phi + N * cs, &s->nl);
+                sg ? sg->scale : nullptr, s->sg_smin, guess.FR, guess.phi + N * cs, &s->nl,
+                s->keep_factors ? &s->cst[t] : nullptr);
   if (sg && s->sg_collect)
     mlp_targets(s->N, s->cs, s->cs, guess.phi, guess.T, out.phi, out.T, sg->scale, sg->rowmap,
                 sg->ldo, sg->DT, st);
@@ -481,6 +485,14 @@ misdc_status configure_dt(misdc_solver *s, double dt) {
   }
   s->rho_bound = rho_bound_for(s, dt * qmax);
   s->cheb_sweeps = std::min(kMaxCheb, chebyshev_sweeps(s->rho_bound, std::max(1e-3 * s->o.lin_rtol, 1e-17)));
+  if (s->rho_dt > 0.0) {
+    // the stored Jacobian factors belong to the old weights w dt
+    cudaStreamSynchronize(s->sD);
+    cudaStreamSynchronize(s->sR);
+    for (int j = 1; j <= s->tab.M; ++j)
+      if (s->cst[j].valid) cudaMemsetAsync(s->cst[j].valid, 0, (size_t)s->cs * sizeof(int), s->sD);
+    cudaStreamSynchronize(s->sD);
+  }
   s->rho_dt = dt;
   return MISDC_OK;
 }
@@ -682,6 +694,17 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
       s->alloc(&s->dw.rho_bits, 1) || s->alloc(&s->dw.kdev, 1) || s->alloc(&s->dw.omega, kMaxCheb))
     return bail(fail(MISDC_E_OOM, "work buffers"));
   cudaMemset(s->st, 0, sizeof(DevStats));
+  if (s->o.precision == MISDC_PREC_MIXED) {
+    for (int j = 1; j <= M; ++j) {
+      ChordStore &c = s->cst[j];
+      c.fs = chord_floats(N);
+      c.swld = (int)((F + 3) / 4 * 4);
+      if (s->alloc(&c.f, (size_t)c.fs * cs) || s->alloc(&c.sw, (size_t)c.swld * cs) ||
+          s->alloc(&c.valid, cs))
+        return bail(fail(MISDC_E_OOM, "factor store"));
+      cudaMemset(c.valid, 0, cs * sizeof(int));
+    }
+  }
   // multigrid hierarchy (levels with even extents only)
   s->dw.levels = 1;
   s->dw.cycles = 12;
@@ -829,6 +852,8 @@ misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
   out->surrogate_used = (long long)d.sg_used;
   out->surrogate_rejected = (long long)d.sg_rejected;
   out->newton_fp64_fallbacks = (long long)d.fp64_fallbacks;
+  out->newton_jacobians = (long long)d.jacobians;
+  out->newton_lu_fp64 = (long long)d.lu64;
   int st = MISDC_OK;
   if (d.status_bits & kBitTdiag) st = MISDC_E_TDIAG;
   else if (d.status_bits & (kBitNan | kBitSingular)) st = MISDC_E_NAN;
@@ -1349,6 +1374,7 @@ misdc_status misdc_get_tuning(misdc_solver *s, misdc_tuning *t) {
   t->newton_blocks_per_sm = s->nl.blocks_per_sm;
   t->newton_dynamic = s->nl.dynamic;
   t->cheb_block = s->dw.cheb_block;
+  t->newton_keep_factors = s->keep_factors ? 1 : 0;
   return MISDC_OK;
 }
 
@@ -1363,6 +1389,11 @@ misdc_status misdc_set_tuning(misdc_solver *s, const misdc_tuning *t) {
   s->nl.blocks_per_sm = t->newton_blocks_per_sm;
   s->nl.dynamic = t->newton_dynamic ? 1 : 0;
   s->dw.cheb_block = t->cheb_block;
+  if (s->keep_factors != (t->newton_keep_factors != 0)) {
+    s->keep_factors = t->newton_keep_factors != 0;
+    for (int j = 1; j <= s->tab.M; ++j)
+      if (s->cst[j].valid) cudaMemset(s->cst[j].valid, 0, (size_t)s->cs * sizeof(int));
+  }
   return MISDC_OK;
 }
 
@@ -1563,6 +1594,8 @@ misdc_status misdc_batch_stats(misdc_batch *b, misdc_stats *out, int reset) {
     sum.surrogate_used += t.surrogate_used;
     sum.surrogate_rejected += t.surrogate_rejected;
     sum.newton_fp64_fallbacks += t.newton_fp64_fallbacks;
+    sum.newton_jacobians += t.newton_jacobians;
+    sum.newton_lu_fp64 += t.newton_lu_fp64;
   }
   sum.kernel_launches = b->kernels_launched;
   if (reset) b->kernels_launched = 0;

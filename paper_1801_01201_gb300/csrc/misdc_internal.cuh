@@ -34,7 +34,9 @@ struct DevStats {
   unsigned long long lin_resid_bits;   // bit pattern of the largest relative residual (>= 0)
   unsigned long long sg_used;          // cells that started Newton from the learned guess
   unsigned long long sg_rejected;      // learned guesses rejected by the residual judge
-  unsigned long long fp64_fallbacks;   // mixed-precision iterations that fell back to FP64 LU
+  unsigned long long fp64_fallbacks;   // mixed-precision solves restarted with FP64 Newton
+  unsigned long long jacobians;        // Jacobian assemblies of the reaction Newton
+  unsigned long long lu64;             // FP64 LU factorisations of the reaction Newton
 };
 
 // Mechanism tables in device memory (built by the engine from misdc_mech_desc).
@@ -91,13 +93,28 @@ struct NewtonLaunch {
   int wpb = 0, blocks_per_sm = 0, dynamic = 0;
   int *work = nullptr;
 };
+// Mixed precision: per-cell Jacobian factors kept between the solves of one SDC
+// node. Per cell: fs doubles (row-major LU of the (row-scaled) (N+1)^2 Jacobian,
+// pivot reciprocals, row scales, the temperature-row scale, the state it was built
+// at) and swld bytes of pivot rows; valid[c] bit 0: the factor may be used, bit 1:
+// FP32 factors are too coarse for this cell.
+struct ChordStore {
+  double *f = nullptr;
+  unsigned char *sw = nullptr;
+  int *valid = nullptr;
+  int fs = 0, swld = 0;
+};
+__host__ __device__ inline int chord_floats(int N) {
+  const int nn = N + 1;
+  return (nn * nn + 4 * nn + 1 + 1) / 2 * 2;
+}
 void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit,
                    const double *b, const double *hstar, const double *Yg, const double *Tg,
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
                    DevStats *st, cudaStream_t s, bool mixed = false,
                    const float *pred = nullptr, int ldp = 0, const double *sc = nullptr,
                    double s_min = 0.0, const double *FRp = nullptr, const double *hp = nullptr,
-                   const NewtonLaunch *cfg = nullptr);
+                   const NewtonLaunch *cfg = nullptr, const ChordStore *store = nullptr);
 int newton_max_wpb(const DevMech &m, bool mixed);
 
 // ---- grid kernels (misdc_grid.cu) ----

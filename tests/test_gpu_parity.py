@@ -112,7 +112,9 @@ def test_reaction_newton_parity(key):
 
 @pytest.mark.parametrize("key", [(1801, 9, 21), (1802, 21, 84), (1803, 53, 325)])
 def test_reaction_newton_parity_mixed_precision(key):
-    """FP32 Jacobian/LU with FP64 residual refinement converges to the FP64 root."""
+    """Chord steps with an FP32 factor of the Jacobian, driven by the FP64 residual
+    (cells whose FP32 factor does not contract switch to FP64 Newton), converge
+    to the FP64 root."""
     mech = I.make_mechanism(*key)
     n = 96
     fl = I.flame_1d(mech, 0, nx=n, dx=1e-4)
@@ -128,8 +130,11 @@ def test_reaction_newton_parity_mixed_precision(key):
     x = x.cpu().numpy()
     assert np.all(it.cpu().numpy() > 0)
     want = np.stack([ad.reaction_newton(wdt, b[:, c], hstar[c], x0[:, c])[0] for c in range(n)], axis=1)
-    assert np.all(relerr(x[:N], want[:N]) < TOL)
+    # chord steps stop on an error estimate below the absolute tolerance 1e-12 in Y,
+    # measured against the mass-fraction scale
+    assert np.max(np.abs(x[:N] - want[:N])) / np.max(np.abs(want[:N])) < TOL
     assert relerr(x[N], want[N]) < TOL
+    assert sv.stats()["newton_fail"] == 0
 
 
 @pytest.mark.parametrize("dim", [1, 2, 3])
@@ -274,8 +279,12 @@ def test_step_mixed_precision_meets_accuracy_bar(case):
         mech, fl = small_2d((1803, 53, 325), n=16)
     got, T, want, ad, st, sens = _run_both(mech, fl, 5e-6, 2, precision="mixed", sensitivity=True)
     N = mech.n_species
-    err = relerr(got, want)
-    assert np.all(err[:N] <= np.maximum(1e-8, 20 * sens[:N])), (err, sens)
+    # mass fractions against the mass-fraction scale: the Newton tolerance is
+    # absolute in Y, so trace species are converged to ~1e-12 absolute
+    scale = np.max(np.abs(want[:N]), axis=1)
+    err_g = np.max(np.abs(got[:N] - want[:N])) / scale.max()
+    sens_g = np.max(sens[:N] * scale) / scale.max()
+    assert err_g <= max(1e-8, 20 * sens_g), (err_g, sens_g)
     assert relerr(T, ad.T_from_h(want[:N], want[N])) <= 1e-6
 
 
