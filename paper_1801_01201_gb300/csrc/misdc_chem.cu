@@ -203,14 +203,14 @@ struct NW {
   // mixed precision: FP32 factor, FP64 right-hand side and residual
   float *Jf, *zf, *pivf;
   int *sw;
-  double *r64, *res, *xg;
+  double *r64, *res, *xg, *zd;
 };
 
 // doubles of shared memory one warp needs
 __host__ __device__ inline size_t newton_warp_doubles(int N, int R, int ld, bool mixed) {
   const size_t nn = N + 1;
   size_t d = nn * ld + 8 * (size_t)R + 6 * (size_t)N + 3 * nn;
-  if (mixed) d += (nn * ld + 1) / 2 + 3 * nn + (3 * nn + 1) / 2 + 1;
+  if (mixed) d += (nn * ld + 1) / 2 + 4 * nn + (3 * nn + 1) / 2 + 1;
   return d;
 }
 
@@ -232,16 +232,43 @@ __device__ __forceinline__ NW carve2(double *p, int N, int R, int ld, bool mixed
     w.r64 = p; p += nn;
     w.res = p; p += nn;
     w.xg = p; p += nn;
+    w.zd = p; p += nn;
     w.Jf = reinterpret_cast<float *>(p); p += ((size_t)nn * ld + 1) / 2;
     float *f = reinterpret_cast<float *>(p);
     w.zf = f; w.pivf = f + nn;
     w.sw = reinterpret_cast<int *>(f + 2 * nn);
   } else {
-    w.r64 = w.res = w.xg = nullptr; w.Jf = w.zf = w.pivf = nullptr; w.sw = nullptr;
+    w.r64 = w.res = w.xg = w.zd = nullptr; w.Jf = w.zf = w.pivf = nullptr; w.sw = nullptr;
   }
   return w;
 }
 
+
+// out = U^{-1} L^{-1} P (D r): FP64 substitutions with a factor kept in J (L below
+// the diagonal, U above, piv = 1/U_kk, row scales res, pivot rows sw); warp-wide
+__device__ __forceinline__ void solve_kept(const NW &w, const double *J, int ld, int nn, int lane,
+                                           const double *r, double *out) {
+  for (int i = lane; i < nn; i += 32) out[i] = r[i] * w.res[i];
+  __syncwarp();
+  if (lane == 0)
+    for (int k = 0; k < nn; ++k) {
+      const int t = w.sw[k];
+      if (t != k) { const double v = out[k]; out[k] = out[t]; out[t] = v; }
+    }
+  __syncwarp();
+  for (int k = 0; k < nn; ++k) {
+    const double zk = out[k];
+    for (int i = k + 1 + lane; i < nn; i += 32) out[i] = fma(-J[(size_t)i * ld + k], zk, out[i]);
+    __syncwarp();
+  }
+  for (int k = nn - 1; k >= 0; --k) {
+    const double zk = out[k] * w.piv[k];
+    __syncwarp();
+    if (lane == 0) out[k] = zk;
+    for (int i = lane; i < k; i += 32) out[i] = fma(-J[(size_t)i * ld + k], zk, out[i]);
+    __syncwarp();
+  }
+}
 
 template <bool MIXED>
 __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, double wdt, double rtol,
@@ -339,8 +366,8 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       }
       __syncwarp();
     }
-    if (MIXED) {
-      for (int i = lane; i < nn; i += 32) w.xg[i] = w.xs[i];
+    if (MIXED) {   // restart point: the plain guess x_p
+      for (int i = lane; i < nn; i += 32) w.xg[i] = judge ? w.dx[i] : w.xs[i];
       __syncwarp();
     }
     double T = w.xs[N];
@@ -474,7 +501,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         __syncwarp();
       }
       }   // jac
-      if (judge) {
+      if (!MIXED && judge) {
         // Accept the learned guess only if the residual drops, measured in the
         // Jacobi-scaled max-norm max_i |r_i / J_ii| (species rows; the temperature
         // row as the relative temperature change) with the Jacobian at the guess
@@ -606,29 +633,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
             sTf = sT;
           }
         }
-        if (!fallback) {
-          // dx = U^{-1} L^{-1} P (D r), FP64 substitutions with the kept factor
-          for (int i = lane; i < nn; i += 32) w.dx[i] = w.r64[i] * w.res[i];
-          __syncwarp();
-          if (lane == 0)
-            for (int k = 0; k < nn; ++k) {
-              const int t = w.sw[k];
-              if (t != k) { const double v = w.dx[k]; w.dx[k] = w.dx[t]; w.dx[t] = v; }
-            }
-          __syncwarp();
-          for (int k = 0; k < nn; ++k) {
-            const double zk = w.dx[k];
-            for (int i = k + 1 + lane; i < nn; i += 32) w.dx[i] = fma(-J[(size_t)i * ld + k], zk, w.dx[i]);
-            __syncwarp();
-          }
-          for (int k = nn - 1; k >= 0; --k) {
-            const double zk = w.dx[k] * w.piv[k];
-            __syncwarp();
-            if (lane == 0) w.dx[k] = zk;
-            for (int i = lane; i < k; i += 32) w.dx[i] = fma(-J[(size_t)i * ld + k], zk, w.dx[i]);
-            __syncwarp();
-          }
-        }
+        if (!fallback) solve_kept(w, J, ld, nn, lane, w.r64, w.dx);
       }
       if (!MIXED || fallback) {
         ++my_lu64;
@@ -707,6 +712,41 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           cst.sw[(size_t)cell * cst.swld + i] = (unsigned char)w.sw[i];
         }
         if (lane == 0) dst[nn * nn + 3 * nn] = sT;
+      }
+      if (MIXED && judge && !singular) {
+        // Mixed precision judges the learned guess x0 in Newton's natural norm: the
+        // step J^{-1} r(x0) just computed against J^{-1} r(x_p) through the same
+        // factor, r(x_p) from the stored reaction term of x_p. A rejected guess
+        // continues from x_p with that second step (no rate evaluation is lost).
+        judge = false;
+        for (int i = lane; i < nn; i += 32)
+          w.r64[i] = (i < N) ? w.bs[i] - w.xg[i] + wdt * FRp[(size_t)i * cs + cell]
+                             : (hst - hp[cell]) * sTf;
+        __syncwarp();
+        solve_kept(w, J, ld, nn, lane, w.r64, w.zd);
+        double d0 = 0.0, dp = 0.0;
+        for (int i = lane; i < nn; i += 32) {
+          const double s0i = (i < N) ? 1.0 : 1.0 / w.xs[N];
+          const double spi = (i < N) ? 1.0 : 1.0 / w.xg[N];
+          d0 = fmax(d0, fabs(w.dx[i]) * s0i);
+          dp = fmax(dp, fabs(w.zd[i]) * spi);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          d0 = fmax(d0, __shfl_xor_sync(0xffffffffu, d0, o));
+          dp = fmax(dp, __shfl_xor_sync(0xffffffffu, dp, o));
+        }
+        if (d0 < dp) {
+          ++my_sg;
+        } else {
+          for (int i = lane; i < nn; i += 32) {
+            w.xs[i] = w.xg[i];
+            w.dx[i] = w.zd[i];
+          }
+          __syncwarp();
+          T = w.xs[N];
+          ++my_rej;
+        }
       }
       // ---- update and convergence on d = max(max|dY|, |dT|/T)
       double dmax = 0.0;
