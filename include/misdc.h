@@ -117,6 +117,9 @@ typedef struct misdc_stats {
   long long newton_jacobians;   /* Jacobian assemblies (every iteration in FP64 mode;
                                    mixed precision reuses factors between them) */
   long long newton_lu_fp64;     /* of which factorised in FP64 (the rest in FP32) */
+  long long newton_certified;   /* mixed precision: solves whose guess a kept factor
+                                   certified from the stored reaction term alone
+                                   (counted as one iteration, no rate evaluated) */
 } misdc_stats;
 
 typedef struct misdc_solver misdc_solver;

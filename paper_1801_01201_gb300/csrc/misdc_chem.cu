@@ -62,14 +62,28 @@ __global__ void k_temperature(DevMech m, int n, int cs, const double *__restrict
   if (c >= n) return;
   const double h = hin[c];
   double lo = kTlo, hi = kThi, fl, fh, d;
+  double T = (Tg && Tg[c] > lo && Tg[c] < hi) ? Tg[c] : 1000.0;
+  // plain Newton from the guess first (h is monotone in T: cp > 0); the bracketed
+  // iteration below, with its check that [50, 6000] K holds the root, runs only
+  // when Newton leaves the range or does not settle
+  bool done = false;
+  for (int it = 0; it < 12; ++it) {
+    double f, df;
+    mix_h_cp(m, Y, cs, c, T, f, df);
+    const double Tn = T - (f - h) / df;
+    if (!(Tn > lo && Tn < hi)) break;
+    const double dT = Tn - T;
+    T = Tn;
+    if (fabs(dT) <= 1e-14 * T) { done = true; break; }
+  }
+  if (!done) {
+  T = (Tg && Tg[c] > lo && Tg[c] < hi) ? Tg[c] : 1000.0;
   mix_h_cp(m, Y, cs, c, lo, fl, d);
   mix_h_cp(m, Y, cs, c, hi, fh, d);
-  double T;
   if (!(fl - h <= 0.0 && fh - h >= 0.0)) {
     atomicOr(&st->status_bits, kBitTdiag);
     T = NAN;
   } else {
-    T = (Tg && Tg[c] > lo && Tg[c] < hi) ? Tg[c] : 1000.0;
     for (int it = 0; it < 200; ++it) {
       double f, df;
       mix_h_cp(m, Y, cs, c, T, f, df);
@@ -81,6 +95,7 @@ __global__ void k_temperature(DevMech m, int n, int cs, const double *__restrict
       T = Tn;
       if (fabs(dT) <= 1e-14 * T) break;
     }
+  }
   }
   Tout[c] = T;
   if (theta) theta[c] = pow(T / m.T_ref, m.theta_exp);
@@ -283,7 +298,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
                                                  const double *__restrict__ sc, double s_min,
                                                  const double *__restrict__ FRp,
                                                  const double *__restrict__ hp,
-                                                 int *__restrict__ work, ChordStore cst) {
+                                                 int *__restrict__ work, ChordStore cst,
+                                                 const int *__restrict__ prow,
+                                                 const double *__restrict__ hspp,
+                                                 const double *__restrict__ thp) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int N = m.N, R = m.R, nn = N + 1, na = nn + 1;   // na: columns of the augmented matrix
@@ -292,7 +310,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
   double *J = w.J;
   const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
   unsigned long long my_solves = 0, my_iters = 0, my_fail = 0, my_sg = 0, my_rej = 0, my_fb = 0,
-                     my_jac = 0, my_lu64 = 0;
+                     my_jac = 0, my_lu64 = 0, my_cert = 0;
   int my_max = 0;
   unsigned bits = 0;
 
@@ -315,13 +333,15 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     // residual at x_p (whose scaled max-norm is s); x_p is kept in dx until then
     bool judge = false;
     double s0 = 0.0;
+    int prw = cell;
     if (pred) {
       s0 = sc[cell];
-      judge = s0 > s_min && isfinite(s0);
+      if (prow) prw = prow[cell];
+      judge = prw >= 0 && s0 > s_min && isfinite(s0);
     }
     __syncwarp();
     if (judge) {
-      const float *pc = pred + (size_t)cell * ldp;
+      const float *pc = pred + (size_t)prw * ldp;
       for (int i = lane; i < nn; i += 32) {
         const double xp = w.xs[i];
         w.dx[i] = xp;
@@ -334,6 +354,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     // iterations and across calls (the node's previous solve) while the chord
     // iteration contracts; `have` says the shared-memory factor is usable
     bool have = false, fresh = false, from_store = false, fresh_exact = false, no32 = false;
+    bool fac32 = false;   // the factor at hand was built in FP32 (its first step may mislead)
     bool exact = false;   // retry: plain FP64 Newton, no factor reuse
     double sTf = 0.0;
     if (MIXED && cst.valid) no32 = (cst.valid[cell] & 2) != 0;   // FP32 factors failed this cell
@@ -342,7 +363,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       // relative) of the state it was built at: a stale factor of a stiffer
       // Jacobian would shrink the chord step and fake convergence
       const double *src = cst.f + (size_t)cell * cst.fs;
-      const double *xf = src + nn * nn + 3 * nn + 1;
+      const double *xf = src + nn * nn + 2 * nn + 2;
       double dist = 0.0;
       for (int i = lane; i < nn; i += 32) {
         const double xi = w.xs[i];
@@ -360,7 +381,8 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           w.res[i] = src[nn * nn + nn + i];
           w.sw[i] = cst.sw[(size_t)cell * cst.swld + i];
         }
-        sTf = src[nn * nn + 3 * nn];
+        sTf = src[nn * nn + 2 * nn];
+        fac32 = src[nn * nn + 2 * nn + 1] != 0.0;
         have = true;
         from_store = true;
       }
@@ -369,6 +391,44 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     if (MIXED) {   // restart point: the plain guess x_p
       for (int i = lane; i < nn; i += 32) w.xg[i] = judge ? w.dx[i] : w.xs[i];
       __syncwarp();
+    }
+    if (MIXED && from_store && !fac32 && !judge && FRp && hspp) {
+      // A chord step certified without evaluating any rate: the residual of the
+      // guess follows from its stored reaction term, r = b - Y_p + wdt F_p (and
+      // h* - h_p), and the kept factor gives the step. A guess whose step is
+      // below rtol / 100 is the solution: the cell keeps x_p, its species
+      // enthalpies and theta, and only its reaction term (Y - b)/wdt is new.
+      for (int i = lane; i < nn; i += 32)
+        w.r64[i] = (i < N) ? w.bs[i] - w.xs[i] + wdt * FRp[(size_t)i * cs + cell]
+                           : (hst - hp[cell]) * sTf;
+      __syncwarp();
+      solve_kept(w, J, ld, nn, lane, w.r64, w.zd);
+      double d0 = 0.0;
+      for (int i = lane; i < nn; i += 32) d0 = fmax(d0, fabs(w.zd[i]) * ((i < N) ? 1.0 : 1.0 / w.xs[N]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d0 = fmax(d0, __shfl_xor_sync(0xffffffffu, d0, o));
+      if (d0 <= 0.01 * rtol) {
+        double invw = 0.0;
+        if (lane == 0 && wdt > 0.0) invw = 1.0 / wdt;
+        invw = __shfl_sync(0xffffffffu, invw, 0);
+        for (int i = lane; i < N; i += 32) {
+          const double y = w.xs[i];
+          Yout[(size_t)i * cs + cell] = y;
+          if (FR) FR[(size_t)i * cs + cell] = (y - w.bs[i]) * invw;
+          if (hsp) hsp[(size_t)i * cs + cell] = hspp[(size_t)i * cs + cell];
+        }
+        if (lane == 0) {
+          Tout[cell] = w.xs[N];
+          if (theta) theta[cell] = thp[cell];
+          if (iters) iters[cell] = 1;
+        }
+        __syncwarp();
+        ++my_solves;
+        ++my_iters;
+        ++my_cert;
+        my_max = max(my_max, 1);
+        continue;
+      }
     }
     double T = w.xs[N];
     double dprev = INFINITY;
@@ -630,6 +690,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
             have = fresh = true;
             fresh_exact = false;
             from_store = false;
+            fac32 = true;
             sTf = sT;
           }
         }
@@ -696,6 +757,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           __syncwarp();
           have = fresh = fresh_exact = true;
           from_store = false;
+          fac32 = false;
           sTf = sT;
         }
       }
@@ -708,10 +770,13 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         for (int i = lane; i < nn; i += 32) {
           dst[nn * nn + i] = w.piv[i];
           dst[nn * nn + nn + i] = w.res[i];
-          dst[nn * nn + 3 * nn + 1 + i] = w.xs[i];
+          dst[nn * nn + 2 * nn + 2 + i] = w.xs[i];
           cst.sw[(size_t)cell * cst.swld + i] = (unsigned char)w.sw[i];
         }
-        if (lane == 0) dst[nn * nn + 3 * nn] = sT;
+        if (lane == 0) {
+          dst[nn * nn + 2 * nn] = sT;
+          dst[nn * nn + 2 * nn + 1] = fac32 ? 1.0 : 0.0;
+        }
       }
       if (MIXED && judge && !singular) {
         // Mixed precision judges the learned guess x0 in Newton's natural norm: the
@@ -749,6 +814,21 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         }
       }
       // ---- update and convergence on d = max(max|dY|, |dT|/T)
+      if (MIXED && exact) {
+        // the restart of a failed mixed solve limits its steps to |dT| <= T/2 and
+        // |dY_i| <= 1/2 (plain Newton from the previous iterate can overshoot at
+        // steep fronts); converged steps are far inside the limits
+        double big = 0.0;
+        for (int i = lane; i < nn; i += 32)
+          big = fmax(big, (i < N) ? 2.0 * fabs(w.dx[i]) : 2.0 * fabs(w.dx[i]) / w.xs[N]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) big = fmax(big, __shfl_xor_sync(0xffffffffu, big, o));
+        if (big > 1.0) {
+          const double lam = 1.0 / big;
+          for (int i = lane; i < nn; i += 32) w.dx[i] *= lam;
+          __syncwarp();
+        }
+      }
       double dmax = 0.0;
       bool fin = true;
       for (int i = lane; i < nn; i += 32) {
@@ -772,16 +852,15 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         // very stiff cells (the step no longer halves below 1e-8)
         if (d <= rtol || (d <= 1e-8 && d >= 0.5 * dprev)) break;
       } else if (fresh) {
-        // a step with a new FP32 factor: converged when far below rtol
-        if (d <= 0.01 * rtol) break;
+        // a step with a new FP32 factor is judged only by the chord steps after it
       } else {
         // chord steps converge linearly: with the contraction th = d_k / d_{k-1} of
         // two steps on the same factor the remaining error is about d th / (1 - th);
         // a chord contracting by less than 10 gets a new factor. A first step on a
-        // stored factor that is far below rtol is converged; one that is large is
-        // undone and the factor rebuilt.
+        // stored FP64-built factor that is far below rtol is converged; one that is
+        // large is undone and the factor rebuilt.
         if (it == 1) {
-          if (d <= 0.01 * rtol) break;
+          if (!fac32 && d <= 0.01 * rtol) break;
           if (d > 1e-2) {
             for (int i = lane; i < nn; i += 32) w.xs[i] -= w.dx[i];
             __syncwarp();
@@ -802,8 +881,15 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     }
     if (code == 0 && it > maxit) code = -1;
     }   // attempt
+    if (MIXED && code) {
+      // both attempts failed: the cell keeps its finite starting point (the
+      // failure is reported through the status word)
+      for (int i = lane; i < nn; i += 32) w.xs[i] = w.xg[i];
+      __syncwarp();
+      T = w.xs[N];
+    }
     // species enthalpies and theta at the solution; reaction term (Y - b)/wdt
-    const double Tf = (code == -3) ? 1000.0 : T;
+    const double Tf = (code == -3 && !MIXED) ? 1000.0 : T;
     double invw = 0.0;
     if (lane == 0 && wdt > 0.0) invw = 1.0 / wdt;
     invw = __shfl_sync(0xffffffffu, invw, 0);
@@ -849,6 +935,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     if (my_fb) atomicAdd(&st->fp64_fallbacks, my_fb);
     if (my_jac) atomicAdd(&st->jacobians, my_jac);
     if (my_lu64) atomicAdd(&st->lu64, my_lu64);
+    if (my_cert) atomicAdd(&st->certified, my_cert);
   }
 }
 
@@ -927,7 +1014,8 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
                    DevStats *st, cudaStream_t s, bool mixed, const float *pred, int ldp,
                    const double *sc, double s_min, const double *FRp, const double *hp,
-                   const NewtonLaunch *cfg, const ChordStore *store) {
+                   const NewtonLaunch *cfg, const ChordStore *store, const int *prow,
+                   const double *hspp, const double *thp) {
   if (n <= 0) return;
   int ld, wpb;
   const size_t sm = newton_smem(m, mixed, ld, wpb, cfg ? cfg->wpb : 0);
@@ -942,11 +1030,11 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
   if (mixed)
     k_newton2<true><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
                                                FR, hsp, theta, iters, st, pred, ldp, sc,
-                                               s_min, FRp, hp, work, cst);
+                                               s_min, FRp, hp, work, cst, prow, hspp, thp);
   else
     k_newton2<false><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
                                                 FR, hsp, theta, iters, st, pred, ldp, sc,
-                                                s_min, FRp, hp, work, cst);
+                                                s_min, FRp, hp, work, cst, prow, hspp, thp);
 }
 
 }  // namespace misdc

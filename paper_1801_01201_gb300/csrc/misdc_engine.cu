@@ -347,16 +347,22 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
                  guess.phi + N * cs, sg->ldx, sg->DX, sg->scale, s->sg_smin, sg->ds_count,
                  sg->ds_cap, sg->rowmap, st);
   } else if (sg && s->sg_on) {
-    // learned guess: features and the four layers in one fused kernel
-    mlp_fused_forward(*sg, &s->m, s->cs, wdt, s->bR, ad.phi + N * cs, guess.phi, guess.T,
-                      guess.FR, guess.phi + N * cs, sg->scale, nullptr, s->cs, sg->Oi, st);
+    // learned guess: features of the cells worth it (s > s_min) gathered into
+    // compact rows, then the four layers in one fused kernel over those rows
+    cudaMemsetAsync(sg->inf_count, 0, sizeof(unsigned long long), st);
+    mlp_features(s->m, s->cs, s->cs, wdt, s->bR, ad.phi + N * cs, guess.phi, guess.T, guess.FR,
+                 guess.phi + N * cs, sg->ldx, sg->Xi, sg->scale, s->sg_smin, sg->inf_count, s->cs,
+                 sg->rowmap, st);
+    mlp_fused_forward(*sg, nullptr, 0, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, sg->Xi, s->cs, sg->Oi, st, sg->inf_count);
     pred = sg->Oi;
   }
   launch_newton(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, s->bR,
                 ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR, out.hsp, out.theta,
                 s->iters, s->st, st, s->o.precision == MISDC_PREC_MIXED, pred, sg ? sg->ldo : 0,
                 sg ? sg->scale : nullptr, s->sg_smin, guess.FR, guess.phi + N * cs, &s->nl,
-                s->keep_factors ? &s->cst[t] : nullptr);
+                s->keep_factors ? &s->cst[t] : nullptr, pred ? sg->rowmap : nullptr, guess.hsp,
+                guess.theta);
   if (sg && s->sg_collect)
     mlp_targets(s->N, s->cs, s->cs, guess.phi, guess.T, out.phi, out.T, sg->scale, sg->rowmap,
                 sg->ldo, sg->DT, st);
@@ -854,6 +860,7 @@ misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
   out->newton_fp64_fallbacks = (long long)d.fp64_fallbacks;
   out->newton_jacobians = (long long)d.jacobians;
   out->newton_lu_fp64 = (long long)d.lu64;
+  out->newton_certified = (long long)d.certified;
   int st = MISDC_OK;
   if (d.status_bits & kBitTdiag) st = MISDC_E_TDIAG;
   else if (d.status_bits & (kBitNan | kBitSingular)) st = MISDC_E_NAN;
@@ -1596,6 +1603,7 @@ misdc_status misdc_batch_stats(misdc_batch *b, misdc_stats *out, int reset) {
     sum.newton_fp64_fallbacks += t.newton_fp64_fallbacks;
     sum.newton_jacobians += t.newton_jacobians;
     sum.newton_lu_fp64 += t.newton_lu_fp64;
+    sum.newton_certified += t.newton_certified;
   }
   sum.kernel_launches = b->kernels_launched;
   if (reset) b->kernels_launched = 0;

@@ -37,6 +37,7 @@ struct DevStats {
   unsigned long long fp64_fallbacks;   // mixed-precision solves restarted with FP64 Newton
   unsigned long long jacobians;        // Jacobian assemblies of the reaction Newton
   unsigned long long lu64;             // FP64 LU factorisations of the reaction Newton
+  unsigned long long certified;        // solves whose guess was certified without rates
 };
 
 // Mechanism tables in device memory (built by the engine from misdc_mech_desc).
@@ -82,10 +83,13 @@ void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double
                   double *FR, cudaStream_t s);
 // Reaction Newton (S5). b [N][cs], hstar [cs], guess Yg [N][cs], Tg [cs];
 // outputs Y, T, FR (wdot/rho at the solution), hsp [N][cs] and theta at the solution.
-// pred [n][ldp] (optional): learned correction, applied to cells with sc[c] > s_min as
+// pred [.][ldp] (optional): learned correction, row prow[c] of cell c (prow NULL: row c;
+// negative: none), applied to cells with sc[c] > s_min as
 // x0 = x_p + sc p (T scaled by T_p) and kept only if the Jacobi-scaled residual at x0 is
 // below that at the guess x_p, whose reaction term FRp [N][cs] and enthalpy hp [cs] give
-// its residual without a rate evaluation.
+// its residual without a rate evaluation. Mixed precision with a kept factor: a guess
+// certified converged from FRp and hp alone is returned as is, with the guess's species
+// enthalpies hspp [N][cs] and theta thp [cs].
 // Launch shape of the reaction Newton (chosen by the autotuner): warps per block
 // (0: largest that fits), resident-block cap per SM (0: default), and dynamic
 // cell scheduling through the device counter `work`.
@@ -95,9 +99,9 @@ struct NewtonLaunch {
 };
 // Mixed precision: per-cell Jacobian factors kept between the solves of one SDC
 // node. Per cell: fs doubles (row-major LU of the (row-scaled) (N+1)^2 Jacobian,
-// pivot reciprocals, row scales, the temperature-row scale, the state it was built
-// at) and swld bytes of pivot rows; valid[c] bit 0: the factor may be used, bit 1:
-// FP32 factors are too coarse for this cell.
+// pivot reciprocals, row scales, the temperature-row scale, an FP32-built flag, the
+// state it was built at) and swld bytes of pivot rows; valid[c] bit 0: the factor
+// may be used, bit 1: FP32 factors are too coarse for this cell.
 struct ChordStore {
   double *f = nullptr;
   unsigned char *sw = nullptr;
@@ -106,7 +110,7 @@ struct ChordStore {
 };
 __host__ __device__ inline int chord_floats(int N) {
   const int nn = N + 1;
-  return (nn * nn + 4 * nn + 1 + 1) / 2 * 2;
+  return (nn * nn + 3 * nn + 2 + 1) / 2 * 2;
 }
 void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit,
                    const double *b, const double *hstar, const double *Yg, const double *Tg,
@@ -114,7 +118,9 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                    DevStats *st, cudaStream_t s, bool mixed = false,
                    const float *pred = nullptr, int ldp = 0, const double *sc = nullptr,
                    double s_min = 0.0, const double *FRp = nullptr, const double *hp = nullptr,
-                   const NewtonLaunch *cfg = nullptr, const ChordStore *store = nullptr);
+                   const NewtonLaunch *cfg = nullptr, const ChordStore *store = nullptr,
+                   const int *prow = nullptr, const double *hspp = nullptr,
+                   const double *thp = nullptr);
 int newton_max_wpb(const DevMech &m, bool mixed);
 
 // ---- grid kernels (misdc_grid.cu) ----
@@ -187,7 +193,7 @@ struct Surrogate;
 void mlp_fused_forward(const Surrogate &g, const DevMech *m, int cs, double wdt, const double *b,
                        const double *hstar, const double *Yp, const double *Tp, const double *FRp,
                        const double *hp, double *scale, const __nv_bfloat16 *X, int n, float *out,
-                       cudaStream_t s);
+                       cudaStream_t s, const unsigned long long *count = nullptr);
 void mlp_features(const DevMech &m, int n, int cs, double wdt, const double *b,
                   const double *hstar, const double *Yp, const double *Tp, const double *FRp,
                   const double *hp, int ldx, __nv_bfloat16 *X, double *scale, double s_min,
@@ -226,6 +232,7 @@ struct Surrogate {
   float *Oi = nullptr;
   double *scale = nullptr;
   int *rowmap = nullptr;
+  unsigned long long *inf_count = nullptr;   // rows of the compacted inference batch
   // training batch
   int cap_tr = 0;
   __nv_bfloat16 *Xt = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *dOb = nullptr,

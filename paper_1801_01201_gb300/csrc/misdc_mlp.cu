@@ -438,6 +438,7 @@ struct FusedArgs {
   double *scale;
   // ... or BF16 rows X [n][ldx]
   const __nv_bfloat16 *X;
+  const unsigned long long *count;   // optional: rows actually present (device), <= n
   int n, ldx, k1;          // rows, feature row length, layer-1 K (ldx rounded up to 64)
   const __nv_bfloat16 *W[4];
   const float *bias[4];
@@ -460,6 +461,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(FusedArgs a) {
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r0 = blockIdx.x * kTileM;
+  if (a.count) {   // compacted rows: tiles past the device count have nothing to do
+    const unsigned long long nr = *a.count;
+    if ((unsigned long long)r0 >= nr) return;
+    if (nr < (unsigned long long)a.n) a.n = (int)nr;
+  }
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -623,7 +629,7 @@ void mlp_prepare() {
 void mlp_fused_forward(const Surrogate &g, const DevMech *m, int cs, double wdt, const double *b,
                        const double *hstar, const double *Yp, const double *Tp, const double *FRp,
                        const double *hp, double *scale, const __nv_bfloat16 *X, int n, float *out,
-                       cudaStream_t s) {
+                       cudaStream_t s, const unsigned long long *count) {
   if (n <= 0) return;
   FusedArgs a;
   memset(&a, 0, sizeof(a));
@@ -632,6 +638,7 @@ void mlp_fused_forward(const Surrogate &g, const DevMech *m, int cs, double wdt,
   a.wdt = wdt;
   a.b = b; a.hstar = hstar; a.Yp = Yp; a.Tp = Tp; a.FRp = FRp; a.hp = hp; a.scale = scale;
   a.X = X;
+  a.count = count;
   a.n = n;
   a.ldx = g.ldx;
   a.k1 = (g.ldx + kTileK - 1) / kTileK * kTileK;
@@ -797,6 +804,7 @@ cudaError_t Surrogate::ensure_inference(int cells) {
   SG_CK(alloc(&Oi, (size_t)cells * ldo));
   SG_CK(alloc(&scale, (size_t)cells));
   SG_CK(alloc(&rowmap, (size_t)cells));
+  if (!inf_count) SG_CK(alloc(&inf_count, 1));
   return cudaSuccess;
 }
 
