@@ -500,6 +500,9 @@ def main():
              "status": s_["status_name"]}
         if r["newton_launches"]:
             d["newton_ms_per_step"] = r["newton_ms"] / args.steps
+        ns = max(s_["newton_solves"], 1)
+        d["newton_jacobians_per_solve"] = s_["newton_jacobians"] / ns
+        d["newton_certified_per_solve"] = s_["newton_certified"] / ns
         if k == "learned_mixed":
             d["surrogate_used"] = s_["surrogate_used"]
             d["surrogate_rejected"] = s_["surrogate_rejected"]

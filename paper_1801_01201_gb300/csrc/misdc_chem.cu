@@ -857,11 +857,11 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         // chord steps converge linearly: with the contraction th = d_k / d_{k-1} of
         // two steps on the same factor the remaining error is about d th / (1 - th);
         // a chord contracting by less than 10 gets a new factor. A first step on a
-        // stored FP64-built factor that is far below rtol is converged; one that is
-        // large is undone and the factor rebuilt.
+        // stored FP64-built factor that is far below rtol is converged; one above
+        // 1e-4 is undone and the factor rebuilt.
         if (it == 1) {
           if (!fac32 && d <= 0.01 * rtol) break;
-          if (d > 1e-2) {
+          if (d > 1e-4) {
             for (int i = lane; i < nn; i += 32) w.xs[i] -= w.dx[i];
             __syncwarp();
             T = w.xs[N];
@@ -877,6 +877,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           }
         }
       }
+      // chord steps only near the root: after a large step (d > 1e-4) the next
+      // iteration builds a new factor, so far from convergence the iterates follow
+      // Newton's own path (and the root it finds)
+      if (MIXED && !exact && d > 1e-4) have = false;
       dprev = d;
     }
     if (code == 0 && it > maxit) code = -1;
