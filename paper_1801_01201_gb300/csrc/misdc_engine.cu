@@ -170,6 +170,7 @@ struct misdc_solver {
   // mixed precision: FP32 Jacobian factors kept per node between its solves
   ChordStore cst[kMaxNodes + 1];
   bool keep_factors = true;
+  double store_dt = -1.0;   // the time step the kept factors belong to
   DiffWork dw{};
   DevStats *st = nullptr;
   cudaStream_t sD = nullptr, sR = nullptr;
@@ -491,15 +492,18 @@ misdc_status configure_dt(misdc_solver *s, double dt) {
   }
   s->rho_bound = rho_bound_for(s, dt * qmax);
   s->cheb_sweeps = std::min(kMaxCheb, chebyshev_sweeps(s->rho_bound, std::max(1e-3 * s->o.lin_rtol, 1e-17)));
-  if (s->rho_dt > 0.0) {
-    // the stored Jacobian factors belong to the old weights w dt
-    cudaStreamSynchronize(s->sD);
-    cudaStreamSynchronize(s->sR);
-    for (int j = 1; j <= s->tab.M; ++j)
-      if (s->cst[j].valid) cudaMemsetAsync(s->cst[j].valid, 0, (size_t)s->cs * sizeof(int), s->sD);
-    cudaStreamSynchronize(s->sD);
-  }
   s->rho_dt = dt;
+  if (s->store_dt != dt) {
+    // kept Jacobian factors belong to the weights w dt of another time step
+    if (s->store_dt > 0.0) {
+      cudaStreamSynchronize(s->sD);
+      cudaStreamSynchronize(s->sR);
+      for (int j = 1; j <= s->tab.M; ++j)
+        if (s->cst[j].valid) cudaMemsetAsync(s->cst[j].valid, 0, (size_t)s->cs * sizeof(int), s->sD);
+      cudaStreamSynchronize(s->sD);
+    }
+    s->store_dt = dt;
+  }
   return MISDC_OK;
 }
 
@@ -701,6 +705,12 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     return bail(fail(MISDC_E_OOM, "work buffers"));
   cudaMemset(s->st, 0, sizeof(DevStats));
   if (s->o.precision == MISDC_PREC_MIXED) {
+    DiffWork &w = s->dw;
+    if (s->alloc(&w.thf32, 3 * cs) || s->alloc(&w.invdiag32, F * cs) || s->alloc(&w.r32, F * cs) ||
+        s->alloc(&w.e32[0], F * cs) || s->alloc(&w.e32[1], F * cs) || s->alloc(&w.e32[2], F * cs) ||
+        s->alloc(&w.kdev32, 1) || s->alloc(&w.omega32, kMaxCheb))
+      return bail(fail(MISDC_E_OOM, "mixed diffusion buffers"));
+    w.refine_rounds = 3;
     for (int j = 1; j <= M; ++j) {
       ChordStore &c = s->cst[j];
       c.fs = chord_floats(N);

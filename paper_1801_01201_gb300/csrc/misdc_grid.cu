@@ -144,7 +144,8 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
 // cells, for the largest c_f (bit pattern of a non-negative double).
 __global__ void k_face_coef(DevGrid g, FieldMap fm, const double *__restrict__ theta,
                             double *__restrict__ thf, double *__restrict__ invdiag, double cmax,
-                            unsigned long long *rho_bits) {
+                            unsigned long long *rho_bits, float *__restrict__ thf32,
+                            float *__restrict__ invdiag32) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int cs = g.cells;
   double ratio = 0.0;
@@ -156,9 +157,14 @@ __global__ void k_face_coef(DevGrid g, FieldMap fm, const double *__restrict__ t
       const double a = theta[nb.cm[d]], b = theta[nb.cp[d]];
       const double lo = 2.0 * a * tc / (a + tc), hi = 2.0 * tc * b / (tc + b);
       thf[(size_t)d * cs + c] = lo;
+      if (thf32) thf32[(size_t)d * cs + c] = (float)lo;
       S += lo + hi;
     }
-    for (int k = 0; k < fm.nfs; ++k) invdiag[(size_t)k * cs + c] = 1.0 / (1.0 + fm.cf[k] * S);
+    for (int k = 0; k < fm.nfs; ++k) {
+      const double di = 1.0 / (1.0 + fm.cf[k] * S);
+      invdiag[(size_t)k * cs + c] = di;
+      if (invdiag32) invdiag32[(size_t)k * cs + c] = (float)di;
+    }
     ratio = cmax * S / (1.0 + cmax * S);
   }
   if (rho_bits) {
@@ -188,6 +194,80 @@ __global__ void k_cheb_plan(const unsigned long long *rho_bits, int kmax, double
     if (k == 1) om = 1.0 / (1.0 - 0.5 * r2);
     else if (k > 1) om = 1.0 / (1.0 - 0.25 * r2 * om);
     omega[k] = om;
+  }
+}
+
+// ---- mixed precision: iterative refinement with FP32 inner Chebyshev solves
+// x_{j+1} = x_j + e_j, A e_j = r_j = b - A x_j solved approximately in FP32 from
+// e_j = 0; r_j and the update in FP64.
+
+// x_out = x_in + e (e: the buffer the last planned inner sweep wrote; none in the
+// first round, where x_in = b), r32 = b - A x_out, for every solved field
+__global__ void k_refine_residual(DevGrid g, FieldMap fm, const double *__restrict__ thf,
+                                  const double *__restrict__ rhs, const double *x_in,
+                                  const float *e0, const float *e1, const float *e2,
+                                  const int *__restrict__ kdev, double *x_out,
+                                  float *__restrict__ r32) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cs = g.cells;
+  if (c >= cs) return;
+  const float *e = nullptr;
+  if (e0) {
+    const int sl = (*kdev - 1) % 3;
+    e = sl == 0 ? e0 : (sl == 1 ? e1 : e2);
+  }
+  const Nbr nb = neighbours(g, c);
+  const int k0 = blockIdx.y * 4, k1 = min(fm.nfs, k0 + 4);
+  for (int k = k0; k < k1; ++k) {
+    const size_t off = (size_t)fm.fld[k] * cs;
+    // the updated iterate at this cell and its neighbours (x_in + e on the fly)
+    auto xv = [&](int q) -> double { return x_in[off + q] + (e ? (double)e[off + q] : 0.0); };
+    const double xc = xv(c);
+    double L = 0.0;
+    for (int d = 0; d < g.dim; ++d)
+      L += thf[(size_t)d * cs + nb.cp[d]] * (xv(nb.cp[d]) - xc) - thf[(size_t)d * cs + c] * (xc - xv(nb.cm[d]));
+    x_out[off + c] = xc;
+    r32[off + c] = (float)(rhs[off + c] - (xc - fm.cf[k] * L));
+  }
+}
+
+// one FP32 Chebyshev-accelerated Jacobi sweep of A e = r from e = 0 (same method
+// as k_cheb; weights from the FP64 plan of the inner reduction)
+__global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
+                         const float *__restrict__ invdiag, const float *__restrict__ rhs,
+                         const float *__restrict__ xk, const float *__restrict__ xkm1,
+                         float *__restrict__ xkp1, int it, const int *__restrict__ kdev,
+                         const double *__restrict__ omega) {
+  if (it >= *kdev) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cs = g.cells;
+  if (c >= cs) return;
+  const Nbr nb = neighbours(g, c);
+  float tlo[3], thi[3];
+  int cm[3], cp[3];
+  for (int d = 0; d < g.dim; ++d) {
+    cm[d] = nb.cm[d];
+    cp[d] = nb.cp[d];
+    tlo[d] = thf[(size_t)d * cs + c];
+    thi[d] = thf[(size_t)d * cs + cp[d]];
+  }
+  const float om = (float)omega[it];
+  const int k0 = blockIdx.y * 4, k1 = min(fm.nfs, k0 + 4);
+  for (int k = k0; k < k1; ++k) {
+    const size_t off = (size_t)fm.fld[k] * cs;
+    const float cf = (float)fm.cf[k];
+    float y;
+    if (it == 0) {   // e_0 = 0: the first sweep is D^{-1} r
+      y = rhs[off + c] * invdiag[(size_t)k * cs + c];
+      xkp1[off + c] = y;
+    } else {
+      const float *x = xk + off;
+      float sx = 0.0f;
+      for (int d = 0; d < g.dim; ++d) sx += thi[d] * x[cp[d]] + tlo[d] * x[cm[d]];
+      y = (rhs[off + c] + cf * sx) * invdiag[(size_t)k * cs + c];
+      const float prev = xkm1 ? xkm1[off + c] : 0.0f;
+      xkp1[off + c] = fmaf(om, y - prev, prev);
+    }
   }
 }
 
@@ -428,7 +508,8 @@ void launch_operators(const DevMech &m, const DevGrid &g, int i0, const double *
 void launch_theta_faces(const DevGrid &g, const double *theta, double *thf, cudaStream_t s) {
   FieldMap fm;
   fm.nfs = 0;
-  k_face_coef<<<(g.cells + 255) / 256, 256, 0, s>>>(g, fm, theta, thf, nullptr, 0.0, nullptr);
+  k_face_coef<<<(g.cells + 255) / 256, 256, 0, s>>>(g, fm, theta, thf, nullptr, 0.0, nullptr,
+                                                     nullptr, nullptr);
 }
 
 void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, const double *theta,
@@ -440,7 +521,35 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
   double cmax = 0.0;
   for (int k = 0; k < fm.nfs; ++k) cmax = std::max(cmax, fm.cf[k]);
   cudaMemsetAsync(w.rho_bits, 0, sizeof(unsigned long long), s);
-  k_face_coef<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, theta, w.thf, w.invdiag, cmax, w.rho_bits);
+  k_face_coef<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, theta, w.thf, w.invdiag, cmax, w.rho_bits,
+                                               w.thf32, w.invdiag32);
+  if (w.refine_rounds > 0 && w.levels <= 1) {
+    // mixed precision: FP64 residuals, FP32 inner Chebyshev solves (reduction 1e-6
+    // each), three rounds, then the same reconstruction and checks as below
+    const int k32 = std::min(sweeps, chebyshev_sweeps(rho_bound, 1e-6));
+    k_cheb_plan<<<1, 32, 0, s>>>(w.rho_bits, k32, 1e-6, w.kdev32, w.omega32);
+    const dim3 gr4((cs + 255) / 256, (fm.nfs + 3) / 4);
+    const double *xin = rhs;
+    double *xr[2] = {w.xa, w.xb};
+    for (int round = 0; round < w.refine_rounds; ++round) {
+      double *xo = xr[round & 1];
+      k_refine_residual<<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xin, round ? w.e32[0] : nullptr,
+                                            w.e32[1], w.e32[2], w.kdev32, xo, w.r32);
+      for (int it = 0; it < k32; ++it) {
+        const float *ek = w.e32[(it + 2) % 3];
+        const float *ekm1 = (it >= 2) ? w.e32[(it + 1) % 3] : nullptr;   // e_0 = 0
+        k_cheb32<<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
+                                     w.e32[it % 3], it, w.kdev32, w.omega32);
+      }
+      xin = xo;
+    }
+    // last update x += e into xc, then the reconstruction and residual check
+    k_refine_residual<<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xin, w.e32[0], w.e32[1], w.e32[2],
+                                          w.kdev32, w.xc, w.r32);
+    k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, w.xc,
+                                              w.xc, w.xc, nullptr, out, st);
+    return;
+  }
   // sweeps: planned on the device from the measured Gershgorin bound, at most
   // `sweeps` (the a-priori bound with theta at the 6000 K cap)
   (void)rho_bound;

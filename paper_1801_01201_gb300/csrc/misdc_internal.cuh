@@ -150,6 +150,11 @@ struct DiffWork {
   // multigrid levels (level 0 = this grid, compact [solved field][cells] storage)
   int levels, cycles;
   int cheb_block;   // threads per block of the Chebyshev sweep (autotuned; 0 = 256)
+  // mixed precision: refinement rounds (0: plain FP64 Chebyshev) and FP32 work
+  int refine_rounds;
+  float *thf32, *invdiag32, *r32, *e32[3];
+  int *kdev32;
+  double *omega32;
   DevGrid lg[8];
   double *lthf[8], *linvdiag[8], *lb[8], *lx[8], *lr[8], *ly[8];
 };

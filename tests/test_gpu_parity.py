@@ -160,8 +160,10 @@ def test_operators_parity(dim):
         assert np.all(np.max(np.abs(got - want), axis=1) <= 1e-11 * scale + 1e-300)
 
 
-@pytest.mark.parametrize("levels", [1, 3])
-def test_diffusion_solve_parity(levels):
+@pytest.mark.parametrize("levels,precision", [(1, "fp64"), (3, "fp64"), (1, "mixed")])
+def test_diffusion_solve_parity(levels, precision):
+    """FP64 Chebyshev (with and without multigrid) and the mixed-precision
+    refinement (FP64 residuals, FP32 inner Chebyshev solves) against the oracle."""
     mech, fl = small_2d(n=32)
     ad = O.ADR(mech, fl)
     coef = ad.state_from_YT(fl.Y, fl.T)
@@ -170,7 +172,7 @@ def test_diffusion_solve_parity(levels):
     wdt = 5e-6 / 3
     want, rc = ad.solve_diff(wdt, coef, rhs)
     assert rc == 0
-    sv = S().Solver(mech, fl, mg_levels=levels)
+    sv = S().Solver(mech, fl, mg_levels=levels, precision=precision)
     got = sv.diffusion_solve(wdt, coef, rhs).cpu().numpy()
     assert np.all(relerr(got, want) < 1e-12)
     st = sv.stats()
