@@ -111,7 +111,7 @@ typedef struct misdc_stats {
   double lin_resid_max;         /* largest relative residual seen        */
   long long kernel_launches;    /* library kernels launched by misdc_step */
   long long surrogate_used;     /* cells whose Newton started from the learned guess */
-  long long surrogate_rejected; /* learned guesses the residual judge rejected */
+  long long surrogate_rejected; /* learned guesses the residual test rejected */
   long long newton_fp64_fallbacks; /* mixed precision: solves restarted with FP64
                                       Newton after the mixed iteration failed */
   long long newton_jacobians;   /* Jacobian assemblies (every iteration in FP64 mode;

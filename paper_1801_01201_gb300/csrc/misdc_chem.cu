@@ -331,16 +331,16 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     const double hst = hstar[cell];
     // learned guess: x0 = x_p + s p, judged below by its residual against the
     // residual at x_p (whose scaled max-norm is s); x_p is kept in dx until then
-    bool judge = false;
+    bool vet = false;
     double s0 = 0.0;
     int prw = cell;
     if (pred) {
       s0 = sc[cell];
       if (prow) prw = prow[cell];
-      judge = prw >= 0 && s0 > s_min && isfinite(s0);
+      vet = prw >= 0 && s0 > s_min && isfinite(s0);
     }
     __syncwarp();
-    if (judge) {
+    if (vet) {
       const float *pc = pred + (size_t)prw * ldp;
       for (int i = lane; i < nn; i += 32) {
         const double xp = w.xs[i];
@@ -389,10 +389,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       __syncwarp();
     }
     if (MIXED) {   // restart point: the plain guess x_p
-      for (int i = lane; i < nn; i += 32) w.xg[i] = judge ? w.dx[i] : w.xs[i];
+      for (int i = lane; i < nn; i += 32) w.xg[i] = vet ? w.dx[i] : w.xs[i];
       __syncwarp();
     }
-    if (MIXED && from_store && !fac32 && !judge && FRp && hspp) {
+    if (MIXED && from_store && !fac32 && !vet && FRp && hspp) {
       // A chord step certified without evaluating any rate: the residual of the
       // guess follows from its stored reaction term, r = b - Y_p + wdt F_p (and
       // h* - h_p), and the kept factor gives the step. A guess whose step is
@@ -561,14 +561,14 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         __syncwarp();
       }
       }   // jac
-      if (!MIXED && judge) {
+      if (!MIXED && vet) {
         // Accept the learned guess only if the residual drops, measured in the
         // Jacobi-scaled max-norm max_i |r_i / J_ii| (species rows; the temperature
         // row as the relative temperature change) with the Jacobian at the guess
         // (a diagonal stand-in for the natural norm |J^{-1} r| of Newton's method,
         // which a plain residual norm would overweight along stiff directions).
         // The residual at x_p comes from the stored reaction term of x_p.
-        judge = false;
+        vet = false;
         double rm = 0.0, rp = 0.0;
         for (int i = lane; i < nn; i += 32) {
           // the temperature row is already in units of dT/T; MIXED scales the
@@ -778,12 +778,12 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           dst[nn * nn + 2 * nn + 1] = fac32 ? 1.0 : 0.0;
         }
       }
-      if (MIXED && judge && !singular) {
-        // Mixed precision judges the learned guess x0 in Newton's natural norm: the
+      if (MIXED && vet && !singular) {
+        // Mixed precision tests the learned guess x0 in Newton's natural norm: the
         // step J^{-1} r(x0) just computed against J^{-1} r(x_p) through the same
         // factor, r(x_p) from the stored reaction term of x_p. A rejected guess
         // continues from x_p with that second step (no rate evaluation is lost).
-        judge = false;
+        vet = false;
         for (int i = lane; i < nn; i += 32)
           w.r64[i] = (i < N) ? w.bs[i] - w.xg[i] + wdt * FRp[(size_t)i * cs + cell]
                              : (hst - hp[cell]) * sTf;

@@ -33,7 +33,7 @@ struct DevStats {
   unsigned status_bits;
   unsigned long long lin_resid_bits;   // bit pattern of the largest relative residual (>= 0)
   unsigned long long sg_used;          // cells that started Newton from the learned guess
-  unsigned long long sg_rejected;      // learned guesses rejected by the residual judge
+  unsigned long long sg_rejected;      // learned guesses rejected by the residual test
   unsigned long long fp64_fallbacks;   // mixed-precision solves restarted with FP64 Newton
   unsigned long long jacobians;        // Jacobian assemblies of the reaction Newton
   unsigned long long lu64;             // FP64 LU factorisations of the reaction Newton

@@ -248,7 +248,7 @@ def test_dataset_rows_valid():
 
 def test_learned_guess_fallback_and_agreement():
     """A useless network (huge random output layer) is rejected by the residual
-    judge on every cell: the steps equal plain Newton's and take the same number
+    residual test on every cell: the steps equal plain Newton's and take the same number
     of iterations. A trained network leaves the answer unchanged too."""
     mech, fl = _mild_flame()
     dt = 5e-6
