@@ -460,12 +460,13 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(FusedArgs a) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw + kFSmemA + 2 * kFSmemB);   // [2]
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int r0 = blockIdx.x * kTileM;
-  if (a.count) {   // compacted rows: tiles past the device count have nothing to do
+  int nrows = a.n;
+  if (a.count) {   // compacted rows: only the tiles below the device row count
     const unsigned long long nr = *a.count;
-    if ((unsigned long long)r0 >= nr) return;
-    if (nr < (unsigned long long)a.n) a.n = (int)nr;
+    if (nr < (unsigned long long)nrows) nrows = (int)nr;
   }
+  const int ntiles = (nrows + kTileM - 1) / kTileM;
+  if ((int)blockIdx.x >= ntiles) return;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -477,12 +478,21 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(FusedArgs a) {
     mbar_init(bar, 1);
     mbar_init(bar + 1, 1);
   }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  uint32_t phase[2] = {0u, 0u};
+  bool ok = true;
+  // persistent CTAs: one 128-row tile after another
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+  const int r0 = tile * kTileM;
   // ---- layer-1 input rows into the A buffer
   if (FEAT) {
     if (tid < kTileM) {
       const int r = tid, c = r0 + r;
       const int N = a.m.N;
-      if (c < a.n) {
+      if (c < nrows) {
         const int cs = a.cs;
         const double T = a.Tp[c];
         double cp = 0.0, rmax = 0.0;
@@ -516,7 +526,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(FusedArgs a) {
     for (int e = tid; e < kTileM * a.k1; e += kFThreads) {
       const int r = e / a.k1, k = e - r * a.k1, c = r0 + r;
       __nv_bfloat16 v = __float2bfloat16(0.0f);
-      if (c < a.n && k < a.ldx) v = a.X[(size_t)c * a.ldx + k];
+      if (c < nrows && k < a.ldx) v = a.X[(size_t)c * a.ldx + k];
       sA[a_index(r, k)] = v;
     }
   }
@@ -524,9 +534,6 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(FusedArgs a) {
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = *tslot;
-  uint32_t phase[2] = {0u, 0u};
-  bool ok = true;
 
   for (int L = 0; L < 4; ++L) {
     const int K = (L == 0) ? a.k1 : kFKmax;
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(FusedArgs a) {
       if (L < 3) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) sA[a_index(row, c0 + i)] = __float2bfloat16(gelu(v[i] + bias[c0 + i]));
-      } else if (r0 + row < a.n) {
+      } else if (r0 + row < nrows) {
         float *o = a.out + (size_t)(r0 + row) * a.ldo;
 #pragma unroll
         for (int i = 0; i < 16; ++i) o[c0 + i] = v[i] + bias[c0 + i];
@@ -601,6 +608,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fused(FusedArgs a) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
   }
+  }   // tile
   if (!ok && tid == 0) atomicExch(a.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -649,7 +657,15 @@ void mlp_fused_forward(const Surrogate &g, const DevMech *m, int cs, double wdt,
   a.ldo = g.ldo;
   a.out = out;
   a.err = g.err;
-  const unsigned grid = (unsigned)((n + kTileM - 1) / kTileM);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int tiles = (n + kTileM - 1) / kTileM;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);   // one 160 KB CTA per SM
   if (m)
     k_mlp_fused<true><<<grid, kFThreads, kFSmem, s>>>(a);
   else

@@ -58,8 +58,9 @@ def _data(lay, n, seed):
     return MO.round_bf16(X), t
 
 
-@pytest.mark.parametrize("n", [1, 200, 1000])
+@pytest.mark.parametrize("n", [1, 200, 1000, 40000])
 def test_forward_parity(setup21, n):
+    """Row counts from one partial tile to 313 tiles (more than one tile per CTA)."""
     mech, fl, sv = setup21
     d = sv.surrogate_dims()
     lay = MO.Layout(mech.n_species)
