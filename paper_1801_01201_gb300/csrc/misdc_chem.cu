@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       // A chord step certified without evaluating any rate: the residual of the
       // guess follows from its stored reaction term, r = b - Y_p + wdt F_p (and
       // h* - h_p), and the kept factor gives the step. A guess whose step is
-      // below rtol / 100 is the solution: the cell keeps x_p, its species
+      // below rtol / 10 is the solution: the cell keeps x_p, its species
       // enthalpies and theta, and only its reaction term (Y - b)/wdt is new.
       for (int i = lane; i < nn; i += 32)
         w.r64[i] = (i < N) ? w.bs[i] - w.xs[i] + wdt * FRp[(size_t)i * cs + cell]
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       for (int i = lane; i < nn; i += 32) d0 = fmax(d0, fabs(w.zd[i]) * ((i < N) ? 1.0 : 1.0 / w.xs[N]));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) d0 = fmax(d0, __shfl_xor_sync(0xffffffffu, d0, o));
-      if (d0 <= 0.01 * rtol) {
+      if (d0 <= 0.1 * rtol) {
         double invw = 0.0;
         if (lane == 0 && wdt > 0.0) invw = 1.0 / wdt;
         invw = __shfl_sync(0xffffffffu, invw, 0);
@@ -857,10 +857,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         // chord steps converge linearly: with the contraction th = d_k / d_{k-1} of
         // two steps on the same factor the remaining error is about d th / (1 - th);
         // a chord contracting by less than 10 gets a new factor. A first step on a
-        // stored FP64-built factor that is far below rtol is converged; one above
+        // stored FP64-built factor below rtol / 10 is converged; one above
         // 1e-4 is undone and the factor rebuilt.
         if (it == 1) {
-          if (!fac32 && d <= 0.01 * rtol) break;
+          if (!fac32 && d <= 0.1 * rtol) break;
           if (d > 1e-4) {
             for (int i = lane; i < nn; i += 32) w.xs[i] -= w.dx[i];
             __syncwarp();

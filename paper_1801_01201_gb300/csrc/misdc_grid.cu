@@ -78,6 +78,9 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
   const int N = m.N, dim = g.dim;
   const Nbr nb = neighbours(g, c);
   const double invdx = 1.0 / g.dx, invdx2 = invdx * invdx;
+  // fourth-order face values are (7(a+b) - (c+d))/12; the 1/12 is applied once
+  // per field with 1/dx (an FP64 division per face would dominate the kernel)
+  const double adv = invdx / 12.0;
   double ulo[3], uhi[3], tlo[3], thi[3];
   double qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0}, glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
   for (int d = 0; d < dim; ++d) {
@@ -93,8 +96,8 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
     double fa = 0.0, fdl = 0.0;
     for (int d = 0; d < dim; ++d) {
       const double xm2 = x[nb.cm2[d]], xm = x[nb.cm[d]], xp = x[nb.cp[d]], xp2 = x[nb.cp2[d]];
-      const double lo = (7.0 * (xm + xc) - (xm2 + xp)) / 12.0;
-      const double hi = (7.0 * (xc + xp) - (xm + xp2)) / 12.0;
+      const double lo = 7.0 * (xm + xc) - (xm2 + xp);    // 12 x face value
+      const double hi = 7.0 * (xc + xp) - (xm + xp2);
       fa += uhi[d] * hi - ulo[d] * lo;
       fdl += thi[d] * (xp - xc) - tlo[d] * (xc - xm);
       if (f < N) {
@@ -114,7 +117,7 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
       }
     }
     if (f < N) {
-      if (FE) FE[(size_t)f * cs + c] = -fa * invdx;
+      if (FE) FE[(size_t)f * cs + c] = -fa * adv;
       if (f != i0) {
         const double v = m.D0[f] * fdl * invdx2;
         if (FD) FD[(size_t)f * cs + c] = v;
@@ -134,7 +137,7 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
       const double hbh = 0.5 * (hs0[c] + hs0[nb.cp[d]]);
       div += (qhi[d] + hbh * ghi[d]) - (qlo[d] + hbl * glo[d]);
     }
-    FE[(size_t)N * cs + c] = -fa_h * invdx - div * invdx;
+    FE[(size_t)N * cs + c] = -fa_h * adv - div * invdx;
   }
 }
 
