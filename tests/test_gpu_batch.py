@@ -111,3 +111,27 @@ def test_batch_rejects_bad_input():
     x = _state(s, fl[0][1])
     with pytest.raises(L.MisdcError):
         B.step([x], [0.0], 1)
+
+
+def test_batch_mixed_precision_bitwise_and_accurate():
+    """Mixed precision (kept Jacobian factors, learned guess off) in a batch equals
+    stepping each flame alone, and stays within the mixed bar of the FP64 oracle."""
+    fl = _flames()[:3]
+    single = [S().Solver(m, f, precision="mixed") for m, f, _ in fl]
+    batched = [S().Solver(m, f, precision="mixed") for m, f, _ in fl]
+    states = [_state(s, f) for s, (_, f, _) in zip(single, fl)]
+    ref = [x.clone() for x in states]
+    for s, x, (_, _, dt) in zip(single, ref, fl):
+        s.step(x, dt, 2)
+    got = [x.clone() for x in states]
+    B = S().Batch(batched)
+    B.step(got, [dt for _, _, dt in fl], 2)
+    assert B.stats()["status_name"] == "OK"
+    for x, y in zip(ref, got):
+        assert torch.equal(x, y)
+    m, f, dt = fl[0]
+    ad = O.ADR(m, f)
+    want, _ = ad.step(ad.state_from_YT(f.Y, f.T), dt, "CISDCQ", 2, 4, 2, n_steps=2)
+    g = got[0].cpu().numpy()
+    N = m.n_species
+    assert np.max(np.abs(g[:N] - want[:N])) / np.max(np.abs(want[:N])) < 1e-8

@@ -272,13 +272,16 @@ def test_step_parity_full_chemistry_multid(case):
     assert np.all(err <= tol_from(sens)), (err, sens)
 
 
-@pytest.mark.parametrize("case", ["2d_n21", "2d_n53"])
+@pytest.mark.parametrize("case", ["2d_n21", "2d_n53", "3d_n21"])
 def test_step_mixed_precision_meets_accuracy_bar(case):
     """Mixed mode against the FP64 oracle: Y within 1e-8, T within 1e-6 relative."""
     if case == "2d_n21":
         mech, fl = small_2d(n=32)
-    else:
+    elif case == "2d_n53":
         mech, fl = small_2d((1803, 53, 325), n=16)
+    else:
+        mech = I.make_mechanism(1802, 21, 84)
+        fl = I.flame_3d(mech, 0, n=12, dx=1e-4, radius=3e-4, delta=2e-4)
     got, T, want, ad, st, sens = _run_both(mech, fl, 5e-6, 2, precision="mixed", sensitivity=True)
     N = mech.n_species
     # mass fractions against the mass-fraction scale: the Newton tolerance is
