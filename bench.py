@@ -244,7 +244,8 @@ class Runner:
         self.states0 = []
         for mech, fl, dt in entries:
             sv = Solver(mech, fl, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"],
-                        scheme=args.scheme, precision=precision, profile=len(entries) == 1, device=dev)
+                        scheme=args.scheme, precision=precision, profile=len(entries) == 1,
+                        mg_levels=args.mg_levels, rates_mma=bool(args.rates_mma), device=dev)
             st = sv.state_from_YT(fl.Y, fl.T)
             if params is not None:
                 sv.surrogate_load(params[id(mech)])
@@ -345,6 +346,91 @@ def field_errors(solver, a, b):
             "T": float(np.max(np.abs(Ta - Tb)) / np.max(np.abs(Tb)))}
 
 
+def rates_compare(entries, args, dev, rank):
+    """Production rates wdot = diag(W) nu^T q of every cell of the first flame, as
+    the sparse FP64 FMA sum and as FP64 tensor-core (m8n8k4) tiles: CUDA-event time
+    per launch (after warm-up, L2 flushed between launches) and the largest
+    difference between the two, relative to the largest rate."""
+    import torch
+    from paper_1801_01201_gb300.solver import Solver
+    mech, fl, dt = entries[0]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    Y = torch.as_tensor(fl.Y, device=dev).contiguous()
+    T = torch.as_tensor(fl.T, device=dev).contiguous()
+    out, res = {}, {}
+    for mma in (False, True):
+        sv = Solver(mech, fl, rates_mma=mma, device=dev)
+        st = torch.cuda.current_stream()
+        for _ in range(args.warmup):
+            res[mma] = sv.production_rates(Y, T, stream=st)
+        ms = []
+        for _ in range(max(args.steps, 1)):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            res[mma] = sv.production_rates(Y, T, stream=st)
+            b.record(st)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        out["tensor_core_ms" if mma else "sparse_fma_ms"] = statistics.median(ms)
+    d = (res[True] - res[False]).abs().max().item() / res[False].abs().max().item()
+    nnz = int(np.count_nonzero(mech.nu_r - mech.nu_f))
+    n_tiles = sum(1 for j in range(0, mech.n_species, 8) for k in range(0, mech.n_reactions, 4)
+                  if np.any((mech.nu_r - mech.nu_f)[k:k + 4, j:j + 8]))
+    line = {"rates_compare": out, "cells": fl.cells, "species": mech.n_species,
+            "reactions": mech.n_reactions, "nnz_nu": nnz, "mma_tiles": n_tiles,
+            "contraction_flops_per_cell": {"sparse_fma": 2 * nnz, "tensor_core": 512 * n_tiles / 8},
+            "max_rel_diff": d, "workload": args.workload}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def diffusion_compare(entries, args, dev, rank):
+    """One implicit diffusion solve (I - wdt D L_theta) x = rhs of every solved field
+    of the first flame, with wdt = --diffusion-compare: Chebyshev-accelerated Jacobi
+    against multigrid V-cycles (--mg-levels, default 4), each in FP64 and in mixed
+    precision (FP32 inner solves / FP32 coarse levels). CUDA-event time per solve
+    (L2 flushed before each), fine-level sweeps per field, and the largest
+    difference from the FP64 Chebyshev solution relative to each field's scale."""
+    import torch
+    from paper_1801_01201_gb300.solver import Solver
+    mech, fl, dt = entries[0]
+    wdt = args.diffusion_compare
+    levels = args.mg_levels if args.mg_levels > 1 else 4
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out, ref = {}, None
+    for lv, prec in ((1, "fp64"), (1, "mixed"), (levels, "fp64"), (levels, "mixed")):
+        sv = Solver(mech, fl, mg_levels=lv, precision=prec, device=dev)
+        coef = sv.state_from_YT(fl.Y, fl.T)
+        st = torch.cuda.current_stream()
+        for _ in range(args.warmup):
+            x = sv.diffusion_solve(wdt, coef, coef, stream=st)
+        sv.stats()   # reset the counters after the warm-up
+        ms = []
+        for _ in range(max(args.steps, 1)):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            x = sv.diffusion_solve(wdt, coef, coef, stream=st)
+            b.record(st)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        stt = sv.stats()
+        key = "%s_%s" % ("chebyshev" if lv == 1 else "multigrid%d" % levels, prec)
+        if ref is None:
+            ref = x
+        scale = ref.abs().amax(dim=1, keepdim=True).clamp_min(1e-300)
+        out[key] = {"ms": statistics.median(ms), "status": stt["status_name"],
+                    "fine_sweeps_per_solve": stt["lin_sweeps"] / max(args.steps, 1),
+                    "max_rel_diff_vs_fp64_chebyshev": ((x - ref).abs() / scale).max().item()}
+    line = {"diffusion_compare": out, "wdt": wdt, "cells": fl.cells, "fields": mech.n_species,
+            "workload": args.workload}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,6 +452,16 @@ def main():
     ap.add_argument("--train-lr", type=float, default=2e-3)
     ap.add_argument("--s-min", type=float, default=1e-4)
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--rates-mma", type=int, default=0,
+                    help="1: production rates on the FP64 tensor cores (all variants)")
+    ap.add_argument("--mg-levels", type=int, default=1,
+                    help=">1: multigrid diffusion solves (FP32 coarse levels when mixed)")
+    ap.add_argument("--diffusion-compare", type=float, default=0.0, metavar="WDT",
+                    help="instead of the step: time one implicit diffusion solve of weight WDT "
+                         "on the workload's initial state, Chebyshev against multigrid, FP64 and mixed")
+    ap.add_argument("--rates-compare", action="store_true",
+                    help="instead of the step: time the production-rate kernel, sparse FP64 FMA "
+                         "against FP64 tensor cores, on the workload's initial state")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -384,6 +480,10 @@ def main():
 
     name = args.workload
     entries, w = entries_for(name)
+    if args.rates_compare:
+        return rates_compare(entries, args, dev, rank)
+    if args.diffusion_compare > 0:
+        return diffusion_compare(entries, args, dev, rank)
     tune = (len(entries) > 1) if args.autotune < 0 else bool(args.autotune)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -514,7 +614,9 @@ def main():
     dtype = {"fp64": "f64", "mixed": "f64+f32", "learned_mixed": "f64+f32, bf16 MLP"}[args.headline]
     cfg = {"workload": name, "flames": len(entries), "cells": cells, "nodes": w["nodes"],
            "sweeps": w["sweeps"], "nu": w["nu"], "scheme": args.scheme, "variant": args.headline,
-           "autotuned": tune, "l2": "flushed between steps (256 MB write)"}
+           "autotuned": tune, "l2": "flushed between steps (256 MB write)",
+           "rates": "fp64 tensor cores" if args.rates_mma else "sparse fp64 fma",
+           "diffusion": "multigrid %d levels" % args.mg_levels if args.mg_levels > 1 else "chebyshev"}
     if len(entries) == 1:
         mech, fl, dt = entries[0]
         cfg.update({"grid": [fl.nx, fl.ny, fl.nz], "species": mech.n_species,

@@ -95,10 +95,15 @@ typedef struct misdc_opts {
   double newton_rtol;     /* stop once max|dY| <= rtol, |dT| <= rtol T  */
   int newton_maxit;       /* iteration limit per cell                  */
   double lin_rtol;        /* diffusion solve: relative residual target  */
-  int mg_levels;          /* multigrid levels (0 = automatic)          */
+  int mg_levels;          /* 0 or 1: Chebyshev-accelerated Jacobi alone; > 1: multigrid
+                             V-cycles on that many levels (fewer where an extent turns
+                             odd), FP32 coarse levels in mixed precision              */
   int two_streams;        /* 1: D and R stages on separate streams     */
   int use_graph;          /* 1: capture the step in a CUDA graph       */
   int profile;            /* 1: time every Newton and diffusion-solve launch with CUDA events */
+  int rates_mma;          /* 1: production rates (Sec. 2, omega-dot) contract diag(W) nu^T q
+                             on the FP64 tensor cores (mma m8n8k4) instead of the sparse
+                             FMA sum; the same values up to FP64 summation order     */
 } misdc_opts;
 
 typedef struct misdc_stats {

@@ -36,7 +36,7 @@ class Opts(C.Structure):
                 ("precision", C.c_int), ("dominant_species", C.c_int), ("rho", C.c_double),
                 ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("lin_rtol", C.c_double),
                 ("mg_levels", C.c_int), ("two_streams", C.c_int), ("use_graph", C.c_int),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("rates_mma", C.c_int)]
 
 
 class Stats(C.Structure):

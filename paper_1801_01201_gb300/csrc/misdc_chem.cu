@@ -200,6 +200,74 @@ __global__ void __launch_bounds__(128) k_rates(DevMech m, int n, int cs,
   }
 }
 
+// Production rates with the contraction wdot = diag(W) nu^T q on the FP64 tensor
+// cores. A block takes 32 cells at a time: each warp evaluates the reaction
+// rates q of 8 cells (lanes over reactions, as above) into a [32][qld] tile in
+// shared memory; then each warp takes every 4th species tile and, per nonzero
+// (4 reactions x 8 species) tile of [W_i nu_ri], loads the B fragment once and
+// issues one m8n8k4 FP64 MMA for each of the four 8-cell row tiles.
+constexpr int kMmaCells = 32;
+
+__device__ __forceinline__ void dmma_8x8x4(double &d0, double &d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(128) k_rates_mma(DevMech m, int n, int cs,
+                                                   const double *__restrict__ Y,
+                                                   const double *__restrict__ T,
+                                                   double *__restrict__ FR) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int N = m.N, R = m.R, qld = mma_qld(R), R4 = (R + 3) & ~3;
+  double *Q = smem;                                        // [32][qld]
+  double *scratch = smem + (size_t)kMmaCells * qld + (size_t)wib * 5 * N;
+  WarpChem w;
+  w.c = scratch; w.g = scratch + N; w.hRT = scratch + 2 * N; w.hm = scratch + 3 * N;
+  w.cpm = scratch + 4 * N;
+  w.kf = w.kr = w.dqdT = nullptr;
+  const double invrho = 1.0 / m.rho;
+  const int row = lane >> 2, col = lane & 3;
+  const int groups = (n + kMmaCells - 1) / kMmaCells;
+  for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+    const int c0 = grp * kMmaCells;
+    for (int j = wib; j < kMmaCells; j += wpb) {
+      const int cell = c0 + j;
+      w.q = Q + (size_t)j * qld;
+      if (cell < n) {
+        for (int i = lane; i < N; i += 32) w.c[i] = m.rho * Y[(size_t)i * cs + cell] * m.invW[i];
+        __syncwarp();
+        eval_chem(m, w, lane, T[cell], false);
+        for (int r = R + lane; r < R4; r += 32) w.q[r] = 0.0;   // reaction padding
+      } else {
+        for (int r = lane; r < R4; r += 32) w.q[r] = 0.0;       // ragged tail
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int jt = wib; jt < m.mma_nt; jt += wpb) {
+      double d[4][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+      for (int p = m.mma_ptr[jt]; p < m.mma_ptr[jt + 1]; ++p) {
+        const double b = __ldg(m.mma_b + (size_t)p * 32 + lane);
+        const int k = 4 * m.mma_kb[p] + col;
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) dmma_8x8x4(d[mt][0], d[mt][1], Q[(size_t)(8 * mt + row) * qld + k], b);
+      }
+      const int sp = 8 * jt + 2 * col;
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt) {
+        const int cell = c0 + 8 * mt + row;
+        if (cell < n) {
+          if (sp < N) FR[(size_t)sp * cs + cell] = d[mt][0] * invrho;
+          if (sp + 1 < N) FR[(size_t)(sp + 1) * cs + cell] = d[mt][1] * invrho;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Reaction Newton, lane-balanced form: one warp per cell; the iterate, the
 // augmented Jacobian and the per-reaction quantities live in shared memory and
@@ -972,18 +1040,22 @@ int newton_max_wpb(const DevMech &m, bool mixed) {
   return wpb;
 }
 
+static size_t rates_mma_smem(const DevMech &m) {
+  return ((size_t)kMmaCells * mma_qld(m.R) + (size_t)4 * 5 * m.N) * sizeof(double);
+}
+
 // The shared-memory limit is an attribute of the kernel, not of a launch: every
 // solver in the process shares it, so it only ever grows to the largest need.
 void prepare_chem_kernels(const DevMech &m) {
   static std::mutex mu;
-  static size_t have[3] = {0, 0, 0};
+  static size_t have[4] = {0, 0, 0, 0};
   std::lock_guard<std::mutex> lock(mu);
   int ld, wpb;
-  const size_t need[3] = {newton_smem(m, false, ld, wpb), newton_smem(m, true, ld, wpb),
-                          (size_t)4 * (5 * m.N + 4 * m.R) * sizeof(double)};
-  const void *fn[3] = {(const void *)k_newton2<false>, (const void *)k_newton2<true>,
-                       (const void *)k_rates};
-  for (int k = 0; k < 3; ++k)
+  const size_t need[4] = {newton_smem(m, false, ld, wpb), newton_smem(m, true, ld, wpb),
+                          (size_t)4 * (5 * m.N + 4 * m.R) * sizeof(double), rates_mma_smem(m)};
+  const void *fn[4] = {(const void *)k_newton2<false>, (const void *)k_newton2<true>,
+                       (const void *)k_rates, (const void *)k_rates_mma};
+  for (int k = 0; k < 4; ++k)
     if (need[k] > have[k]) {
       cudaFuncSetAttribute(fn[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need[k]);
       have[k] = need[k];
@@ -1004,8 +1076,14 @@ void launch_enthalpy(const DevMech &m, int n, int cs, const double *Y, const dou
 }
 
 void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double *T,
-                  double *FR, cudaStream_t s) {
+                  double *FR, cudaStream_t s, bool mma) {
   if (n <= 0) return;
+  if (mma) {
+    int grid = (n + kMmaCells - 1) / kMmaCells;
+    grid = grid < sm_count() * 2 ? grid : sm_count() * 2;
+    k_rates_mma<<<grid, 128, rates_mma_smem(m), s>>>(m, n, cs, Y, T, FR);
+    return;
+  }
   const int wpb = 4;
   size_t sm = (size_t)wpb * (5 * m.N + 4 * m.R) * sizeof(double);
   int grid = (n + wpb - 1) / wpb;

@@ -314,7 +314,7 @@ void prepare_node0(misdc_solver *s, const double *state, const double *Tin, cuda
   launch_temperature(s->m, s->cs, s->cs, b.phi, b.phi + (size_t)s->N * cs, guess, b.T, b.theta,
                      b.hsp, s->st, st);
   node_operators(s, b, s->thfD, st);
-  launch_rates(s->m, s->cs, s->cs, b.phi, b.T, b.FR, st);
+  launch_rates(s->m, s->cs, s->cs, b.phi, b.T, b.FR, st, s->o.rates_mma != 0);
 }
 
 // diffusion step at node t: rhs already in s->rhsD; writes AD[t]
@@ -556,6 +556,13 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   if (N < 1 || N > kMaxSpecies || R < 1 || R > 1024) return fail(MISDC_E_INVALID, "n_species must be 1..63 and n_reactions 1..1024");
   if (!md->W || !md->nasa7 || !md->A || !md->beta || !md->Ea || !md->nu_f || !md->nu_r || !md->D0)
     return fail(MISDC_E_INVALID, "null mechanism array");
+  if (op->rates_mma) {   // 32 cells' reaction rates are staged in shared memory
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((size_t)(32 * (size_t)mma_qld(R) + 20 * (size_t)N) * sizeof(double) > (size_t)optin)
+      return fail(MISDC_E_INVALID, "rates_mma: too many reactions for shared memory");
+  }
   if (gd->dim < 1 || gd->dim > 3 || gd->nx < 2 || gd->ny < 1 || gd->nz < 1 || !(gd->dx > 0.0))
     return fail(MISDC_E_INVALID, "bad grid");
   if ((gd->dim < 2 && gd->ny != 1) || (gd->dim < 3 && gd->nz != 1) || (gd->dim >= 2 && gd->ny < 2) ||
@@ -656,6 +663,28 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     for (size_t k = 1; k < cl.size() && lanes < 32; ++k)
       if (cl[k].t != cl[k - 1].t && (double)k >= per * lanes) jc_seg[lanes++] = (int)k;
   }
+  // tensor-core tiles of [W_i nu_ri] (see DevMech::mma_b)
+  const int mma_nt = (N + 7) / 8, mma_kbs = (R + 3) / 4;
+  std::vector<int> mma_ptr(1, 0), mma_kb;
+  std::vector<double> mma_b;
+  for (int jt = 0; jt < mma_nt; ++jt) {
+    for (int kb = 0; kb < mma_kbs; ++kb) {
+      double frag[32];
+      bool any = false;
+      for (int l = 0; l < 32; ++l) {
+        const int r = 4 * kb + (l & 3), i = 8 * jt + (l >> 2);
+        frag[l] = 0.0;
+        if (r < R && i < N) {
+          const int nu = md->nu_r[(size_t)r * N + i] - md->nu_f[(size_t)r * N + i];
+          if (nu) { frag[l] = md->W[i] * nu; any = true; }
+        }
+      }
+      if (!any) continue;
+      mma_kb.push_back(kb);
+      mma_b.insert(mma_b.end(), frag, frag + 32);
+    }
+    mma_ptr.push_back((int)mma_kb.size());
+  }
   auto up = [&](auto &vec, auto **dst) -> cudaError_t {
     using T = typename std::remove_reference<decltype(vec)>::type::value_type;
     cudaError_t e = s->alloc((T **)dst, vec.size());
@@ -663,13 +692,14 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     return cudaMemcpy((void *)*dst, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice);
   };
   std::vector<double> D0v(md->D0, md->D0 + N);
-  double *p_invW, *p_hc, *p_sc, *p_cpc, *p_D0, *p_lnA, *p_beta, *p_TA, *p_dn, *p_spc, *p_jcw;
+  double *p_invW, *p_hc, *p_sc, *p_cpc, *p_D0, *p_lnA, *p_beta, *p_TA, *p_dn, *p_spc, *p_jcw, *p_mb;
   signed char *p_fwd, *p_rev;
-  int *p_spp, *p_spr, *p_jcp, *p_jcs;
+  int *p_spp, *p_spr, *p_jcp, *p_jcs, *p_mp, *p_mk;
   if (up(invW, &p_invW) || up(hc, &p_hc) || up(sc, &p_sc) || up(cpc, &p_cpc) || up(D0v, &p_D0) ||
       up(lnA, &p_lnA) || up(beta, &p_beta) || up(TA, &p_TA) || up(dn, &p_dn) || up(fwd, &p_fwd) ||
       up(rev, &p_rev) || up(sp_ptr, &p_spp) || up(sp_rx, &p_spr) || up(sp_coef, &p_spc) ||
-      up(jc_pack, &p_jcp) || up(jc_w, &p_jcw) || up(jc_seg, &p_jcs))
+      up(jc_pack, &p_jcp) || up(jc_w, &p_jcw) || up(jc_seg, &p_jcs) || up(mma_b, &p_mb) ||
+      up(mma_ptr, &p_mp) || up(mma_kb, &p_mk))
     return bail(fail(MISDC_E_OOM, "mechanism upload failed"));
   DevMech &m = s->m;
   m.N = N; m.R = R; m.rho = op->rho; m.T_ref = md->T_ref; m.theta_exp = md->theta_exp;
@@ -679,6 +709,8 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   m.sp_ptr = p_spp; m.sp_rx = p_spr; m.sp_coef = p_spc;
   m.D0_host = s->D0h.data();
   m.jc_pack = p_jcp; m.jc_w = p_jcw; m.jc_seg = p_jcs;
+  m.mma_b = p_mb; m.mma_ptr = p_mp; m.mma_kb = p_mk; m.mma_nt = mma_nt;
+  m.mma_ntiles = (int)mma_kb.size();
   prepare_chem_kernels(m);
 
   // ---- buffers ----
@@ -721,30 +753,37 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
       cudaMemset(c.valid, 0, cs * sizeof(int));
     }
   }
-  // multigrid hierarchy (levels with even extents only)
+  // multigrid hierarchy (levels with even extents only); in mixed precision the
+  // coarse levels are FP32
   s->dw.levels = 1;
-  s->dw.cycles = 12;
+  s->dw.cycles = 40;
   s->dw.lg[0] = s->g;
   if (s->o.mg_levels > 1) {
+    DiffWork &w = s->dw;
     const size_t nfs = N;
-    if (s->alloc(&s->dw.lb[0], nfs * cs) || s->alloc(&s->dw.lx[0], nfs * cs) ||
-        s->alloc(&s->dw.lr[0], nfs * cs) || s->alloc(&s->dw.ly[0], nfs * cs))
+    w.mg32 = s->o.precision == MISDC_PREC_MIXED;
+    if (s->alloc(&w.lb[0], nfs * cs) || s->alloc(&w.lx[0], nfs * cs) || s->alloc(&w.lr[0], nfs * cs) ||
+        s->alloc(&w.ly[0], nfs * cs) || s->alloc(&w.mg_done, 1) || s->alloc(&w.mg_res, 1))
       return bail(fail(MISDC_E_OOM, "multigrid"));
     for (int l = 1; l < s->o.mg_levels; ++l) {
-      DevGrid c = s->dw.lg[l - 1];
+      DevGrid c = w.lg[l - 1];
       if ((c.nx % 2) || (c.dim > 1 && c.ny % 2) || (c.dim > 2 && c.nz % 2) || c.nx < 4) break;
       c.nx /= 2;
       if (c.dim > 1) c.ny /= 2;
       if (c.dim > 2) c.nz /= 2;
       c.cells = c.nx * c.ny * c.nz;
       c.dx *= 2.0;
-      s->dw.lg[l] = c;
+      w.lg[l] = c;
       const size_t cc = c.cells;
-      if (s->alloc(&s->dw.lthf[l], 3 * cc) || s->alloc(&s->dw.linvdiag[l], nfs * cc) ||
-          s->alloc(&s->dw.lb[l], nfs * cc) || s->alloc(&s->dw.lx[l], nfs * cc) ||
-          s->alloc(&s->dw.lr[l], nfs * cc) || s->alloc(&s->dw.ly[l], nfs * cc))
-        return bail(fail(MISDC_E_OOM, "multigrid"));
-      s->dw.levels = l + 1;
+      const bool bad = w.mg32
+          ? (s->alloc(&w.lthf32[l], 3 * cc) || s->alloc(&w.linvdiag32[l], nfs * cc) ||
+             s->alloc(&w.lb32[l], nfs * cc) || s->alloc(&w.lx32[l], nfs * cc) ||
+             s->alloc(&w.lr32[l], nfs * cc) || s->alloc(&w.ly32[l], nfs * cc))
+          : (s->alloc(&w.lthf[l], 3 * cc) || s->alloc(&w.linvdiag[l], nfs * cc) ||
+             s->alloc(&w.lb[l], nfs * cc) || s->alloc(&w.lx[l], nfs * cc) ||
+             s->alloc(&w.lr[l], nfs * cc) || s->alloc(&w.ly[l], nfs * cc));
+      if (bad) return bail(fail(MISDC_E_OOM, "multigrid"));
+      w.levels = l + 1;
     }
   }
   if (cudaStreamCreateWithFlags(&s->sD, cudaStreamNonBlocking) ||
@@ -928,7 +967,7 @@ misdc_status misdc_temperature(misdc_solver *s, const double *Y, const double *h
 misdc_status misdc_production_rates(misdc_solver *s, const double *Y, const double *T, double *FR,
                                     int n, void *stream) {
   if (!s || !Y || !T || !FR || n < 0) return fail(MISDC_E_INVALID, "bad argument");
-  launch_rates(s->m, n, n, Y, T, FR, (cudaStream_t)stream);
+  launch_rates(s->m, n, n, Y, T, FR, (cudaStream_t)stream, s->o.rates_mma != 0);
   CK(cudaGetLastError());
   return MISDC_OK;
 }
@@ -966,7 +1005,7 @@ misdc_status misdc_operators(misdc_solver *s, const double *state, double *FE, d
   launch_theta_faces(s->g, b.theta, s->thfD, st);
   if (FE || FD) launch_operators(s->m, s->g, s->i0, b.phi, b.hsp, s->thfD, s->vel, FE, FD, st);
   if (FR) {
-    launch_rates(s->m, s->cs, s->cs, b.phi, b.T, FR, st);
+    launch_rates(s->m, s->cs, s->cs, b.phi, b.T, FR, st, s->o.rates_mma != 0);
     CK(cudaMemsetAsync(FR + (size_t)s->N * cs, 0, cs * sizeof(double), st));
   }
   CK(cudaGetLastError());

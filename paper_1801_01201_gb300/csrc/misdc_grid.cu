@@ -181,7 +181,7 @@ __global__ void k_face_coef(DevGrid g, FieldMap fm, const double *__restrict__ t
 // Chebyshev plan from the measured bound: sweep count K (at most kmax) for an
 // error reduction `red`, and the weights omega_k of the semi-iterative method.
 __global__ void k_cheb_plan(const unsigned long long *rho_bits, int kmax, double red, int *kdev,
-                            double *omega) {
+                            double *omega, DevStats *st, int solves) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double rho = __longlong_as_double((long long)*rho_bits) * (1.0 + 1e-12);
   int K = 1;
@@ -191,6 +191,7 @@ __global__ void k_cheb_plan(const unsigned long long *rho_bits, int kmax, double
   }
   K = max(1, min(K, kmax));
   *kdev = K;
+  if (st) atomicAdd(&st->lin_sweeps, (unsigned long long)K * solves);   // sweeps per field
   const double r2 = rho * rho;
   double om = 1.0;
   for (int k = 0; k < K; ++k) {
@@ -274,11 +275,11 @@ __global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
   }
 }
 
-__device__ __forceinline__ double lap_theta(const DevGrid &g, const Nbr &nb, int c, int cs,
-                                            const double *__restrict__ thf,
-                                            const double *__restrict__ x) {
-  const double xc = x[c];
-  double s = 0.0;
+template <class T>
+__device__ __forceinline__ T lap_theta(const DevGrid &g, const Nbr &nb, int c, int cs,
+                                       const T *__restrict__ thf, const T *__restrict__ x) {
+  const T xc = x[c];
+  T s = 0;
   for (int d = 0; d < g.dim; ++d)
     s += thf[(size_t)d * cs + nb.cp[d]] * (x[nb.cp[d]] - xc) - thf[(size_t)d * cs + c] * (xc - x[nb.cm[d]]);
   return s;
@@ -364,43 +365,54 @@ __global__ void k_finish(DevGrid g, FieldMap fm, int N, int i0, double tol,
   }
 }
 
-// ---- multigrid transfer (cell-centred, coarsening by 2 in every used direction)
+// ---- multigrid (cell-centred, coarsening by 2 in every used direction) on
+// compact [solved field][cells] storage. Level kernels are templated on the
+// storage type: FP64 everywhere in FP64 mode; in mixed precision the fine level
+// stays FP64 (its residual decides convergence) and the coarse levels run in FP32.
+// Every level kernel returns at once when *done is set (the fine residual met the
+// target); smoothing counts are even, so a skipped pair leaves the iterate in the
+// buffer the host expects.
+
 // restriction: coarse residual = mean of the 2^dim fine residuals
-__global__ void k_restrict(DevGrid gf, DevGrid gc, int nfs, const int *__restrict__ dummy,
-                           const double *__restrict__ rf, double *__restrict__ rc) {
+template <class TF, class TC>
+__global__ void k_restrict(DevGrid gf, DevGrid gc, const TF *__restrict__ rf, TC *__restrict__ rc,
+                           const int *__restrict__ done) {
+  if (*done) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (c >= gc.cells) return;
-  (void)dummy;
   const int X = c % gc.nx, Y = (c / gc.nx) % gc.ny, Z = c / (gc.nx * gc.ny);
   const int sx = gf.dim > 0 ? 2 : 1, sy = gf.dim > 1 ? 2 : 1, sz = gf.dim > 2 ? 2 : 1;
-  double s = 0.0;
+  TF s = 0;
   for (int dz = 0; dz < sz; ++dz)
     for (int dy = 0; dy < sy; ++dy)
       for (int dx = 0; dx < sx; ++dx)
         s += rf[(size_t)k * gf.cells + (size_t)(X * sx + dx) + gf.nx * ((size_t)(Y * sy + dy) + (size_t)gf.ny * (Z * sz + dz))];
-  rc[(size_t)k * gc.cells + c] = s / (sx * sy * sz);
+  rc[(size_t)k * gc.cells + c] = (TC)(s * ((TF)1 / (TF)(sx * sy * sz)));   // 1/2^d: exact
 }
 
 // prolongation: fine correction += coarse value of the parent cell
-__global__ void k_prolong(DevGrid gf, DevGrid gc, const double *__restrict__ xc,
-                          double *__restrict__ xf) {
+template <class TC, class TF>
+__global__ void k_prolong(DevGrid gf, DevGrid gc, const TC *__restrict__ xc, TF *__restrict__ xf,
+                          const int *__restrict__ done) {
+  if (*done) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (c >= gf.cells) return;
   const int x = c % gf.nx, y = (c / gf.nx) % gf.ny, z = c / (gf.nx * gf.ny);
   const int X = gf.dim > 0 ? x / 2 : x, Y = gf.dim > 1 ? y / 2 : y, Z = gf.dim > 2 ? z / 2 : z;
-  xf[(size_t)k * gf.cells + c] += xc[(size_t)k * gc.cells + X + gc.nx * (Y + gc.ny * Z)];
+  xf[(size_t)k * gf.cells + c] += (TF)xc[(size_t)k * gc.cells + X + gc.nx * (Y + gc.ny * Z)];
 }
 
 // coarse face coefficient: mean of the fine faces that tile the coarse face
-__global__ void k_coarsen_faces(DevGrid gf, DevGrid gc, const double *__restrict__ tf,
-                                double *__restrict__ tc) {
+template <class TF, class TC>
+__global__ void k_coarsen_faces(DevGrid gf, DevGrid gc, const TF *__restrict__ tf,
+                                TC *__restrict__ tc) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= gc.cells) return;
   const int X = c % gc.nx, Y = (c / gc.nx) % gc.ny, Z = c / (gc.nx * gc.ny);
   for (int d = 0; d < gf.dim; ++d) {
-    double s = 0.0;
+    TF s = 0;
     int cnt = 0;
     const int ox = (d == 0) ? 1 : 2, oy = (gf.dim > 1) ? ((d == 1) ? 1 : 2) : 1,
               oz = (gf.dim > 2) ? ((d == 2) ? 1 : 2) : 1;
@@ -412,43 +424,77 @@ __global__ void k_coarsen_faces(DevGrid gf, DevGrid gc, const double *__restrict
           s += tf[(size_t)d * gf.cells + fx + (size_t)gf.nx * (fy + (size_t)gf.ny * fz)];
           ++cnt;
         }
-    tc[(size_t)d * gc.cells + c] = s / cnt;
+    tc[(size_t)d * gc.cells + c] = (TC)(s / (TF)cnt);
   }
 }
 
-// residual r = b - (I - c L) x on one level for the solved fields (compact storage [k][cells])
-__global__ void k_residual(DevGrid g, FieldMap fm, const double *__restrict__ thf,
-                           const double *__restrict__ b, const double *__restrict__ x,
-                           double *__restrict__ r) {
+// residual r = b - (I - c L) x on one level for the solved fields; on the fine
+// level (res_bits set) also the largest scaled residual |r| / (|b| + |c L x| + |x|)
+// of the launch (the scale of the final check), the convergence measure of the
+// V-cycles
+template <class T>
+__global__ void k_residual(DevGrid g, FieldMap fm, const T *__restrict__ thf,
+                           const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ r,
+                           const int *__restrict__ done, unsigned long long *res_bits) {
+  if (*done) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
-  if (c >= g.cells) return;
-  const Nbr nb = neighbours(g, c);
-  const size_t off = (size_t)k * g.cells;
-  r[off + c] = b[off + c] - (x[off + c] - fm.cf[k] * lap_theta(g, nb, c, g.cells, thf, x + off));
+  float q = 0.0f;
+  if (c < g.cells) {
+    const Nbr nb = neighbours(g, c);
+    const size_t off = (size_t)k * g.cells;
+    const T xc = x[off + c], bc = b[off + c];
+    const T cl = (T)fm.cf[k] * lap_theta<T>(g, nb, c, g.cells, thf, x + off);
+    const T rc = bc - (xc - cl);
+    r[off + c] = rc;
+    // the ratio in FP32, rounded up (FP64 divisions are scarce on this part)
+    if (res_bits)
+      q = __double2float_ru(fabs((double)rc)) /
+          fmaxf(__double2float_rd(fabs((double)bc) + fabs((double)cl) + fabs((double)xc)), 1e-30f);
+  }
+  if (!res_bits) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) q = fmaxf(q, __shfl_xor_sync(0xffffffffu, q, o));
+  if ((threadIdx.x & 31) == 0 && q > 0.0f) atomicMax(res_bits, dbits((double)q));
 }
 
-// damped Jacobi on a coarse level (compact storage): x_new = x + w D^{-1} (b - A x)
-__global__ void k_jacobi_level(DevGrid g, FieldMap fm, const double *__restrict__ thf,
-                               const double *__restrict__ invdiag, const double *__restrict__ b,
-                               const double *__restrict__ x, double *__restrict__ y, double w) {
+// after the fine residual of a V-cycle: stop the cycles once it meets the target;
+// counts the fine smoothing sweeps that ran (two before the residual, two after
+// it unless the cycles stop here)
+__global__ void k_mg_check(unsigned long long *res_bits, double tol, int *done, DevStats *st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || *done) return;
+  const double r = __longlong_as_double((long long)*res_bits);
+  *res_bits = 0ull;
+  const bool stop = r <= tol;
+  if (stop) *done = 1;
+  atomicAdd(&st->lin_sweeps, stop ? 2ull : 4ull);
+}
+
+// damped Jacobi on one level: y = x + w D^{-1} (b - A x)
+template <class T>
+__global__ void k_jacobi_level(DevGrid g, FieldMap fm, const T *__restrict__ thf,
+                               const T *__restrict__ invdiag, const T *__restrict__ b,
+                               const T *__restrict__ x, T *__restrict__ y, T w,
+                               const int *__restrict__ done) {
+  if (*done) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (c >= g.cells) return;
   const Nbr nb = neighbours(g, c);
   const size_t off = (size_t)k * g.cells;
-  const double r = b[off + c] - (x[off + c] - fm.cf[k] * lap_theta(g, nb, c, g.cells, thf, x + off));
+  const T r = b[off + c] - (x[off + c] - (T)fm.cf[k] * lap_theta<T>(g, nb, c, g.cells, thf, x + off));
   y[off + c] = fma(w * invdiag[off + c], r, x[off + c]);
 }
 
-__global__ void k_diag_level(DevGrid g, FieldMap fm, const double *__restrict__ thf,
-                             double *__restrict__ invdiag) {
+template <class T>
+__global__ void k_diag_level(DevGrid g, FieldMap fm, const T *__restrict__ thf,
+                             T *__restrict__ invdiag) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.cells) return;
   const Nbr nb = neighbours(g, c);
-  double S = 0.0;
+  T S = 0;
   for (int d = 0; d < g.dim; ++d) S += thf[(size_t)d * g.cells + c] + thf[(size_t)d * g.cells + nb.cp[d]];
-  for (int k = 0; k < fm.nfs; ++k) invdiag[(size_t)k * g.cells + c] = 1.0 / (1.0 + fm.cf[k] * S);
+  for (int k = 0; k < fm.nfs; ++k) invdiag[(size_t)k * g.cells + c] = (T)1 / ((T)1 + (T)fm.cf[k] * S);
 }
 
 // gather the solved fields of a full-layout array into compact storage and back
@@ -515,6 +561,115 @@ void launch_theta_faces(const DevGrid &g, const double *theta, double *thf, cuda
                                                      nullptr, nullptr);
 }
 
+namespace {
+
+// the storage of level l: FP32 for the coarse levels of a mixed-precision solve
+template <class T> T *lv(double *d, float *f);
+template <> double *lv<double>(double *d, float *) { return d; }
+template <> float *lv<float>(double *, float *f) { return f; }
+
+// n (even) damped-Jacobi sweeps on level l; the iterate ends in lx[l] again
+template <class T>
+void mg_smooth(DiffWork &w, const FieldMap &fm, int l, int n, cudaStream_t s) {
+  const DevGrid &g = w.lg[l];
+  T *x = lv<T>(w.lx[l], w.lx32[l]), *y = lv<T>(w.ly[l], w.ly32[l]);
+  for (int sw = 0; sw < n; ++sw) {
+    k_jacobi_level<T><<<grid2(g.cells, fm.nfs), 256, 0, s>>>(
+        g, fm, lv<T>(w.lthf[l], w.lthf32[l]), lv<T>(w.linvdiag[l], w.linvdiag32[l]),
+        lv<T>(w.lb[l], w.lb32[l]), x, y, (T)0.8, w.mg_done);
+    std::swap(x, y);
+  }
+}
+
+// residual of level l (with the convergence measure on the fine level), restricted
+// into the right-hand side of level l+1, whose iterate starts from zero
+template <class TF, class TC>
+void mg_down(DiffWork &w, const FieldMap &fm, int l, cudaStream_t s) {
+  const DevGrid &gl = w.lg[l], &gc = w.lg[l + 1];
+  TF *r = lv<TF>(w.lr[l], w.lr32[l]);
+  k_residual<TF><<<grid2(gl.cells, fm.nfs), 256, 0, s>>>(
+      gl, fm, lv<TF>(w.lthf[l], w.lthf32[l]), lv<TF>(w.lb[l], w.lb32[l]), lv<TF>(w.lx[l], w.lx32[l]),
+      r, w.mg_done, l == 0 ? w.mg_res : nullptr);
+  if (l == 0) k_mg_check<<<1, 32, 0, s>>>(w.mg_res, w.mg_tol, w.mg_done, w.mg_st);
+  k_restrict<TF, TC><<<grid2(gc.cells, fm.nfs), 256, 0, s>>>(gl, gc, r, lv<TC>(w.lb[l + 1], w.lb32[l + 1]),
+                                                             w.mg_done);
+  cudaMemsetAsync(lv<TC>(w.lx[l + 1], w.lx32[l + 1]), 0, sizeof(TC) * (size_t)fm.nfs * gc.cells, s);
+}
+
+template <class TC, class TF>
+void mg_up(DiffWork &w, const FieldMap &fm, int l, cudaStream_t s) {
+  k_prolong<TC, TF><<<grid2(w.lg[l].cells, fm.nfs), 256, 0, s>>>(
+      w.lg[l], w.lg[l + 1], lv<TC>(w.lx[l + 1], w.lx32[l + 1]), lv<TF>(w.lx[l], w.lx32[l]), w.mg_done);
+}
+
+template <class TF, class TC>
+void mg_coarsen(DiffWork &w, const FieldMap &fc, int l, cudaStream_t s) {
+  const DevGrid &gf = w.lg[l - 1], &gc = w.lg[l];
+  TC *tc = lv<TC>(w.lthf[l], w.lthf32[l]);
+  k_coarsen_faces<TF, TC><<<(gc.cells + 255) / 256, 256, 0, s>>>(gf, gc, lv<TF>(w.lthf[l - 1], w.lthf32[l - 1]), tc);
+  k_diag_level<TC><<<(gc.cells + 255) / 256, 256, 0, s>>>(gc, fc, tc, lv<TC>(w.linvdiag[l], w.linvdiag32[l]));
+}
+
+// Multigrid solve of (I - c L) x = rhs for every solved field: V-cycles of the
+// correction scheme from x0 = rhs, two damped-Jacobi sweeps before and after the
+// coarse correction on every level and eight on the coarsest, mean-value
+// restriction, piecewise-constant prolongation and coefficients re-discretised
+// from the fine face coefficients (c / 4 per level). The cycles stop on the device
+// once the scaled fine residual is below 10 lin_rtol, at most w.cycles of them; the
+// solution goes to w.xa (full layout, the dominant-species row untouched).
+void multigrid_solve(const DevGrid &g, const FieldMap &fm, const double *rhs, DiffWork &w,
+                     double lin_rtol, DevStats *st, cudaStream_t s) {
+  const int cs = g.cells, L = w.levels;
+  const dim3 gr = grid2(cs, fm.nfs);
+  auto f32 = [&](int l) { return w.mg32 && l >= 1; };
+  w.lthf[0] = w.thf;
+  w.linvdiag[0] = w.invdiag;
+  FieldMap fl[8];
+  fl[0] = fm;
+  for (int l = 1; l < L; ++l) {
+    fl[l] = fm;
+    for (int k = 0; k < fm.nfs; ++k) fl[l].cf[k] = fm.cf[k] / (double)(1 << (2 * l));
+    if (!f32(l)) mg_coarsen<double, double>(w, fl[l], l, s);
+    else if (!f32(l - 1)) mg_coarsen<double, float>(w, fl[l], l, s);
+    else mg_coarsen<float, float>(w, fl[l], l, s);
+  }
+  // the stop target sits 10x below the final check (100 lin_rtol, same measure):
+  // the scaled residual bottoms out at round-off near lin_rtol itself
+  w.mg_tol = 10.0 * lin_rtol;
+  w.mg_st = st;
+  cudaMemsetAsync(w.mg_done, 0, sizeof(int), s);
+  cudaMemsetAsync(w.mg_res, 0, sizeof(unsigned long long), s);
+  k_gather<<<gr, 256, 0, s>>>(cs, fm, rhs, nullptr, nullptr, nullptr, w.lb[0]);
+  k_gather<<<gr, 256, 0, s>>>(cs, fm, rhs, nullptr, nullptr, nullptr, w.lx[0]);
+  for (int cyc = 0; cyc < w.cycles; ++cyc) {
+    for (int l = 0; l + 1 < L; ++l) {          // down-leg
+      if (f32(l)) {
+        mg_smooth<float>(w, fl[l], l, 2, s);
+        mg_down<float, float>(w, fl[l], l, s);
+      } else {
+        mg_smooth<double>(w, fl[l], l, 2, s);
+        if (f32(l + 1)) mg_down<double, float>(w, fl[l], l, s);
+        else mg_down<double, double>(w, fl[l], l, s);
+      }
+    }
+    if (f32(L - 1)) mg_smooth<float>(w, fl[L - 1], L - 1, 8, s);   // coarsest level
+    else mg_smooth<double>(w, fl[L - 1], L - 1, 8, s);
+    for (int l = L - 2; l >= 0; --l) {         // up-leg
+      if (f32(l)) {
+        mg_up<float, float>(w, fl[l], l, s);
+        mg_smooth<float>(w, fl[l], l, 2, s);
+      } else {
+        if (f32(l + 1)) mg_up<float, double>(w, fl[l], l, s);
+        else mg_up<double, double>(w, fl[l], l, s);
+        mg_smooth<double>(w, fl[l], l, 2, s);
+      }
+    }
+  }
+  k_scatter_set<<<gr, 256, 0, s>>>(cs, fm, w.lx[0], w.xa);
+}
+
+}  // namespace
+
 void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, const double *theta,
                      const double *rhs, double *out, DiffWork &w, int sweeps, double rho_bound,
                      double lin_rtol, DevStats *st, cudaStream_t s) {
@@ -530,7 +685,7 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
     // mixed precision: FP64 residuals, FP32 inner Chebyshev solves (reduction 1e-6
     // each), three rounds, then the same reconstruction and checks as below
     const int k32 = std::min(sweeps, chebyshev_sweeps(rho_bound, 1e-6));
-    k_cheb_plan<<<1, 32, 0, s>>>(w.rho_bits, k32, 1e-6, w.kdev32, w.omega32);
+    k_cheb_plan<<<1, 32, 0, s>>>(w.rho_bits, k32, 1e-6, w.kdev32, w.omega32, st, w.refine_rounds);
     const dim3 gr4((cs + 255) / 256, (fm.nfs + 3) / 4);
     const double *xin = rhs;
     double *xr[2] = {w.xa, w.xb};
@@ -553,67 +708,27 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
                                               w.xc, w.xc, nullptr, out, st);
     return;
   }
+  if (w.levels > 1) {
+    multigrid_solve(g, fm, rhs, w, lin_rtol, st, s);
+    k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, w.xa,
+                                              w.xb, w.xc, nullptr, out, st);
+    return;
+  }
   // sweeps: planned on the device from the measured Gershgorin bound, at most
   // `sweeps` (the a-priori bound with theta at the 6000 K cap)
   (void)rho_bound;
-  k_cheb_plan<<<1, 32, 0, s>>>(w.rho_bits, sweeps, reduction, w.kdev, w.omega);
-  const dim3 gr = grid2(cs, fm.nfs);
+  k_cheb_plan<<<1, 32, 0, s>>>(w.rho_bits, sweeps, reduction, w.kdev, w.omega, st, 1);
+  const int tb = (w.cheb_block >= 32 && w.cheb_block <= 1024) ? w.cheb_block : 256;
   // Chebyshev-accelerated Jacobi from x0 = rhs (the operator is I - c L)
   double *bufs[3] = {w.xa, w.xb, w.xc};
   for (int it = 0; it < sweeps; ++it) {
     const double *xk = (it == 0) ? rhs : bufs[(it - 1) % 3];
     const double *xkm1 = (it <= 1) ? rhs : bufs[(it - 2) % 3];
-    const int tb = (w.cheb_block >= 32 && w.cheb_block <= 1024) ? w.cheb_block : 256;
     k_cheb<<<dim3((cs + tb - 1) / tb, (fm.nfs + kChebFields - 1) / kChebFields), tb, 0, s>>>(
         g, fm, w.thf, w.invdiag, rhs, xk, xkm1, bufs[it % 3], it, w.kdev, w.omega);
   }
   const int *kdev = w.kdev;
   const double *xfin = w.xa;
-  // Multigrid (levels > 1): V-cycles of the correction scheme on compact
-  // [solved field][cells] storage, damped-Jacobi smoothing on every level,
-  // mean-value restriction and piecewise-constant prolongation, coefficients
-  // re-discretised from the fine face coefficients.
-  if (w.levels > 1) {
-    w.lthf[0] = w.thf;
-    w.linvdiag[0] = w.invdiag;
-    FieldMap fl[8];
-    fl[0] = fm;
-    for (int l = 1; l < w.levels; ++l) {
-      fl[l] = fm;
-      for (int k = 0; k < fm.nfs; ++k) fl[l].cf[k] = fm.cf[k] / (double)(1 << (2 * l));
-      const DevGrid &gf = w.lg[l - 1], &gc = w.lg[l];
-      k_coarsen_faces<<<(gc.cells + 255) / 256, 256, 0, s>>>(gf, gc, w.lthf[l - 1], w.lthf[l]);
-      k_diag_level<<<(gc.cells + 255) / 256, 256, 0, s>>>(gc, fl[l], w.lthf[l], w.linvdiag[l]);
-    }
-    k_gather<<<gr, 256, 0, s>>>(cs, fm, rhs, nullptr, nullptr, nullptr, w.lb[0]);
-    k_gather<<<gr, 256, 0, s>>>(cs, fm, w.xa, w.xb, w.xc, w.kdev, w.lx[0]);
-    auto smooth = [&](int l, int n_sw) {
-      const DevGrid &gl = w.lg[l];
-      for (int sw = 0; sw < n_sw; ++sw) {
-        k_jacobi_level<<<grid2(gl.cells, fm.nfs), 256, 0, s>>>(gl, fl[l], w.lthf[l], w.linvdiag[l], w.lb[l], w.lx[l], w.ly[l], 0.8);
-        std::swap(w.lx[l], w.ly[l]);
-      }
-    };
-    for (int cyc = 0; cyc < w.cycles; ++cyc) {
-      for (int l = 0; l + 1 < w.levels; ++l) {          // down-leg
-        const DevGrid &gl = w.lg[l], &gc = w.lg[l + 1];
-        smooth(l, 2);
-        k_residual<<<grid2(gl.cells, fm.nfs), 256, 0, s>>>(gl, fl[l], w.lthf[l], w.lb[l], w.lx[l], w.lr[l]);
-        k_restrict<<<grid2(gc.cells, fm.nfs), 256, 0, s>>>(gl, gc, fm.nfs, nullptr, w.lr[l], w.lb[l + 1]);
-        cudaMemsetAsync(w.lx[l + 1], 0, sizeof(double) * (size_t)fm.nfs * gc.cells, s);
-      }
-      smooth(w.levels - 1, 8);                            // coarsest level
-      for (int l = w.levels - 2; l >= 0; --l) {          // up-leg
-        k_prolong<<<grid2(w.lg[l].cells, fm.nfs), 256, 0, s>>>(w.lg[l], w.lg[l + 1], w.lx[l + 1], w.lx[l]);
-        smooth(l, 2);
-      }
-    }
-    // the corrected iterate goes to w.xa (its dominant-species row is not written
-    // and never read: k_finish closes that field)
-    k_scatter_set<<<gr, 256, 0, s>>>(cs, fm, w.lx[0], w.xa);
-    kdev = nullptr;
-    xfin = w.xa;
-  }
   k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, xfin, w.xb,
                                             w.xc, kdev, out, st);
 }

@@ -60,7 +60,22 @@ struct DevMech {
   const int *jc_pack;
   const double *jc_w;
   const int *jc_seg;
+  // production rates on the FP64 tensor cores (mma m8n8k4): the nonzero tiles of
+  // the (R x N) matrix [W_i nu_ri], 4 reactions by 8 species each, listed per
+  // species tile (CSR mma_ptr over mma_nt species tiles, reaction block mma_kb);
+  // tile p's B fragment is mma_b[32 p + lane] = entry (4 kb + lane % 4, 8 j + lane / 4)
+  const double *mma_b;
+  const int *mma_ptr, *mma_kb;
+  int mma_nt, mma_ntiles;
 };
+
+// row stride (doubles) of the per-cell reaction rates staged for the tensor-core
+// contraction: R rounded up to 4, then to 4 (mod 16) so the A-fragment loads of a
+// half-warp (8 cells x 4 reactions) fall in distinct shared-memory banks
+__host__ __device__ inline int mma_qld(int R) {
+  const int r = (R + 3) & ~3;
+  return r + ((4 - (r & 15)) & 15);
+}
 
 // leading dimension of the augmented (N+1) x (N+2) Newton matrix in shared memory (odd)
 __host__ __device__ inline int newton_ld(int N) {
@@ -80,7 +95,7 @@ void launch_temperature(const DevMech &m, int n, int cs, const double *Y, const 
 void launch_enthalpy(const DevMech &m, int n, int cs, const double *Y, const double *T,
                      double *h, cudaStream_t s);
 void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double *T,
-                  double *FR, cudaStream_t s);
+                  double *FR, cudaStream_t s, bool mma = false);
 // Reaction Newton (S5). b [N][cs], hstar [cs], guess Yg [N][cs], Tg [cs];
 // outputs Y, T, FR (wdot/rho at the solution), hsp [N][cs] and theta at the solution.
 // pred [.][ldp] (optional): learned correction, row prow[c] of cell c (prow NULL: row c;
@@ -157,6 +172,15 @@ struct DiffWork {
   double *omega32;
   DevGrid lg[8];
   double *lthf[8], *linvdiag[8], *lb[8], *lx[8], *lr[8], *ly[8];
+  // mixed precision: the coarse levels (l >= 1) in FP32 when mg32 is set
+  int mg32;
+  float *lthf32[8], *linvdiag32[8], *lb32[8], *lx32[8], *lr32[8], *ly32[8];
+  // V-cycle stop: flag, largest scaled fine residual of the cycle (bit pattern),
+  // its target and the statistics it is counted in (set per solve)
+  int *mg_done;
+  unsigned long long *mg_res;
+  double mg_tol;
+  DevStats *mg_st;
 };
 void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, const double *theta,
                      const double *rhs, double *out, DiffWork &w, int sweeps, double rho_bound,

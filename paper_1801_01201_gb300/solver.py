@@ -66,7 +66,8 @@ class Solver:
 
     def __init__(self, mech, flame, *, n_nodes=3, n_sweeps=4, nu=2, scheme="CISDCQ",
                  precision="fp64", newton_rtol=1e-12, newton_maxit=50, lin_rtol=1e-14,
-                 mg_levels=1, two_streams=True, use_graph=True, profile=False, device="cuda"):
+                 mg_levels=1, two_streams=True, use_graph=True, profile=False, rates_mma=False,
+                 device="cuda"):
         self.lib = L.load()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -96,6 +97,7 @@ class Solver:
         o.mg_levels = mg_levels
         o.two_streams, o.use_graph = int(two_streams), int(use_graph)
         o.profile = int(profile)
+        o.rates_mma = int(rates_mma)
         self.opts = o
         vel = _dev(flame.vel, self.device)
         h = C.c_void_p()

@@ -67,19 +67,29 @@ def test_thermo_parity(flame1d):
     assert relerr(T_gpu, fl.T) < 1e-12
 
 
+@pytest.mark.parametrize("mma", [False, True])
 @pytest.mark.parametrize("key", [(1801, 9, 21), (1802, 21, 84), (1803, 53, 325)])
-def test_production_rates_parity(key):
+def test_production_rates_parity(key, mma):
+    """Sparse FMA and FP64 tensor-core (m8n8k4) contractions of nu^T q against the
+    oracle; 75 cells leave a ragged tail after two 32-cell tensor-core groups."""
     mech = I.make_mechanism(*key)
-    fl = I.flame_1d(mech, 0, nx=64, dx=1e-4)
+    n = 75
+    fl = I.flame_1d(mech, 0, nx=n, dx=1e-4)
     rng = np.random.default_rng(5)
     Y = fl.Y * (1 + 0.05 * rng.standard_normal(fl.Y.shape))
     T = fl.T * (1 + 0.01 * rng.standard_normal(fl.T.shape))
-    sv = S().Solver(mech, fl)
+    sv = S().Solver(mech, fl, rates_mma=mma)
     FR = sv.production_rates(Y, T).cpu().numpy()
     ad = O.ADR(mech, fl)
-    want = np.stack([ad.wdot(Y[:, c], T[c])[0] / fl.rho for c in range(64)], axis=1)
+    want = np.stack([ad.wdot(Y[:, c], T[c])[0] / fl.rho for c in range(n)], axis=1)
     scale = np.max(np.abs(want))
     assert np.max(np.abs(FR - want)) <= 1e-12 * scale
+
+
+def test_step_with_tensor_core_rates_matches_oracle():
+    mech, fl = small_2d((1803, 53, 325), n=16, logA=MILD)
+    got, T, want, ad, st, _ = _run_both(mech, fl, 5e-6, 1, rates_mma=True)
+    assert np.all(relerr(got, want) < 1e-10)
 
 
 @pytest.mark.parametrize("key", [(1801, 9, 21), (1802, 21, 84), (1803, 53, 325)])
@@ -160,10 +170,11 @@ def test_operators_parity(dim):
         assert np.all(np.max(np.abs(got - want), axis=1) <= 1e-11 * scale + 1e-300)
 
 
-@pytest.mark.parametrize("levels,precision", [(1, "fp64"), (3, "fp64"), (1, "mixed")])
+@pytest.mark.parametrize("levels,precision", [(1, "fp64"), (3, "fp64"), (1, "mixed"), (3, "mixed")])
 def test_diffusion_solve_parity(levels, precision):
-    """FP64 Chebyshev (with and without multigrid) and the mixed-precision
-    refinement (FP64 residuals, FP32 inner Chebyshev solves) against the oracle."""
+    """FP64 Chebyshev, multigrid V-cycles (FP64, and FP32 coarse levels under the
+    FP64 fine residual) and the mixed-precision refinement (FP64 residuals, FP32
+    inner Chebyshev solves) against the oracle."""
     mech, fl = small_2d(n=32)
     ad = O.ADR(mech, fl)
     coef = ad.state_from_YT(fl.Y, fl.T)
@@ -177,6 +188,29 @@ def test_diffusion_solve_parity(levels, precision):
     assert np.all(relerr(got, want) < 1e-12)
     st = sv.stats()
     assert st["status_name"] == "OK", st
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multigrid_stiff_diffusion(precision):
+    """A stiff solve (wdt D / dx^2 summed over the faces up to ~250): the
+    V-cycles reach the oracle's conjugate-gradient solution, with FP32 coarse
+    levels in mixed precision, on far fewer fine sweeps than Chebyshev alone."""
+    mech, fl = small_2d(n=32)
+    ad = O.ADR(mech, fl)
+    coef = ad.state_from_YT(fl.Y, fl.T)
+    rng = np.random.default_rng(8)
+    rhs = coef * (1 + 0.1 * rng.standard_normal(coef.shape))
+    wdt = 1e-3
+    want, rc = ad.solve_diff(wdt, coef, rhs)
+    assert rc == 0
+    mg = S().Solver(mech, fl, mg_levels=4, precision=precision)
+    got = mg.diffusion_solve(wdt, coef, rhs).cpu().numpy()
+    st = mg.stats()
+    assert st["status_name"] == "OK", st
+    assert np.all(relerr(got, want) < 1e-11)
+    cheb = S().Solver(mech, fl)
+    cheb.diffusion_solve(wdt, coef, rhs)
+    assert 0 < 3 * st["lin_sweeps"] < cheb.stats()["lin_sweeps"]
 
 
 def _run_both(mech, fl, dt, steps, scheme="CISDCQ", nu=2, sweeps=4, sensitivity=False, M=2, **kw):
@@ -313,6 +347,17 @@ def test_multigrid_levels_agree():
     a = _run_both(mech, fl, 5e-6, 1, mg_levels=1)[0]
     b = _run_both(mech, fl, 5e-6, 1, mg_levels=3)[0]
     assert np.all(relerr(a, b) < 1e-11)
+
+
+def test_multigrid_mixed_step_meets_accuracy_bar():
+    """Full steps with FP32 coarse multigrid levels (and the rest of the mixed
+    path) against the FP64 oracle: species to 1e-8, T to 1e-6 relative."""
+    mech, fl = small_2d(n=32, logA=MILD)
+    got, T, want, ad, st, _ = _run_both(mech, fl, 5e-6, 2, mg_levels=3, precision="mixed")
+    N = mech.n_species
+    assert np.max(np.abs(got[:N] - want[:N])) / np.max(np.abs(want[:N])) < 1e-8
+    assert relerr(T, ad.T_from_h(want[:N], want[N])) <= 1e-6
+    assert st["lin_sweeps"] > 0
 
 
 def test_host_step_matches_device_step(flame1d):
