@@ -63,6 +63,11 @@ class AdrCfg(C.Structure):
                 ("lin_rtol", C.c_double), ("lin_maxit", C.c_int)]
 
 
+class NuRule(C.Structure):
+    """Adaptive nested iterations (see or_nu_rule): eta <= 0 runs all nu."""
+    _fields_ = [("eta", C.c_double), ("rho_stall", C.c_double)]
+
+
 class AdrStats(C.Structure):
     _fields_ = [("newton_solves", C.c_long), ("newton_iters", C.c_long), ("newton_fail", C.c_long),
                 ("newton_maxit_seen", C.c_long), ("lin_solves", C.c_long), ("lin_iters", C.c_long),
@@ -82,6 +87,10 @@ def _declare(L):
                               C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp, dp]
     L.or_adr_step.argtypes = [C.POINTER(Mech), C.POINTER(AdrCfg), C.c_int, C.c_int, C.c_int, C.c_int,
                               C.c_double, dp, dp, dp, C.POINTER(AdrStats)]
+    L.or_linear_step_ex.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(NuRule), C.c_double,
+                                    C.c_double, C.c_double, C.c_double, C.c_double, dp, dp, ip]
+    L.or_adr_step_ex.argtypes = [C.POINTER(Mech), C.POINTER(AdrCfg), C.c_int, C.c_int, C.c_int, C.c_int,
+                                 C.POINTER(NuRule), C.c_double, dp, dp, dp, ip, C.POINTER(AdrStats)]
     L.or_species_h.restype = C.c_double
     L.or_species_h.argtypes = [C.POINTER(Mech), C.c_int, C.c_double]
     L.or_species_cp.restype = C.c_double
@@ -119,14 +128,24 @@ def lobatto(M):
     return tau, Q, S, QI, QE
 
 
-def linear_step(scheme, M, n_sweeps, nu, dt, a, d, r, phi0=1.0):
+def linear_step(scheme, M, n_sweeps, nu, dt, a, d, r, phi0=1.0, nu_rule=None):
+    """One step of the linear model problem; with nu_rule = (eta, rho_stall) the
+    nested iterations are adaptive and (phi, incr, nu_used per sweep) is returned."""
     out = np.zeros(1)
     incr = np.zeros(max(n_sweeps, 1))
-    rc = lib().or_linear_step(SCHEMES.get(scheme, scheme), M, n_sweeps, nu, dt, a, d, r, phi0,
-                              _p(out), _p(incr))
+    if nu_rule is None:
+        rc = lib().or_linear_step(SCHEMES.get(scheme, scheme), M, n_sweeps, nu, dt, a, d, r, phi0,
+                                  _p(out), _p(incr))
+        if rc:
+            raise RuntimeError("linear step failed")
+        return out[0], incr[:n_sweeps]
+    used = np.zeros(max(n_sweeps, 1), dtype=np.int32)
+    rule = NuRule(*nu_rule)
+    rc = lib().or_linear_step_ex(SCHEMES.get(scheme, scheme), M, n_sweeps, nu, C.byref(rule), dt, a, d,
+                                 r, phi0, _p(out), _p(incr), used.ctypes.data_as(C.POINTER(C.c_int)))
     if rc:
         raise RuntimeError("linear step failed")
-    return out[0], incr[:n_sweeps]
+    return out[0], incr[:n_sweeps], used[:n_sweeps]
 
 
 def linear_G(scheme, M, nu, dt, a, d, r):
@@ -227,17 +246,25 @@ class ADR:
         rc = lib().or_adr_solve_diff(C.byref(self.m), C.byref(self.cfg), wdt, _p(coef_state), _p(rhs), _p(x))
         return x, rc
 
-    def step(self, phi, dt, scheme="CISDCQ", M=2, n_sweeps=4, nu=2, n_steps=1, incr_out=None):
-        """Advance phi [(N+1) x cells] by n_steps time steps; returns (phi, stats)."""
+    def step(self, phi, dt, scheme="CISDCQ", M=2, n_sweeps=4, nu=2, n_steps=1, incr_out=None,
+             nu_rule=None, nu_used_out=None):
+        """Advance phi [(N+1) x cells] by n_steps time steps; returns (phi, stats).
+        nu_rule = (eta, rho_stall): adaptive nested iterations (or_nu_rule); the
+        iterations each sweep ran are appended to nu_used_out (one array per step)."""
         phi = _f64(phi).copy()
         st = AdrStats()
         out = np.zeros_like(phi)
+        rule = NuRule(*(nu_rule if nu_rule is not None else (0.0, 0.0)))
         for _ in range(n_steps):
             incr = np.zeros(max(n_sweeps, 1))
-            rc = lib().or_adr_step(C.byref(self.m), C.byref(self.cfg), SCHEMES.get(scheme, scheme), M,
-                                   n_sweeps, nu, dt, _p(phi), _p(out), _p(incr), C.byref(st))
+            used = np.zeros(max(n_sweeps, 1), dtype=np.int32)
+            rc = lib().or_adr_step_ex(C.byref(self.m), C.byref(self.cfg), SCHEMES.get(scheme, scheme), M,
+                                      n_sweeps, nu, C.byref(rule), dt, _p(phi), _p(out), _p(incr),
+                                      used.ctypes.data_as(C.POINTER(C.c_int)), C.byref(st))
             if incr_out is not None:
                 incr_out.append(incr[:n_sweeps].copy())
+            if nu_used_out is not None:
+                nu_used_out.append(used[:n_sweeps].copy())
             if rc:
                 raise RuntimeError("oracle step failed: %r" % st.as_dict())
             phi, out = out, phi

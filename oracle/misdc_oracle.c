@@ -186,8 +186,31 @@ static void base_rhs(const or_problem *p, const sweep_tables *T, int t, double d
   }
 }
 
+/* field-relative max-norm of now - before over nodes 1..M (adaptive rule) */
+static double nested_incr(const or_problem *p, int M, double *const *now, double *const *before) {
+  const int F = p->n_fields > 0 ? p->n_fields : 1, C = p->n / F;
+  double worst = 0.0;
+  for (int f = 0; f < F; ++f) {
+    double dmax = 0.0, smax = 0.0;
+    for (int m = 1; m <= M; ++m)
+      for (int c = 0; c < C; ++c) {
+        const double a = now[m][(size_t)f * C + c], b = before[m][(size_t)f * C + c];
+        dmax = fmax(dmax, fabs(a - b));
+        smax = fmax(smax, fabs(a));
+      }
+    if (smax > 0.0) worst = fmax(worst, dmax / smax);
+  }
+  return worst;
+}
+
 int or_sweep(const or_problem *p, int scheme, int M, int nu, double dt,
              const double *Phi_k, double *Phi_out) {
+  return or_sweep_ex(p, scheme, M, nu, NULL, dt, Phi_k, Phi_out, NULL);
+}
+
+int or_sweep_ex(const or_problem *p, int scheme, int M, int nu, const or_nu_rule *rule,
+                double dt, const double *Phi_k, double *Phi_out, int *nu_used) {
+  if (nu_used) *nu_used = 1;
   sweep_tables T;
   T.M = M;
   if (or_lobatto(M, T.tau, T.Q, T.S, T.QI, T.QE)) return 1;
@@ -280,6 +303,8 @@ int or_sweep(const or_problem *p, int scheme, int M, int nu, double dt,
       memcpy(FDp[m], FDk[m], sizeof(double) * n);
       memcpy(FRp[m], FRk[m], sizeof(double) * n);
     }
+    double delta[17] = {0};
+    int ran = 0;
     for (int l = 0; l < nu && !rc; ++l) {
       for (int m = 0; m < M && !rc; ++m) {
         int t = m + 1;
@@ -325,7 +350,15 @@ int or_sweep(const or_problem *p, int scheme, int M, int nu, double dt,
         s = FDp[m]; FDp[m] = FDc[m]; FDc[m] = s;
         s = FRp[m]; FRp[m] = FRc[m]; FRc[m] = s;
       }
+      ran = l + 1;
+      if (rule && rule->eta > 0.0 && l < 16) {   /* adaptive rule (or_nu_rule) */
+        delta[l] = nested_incr(p, M, prv, cur);
+        if (l >= 1 && l + 1 < nu &&
+            !(delta[l] > rule->eta * delta[0] && delta[l] < rule->rho_stall * delta[l - 1]))
+          break;
+      }
     }
+    if (nu_used) *nu_used = ran;
     /* S7 */
     for (int m = 1; m <= M; ++m) memcpy(Phi_out + (size_t)m * n, prv[m], sizeof(double) * n);
   } else {
@@ -344,12 +377,18 @@ int or_sweep(const or_problem *p, int scheme, int M, int nu, double dt,
 
 int or_step(const or_problem *p, int scheme, int M, int n_sweeps, int nu,
             double dt, const double *phi_n, double *phi_out, double *incr) {
+  return or_step_ex(p, scheme, M, n_sweeps, nu, NULL, dt, phi_n, phi_out, incr, NULL);
+}
+
+int or_step_ex(const or_problem *p, int scheme, int M, int n_sweeps, int nu,
+               const or_nu_rule *rule, double dt, const double *phi_n, double *phi_out,
+               double *incr, int *nu_used) {
   int n = p->n, rc = 0;
   size_t sz = (size_t)(M + 1) * n;
   double *A = vec((int)sz), *B = vec((int)sz);
   for (int m = 0; m <= M; ++m) memcpy(A + (size_t)m * n, phi_n, sizeof(double) * n);   /* I1, I2 */
   for (int k = 0; k < n_sweeps && !rc; ++k) {
-    rc |= or_sweep(p, scheme, M, nu, dt, A, B);
+    rc |= or_sweep_ex(p, scheme, M, nu, rule, dt, A, B, nu_used ? nu_used + k : NULL);
     if (incr) {
       double s = 0.0;
       for (int i = 0; i < n; ++i) s += fabs(B[(size_t)M * n + i] - A[(size_t)M * n + i]);
@@ -391,6 +430,14 @@ int or_linear_step(int scheme, int M, int n_sweeps, int nu, double dt,
   lin_ctx c = {a, d, r};
   or_problem p = lin_problem(&c);
   return or_step(&p, scheme, M, n_sweeps, nu, dt, &phi0, phi_out, incr);
+}
+
+int or_linear_step_ex(int scheme, int M, int n_sweeps, int nu, const or_nu_rule *rule,
+                      double dt, double a, double d, double r, double phi0,
+                      double *phi_out, double *incr, int *nu_used) {
+  lin_ctx c = {a, d, r};
+  or_problem p = lin_problem(&c);
+  return or_step_ex(&p, scheme, M, n_sweeps, nu, rule, dt, &phi0, phi_out, incr, nu_used);
 }
 
 int or_linear_G(int scheme, int M, int nu, double dt, double a, double d,
@@ -1022,9 +1069,18 @@ static int adr_sr(void *cv, double wdt, const double *b, const double *guess, do
 int or_adr_step(const or_mech *mech, const or_adr_cfg *cfg, int scheme, int M,
                 int n_sweeps, int nu, double dt, const double *phi_n,
                 double *phi_out, double *incr, or_adr_stats *stats) {
+  return or_adr_step_ex(mech, cfg, scheme, M, n_sweeps, nu, NULL, dt, phi_n, phi_out, incr,
+                        NULL, stats);
+}
+
+int or_adr_step_ex(const or_mech *mech, const or_adr_cfg *cfg, int scheme, int M,
+                   int n_sweeps, int nu, const or_nu_rule *rule, double dt,
+                   const double *phi_n, double *phi_out, double *incr, int *nu_used,
+                   or_adr_stats *stats) {
   adr_ctx a = {mech, cfg, cfg->nx * cfg->ny * cfg->nz, mech->N, stats};
-  or_problem p = {(mech->N + 1) * a.cells, &a, adr_fe, adr_fd, adr_fr, adr_sd, adr_sr, NULL};
-  return or_step(&p, scheme, M, n_sweeps, nu, dt, phi_n, phi_out, incr);
+  or_problem p = {(mech->N + 1) * a.cells, &a, adr_fe, adr_fd, adr_fr, adr_sd, adr_sr, NULL,
+                  mech->N + 1};
+  return or_step_ex(&p, scheme, M, n_sweeps, nu, rule, dt, phi_n, phi_out, incr, nu_used);
 }
 
 int or_adr_operators(const or_mech *mech, const or_adr_cfg *cfg, const double *phi,

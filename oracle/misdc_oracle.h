@@ -51,23 +51,50 @@ typedef struct or_problem {
   /* x - wdt * (F_D + F_R)(x) = rhs (IMEXQ only; may be NULL) */
   int (*solve_coupled)(void *ctx, double wdt, const double *rhs,
                        const double *guess, double *x);
+  /* the state is n_fields contiguous fields of n / n_fields entries (0 = 1);
+   * only the adaptive nested-iteration rule looks at it */
+  int n_fields;
 } or_problem;
+
+/* Adaptive number of nested iterations of a CISDCQ sweep (the paper leaves the
+ * mechanism to future work, Sec. 4 and 5; this rule is a reading). delta_l is
+ * the field-relative max-norm of phi^{(k+1,l+1)} - phi^{(k+1,l)} over nodes
+ * 1..M (delta_0: the first nested iteration against sweep k). Iterations 0 and
+ * 1 always run; after iteration l >= 1, iteration l+1 runs only while l+1 < nu,
+ * delta_l > eta delta_0 (the nested iterations have not yet settled relative
+ * to the sweep's own change) and delta_l < rho_stall delta_{l-1} (they still
+ * contract fast enough to pay for another pass). eta <= 0: all nu run. */
+typedef struct or_nu_rule {
+  double eta, rho_stall;
+} or_nu_rule;
 
 /* One sweep (k) -> (k+1). Phi_k[(M+1)*n] holds node values of sweep k
  * (node 0 = phi^n), Phi_out[(M+1)*n] receives sweep k+1. */
 int or_sweep(const or_problem *p, int scheme, int M, int nu, double dt,
              const double *Phi_k, double *Phi_out);
 
+/* As or_sweep, with the adaptive rule (NULL: all nu); *nu_used (optional)
+ * receives the nested iterations the sweep ran (1 for the other schemes). */
+int or_sweep_ex(const or_problem *p, int scheme, int M, int nu, const or_nu_rule *rule,
+                double dt, const double *Phi_k, double *Phi_out, int *nu_used);
+
 /* One time step: spread phi_n to all nodes (I1-I2), n_sweeps sweeps,
  * phi_out = node M. incr[n_sweeps] (optional) receives the L1 norm (mean
  * over entries) of phi^{M,(k+1)} - phi^{M,(k)} per sweep. */
 int or_step(const or_problem *p, int scheme, int M, int n_sweeps, int nu,
             double dt, const double *phi_n, double *phi_out, double *incr);
+/* ... with the adaptive rule; nu_used[n_sweeps] optional */
+int or_step_ex(const or_problem *p, int scheme, int M, int n_sweeps, int nu,
+               const or_nu_rule *rule, double dt, const double *phi_n, double *phi_out,
+               double *incr, int *nu_used);
 
 /* ---- linear model problem phi' = (a + d + r) phi (Sec. 4) ------------- */
 int or_linear_step(int scheme, int M, int n_sweeps, int nu, double dt,
                    double a, double d, double r, double phi0,
                    double *phi_out, double *incr);
+int or_linear_step_ex(int scheme, int M, int n_sweeps, int nu, const or_nu_rule *rule,
+                      double dt, double a, double d, double r, double phi0,
+                      double *phi_out, double *incr, int *nu_used);
 /* Iteration matrix G (M x M) of one sweep on the linear model problem. */
 int or_linear_G(int scheme, int M, int nu, double dt, double a, double d,
                 double r, double *G);
@@ -113,6 +140,10 @@ typedef struct or_adr_stats {
 int or_adr_step(const or_mech *mech, const or_adr_cfg *cfg, int scheme, int M,
                 int n_sweeps, int nu, double dt, const double *phi_n,
                 double *phi_out, double *incr, or_adr_stats *stats);
+int or_adr_step_ex(const or_mech *mech, const or_adr_cfg *cfg, int scheme, int M,
+                   int n_sweeps, int nu, const or_nu_rule *rule, double dt,
+                   const double *phi_n, double *phi_out, double *incr, int *nu_used,
+                   or_adr_stats *stats);
 
 /* pieces, exposed for pins */
 double or_species_h(const or_mech *m, int i, double T);     /* J/kg */
