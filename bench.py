@@ -431,6 +431,54 @@ def diffusion_compare(entries, args, dev, rank):
     return 0
 
 
+def nu_compare(entries, w, args, dev, rank):
+    """Adaptive nested iterations against fixed nu on the first flame: K FP64 steps
+    (after W warm-up steps, L2 flushed before each) with the workload's nu, with
+    fixed nu = NUMAX and with the adaptive rule capped at NUMAX. Reports ms per
+    step, nested iterations per sweep and each state's difference from the fixed
+    nu = NUMAX state (per-field max-norm relative to the field's scale)."""
+    import torch
+    from paper_1801_01201_gb300.solver import Solver
+    numax, eta, rho = args.nu_compare.split(",")
+    numax, eta, rho = int(numax), float(eta), float(rho)
+    mech, fl, dt = entries[0]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    out, states = {}, {}
+    for key, nu, rule in (("fixed_nu%d" % w["nu"], w["nu"], None), ("fixed_nu%d" % numax, numax, None),
+                          ("adaptive_max%d" % numax, numax, (eta, rho))):
+        sv = Solver(mech, fl, n_sweeps=w["sweeps"], nu=nu, n_nodes=w["nodes"], nu_rule=rule, device=dev)
+        x0 = sv.state_from_YT(fl.Y, fl.T)
+        x = x0.clone()
+        for _ in range(args.warmup):
+            sv.step(x, dt, 1, stream=st)
+        sv.stats()
+        x.copy_(x0)   # the same buffer: the captured step is reused
+        ms = []
+        for _ in range(max(args.steps, 1)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            sv.step(x, dt, 1, stream=st)
+            b.record(st)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = sv.stats()
+        states[key] = x
+        out[key] = {"ms_per_step": statistics.median(ms), "status": t["status_name"],
+                    "nested_per_sweep": t["nested_iterations"] / (max(args.steps, 1) * w["sweeps"]),
+                    "newton_iters_per_solve": t["newton_iters"] / max(t["newton_solves"], 1)}
+    ref = states["fixed_nu%d" % numax]
+    scale = ref.abs().amax(dim=1, keepdim=True).clamp_min(1e-300)
+    for k, x in states.items():
+        out[k]["max_rel_diff_vs_fixed_max"] = ((x - ref).abs() / scale).max().item()
+    line = {"nu_compare": out, "rule": {"nu_max": numax, "eta": eta, "rho_stall": rho},
+            "steps": args.steps, "workload": args.workload, "cells": fl.cells}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -459,6 +507,9 @@ def main():
     ap.add_argument("--diffusion-compare", type=float, default=0.0, metavar="WDT",
                     help="instead of the step: time one implicit diffusion solve of weight WDT "
                          "on the workload's initial state, Chebyshev against multigrid, FP64 and mixed")
+    ap.add_argument("--nu-compare", default="", metavar="NUMAX,ETA,RHO",
+                    help="instead of the headline: FP64 steps with the workload's nu, with fixed "
+                         "nu = NUMAX and with adaptive nested iterations (cap NUMAX, rule ETA, RHO)")
     ap.add_argument("--rates-compare", action="store_true",
                     help="instead of the step: time the production-rate kernel, sparse FP64 FMA "
                          "against FP64 tensor cores, on the workload's initial state")
@@ -484,6 +535,8 @@ def main():
         return rates_compare(entries, args, dev, rank)
     if args.diffusion_compare > 0:
         return diffusion_compare(entries, args, dev, rank)
+    if args.nu_compare:
+        return nu_compare(entries, w, args, dev, rank)
     tune = (len(entries) > 1) if args.autotune < 0 else bool(args.autotune)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

@@ -104,6 +104,16 @@ typedef struct misdc_opts {
   int rates_mma;          /* 1: production rates (Sec. 2, omega-dot) contract diag(W) nu^T q
                              on the FP64 tensor cores (mma m8n8k4) instead of the sparse
                              FMA sum; the same values up to FP64 summation order     */
+  double nu_eta;          /* > 0 (CISDCQ, nu > 2): adaptive nested iterations. The paper
+                             asks for such a rule as future work (Sec. 4, 5); this one
+                             runs iterations 0 and 1 of every sweep, then iteration l+1
+                             only while delta_l > nu_eta delta_0 and delta_l <
+                             nu_rho_stall delta_{l-1}, delta_l being the largest
+                             field-relative max-norm change of the node states made by
+                             iteration l (iteration 0: against sweep k); nu is the cap.
+                             Captured steps decide on the device (IF graph nodes);
+                             eager steps read the decision on the host.           */
+  double nu_rho_stall;    /* the contraction bound of that rule (> 0 when nu_eta > 0) */
 } misdc_opts;
 
 typedef struct misdc_stats {
@@ -125,6 +135,7 @@ typedef struct misdc_stats {
   long long newton_certified;   /* mixed precision: solves whose guess a kept factor
                                    certified from the stored reaction term alone
                                    (counted as one iteration, no rate evaluated) */
+  long long nested_iterations;  /* CISDCQ nested iterations run, summed over sweeps */
 } misdc_stats;
 
 typedef struct misdc_solver misdc_solver;

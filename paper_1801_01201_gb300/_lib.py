@@ -36,7 +36,8 @@ class Opts(C.Structure):
                 ("precision", C.c_int), ("dominant_species", C.c_int), ("rho", C.c_double),
                 ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("lin_rtol", C.c_double),
                 ("mg_levels", C.c_int), ("two_streams", C.c_int), ("use_graph", C.c_int),
-                ("profile", C.c_int), ("rates_mma", C.c_int)]
+                ("profile", C.c_int), ("rates_mma", C.c_int), ("nu_eta", C.c_double),
+                ("nu_rho_stall", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -46,7 +47,7 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_longlong), ("surrogate_used", C.c_longlong),
                 ("surrogate_rejected", C.c_longlong), ("newton_fp64_fallbacks", C.c_longlong),
                 ("newton_jacobians", C.c_longlong), ("newton_lu_fp64", C.c_longlong),
-                ("newton_certified", C.c_longlong)]
+                ("newton_certified", C.c_longlong), ("nested_iterations", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

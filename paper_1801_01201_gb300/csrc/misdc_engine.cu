@@ -178,6 +178,21 @@ struct misdc_solver {
   cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr, evJoin = nullptr;
   // CUDA graph of one step
   cudaGraphExec_t gexec = nullptr;
+  // adaptive nested iterations (opts.nu_eta > 0, CISDCQ, nu > 2): per-field
+  // reduction bits [2F], delta_l [nu], flags {continue, iterations run}, a
+  // stream pair and a fork event per nesting level of the IF bodies
+  unsigned long long *nu_bits = nullptr;
+  double *nu_delta = nullptr;
+  int *nu_flags = nullptr;
+  std::vector<cudaStream_t> body_streams;
+  std::vector<cudaEvent_t> evBody;
+  bool in_body = false;
+  long long nested_host = 0;   // nested iterations of fixed-nu steps
+  int nu_body_kernels = 0;     // kernels of one captured nested-iteration body
+  // captured standalone diffusion solve (keyed by its weight) and its output
+  cudaGraphExec_t dgexec = nullptr;
+  double dg_wdt = -1.0;
+  double *dout = nullptr;
   double *g_state = nullptr, *g_T = nullptr;
   double g_dt = 0.0;
   int cheb_sweeps = 0;
@@ -321,7 +336,7 @@ void prepare_node0(misdc_solver *s, const double *state, const double *Tin, cuda
 void d_stage(misdc_solver *s, int t, const double *theta_coef, double wdt, bool lag_source,
              const NodeBuf *Tguess, cudaStream_t st) {
   NodeBuf &ad = s->AD[t];
-  const bool prof = s->o.profile && 2 * (s->d_used + 1) <= (int)s->prof_d.size();
+  const bool prof = s->o.profile && !s->in_body && 2 * (s->d_used + 1) <= (int)s->prof_d.size();
   if (prof) cudaEventRecordWithFlags(s->prof_d[2 * s->d_used], st, cudaEventRecordExternal);
   diffusion_solve(s->m, s->g, s->i0, wdt, theta_coef, s->rhsD, ad.phi, s->dw, s->cheb_sweeps,
                   s->rho_bound, s->o.lin_rtol, s->st, st);
@@ -338,7 +353,7 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
              cudaStream_t st) {
   const size_t cs = s->cs, N = s->N;
   const NodeBuf &ad = s->AD[t];
-  const bool prof = s->o.profile && 2 * (s->n_used + 1) <= (int)s->prof_n.size();
+  const bool prof = s->o.profile && !s->in_body && 2 * (s->n_used + 1) <= (int)s->prof_n.size();
   if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used], st, cudaEventRecordExternal);
   Surrogate *sg = s->sg;
   const float *pred = nullptr;
@@ -390,17 +405,21 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
   for (int k = 0; k < s->o.n_sweeps; ++k) {
     sweep_quadrature(s, dt, sD);
     if (sch == MISDC_SCHEME_CISDCQ) {
-      for (int l = 0; l < nu; ++l) {
+      // one nested iteration l on streams qD (diffusion) and qR (reaction); `fresh`:
+      // everything of iteration l-1 is complete before the first node starts (an
+      // adaptive iteration that starts after the decision), so no waits on it
+      auto iteration = [&](int l, cudaStream_t qD, cudaStream_t qR, bool fresh, bool join) {
+        const bool dual = qD != qR;
         NodeBuf *C = (l % 2 == 0) ? s->X : s->Y;
         NodeBuf *P = (l == 0) ? s->K : ((l % 2 == 1) ? s->X : s->Y);
         for (int m = 0; m < M; ++m) {
           const int t = m + 1;
           // ---- diffusion step at node t ----
-          if (two && l >= 1) {
-            if (m >= 1) cudaStreamWaitEvent(sD, s->eR(m, l - 1), 0);
-            cudaStreamWaitEvent(sD, s->eR(t, l - 1), 0);
+          if (dual && l >= 1 && !fresh) {
+            if (m >= 1) cudaStreamWaitEvent(qD, s->eR(m, l - 1), 0);
+            cudaStreamWaitEvent(qD, s->eR(t, l - 1), 0);
           }
-          if (two) for (int j = 1; j <= m - 1; ++j) cudaStreamWaitEvent(sD, s->eR(j, l), 0);
+          if (dual) for (int j = 1; j <= m - 1; ++j) cudaStreamWaitEvent(qD, s->eR(j, l), 0);
           LC r(s->rhsD);
           r.add(s->B[t], 1.0);
           for (int j = 1; j <= m - 1; ++j) {
@@ -418,13 +437,13 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
           }
           const double *lagR1 = (l == 0) ? s->K[t].FR : P[t].FR;
           r.add(lagR1, dt * T.QI[t - 1][t - 1]);
-          launch_lincomb(r.lc, n, sD);
+          launch_lincomb(r.lc, n, qD);
           const double wdt = dt * T.QI[t - 1][t - 1];
           const double *coef = (l == 0) ? s->K[t].theta : P[t].theta;
-          d_stage(s, t, coef, wdt, l == 0 && t < M, &s->K[t], sD);
-          if (two) cudaEventRecord(s->eD(t, l), sD);
+          d_stage(s, t, coef, wdt, l == 0 && t < M, &s->K[t], qD);
+          if (dual) cudaEventRecord(s->eD(t, l), qD);
           // ---- reaction step at node t (R_alt form) ----
-          if (two) cudaStreamWaitEvent(sR, s->eD(t, l), 0);
+          if (dual) cudaStreamWaitEvent(qR, s->eD(t, l), 0);
           LC b(s->bR);
           b.add(s->AD[t].phi, 1.0);
           if (m >= 1) {
@@ -433,13 +452,103 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
             b.add(lagRm, -dt * T.QI[t - 1][m - 1]);
           }
           b.add(lagR1, -dt * T.QI[t - 1][t - 1]);
-          launch_lincomb(b.lc, n, sR);
-          r_stage(s, t, wdt, P[t], C[t], sR);
-          if (two) cudaEventRecord(s->eR(t, l), sR);
+          launch_lincomb(b.lc, n, qR);
+          r_stage(s, t, wdt, P[t], C[t], qR);
+          if (dual) cudaEventRecord(s->eR(t, l), qR);
         }
+        if (dual && join) cudaStreamWaitEvent(qD, s->eR(M, l), 0);   // the iteration ends on qD
+      };
+      // the adaptive rule after iteration l (on qD): delta_l from the node stacks
+      // of iterations l and l-1 (sweep k for l = 0)
+      auto decide = [&](int l, cudaStream_t qD, const cudaGraphConditionalHandle *h, bool body) {
+        NodePtrs now{}, before{};
+        NodeBuf *C = (l % 2 == 0) ? s->X : s->Y;
+        NodeBuf *P = (l == 0) ? s->K : ((l % 2 == 1) ? s->X : s->Y);
+        for (int m = 1; m <= M; ++m) { now.p[m - 1] = C[m].phi; before.p[m - 1] = P[m].phi; }
+        launch_nu_decide((int)F, (int)cs, M, now, before, l, nu, s->o.nu_eta, s->o.nu_rho_stall,
+                         s->nu_bits, s->nu_delta, s->nu_flags, s->nu_flags + 1, s->st, h,
+                         body ? s->nu_flags + 2 : nullptr, qD);
+      };
+      const bool adapt = s->nu_bits != nullptr;
+      if (!adapt) {
+        for (int l = 0; l < nu; ++l) iteration(l, sD, sR, false, l == nu - 1);
+      } else {
+        // iterations 0 and 1 always run; iteration l >= 2 runs inside an IF graph
+        // node (nested in the body of l-1) that the decision after l-1 sets, or, in
+        // an eager step, after the host has read that decision
+        iteration(0, sD, sR, false, true);
+        decide(0, sD, nullptr, false);
+        iteration(1, sD, sR, false, true);
+        cudaGraphConditionalHandle h;
+        if (graph_conditional_handle(sD, 0, &h)) {
+          decide(1, sD, &h, false);
+          cudaStream_t outer = sD;
+          s->in_body = true;
+          int opened = 0;
+          for (int l = 2; l < nu; ++l) {
+            cudaGraph_t body = graph_conditional_node(outer, cudaGraphCondTypeIf, h);
+            if (!body) break;   // the capture reports the failure at its end
+            cudaStream_t bD = s->body_streams[2 * opened], bR = two ? s->body_streams[2 * opened + 1] : bD;
+            cudaStreamBeginCaptureToGraph(bD, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (two) {
+              cudaEventRecord(s->evBody[opened], bD);
+              cudaStreamWaitEvent(bR, s->evBody[opened], 0);
+            }
+            ++opened;
+            iteration(l, bD, bR, true, true);
+            const bool more = l + 1 < nu && graph_conditional_handle(bD, 0, &h);
+            decide(l, bD, more ? &h : nullptr, true);
+            outer = bD;
+            if (!more) break;
+          }
+          // close the nested captures from the innermost out (the bodies belong to
+          // their conditional nodes)
+          for (int d = opened - 1; d >= 0; --d) {
+            cudaGraph_t done = nullptr;
+            if (cudaStreamEndCapture(s->body_streams[2 * d], &done) == cudaSuccess && d == 0 && done) {
+              // kernels of one nested iteration (a body without its nested IF), counted
+              // by the device each time a body runs
+              size_t nn = 0;
+              cudaGraphGetNodes(done, nullptr, &nn);
+              std::vector<cudaGraphNode_t> nodes(nn);
+              cudaGraphGetNodes(done, nodes.data(), &nn);
+              int kernels = 0;
+              for (auto nd : nodes) {
+                cudaGraphNodeType ty;
+                cudaGraphNodeGetType(nd, &ty);
+                if (ty == cudaGraphNodeTypeKernel) ++kernels;
+              }
+              s->nu_body_kernels = kernels;   // uploaded once the capture has ended
+            }
+          }
+          s->in_body = false;
+        } else {
+          decide(1, sD, nullptr, false);
+          for (int l = 2; l < nu; ++l) {
+            int cont = 0;
+            cudaMemcpyAsync(&cont, s->nu_flags, sizeof(int), cudaMemcpyDeviceToHost, sD);
+            cudaStreamSynchronize(sD);
+            if (!cont) break;
+            iteration(l, sD, sR, false, true);
+            decide(l, sD, nullptr, false);
+          }
+        }
+        // the result must sit in the buffer S7 takes (that of iteration nu-1)
+        CopyList cl{};
+        NodeBuf *last = ((nu - 1) % 2 == 0) ? s->X : s->Y, *other = ((nu - 1) % 2 == 0) ? s->Y : s->X;
+        const size_t sizes[7] = {F * cs, cs, cs, (size_t)s->N * cs, F * cs, F * cs, F * cs};
+        for (int m = 1; m <= M; ++m) {
+          double *dst[7] = {last[m].phi, last[m].T, last[m].theta, last[m].hsp, last[m].FE, last[m].FD, last[m].FR};
+          const double *src[7] = {other[m].phi, other[m].T, other[m].theta, other[m].hsp, other[m].FE, other[m].FD, other[m].FR};
+          for (int q = 0; q < 7; ++q) {
+            cl.dst[cl.count] = dst[q];
+            cl.src[cl.count] = src[q];
+            cl.n[cl.count++] = sizes[q];
+          }
+        }
+        launch_copy_if_parity(cl, s->nu_flags + 1, (nu - 1) & 1, sD);
       }
       NodeBuf *last = ((nu - 1) % 2 == 0) ? s->X : s->Y;   // S7
-      if (two) cudaStreamWaitEvent(sD, s->eR(M, nu - 1), 0);
       for (int m = 1; m <= M; ++m) std::swap(s->K[m], last[m]);
     } else {
       NodeBuf *C = s->X;
@@ -572,6 +681,8 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   if (cells > (1LL << 30)) return fail(MISDC_E_INVALID, "grid too large");
   if (op->n_nodes < 2 || op->n_nodes > 5) return fail(MISDC_E_INVALID, "n_nodes must be 2..5");
   if (op->n_sweeps < 1 || op->nu < 1 || op->nu > 16) return fail(MISDC_E_INVALID, "bad n_sweeps/nu");
+  if (op->nu_eta > 0.0 && !(op->nu_rho_stall > 0.0))
+    return fail(MISDC_E_INVALID, "adaptive nu needs nu_rho_stall > 0");
   if (op->scheme < 0 || op->scheme > 2) return fail(MISDC_E_INVALID, "bad scheme");
   if (op->precision != MISDC_PREC_FP64 && op->precision != MISDC_PREC_MIXED)
     return fail(MISDC_E_INVALID, "precision must be MISDC_PREC_FP64 or MISDC_PREC_MIXED");
@@ -763,8 +874,11 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     const size_t nfs = N;
     w.mg32 = s->o.precision == MISDC_PREC_MIXED;
     if (s->alloc(&w.lb[0], nfs * cs) || s->alloc(&w.lx[0], nfs * cs) || s->alloc(&w.lr[0], nfs * cs) ||
-        s->alloc(&w.ly[0], nfs * cs) || s->alloc(&w.mg_done, 1) || s->alloc(&w.mg_res, 1))
+        s->alloc(&w.ly[0], nfs * cs) || s->alloc(&w.mg_done, 1) || s->alloc(&w.mg_res, 1) ||
+        s->alloc(&w.mg_cycle, 1))
       return bail(fail(MISDC_E_OOM, "multigrid"));
+    if (cudaStreamCreateWithFlags(&w.mg_stream, cudaStreamNonBlocking))
+      return bail(fail(MISDC_E_CUDA, "stream creation failed"));
     for (int l = 1; l < s->o.mg_levels; ++l) {
       DevGrid c = w.lg[l - 1];
       if ((c.nx % 2) || (c.dim > 1 && c.ny % 2) || (c.dim > 2 && c.nz % 2) || c.nx < 4) break;
@@ -796,6 +910,17 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) return bail(fail(MISDC_E_CUDA, "event"));
   for (cudaEvent_t *e : {&s->evIn, &s->evOut, &s->evFork, &s->evJoin})
     if (cudaEventCreateWithFlags(e, cudaEventDisableTiming)) return bail(fail(MISDC_E_CUDA, "event"));
+  if (op->scheme == MISDC_SCHEME_CISDCQ && op->nu > 2 && op->nu_eta > 0.0) {
+    if (s->alloc(&s->nu_bits, 2 * F) || s->alloc(&s->nu_delta, (size_t)op->nu) || s->alloc(&s->nu_flags, 3))
+      return bail(fail(MISDC_E_OOM, "adaptive nested iterations"));
+    cudaMemset(s->nu_bits, 0, 2 * F * sizeof(unsigned long long));
+    s->body_streams.assign(2 * (size_t)(op->nu - 2), nullptr);
+    s->evBody.assign((size_t)(op->nu - 2), nullptr);
+    for (auto &q : s->body_streams)
+      if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking)) return bail(fail(MISDC_E_CUDA, "stream creation failed"));
+    for (auto &e : s->evBody)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) return bail(fail(MISDC_E_CUDA, "event"));
+  }
   if (op->profile) {
     const int stages = op->n_sweeps * M * (op->scheme == MISDC_SCHEME_CISDCQ ? op->nu : 1);
     s->prof_n.assign(2 * (size_t)stages, nullptr);
@@ -815,6 +940,7 @@ void misdc_destroy(misdc_solver *s) {
   if (s->sD) cudaStreamSynchronize(s->sD);
   if (s->sR) cudaStreamSynchronize(s->sR);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->dgexec) cudaGraphExecDestroy(s->dgexec);
   for (auto *v : {&s->evD, &s->evR})
     for (auto &ev : *v) if (ev) cudaEventDestroy(ev);
   for (cudaEvent_t ev : {s->evIn, s->evOut, s->evFork, s->evJoin}) if (ev) cudaEventDestroy(ev);
@@ -822,6 +948,9 @@ void misdc_destroy(misdc_solver *s) {
     for (auto &ev : *v) if (ev) cudaEventDestroy(ev);
   if (s->sD) cudaStreamDestroy(s->sD);
   if (s->sR) cudaStreamDestroy(s->sR);
+  if (s->dw.mg_stream) cudaStreamDestroy(s->dw.mg_stream);
+  for (cudaStream_t q : s->body_streams) if (q) cudaStreamDestroy(q);
+  for (cudaEvent_t e : s->evBody) if (e) cudaEventDestroy(e);
   for (void *p : s->allocs) cudaFree(p);
   delete s->sg;
   delete s;
@@ -834,6 +963,8 @@ misdc_status misdc_step(misdc_solver *s, double *state, double *T, double dt, in
   if (n_steps == 0) return MISDC_OK;
   cudaStream_t us = (cudaStream_t)stream;
   configure_dt(s, dt);
+  if (s->o.scheme == MISDC_SCHEME_CISDCQ && !s->nu_bits)
+    s->nested_host += (long long)n_steps * s->o.n_sweeps * s->o.nu;
   CK(cudaEventRecord(s->evIn, us));
   CK(cudaStreamWaitEvent(s->sD, s->evIn, 0));
   if (s->o.use_graph) {
@@ -858,6 +989,7 @@ misdc_status misdc_step(misdc_solver *s, double *state, double *T, double dt, in
       cudaGraphDestroy(graph);
       if (ec != cudaSuccess) return fail(MISDC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
       s->g_state = state; s->g_T = T; s->g_dt = dt;
+      if (s->nu_flags) CK(cudaMemcpy(s->nu_flags + 2, &s->nu_body_kernels, sizeof(int), cudaMemcpyHostToDevice));
     }
     for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(s->gexec, s->sD));
     s->kernels_launched += s->kernels_per_step * n_steps;
@@ -903,7 +1035,8 @@ misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
   double r;
   memcpy(&r, &d.lin_resid_bits, sizeof(r));
   out->lin_resid_max = r;
-  out->kernel_launches = s->kernels_launched;
+  out->kernel_launches = s->kernels_launched + (long long)d.body_launches;
+  out->nested_iterations = (long long)d.nested_iters + s->nested_host;
   out->surrogate_used = (long long)d.sg_used;
   out->surrogate_rejected = (long long)d.sg_rejected;
   out->newton_fp64_fallbacks = (long long)d.fp64_fallbacks;
@@ -920,6 +1053,7 @@ misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
   if (reset) {
     CK(cudaMemset(s->st, 0, sizeof(DevStats)));
     s->kernels_launched = 0;
+    s->nested_host = 0;
   }
   return MISDC_OK;
 }
@@ -1020,16 +1154,45 @@ misdc_status misdc_diffusion_solve(misdc_solver *s, double wdt, const double *co
   CK(cudaStreamSynchronize(s->sD));
   NodeBuf &b = s->node0;
   const size_t cs = s->cs, F = s->N + 1;
-  CK(cudaMemcpyAsync(b.phi, coef_state, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  launch_temperature(s->m, s->cs, s->cs, b.phi, b.phi + (size_t)s->N * cs, nullptr, b.T, b.theta,
-                     nullptr, s->st, st);
   s->rho_dt = -1.0;
   s->rho_bound = rho_bound_for(s, wdt);
   s->cheb_sweeps = std::min(kMaxCheb, chebyshev_sweeps(s->rho_bound, std::max(1e-3 * s->o.lin_rtol, 1e-17)));
-  CK(cudaMemcpyAsync(s->rhsD, rhs, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  diffusion_solve(s->m, s->g, s->i0, wdt, b.theta, s->rhsD, x, s->dw, s->cheb_sweeps, s->rho_bound,
-                  s->o.lin_rtol, s->st, st);
-  CK(cudaGetLastError());
+  auto enqueue = [&](double *out, cudaStream_t q) {
+    launch_temperature(s->m, s->cs, s->cs, b.phi, b.phi + (size_t)s->N * cs, nullptr, b.T, b.theta,
+                       nullptr, s->st, q);
+    diffusion_solve(s->m, s->g, s->i0, wdt, b.theta, s->rhsD, out, s->dw, s->cheb_sweeps,
+                    s->rho_bound, s->o.lin_rtol, s->st, q);
+  };
+  if (!s->o.use_graph) {
+    CK(cudaMemcpyAsync(b.phi, coef_state, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(s->rhsD, rhs, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    enqueue(x, st);
+    CK(cudaGetLastError());
+    return MISDC_OK;
+  }
+  // captured once per weight (multigrid cycles then run as a WHILE graph node):
+  // inputs copied into the solver's buffers, the result copied out
+  if (!s->dout) CK(s->alloc(&s->dout, F * cs));
+  CK(cudaEventRecord(s->evIn, st));
+  CK(cudaStreamWaitEvent(s->sD, s->evIn, 0));
+  CK(cudaMemcpyAsync(b.phi, coef_state, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, s->sD));
+  CK(cudaMemcpyAsync(s->rhsD, rhs, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, s->sD));
+  if (!s->dgexec || s->dg_wdt != wdt) {
+    if (s->dgexec) { cudaGraphExecDestroy(s->dgexec); s->dgexec = nullptr; }
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(s->sD, cudaStreamCaptureModeThreadLocal));
+    enqueue(s->dout, s->sD);
+    cudaError_t ec = cudaStreamEndCapture(s->sD, &graph);
+    if (ec != cudaSuccess) return fail(MISDC_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    ec = cudaGraphInstantiate(&s->dgexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) return fail(MISDC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+    s->dg_wdt = wdt;
+  }
+  CK(cudaGraphLaunch(s->dgexec, s->sD));
+  CK(cudaMemcpyAsync(x, s->dout, F * cs * sizeof(double), cudaMemcpyDeviceToDevice, s->sD));
+  CK(cudaEventRecord(s->evOut, s->sD));
+  CK(cudaStreamWaitEvent(st, s->evOut, 0));
   return MISDC_OK;
 }
 
@@ -1161,10 +1324,14 @@ misdc_status sg_ready(misdc_solver *s, bool need_params) {
 
 // a changed step program must be captured again
 void drop_graph(misdc_solver *s) {
+  if (s->gexec || s->dgexec) cudaStreamSynchronize(s->sD);
   if (s->gexec) {
-    cudaStreamSynchronize(s->sD);
     cudaGraphExecDestroy(s->gexec);
     s->gexec = nullptr;
+  }
+  if (s->dgexec) {
+    cudaGraphExecDestroy(s->dgexec);
+    s->dgexec = nullptr;
   }
 }
 
@@ -1616,6 +1783,8 @@ misdc_status misdc_batch_step(misdc_batch *b, double *const *states, double *con
     ec = cudaGraphInstantiate(&b->gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (ec != cudaSuccess) return fail(MISDC_E_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(ec));
+    for (misdc_solver *s : b->sv)
+      if (s->nu_flags) CK(cudaMemcpy(s->nu_flags + 2, &s->nu_body_kernels, sizeof(int), cudaMemcpyHostToDevice));
     b->g_state.assign(states, states + n);
     b->g_T.assign(n, nullptr);
     if (T) b->g_T.assign(T, T + n);
@@ -1625,6 +1794,9 @@ misdc_status misdc_batch_step(misdc_batch *b, double *const *states, double *con
   CK(cudaEventRecord(b->evIn, us));
   CK(cudaStreamWaitEvent(b->cs, b->evIn, 0));
   for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(b->gexec, b->cs));
+  for (misdc_solver *s : b->sv)
+    if (s->o.scheme == MISDC_SCHEME_CISDCQ && !s->nu_bits)
+      s->nested_host += (long long)n_steps * s->o.n_sweeps * s->o.nu;
   b->kernels_launched += b->kernels_per_step * n_steps;
   CK(cudaEventRecord(b->evOut, b->cs));
   CK(cudaStreamWaitEvent(us, b->evOut, 0));
@@ -1653,8 +1825,10 @@ misdc_status misdc_batch_stats(misdc_batch *b, misdc_stats *out, int reset) {
     sum.newton_jacobians += t.newton_jacobians;
     sum.newton_lu_fp64 += t.newton_lu_fp64;
     sum.newton_certified += t.newton_certified;
+    sum.kernel_launches += t.kernel_launches;   // kernels in conditional bodies
+    sum.nested_iterations += t.nested_iterations;
   }
-  sum.kernel_launches = b->kernels_launched;
+  sum.kernel_launches += b->kernels_launched;
   if (reset) b->kernels_launched = 0;
   *out = sum;
   return MISDC_OK;

@@ -461,12 +461,23 @@ __global__ void k_residual(DevGrid g, FieldMap fm, const T *__restrict__ thf,
 // after the fine residual of a V-cycle: stop the cycles once it meets the target;
 // counts the fine smoothing sweeps that ran (two before the residual, two after
 // it unless the cycles stop here)
-__global__ void k_mg_check(unsigned long long *res_bits, double tol, int *done, DevStats *st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0 || *done) return;
+// (in a WHILE graph body: also ends the loop once done or after `cap` cycles, and
+// counts the body's kernels)
+__global__ void k_mg_check(unsigned long long *res_bits, double tol, int *done, DevStats *st,
+                           int *cycle, int cap, cudaGraphConditionalHandle h, int body_kernels) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (body_kernels) {
+    atomicAdd(&st->body_launches, (unsigned long long)body_kernels);
+    if (*done || ++*cycle >= cap) cudaGraphSetConditional(h, 0);
+  }
+  if (*done) return;
   const double r = __longlong_as_double((long long)*res_bits);
   *res_bits = 0ull;
   const bool stop = r <= tol;
-  if (stop) *done = 1;
+  if (stop) {
+    *done = 1;
+    if (body_kernels) cudaGraphSetConditional(h, 0);
+  }
   atomicAdd(&st->lin_sweeps, stop ? 2ull : 4ull);
 }
 
@@ -495,6 +506,60 @@ __global__ void k_diag_level(DevGrid g, FieldMap fm, const T *__restrict__ thf,
   T S = 0;
   for (int d = 0; d < g.dim; ++d) S += thf[(size_t)d * g.cells + c] + thf[(size_t)d * g.cells + nb.cp[d]];
   for (int k = 0; k < fm.nfs; ++k) invdiag[(size_t)k * g.cells + c] = (T)1 / ((T)1 + (T)fm.cf[k] * S);
+}
+
+// ---- adaptive nested iterations: per field, max |now - before| and max |now|
+// over the nodes' cells (bit patterns of non-negative doubles, so integer max)
+__global__ void k_nu_incr(int cs, int M, NodePtrs now, NodePtrs before,
+                          unsigned long long *__restrict__ bits) {
+  const int f = blockIdx.y;
+  double dm = 0.0, sm = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const double *a = now.p[m] + (size_t)f * cs, *b = before.p[m] + (size_t)f * cs;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cs; c += gridDim.x * blockDim.x) {
+      const double x = a[c];
+      dm = fmax(dm, fabs(x - b[c]));
+      sm = fmax(sm, fabs(x));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (dm > 0.0) atomicMax(&bits[2 * f], dbits(dm));
+    if (sm > 0.0) atomicMax(&bits[2 * f + 1], dbits(sm));
+  }
+}
+
+__global__ void k_nu_decide(int F, int l, int nu, double eta, double rho,
+                            unsigned long long *bits, double *delta, int *cont, int *ran,
+                            DevStats *st, cudaGraphConditionalHandle h, int has_h,
+                            const int *body_kernels) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (body_kernels) atomicAdd(&st->body_launches, (unsigned long long)*body_kernels);
+  double d = 0.0;
+  for (int f = 0; f < F; ++f) {
+    const double dm = __longlong_as_double((long long)bits[2 * f]);
+    const double sm = __longlong_as_double((long long)bits[2 * f + 1]);
+    if (sm > 0.0) d = fmax(d, dm / sm);
+    bits[2 * f] = bits[2 * f + 1] = 0ull;
+  }
+  delta[l] = d;
+  const bool go = l + 1 < nu && (l < 1 || (d > eta * delta[0] && d < rho * delta[l - 1]));
+  *cont = go ? 1 : 0;
+  *ran = l + 1;
+  if (!go) atomicAdd(&st->nested_iters, (unsigned long long)(l + 1));
+  if (has_h) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_copy_if_parity(CopyList cl, const int *ran, int parity) {
+  if (((*ran - 1) & 1) == parity) return;
+  const int k = blockIdx.y;
+  const size_t n = cl.n[k];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    cl.dst[k][i] = cl.src[k][i];
 }
 
 // gather the solved fields of a full-layout array into compact storage and back
@@ -583,14 +648,21 @@ void mg_smooth(DiffWork &w, const FieldMap &fm, int l, int n, cudaStream_t s) {
 
 // residual of level l (with the convergence measure on the fine level), restricted
 // into the right-hand side of level l+1, whose iterate starts from zero
+struct CycleLoop {   // the WHILE node the cycles run in (body_kernels = 0: none)
+  cudaGraphConditionalHandle h;
+  int body_kernels;
+};
+
 template <class TF, class TC>
-void mg_down(DiffWork &w, const FieldMap &fm, int l, cudaStream_t s) {
+void mg_down(DiffWork &w, const FieldMap &fm, int l, const CycleLoop &loop, cudaStream_t s) {
   const DevGrid &gl = w.lg[l], &gc = w.lg[l + 1];
   TF *r = lv<TF>(w.lr[l], w.lr32[l]);
   k_residual<TF><<<grid2(gl.cells, fm.nfs), 256, 0, s>>>(
       gl, fm, lv<TF>(w.lthf[l], w.lthf32[l]), lv<TF>(w.lb[l], w.lb32[l]), lv<TF>(w.lx[l], w.lx32[l]),
       r, w.mg_done, l == 0 ? w.mg_res : nullptr);
-  if (l == 0) k_mg_check<<<1, 32, 0, s>>>(w.mg_res, w.mg_tol, w.mg_done, w.mg_st);
+  if (l == 0)
+    k_mg_check<<<1, 32, 0, s>>>(w.mg_res, w.mg_tol, w.mg_done, w.mg_st, w.mg_cycle, w.cycles,
+                                loop.h, loop.body_kernels);
   k_restrict<TF, TC><<<grid2(gc.cells, fm.nfs), 256, 0, s>>>(gl, gc, r, lv<TC>(w.lb[l + 1], w.lb32[l + 1]),
                                                              w.mg_done);
   cudaMemsetAsync(lv<TC>(w.lx[l + 1], w.lx32[l + 1]), 0, sizeof(TC) * (size_t)fm.nfs * gc.cells, s);
@@ -639,36 +711,88 @@ void multigrid_solve(const DevGrid &g, const FieldMap &fm, const double *rhs, Di
   w.mg_st = st;
   cudaMemsetAsync(w.mg_done, 0, sizeof(int), s);
   cudaMemsetAsync(w.mg_res, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(w.mg_cycle, 0, sizeof(int), s);
   k_gather<<<gr, 256, 0, s>>>(cs, fm, rhs, nullptr, nullptr, nullptr, w.lb[0]);
   k_gather<<<gr, 256, 0, s>>>(cs, fm, rhs, nullptr, nullptr, nullptr, w.lx[0]);
-  for (int cyc = 0; cyc < w.cycles; ++cyc) {
+  auto cycle = [&](const CycleLoop &loop, cudaStream_t q) {
     for (int l = 0; l + 1 < L; ++l) {          // down-leg
       if (f32(l)) {
-        mg_smooth<float>(w, fl[l], l, 2, s);
-        mg_down<float, float>(w, fl[l], l, s);
+        mg_smooth<float>(w, fl[l], l, 2, q);
+        mg_down<float, float>(w, fl[l], l, loop, q);
       } else {
-        mg_smooth<double>(w, fl[l], l, 2, s);
-        if (f32(l + 1)) mg_down<double, float>(w, fl[l], l, s);
-        else mg_down<double, double>(w, fl[l], l, s);
+        mg_smooth<double>(w, fl[l], l, 2, q);
+        if (f32(l + 1)) mg_down<double, float>(w, fl[l], l, loop, q);
+        else mg_down<double, double>(w, fl[l], l, loop, q);
       }
     }
-    if (f32(L - 1)) mg_smooth<float>(w, fl[L - 1], L - 1, 8, s);   // coarsest level
-    else mg_smooth<double>(w, fl[L - 1], L - 1, 8, s);
+    if (f32(L - 1)) mg_smooth<float>(w, fl[L - 1], L - 1, 8, q);   // coarsest level
+    else mg_smooth<double>(w, fl[L - 1], L - 1, 8, q);
     for (int l = L - 2; l >= 0; --l) {         // up-leg
       if (f32(l)) {
-        mg_up<float, float>(w, fl[l], l, s);
-        mg_smooth<float>(w, fl[l], l, 2, s);
+        mg_up<float, float>(w, fl[l], l, q);
+        mg_smooth<float>(w, fl[l], l, 2, q);
       } else {
-        if (f32(l + 1)) mg_up<float, double>(w, fl[l], l, s);
-        else mg_up<double, double>(w, fl[l], l, s);
-        mg_smooth<double>(w, fl[l], l, 2, s);
+        if (f32(l + 1)) mg_up<float, double>(w, fl[l], l, q);
+        else mg_up<double, double>(w, fl[l], l, q);
+        mg_smooth<double>(w, fl[l], l, 2, q);
       }
     }
+  };
+  // kernels in one cycle: smoothing 2 per level above the coarsest and back, 8 on
+  // the coarsest, residual + restriction + prolongation per level above it, the check
+  const int per_cycle = 4 * (L - 1) + 8 + 3 * (L - 1) + 1;
+  CycleLoop loop{0, 0};
+  cudaGraph_t body = w.mg_stream ? graph_conditional(s, cudaGraphCondTypeWhile, 1, &loop.h) : nullptr;
+  if (body) {
+    // captured: one cycle is the body of a WHILE node that the check ends
+    loop.body_kernels = per_cycle;
+    cudaStreamBeginCaptureToGraph(w.mg_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    cycle(loop, w.mg_stream);
+    cudaStreamEndCapture(w.mg_stream, &body);
+  } else {
+    for (int cyc = 0; cyc < w.cycles; ++cyc) cycle(loop, s);
   }
   k_scatter_set<<<gr, 256, 0, s>>>(cs, fm, w.lx[0], w.xa);
 }
 
 }  // namespace
+
+bool graph_conditional_handle(cudaStream_t s, unsigned dflt, cudaGraphConditionalHandle *h) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive)
+    return false;
+  return cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault) == cudaSuccess;
+}
+
+cudaGraph_t graph_conditional(cudaStream_t s, cudaGraphConditionalNodeType type, unsigned dflt,
+                              cudaGraphConditionalHandle *h) {
+  if (!graph_conditional_handle(s, dflt, h)) return nullptr;
+  return graph_conditional_node(s, type, *h);
+}
+
+cudaGraph_t graph_conditional_node(cudaStream_t s, cudaGraphConditionalNodeType type,
+                                   cudaGraphConditionalHandle h) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive)
+    return nullptr;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, deps, nullptr, nd, &p) != cudaSuccess) return nullptr;
+  if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+      cudaSuccess)
+    return nullptr;
+  return p.conditional.phGraph_out[0];
+}
 
 void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, const double *theta,
                      const double *rhs, double *out, DiffWork &w, int sweeps, double rho_bound,
@@ -731,6 +855,21 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
   const double *xfin = w.xa;
   k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, xfin, w.xb,
                                             w.xc, kdev, out, st);
+}
+
+void launch_nu_decide(int F, int cs, int M, NodePtrs now, NodePtrs before, int l, int nu,
+                      double eta, double rho, unsigned long long *bits, double *delta, int *cont,
+                      int *ran, DevStats *st, const cudaGraphConditionalHandle *h,
+                      const int *body_kernels, cudaStream_t s) {
+  const int bx = std::max(1, std::min((cs + 255) / 256, 64));
+  k_nu_incr<<<dim3(bx, F), 256, 0, s>>>(cs, M, now, before, bits);
+  k_nu_decide<<<1, 32, 0, s>>>(F, l, nu, eta, rho, bits, delta, cont, ran, st, h ? *h : 0, h ? 1 : 0,
+                               body_kernels);
+}
+
+void launch_copy_if_parity(const CopyList &cl, const int *ran, int parity, cudaStream_t s) {
+  if (cl.count <= 0) return;
+  k_copy_if_parity<<<dim3(64, cl.count), 256, 0, s>>>(cl, ran, parity);
 }
 
 }  // namespace misdc

@@ -38,6 +38,8 @@ struct DevStats {
   unsigned long long jacobians;        // Jacobian assemblies of the reaction Newton
   unsigned long long lu64;             // FP64 LU factorisations of the reaction Newton
   unsigned long long certified;        // solves whose guess was certified without rates
+  unsigned long long body_launches;    // kernels run inside conditional graph bodies
+  unsigned long long nested_iters;     // CISDCQ nested iterations run, summed over sweeps
 };
 
 // Mechanism tables in device memory (built by the engine from misdc_mech_desc).
@@ -177,11 +179,53 @@ struct DiffWork {
   float *lthf32[8], *linvdiag32[8], *lb32[8], *lx32[8], *lr32[8], *ly32[8];
   // V-cycle stop: flag, largest scaled fine residual of the cycle (bit pattern),
   // its target and the statistics it is counted in (set per solve)
-  int *mg_done;
+  int *mg_done, *mg_cycle;
   unsigned long long *mg_res;
   double mg_tol;
   DevStats *mg_st;
+  // inside a stream capture the V-cycles become the body of a WHILE graph node,
+  // captured on this private stream (null: unrolled cycles that skip once done)
+  cudaStream_t mg_stream;
 };
+
+// Inside a stream capture on s: append a conditional node (IF or WHILE, default
+// value dflt at every graph launch) after the stream's capture dependencies and
+// make it the stream's only dependency. Returns the body graph to capture into,
+// or nullptr when s is not capturing or the node could not be added.
+cudaGraph_t graph_conditional(cudaStream_t s, cudaGraphConditionalNodeType type, unsigned dflt,
+                              cudaGraphConditionalHandle *h);
+// the two halves of graph_conditional, for a handle that a kernel captured before
+// the node sets: create it on s's capture graph (false when s is not capturing),
+// then add the node that uses it
+bool graph_conditional_handle(cudaStream_t s, unsigned dflt, cudaGraphConditionalHandle *h);
+cudaGraph_t graph_conditional_node(cudaStream_t s, cudaGraphConditionalNodeType type,
+                                   cudaGraphConditionalHandle h);
+
+// ---- adaptive nested iterations of a CISDCQ sweep (misdc_grid.cu) ----
+// After nested iteration l: delta_l = max over fields of max|now - before| / max|now|
+// over the nodes' cells (now/before: the node stacks of iterations l and l-1, node
+// m at [m - 1], fields [F][cs]); delta[l] = delta_l; then the rule: continue while
+// l + 1 < nu and (l < 1 or (delta_l > eta delta_0 and delta_l < rho delta_{l-1})).
+// *cont = the decision, *ran = l + 1; the iterations run are added to st when the
+// sweep's loop ends here; with a handle, the IF node of iteration l + 1 is set;
+// body_kernels (inside an IF body): the body's kernel count, added to st.
+struct NodePtrs {
+  const double *p[kMaxNodes];
+};
+void launch_nu_decide(int F, int cs, int M, NodePtrs now, NodePtrs before, int l, int nu,
+                      double eta, double rho, unsigned long long *bits, double *delta, int *cont,
+                      int *ran, DevStats *st, const cudaGraphConditionalHandle *h,
+                      const int *body_kernels, cudaStream_t s);
+// dst[k] = src[k] (n[k] doubles each, k < count) when the parity of *ran - 1 differs
+// from `parity` (the nested loop ended in the other buffer of the pair)
+constexpr int kMaxCopies = 7 * kMaxNodes;
+struct CopyList {
+  double *dst[kMaxCopies];
+  const double *src[kMaxCopies];
+  size_t n[kMaxCopies];
+  int count;
+};
+void launch_copy_if_parity(const CopyList &cl, const int *ran, int parity, cudaStream_t s);
 void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, const double *theta,
                      const double *rhs, double *out, DiffWork &w, int sweeps, double rho_bound,
                      double lin_rtol, DevStats *st, cudaStream_t s);

@@ -349,6 +349,28 @@ def test_multigrid_levels_agree():
     assert np.all(relerr(a, b) < 1e-11)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multigrid_graph_loop_equals_unrolled_cycles(precision):
+    """Captured steps run the V-cycles as a WHILE graph node that the device check
+    ends; eager steps unroll the cycle cap and skip once done: same cycles, same
+    bits. The captured run also counts the kernels its loop bodies ran."""
+    mech, fl = small_2d(n=32, logA=MILD)
+    ad = O.ADR(mech, fl)
+    phi0 = ad.state_from_YT(fl.Y, fl.T)
+    outs, stats = [], []
+    for graph in (True, False):
+        sv = S().Solver(mech, fl, mg_levels=3, precision=precision, use_graph=graph)
+        st = torch.as_tensor(phi0, device="cuda").contiguous()
+        sv.step(st, 5e-6, 2)
+        torch.cuda.synchronize()
+        outs.append(st.cpu().numpy())
+        stats.append(sv.stats())
+    assert np.array_equal(outs[0], outs[1])
+    assert stats[0]["lin_sweeps"] == stats[1]["lin_sweeps"] > 0
+    assert stats[0]["status_name"] == stats[1]["status_name"] == "OK"
+    assert stats[0]["kernel_launches"] > 0
+
+
 def test_multigrid_mixed_step_meets_accuracy_bar():
     """Full steps with FP32 coarse multigrid levels (and the rest of the mixed
     path) against the FP64 oracle: species to 1e-8, T to 1e-6 relative."""
