@@ -479,6 +479,72 @@ def nu_compare(entries, w, args, dev, rank):
     return 0
 
 
+def pde_bench(args, dev, rank):
+    """The nonlinear test PDE of Sec. 5.2 (n_x = 200 on [0, 20], a = 1, 5 Gauss-Lobatto
+    nodes, dt = 0.05, CISDCQ-3, 10 sweeps) on INSTANCES independent instances in one
+    launch per step (d ~ U[2, 16], r = 2d, random front positions; inputs are
+    read from HBM once per launch, every node array stays in shared memory).
+    Reports cell-updates/s (CUDA events around each launch, L2 flushed between), the
+    kernel's algorithmic FP64 flops against the FP64 peak, and the oracle on one
+    host core on one instance."""
+    import torch
+    import oracle as O
+    from paper_1801_01201_gb300 import solver as SV
+    nx, lx, dt, M, sweeps, nu = 200, 20.0, 0.05, 4, 10, 3
+    n = args.pde
+    rng = np.random.default_rng(args.seed)
+    d = rng.uniform(2.0, 16.0, n)
+    prm = np.stack([np.ones(n), d, 2 * d, np.ones(n), np.zeros(n)], axis=1)
+    x = (np.arange(nx) + 0.5) * lx / nx
+    phi0 = np.stack([0.5 * (1 + np.tanh(rng.uniform(12, 28) - 2 * x)) for _ in range(n)])
+    phi = torch.as_tensor(phi0, device=dev)
+    P = torch.as_tensor(prm, device=dev)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        SV.pde_step(phi, P, dt, scheme="CISDCQ", n_nodes=M + 1, n_sweeps=sweeps, nu=nu, stream=st)
+    ms = []
+    cur = phi
+    for _ in range(max(args.steps, 1)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        cur, incr, status = SV.pde_step(cur, P, dt, scheme="CISDCQ", n_nodes=M + 1, n_sweeps=sweeps,
+                                        nu=nu, stream=st)
+        b.record(st)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    ok = int((status != 0).sum().item()) == 0
+    # first step of instance 0 against the oracle
+    one, _, _ = SV.pde_step(phi[:1].contiguous(), P[:1].contiguous(), dt, scheme="CISDCQ", n_nodes=M + 1,
+                            n_sweeps=sweeps, nu=nu, stream=st)
+    t0 = time.perf_counter()
+    want, _ = O.pde_step("CISDCQ", M, sweeps, nu, dt, phi0[0], Lx=lx, a=1.0, d=d[0], r=2 * d[0])
+    cpu_s = time.perf_counter() - t0
+    err = float(np.max(np.abs(one[0].cpu().numpy() - want)))
+    t = statistics.median(ms) / 1e3
+    rate = n * nx / t
+    # algorithmic FP64 flops per cell and node stage (an FMA counts 2): right-hand
+    # side 8(M+1) + 6(M-1), band substitutions 14, Newton 3 x 14, F_A and F_D 24,
+    # reaction term 3; per cell and step sweeps x nu x M stages + 40 at phi^n
+    per_stage = 8 * (M + 1) + 6 * (M - 1) + 14 + 42 + 24 + 3
+    flops = n * nx * (sweeps * nu * M * per_stage + 40)
+    achieved = flops / t / 1e12
+    line = {"pde": {"workload": "pde1d_200 (Sec. 5.2 nonlinear test PDE), %d instances x %d cells, "
+                                "5 nodes, CISDCQ-%d, %d sweeps, dt %.2g" % (n, nx, nu, sweeps, dt),
+                    "value": rate, "unit": "cell-updates/s", "ms_per_step": t * 1e3, "status_ok": ok,
+                    "max_abs_err_vs_oracle": err,
+                    "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                                 "flops_per_cell_update": flops / (n * nx)},
+                    "cpu_baseline": {"value": nx / cpu_s, "unit": "cell-updates/s", "cores": 1,
+                                     "kind": "oracle", "sample": "one instance, one step"}},
+            "steps": args.steps, "warmup": args.warmup}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -510,6 +576,9 @@ def main():
     ap.add_argument("--nu-compare", default="", metavar="NUMAX,ETA,RHO",
                     help="instead of the headline: FP64 steps with the workload's nu, with fixed "
                          "nu = NUMAX and with adaptive nested iterations (cap NUMAX, rule ETA, RHO)")
+    ap.add_argument("--pde", type=int, default=0, metavar="INSTANCES",
+                    help="instead of the step: the nonlinear test PDE of Sec. 5.2 on INSTANCES "
+                         "independent 200-cell instances, one launch per step")
     ap.add_argument("--rates-compare", action="store_true",
                     help="instead of the step: time the production-rate kernel, sparse FP64 FMA "
                          "against FP64 tensor cores, on the workload's initial state")
@@ -528,6 +597,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1801_01201_gb300.solver import Solver
+    if args.pde > 0:
+        return pde_bench(args, dev, rank)
 
     name = args.workload
     entries, w = entries_for(name)

@@ -217,6 +217,32 @@ misdc_status misdc_diffusion_solve(misdc_solver *s, double wdt, const double *co
 misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double *const *in,
                            const double *w, size_t n, void *stream);
 
+/* ---- nonlinear scalar test PDE (Sec. 5.2, eq. nonlinear_test_pde) ---------
+ * phi_t = a phi_x + d phi_xx + r phi (phi - 1)(phi - 1/2) on [0, length] with
+ * phi(0) = left, phi(length) = right, in nx uniform cells: fourth-order advective
+ * face values (7 (phi_i + phi_{i+1}) - (phi_{i-1} + phi_{i+2}))/12, the
+ * fourth-order five-point Laplacian, and Dirichlet ghost cells from the cubic
+ * through the wall value and the first three cell averages (the paper does not
+ * state its closure). Advances n independent instances n_steps time steps of dt
+ * with the scheme (misdc_scheme), n_nodes Gauss-Lobatto nodes, n_sweeps sweeps
+ * and nu nested iterations (CISDCQ), each step starting from phi^n at all
+ * nodes (Sec. 3.3, I1-I2). Diffusion steps solve (I - w L) x = rhs + w g
+ * directly (banded LU with partial pivoting); reaction steps run scalar Newton
+ * to |dy| <= 1e-15 (1 + |y|), at most 100 iterations.
+ * Device arrays, stream-ordered: params [n][5] = (a, d, r, left, right);
+ * phi_in, phi_out [n][nx] (may alias); incr [n][n_steps][n_sweeps] (may be NULL)
+ * receives the sweep increments (1/nx) sum_i |phi^{M,(k+1)}_i - phi^{M,(k)}_i|;
+ * status [n] (may be NULL): 0, or bits 1 (Newton limit), 2 (non-finite),
+ * 4 (singular diffusion matrix). One block per instance holds all node arrays
+ * in shared memory: misdc_pde_smem_bytes gives the need, and a launch whose need
+ * exceeds the device's per-block limit returns MISDC_E_INVALID (at 5 nodes about
+ * 340 cells, at 3 nodes about 610). nx >= 8. */
+misdc_status misdc_pde_step(int scheme, int n_nodes, int n_sweeps, int nu, double dt, int n_steps,
+                            int nx, double length, int n, const double *params,
+                            const double *phi_in, double *phi_out, double *incr, int *status,
+                            void *stream);
+misdc_status misdc_pde_smem_bytes(int n_nodes, int nx, size_t *bytes);
+
 /* Reaction solve that allocates nothing. The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory during the call (host
  * callbacks, memory-pool-restricted or real-time processes, plugins whose host

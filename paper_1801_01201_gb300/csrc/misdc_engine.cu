@@ -1218,6 +1218,47 @@ misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double
   return MISDC_OK;
 }
 
+misdc_status misdc_pde_smem_bytes(int n_nodes, int nx, size_t *bytes) {
+  if (!bytes || n_nodes < 2 || n_nodes > kMaxNodes || nx < 1)
+    return fail(MISDC_E_INVALID, "pde_smem_bytes: bad argument");
+  *bytes = pde_smem_bytes(n_nodes - 1, nx);
+  return MISDC_OK;
+}
+
+misdc_status misdc_pde_step(int scheme, int n_nodes, int n_sweeps, int nu, double dt, int n_steps,
+                            int nx, double length, int n, const double *params,
+                            const double *phi_in, double *phi_out, double *incr, int *status,
+                            void *stream) {
+  if (scheme < MISDC_SCHEME_MISDC || scheme > MISDC_SCHEME_CISDCQ)
+    return fail(MISDC_E_INVALID, "pde_step: unknown scheme");
+  if (n_sweeps < 1 || nu < 1 || n_steps < 1 || !(dt > 0.0) || !(length > 0.0) || n < 0)
+    return fail(MISDC_E_INVALID, "pde_step: n_sweeps, nu, n_steps, dt, length must be positive");
+  if (nx < 8) return fail(MISDC_E_INVALID, "pde_step: nx must be at least 8");
+  if (n == 0) return MISDC_OK;
+  if (!params || !phi_in || !phi_out) return fail(MISDC_E_INVALID, "pde_step: null array");
+  Tables T;
+  if (!make_tables(n_nodes, T)) return fail(MISDC_E_INVALID, "pde_step: n_nodes must be in 2..9");
+  int dev = 0, smem_max = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (pde_smem_bytes(T.M, nx) > (size_t)smem_max)
+    return fail(MISDC_E_INVALID, "pde_step: nx too large for one block's shared memory (" +
+                                     std::to_string(pde_smem_bytes(T.M, nx)) + " > " +
+                                     std::to_string(smem_max) + " bytes)");
+  PdeLaunch p;
+  memset(&p, 0, sizeof(p));
+  p.scheme = scheme; p.M = T.M; p.n_sweeps = n_sweeps; p.nu = nu; p.n_steps = n_steps;
+  p.nx = nx; p.n = n; p.dt = dt; p.dx = length / nx;
+  memcpy(p.tau, T.tau, sizeof(p.tau));
+  memcpy(p.Q, T.Q, sizeof(p.Q));
+  memcpy(p.S, T.S, sizeof(p.S));
+  memcpy(p.QI, T.QI, sizeof(p.QI));
+  memcpy(p.QE, T.QE, sizeof(p.QE));
+  p.params = params; p.phi_in = phi_in; p.phi_out = phi_out; p.incr = incr; p.status = status;
+  CK(launch_pde_step(p, (cudaStream_t)stream));
+  return MISDC_OK;
+}
+
 }  // extern "C"
 
 // ===========================================================================

@@ -231,6 +231,22 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
                      double lin_rtol, DevStats *st, cudaStream_t s);
 int chebyshev_sweeps(double rho_bound, double reduction);
 
+// ---- nonlinear scalar test PDE of Sec. 5.2 (misdc_pde.cu) ----
+// One CTA per instance; every node array in shared memory (pde_smem_bytes).
+struct PdeLaunch {
+  int scheme, M, n_sweeps, nu, n_steps, nx, n;
+  double dt, dx;
+  double tau[kMaxNodes + 1], Q[kMaxNodes][kMaxNodes + 1], S[kMaxNodes][kMaxNodes + 1];
+  double QI[kMaxNodes][kMaxNodes], QE[kMaxNodes][kMaxNodes];
+  const double *params;   // [n][5]: a, d, r, left, right
+  const double *phi_in;   // [n][nx]
+  double *phi_out;        // [n][nx]
+  double *incr;           // [n][n_steps][n_sweeps] or null
+  int *status;            // [n] or null
+};
+size_t pde_smem_bytes(int M, int nx);
+cudaError_t launch_pde_step(const PdeLaunch &p, cudaStream_t s);
+
 // ---- learned Newton guess: MLP kernels (misdc_mlp.cu) ----
 namespace mlp {
 // BF16 operand: element (r, k) at p[r * sm + k * sk]; rows >= rows read as zero

@@ -52,6 +52,46 @@ def lobatto(n_nodes):
     return tau, Q, QI, QE
 
 
+PDE_STATUS_BITS = {1: "newton_limit", 2: "non_finite", 4: "singular_diffusion"}
+
+
+def pde_step(phi, params, dt, *, length=20.0, scheme="CISDCQ", n_nodes=5, n_sweeps=4, nu=1,
+             n_steps=1, stream=None):
+    """Advance n instances of the nonlinear test PDE of Sec. 5.2 (misdc_pde_step).
+
+    phi: [n, nx] or [nx] FP64 device tensor of cell averages; params: [n, 5] or [5]
+    (a, d, r, left, right). Returns (phi_out [n, nx], incr [n, n_steps, n_sweeps],
+    status [n]) as device tensors (status bits: PDE_STATUS_BITS)."""
+    lib = L.load()
+    one = phi.dim() == 1
+    phi = phi.reshape(1, -1) if one else phi
+    n, nx = phi.shape
+    dev = phi.device
+    phi = _dev(phi, dev)
+    params = _dev(params, dev).reshape(-1, 5)
+    if params.shape[0] == 1 and n > 1:
+        params = params.expand(n, 5).contiguous()
+    if params.shape[0] != n:
+        raise ValueError("params must have one row per instance")
+    out = torch.empty_like(phi)
+    incr = torch.empty((n, n_steps, n_sweeps), dtype=torch.float64, device=dev)
+    status = torch.zeros(n, dtype=torch.int32, device=dev)
+    L.check(lib.misdc_pde_step(L.SCHEMES.get(scheme, scheme), n_nodes, n_sweeps, nu, dt, n_steps,
+                               nx, length, n, _ptr(params), _ptr(phi), _ptr(out), _ptr(incr),
+                               _ptr(status), _stream(stream)))
+    if one:
+        return out[0], incr[0], status[0]
+    return out, incr, status
+
+
+def pde_smem_bytes(n_nodes, nx):
+    """Shared memory one instance of pde_step needs (bytes)."""
+    lib = L.load()
+    b = C.c_size_t(0)
+    L.check(lib.misdc_pde_smem_bytes(n_nodes, nx, C.byref(b)))
+    return b.value
+
+
 def lincomb(outs, ins, w, n, stream=None):
     """out[o] = sum_k w[o][k] in[k] over n elements (device tensors)."""
     lib = L.load()

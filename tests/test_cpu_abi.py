@@ -50,3 +50,19 @@ def test_invalid_arguments_are_rejected_before_device_work():
     o = L.Opts()
     lib.misdc_default_opts(C.byref(o))
     assert (o.n_nodes, o.n_sweeps, o.nu, o.scheme) == (3, 4, 2, L.SCHEMES["CISDCQ"])
+
+
+def test_pde_entry_point_checks_arguments_on_the_host():
+    """misdc_pde_step rejects bad arguments before any device work; n = 0 is a no-op."""
+    lib = L.load()
+    vp = C.c_void_p(1)
+    assert lib.misdc_pde_step(7, 5, 4, 1, 0.05, 1, 200, 20.0, 1, vp, vp, vp, None, None, None) == L.E_INVALID
+    assert lib.misdc_pde_step(2, 5, 4, 1, 0.05, 1, 4, 20.0, 1, vp, vp, vp, None, None, None) == L.E_INVALID
+    assert b"nx" in lib.misdc_last_error()
+    assert lib.misdc_pde_step(2, 5, 0, 1, 0.05, 1, 200, 20.0, 1, vp, vp, vp, None, None, None) == L.E_INVALID
+    assert lib.misdc_pde_step(2, 5, 4, 1, -0.05, 1, 200, 20.0, 1, vp, vp, vp, None, None, None) == L.E_INVALID
+    assert lib.misdc_pde_step(2, 5, 4, 1, 0.05, 1, 200, 20.0, 0, None, None, None, None, None, None) == L.OK
+    # shared memory of one instance: (4 + 12 M + 5 + 7 M) nx + 33 doubles and M nx pivot bytes
+    for n_nodes, nx in ((5, 200), (3, 53)):
+        M = n_nodes - 1
+        assert S.pde_smem_bytes(n_nodes, nx) == 8 * ((9 + 19 * M) * nx + 33) + M * nx
