@@ -217,6 +217,13 @@ misdc_status misdc_diffusion_solve(misdc_solver *s, double wdt, const double *co
 misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double *const *in,
                            const double *w, size_t n, void *stream);
 
+/* The FP64 exponential of the rate kernels (production rates and the reaction
+ * Newton: k_f = exp(ln A + beta ln T - Ea/(R T)) and k_r, Sec. 2), for testing:
+ * y[i] = e^{x[i]} over n device elements, stream-ordered. Tang's table-driven
+ * method (ACM TOMS 15(2), 1989) with a 32-entry table of 2^(j/32); about 1 ulp;
+ * arguments outside (-700, 700) fall back to the CUDA exp. */
+misdc_status misdc_exp(const double *x, double *y, size_t n, void *stream);
+
 /* ---- nonlinear scalar test PDE (Sec. 5.2, eq. nonlinear_test_pde) ---------
  * phi_t = a phi_x + d phi_xx + r phi (phi - 1)(phi - 1/2) on [0, length] with
  * phi(0) = left, phi(length) = right, in nx uniform cells: fourth-order advective

@@ -13,6 +13,42 @@ namespace misdc {
 
 namespace {
 
+// 2^(j/32), j = 0..31, rounded to double; written once per device by
+// init_exp_table() from an extended-precision evaluation on the host.
+__device__ double g_exp2_32[32];
+
+// e^x by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989):
+// x = (32 m + j) ln2/32 + r with |r| <= ln2/64, so e^x = 2^m 2^(j/32) e^r. The
+// reduction rounds x 32/ln2 to an integer by adding 1.5 2^52 (whose low word is
+// then the integer), subtracts it times ln2/32 split into a leading and a trailing
+// double (the leading product is exact here); e^r - 1 is the Taylor polynomial of
+// degree 6 (truncation below 4e-18 relative for |r| <= ln2/64); 2^m goes into the
+// exponent field. Error about 1 ulp, in about twelve FP64 instructions, where the
+// general-purpose exp() costs roughly twice that on the FP64 pipe. Arguments
+// outside (-700, 700), and NaN, take exp().
+__device__ __forceinline__ double exp_tab(double x) {
+  if (!(fabs(x) < 700.0)) return exp(x);
+  const double shift = 6755399441055744.0;                 // 1.5 * 2^52
+  const double t = fma(x, 46.16624130844683, shift);       // x * 32 / ln2, rounded
+  const int k = __double2loint(t);
+  const double kd = t - shift;
+  double r = fma(-kd, 0.02166084939249829, x);             // ln2/32, leading part
+  r = fma(-kd, 7.247021293269686e-19, r);                  // ln2/32, trailing part
+  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+  q = fma(q, r, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double p = fma(q, r * r, r);                        // e^r - 1
+  const double tj = g_exp2_32[k & 31];
+  const double v = fma(tj, p, tj);
+  return __longlong_as_double(__double_as_longlong(v) + ((long long)(k >> 5) << 52));
+}
+
+__global__ void k_exp(const double *__restrict__ x, double *__restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = exp_tab(x[i]);
+}
+
 __device__ __forceinline__ void species_thermo(const DevMech &m, int i, double T, double lnT,
                                                double invT, double &hRT, double &gRT,
                                                double &cpR) {
@@ -161,8 +197,8 @@ __device__ void eval_chem(const DevMech &m, const WarpChem &w, int lane, double 
     const double beta = m.beta[r], TA = m.TA[r], dn = m.dn[r];
     const double lnkf = m.lnA[r] + beta * lnT - TA * invT;
     const double lnKc = -dg + dn * (m.ln_p_over_R - lnT);
-    const double kf = exp(lnkf);
-    const double kr = exp(lnkf - lnKc);
+    const double kf = exp_tab(lnkf);
+    const double kr = exp_tab(lnkf - lnKc);
     w.q[r] = kf * Ff - kr * Fr;
     if (jac) {
       const double dlnkf = (beta + TA * invT) * invT;
@@ -327,30 +363,67 @@ __device__ __forceinline__ NW carve2(double *p, int N, int R, int ld, bool mixed
 }
 
 
-// out = U^{-1} L^{-1} P (D r): FP64 substitutions with a factor kept in J (L below
-// the diagonal, U above, piv = 1/U_kk, row scales res, pivot rows sw); warp-wide
-__device__ __forceinline__ void solve_kept(const NW &w, const double *J, int ld, int nn, int lane,
-                                           const double *r, double *out) {
-  for (int i = lane; i < nn; i += 32) out[i] = r[i] * w.res[i];
-  __syncwarp();
-  if (lane == 0)
-    for (int k = 0; k < nn; ++k) {
-      const int t = w.sw[k];
-      if (t != k) { const double v = out[k]; out[k] = out[t]; out[t] = v; }
+// Kept factors are stored as explicit inverses, so that a chord step is one
+// matrix-vector product (nn FMA warp instructions) instead of a forward and a
+// back substitution (about 3 nn, each on a shrinking set of lanes).
+//
+// invert_kept: Z = U^{-1} L^{-1} P D in place of the factor in J (L unit lower
+// below the diagonal, U on and above it, piv = 1/U_kk, row exchanges sw taken in
+// order k = 0..nn-1, row scales res), the inverse of the unscaled Jacobian. Steps:
+// U^{-1} column by column; then, from the last column to the first, the columns of
+// U^{-1} L^{-1} from those to their right; then the column exchanges in reverse
+// order and the column scaling by D.
+__device__ void invert_kept(const NW &w, double *J, int ld, int nn, int lane) {
+  for (int j = 0; j < nn; ++j) {   // U^{-1}: X[0:j, j] = -X[j][j] X[0:j, 0:j] U[0:j, j]
+    const double xjj = w.piv[j];
+    double t0 = 0.0, t1 = 0.0;
+    if (lane < j)
+      for (int k = lane; k < j; ++k) t0 = fma(J[(size_t)lane * ld + k], J[(size_t)k * ld + j], t0);
+    if (lane + 32 < j)
+      for (int k = lane + 32; k < j; ++k) t1 = fma(J[(size_t)(lane + 32) * ld + k], J[(size_t)k * ld + j], t1);
+    __syncwarp();
+    if (lane < j) J[(size_t)lane * ld + j] = -xjj * t0;
+    if (lane + 32 < j) J[(size_t)(lane + 32) * ld + j] = -xjj * t1;
+    if (lane == 0) J[(size_t)j * ld + j] = xjj;
+    __syncwarp();
+  }
+  for (int j = nn - 2; j >= 0; --j) {   // X[:, j] -= X[:, j+1:] L[j+1:, j]
+    for (int i = j + 1 + lane; i < nn; i += 32) {
+      w.zd[i] = J[(size_t)i * ld + j];
+      J[(size_t)i * ld + j] = 0.0;
     }
+    __syncwarp();
+    for (int i = lane; i < nn; i += 32) {
+      double s = J[(size_t)i * ld + j];
+      for (int k = j + 1; k < nn; ++k) s = fma(-J[(size_t)i * ld + k], w.zd[k], s);
+      J[(size_t)i * ld + j] = s;
+    }
+    __syncwarp();
+  }
+  for (int j = nn - 2; j >= 0; --j) {   // column exchanges, last first
+    const int jp = w.sw[j];
+    if (jp != j)
+      for (int i = lane; i < nn; i += 32) {
+        const double t = J[(size_t)i * ld + j];
+        J[(size_t)i * ld + j] = J[(size_t)i * ld + jp];
+        J[(size_t)i * ld + jp] = t;
+      }
+  }
   __syncwarp();
-  for (int k = 0; k < nn; ++k) {
-    const double zk = out[k];
-    for (int i = k + 1 + lane; i < nn; i += 32) out[i] = fma(-J[(size_t)i * ld + k], zk, out[i]);
-    __syncwarp();
+  for (int i = lane; i < nn; i += 32)   // right-multiply by D
+    for (int j = 0; j < nn; ++j) J[(size_t)i * ld + j] *= w.res[j];
+  __syncwarp();
+}
+
+// out = Z r with the inverse kept in J; warp-wide
+__device__ __forceinline__ void apply_kept(const double *J, int ld, int nn, int lane,
+                                           const double *r, double *out) {
+  for (int i = lane; i < nn; i += 32) {
+    double s = 0.0;
+    for (int j = 0; j < nn; ++j) s = fma(J[(size_t)i * ld + j], r[j], s);
+    out[i] = s;
   }
-  for (int k = nn - 1; k >= 0; --k) {
-    const double zk = out[k] * w.piv[k];
-    __syncwarp();
-    if (lane == 0) out[k] = zk;
-    for (int i = lane; i < k; i += 32) out[i] = fma(-J[(size_t)i * ld + k], zk, out[i]);
-    __syncwarp();
-  }
+  __syncwarp();
 }
 
 template <bool MIXED>
@@ -432,14 +505,12 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       // Jacobian would shrink the chord step and fake convergence
       const double *src = cst.f + (size_t)cell * cst.fs;
       const double *xf = src + nn * nn + 2 * nn + 2;
-      double dist = 0.0;
+      bool near = true;   // compared without dividing by T
       for (int i = lane; i < nn; i += 32) {
         const double xi = w.xs[i];
-        dist = fmax(dist, (i < N) ? fabs(xi - xf[i]) : fabs(xi - xf[i]) / xi);
+        near = near && fabs(xi - xf[i]) <= ((i < N) ? 1e-4 : 1e-4 * xi);
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) dist = fmax(dist, __shfl_xor_sync(0xffffffffu, dist, o));
-      if (dist <= 1e-4) {
+      if (__all_sync(0xffffffffu, near)) {
         for (int e = lane; e < nn * nn; e += 32) {
           const int i = e / nn, j = e - i * nn;
           J[(size_t)i * ld + j] = src[e];
@@ -470,12 +541,11 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         w.r64[i] = (i < N) ? w.bs[i] - w.xs[i] + wdt * FRp[(size_t)i * cs + cell]
                            : (hst - hp[cell]) * sTf;
       __syncwarp();
-      solve_kept(w, J, ld, nn, lane, w.r64, w.zd);
-      double d0 = 0.0;
-      for (int i = lane; i < nn; i += 32) d0 = fmax(d0, fabs(w.zd[i]) * ((i < N) ? 1.0 : 1.0 / w.xs[N]));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) d0 = fmax(d0, __shfl_xor_sync(0xffffffffu, d0, o));
-      if (d0 <= 0.1 * rtol) {
+      apply_kept(J, ld, nn, lane, w.r64, w.zd);
+      bool tiny = true;   // max(max|dY|, |dT|/T) <= rtol / 10, without dividing by T
+      for (int i = lane; i < nn; i += 32)
+        tiny = tiny && fabs(w.zd[i]) <= ((i < N) ? 0.1 * rtol : 0.1 * rtol * w.xs[N]);
+      if (__all_sync(0xffffffffu, tiny)) {
         double invw = 0.0;
         if (lane == 0 && wdt > 0.0) invw = 1.0 / wdt;
         invw = __shfl_sync(0xffffffffu, invw, 0);
@@ -549,14 +619,18 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           const int sf = fs[p], sr = rs[p];
           cf[p] = 1.0;
           cr[p] = 1.0;
-          if (sf >= 0) { dg -= w.g[sf]; dh -= w.hRT[sf]; cf[p] = w.c[sf]; }
-          if (sr >= 0) { dg += w.g[sr]; dh += w.hRT[sr]; cr[p] = w.c[sr]; }
+          if (sf >= 0) { dg -= w.g[sf]; cf[p] = w.c[sf]; }
+          if (sr >= 0) { dg += w.g[sr]; cr[p] = w.c[sr]; }
+          if (jac) {   // the reaction enthalpy only enters the Jacobian (dq/dT)
+            if (sf >= 0) dh -= w.hRT[sf];
+            if (sr >= 0) dh += w.hRT[sr];
+          }
         }
         const double beta = m.beta[r], TA = m.TA[r], dn = m.dn[r];
         const double lnkf = m.lnA[r] + beta * lnT - TA * invT;
         const double lnKc = -dg + dn * (m.ln_p_over_R - lnT);
-        const double kf = exp(lnkf);
-        const double kr = exp(lnkf - lnKc);
+        const double kf = exp_tab(lnkf);
+        const double kr = exp_tab(lnkf - lnKc);
         const double Ff = cf[0] * cf[1] * cf[2], Fr = cr[0] * cr[1] * cr[2];
         w.src[r] = kf * Ff - kr * Fr;
         if (jac) {
@@ -755,6 +829,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
             }
             for (int k = lane; k < nn; k += 32) w.piv[k] = (double)w.pivf[k];
             __syncwarp();
+            invert_kept(w, J, ld, nn, lane);
             have = fresh = true;
             fresh_exact = false;
             from_store = false;
@@ -762,7 +837,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
             sTf = sT;
           }
         }
-        if (!fallback) solve_kept(w, J, ld, nn, lane, w.r64, w.dx);
+        if (!fallback) apply_kept(J, ld, nn, lane, w.r64, w.dx);
       }
       if (!MIXED || fallback) {
         ++my_lu64;
@@ -820,9 +895,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
             J[(size_t)i * ld + nn] = fma(-J[(size_t)i * ld + k], xk, J[(size_t)i * ld + nn]);
           __syncwarp();
         }
-        if (MIXED) {   // an unscaled FP64 factor of the current Jacobian
+        if (MIXED) {   // an unscaled FP64 factor of the current Jacobian, kept as its inverse
           for (int i = lane; i < nn; i += 32) w.res[i] = 1.0;
           __syncwarp();
+          invert_kept(w, J, ld, nn, lane);
           have = fresh = fresh_exact = true;
           from_store = false;
           fac32 = false;
@@ -856,7 +932,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           w.r64[i] = (i < N) ? w.bs[i] - w.xg[i] + wdt * FRp[(size_t)i * cs + cell]
                              : (hst - hp[cell]) * sTf;
         __syncwarp();
-        solve_kept(w, J, ld, nn, lane, w.r64, w.zd);
+        apply_kept(J, ld, nn, lane, w.r64, w.zd);
         double d0 = 0.0, dp = 0.0;
         for (int i = lane; i < nn; i += 32) {
           const double s0i = (i < N) ? 1.0 : 1.0 / w.xs[N];
@@ -911,8 +987,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       __syncwarp();
       T = w.xs[N];
       if (!fin || !(T > 0.0)) { code = -3; break; }
+      // the temperature step relative to T before the step (1/T is at hand; the two
+      // differ by the factor 1 + dT/T, which is 1 to the stopping tolerance)
       double d = 0.0;
-      if (lane == 0) d = fmax(dmax, fabs(w.dx[N]) / T);
+      if (lane == 0) d = fmax(dmax, fabs(w.dx[N]) * invT);
       d = __shfl_sync(0xffffffffu, d, 0);
       if (!isfinite(d)) { code = -3; break; }
       if (!MIXED || exact || (fresh && fresh_exact)) {
@@ -937,9 +1015,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
             d = INFINITY;
           }
         } else {
-          const double th = d / dprev;
-          if (th < 0.1) {
-            if (d * th / (1.0 - th) <= rtol) break;
+          // th = d / dprev < 0.1, and d th / (1 - th) = d^2 / (dprev - d) <= rtol,
+          // both tested without dividing
+          if (d < 0.1 * dprev) {
+            if (d * d <= rtol * (dprev - d)) break;
           } else {
             have = false;
           }
@@ -965,9 +1044,14 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     double invw = 0.0;
     if (lane == 0 && wdt > 0.0) invw = 1.0 / wdt;
     invw = __shfl_sync(0xffffffffu, invw, 0);
+    double th_f = 0.0;   // theta = (T/T_ref)^theta_exp = exp(theta_exp (ln T - ln T_ref))
     {
       double lnT = 0.0, invT = 0.0;
-      if (lane == 0) { lnT = log(Tf); invT = 1.0 / Tf; }
+      if (lane == 0) {
+        lnT = log(Tf);
+        invT = 1.0 / Tf;
+        th_f = exp_tab(m.theta_exp * (lnT - m.ln_Tref));
+      }
       lnT = __shfl_sync(0xffffffffu, lnT, 0);
       invT = __shfl_sync(0xffffffffu, invT, 0);
       for (int i = lane; i < N; i += 32) {
@@ -983,7 +1067,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       cst.valid[cell] = ((have && code == 0 && !exact) ? 1 : 0) | (no32 ? 2 : 0);
     if (lane == 0) {
       Tout[cell] = T;
-      if (theta) theta[cell] = pow(Tf / m.T_ref, m.theta_exp);
+      if (theta) theta[cell] = th_f;
       if (iters) iters[cell] = code ? code : it;
     }
     __syncwarp();
@@ -1117,6 +1201,29 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
     k_newton2<false><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
                                                 FR, hsp, theta, iters, st, pred, ldp, sc,
                                                 s_min, FRp, hp, work, cst, prow, hspp, thp);
+}
+
+
+cudaError_t init_exp_table() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  double tab[32];
+  for (int j = 0; j < 32; ++j) tab[j] = (double)exp2l((long double)j / 32.0L);
+  e = cudaMemcpyToSymbol(g_exp2_32, tab, sizeof(tab));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
+cudaError_t launch_exp(const double *x, double *y, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const size_t blocks = (n + 255) / 256;
+  k_exp<<<(unsigned)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(x, y, n);
+  return cudaGetLastError();
 }
 
 }  // namespace misdc

@@ -693,6 +693,7 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   if (!face_vel) return fail(MISDC_E_INVALID, "null face velocity");
   for (int i = 0; i < N; ++i)
     if (!(md->W[i] > 0.0) || !(md->D0[i] >= 0.0)) return fail(MISDC_E_INVALID, "bad W or D0");
+  CK(init_exp_table());   // the rate kernels' exponential, once per device
 
   misdc_solver *s = new misdc_solver();
   auto bail = [&](misdc_status st) { misdc_destroy(s); return st; };
@@ -814,7 +815,7 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     return bail(fail(MISDC_E_OOM, "mechanism upload failed"));
   DevMech &m = s->m;
   m.N = N; m.R = R; m.rho = op->rho; m.T_ref = md->T_ref; m.theta_exp = md->theta_exp;
-  m.alpha0 = md->alpha0; m.ln_p_over_R = log(md->p_ref / kRu);
+  m.alpha0 = md->alpha0; m.ln_p_over_R = log(md->p_ref / kRu); m.ln_Tref = log(md->T_ref);
   m.invW = p_invW; m.hcoef = p_hc; m.scoef = p_sc; m.cpcoef = p_cpc; m.D0 = p_D0;
   m.lnA = p_lnA; m.beta = p_beta; m.TA = p_TA; m.dn = p_dn; m.fwd = p_fwd; m.rev = p_rev;
   m.sp_ptr = p_spp; m.sp_rx = p_spr; m.sp_coef = p_spc;
@@ -1215,6 +1216,14 @@ misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double
   }
   launch_lincomb(lc, n, (cudaStream_t)stream);
   CK(cudaGetLastError());
+  return MISDC_OK;
+}
+
+misdc_status misdc_exp(const double *x, double *y, size_t n, void *stream) {
+  if (n == 0) return MISDC_OK;
+  if (!x || !y) return fail(MISDC_E_INVALID, "exp: null array");
+  CK(init_exp_table());
+  CK(launch_exp(x, y, n, (cudaStream_t)stream));
   return MISDC_OK;
 }
 

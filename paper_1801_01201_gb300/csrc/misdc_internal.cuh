@@ -45,7 +45,7 @@ struct DevStats {
 // Mechanism tables in device memory (built by the engine from misdc_mech_desc).
 struct DevMech {
   int N, R;
-  double rho, T_ref, theta_exp, alpha0, ln_p_over_R;
+  double rho, T_ref, theta_exp, alpha0, ln_p_over_R, ln_Tref;
   const double *invW;      // [N] 1/W
   const double *hcoef;     // [N][6]  a1, a2/2, a3/3, a4/4, a5/5, a6      (h/RT = poly + a6/T)
   const double *scoef;     // [N][6]  a1, a2, a3/2, a4/3, a5/4, a7        (s/R = a1 lnT + poly + a7)
@@ -129,6 +129,10 @@ __host__ __device__ inline int chord_floats(int N) {
   const int nn = N + 1;
   return (nn * nn + 3 * nn + 2 + 1) / 2 * 2;
 }
+// table of the FP64 exponential the rate kernels use (once per device, before any
+// chemistry kernel runs), and that exponential over n elements
+cudaError_t init_exp_table();
+cudaError_t launch_exp(const double *x, double *y, size_t n, cudaStream_t s);
 void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit,
                    const double *b, const double *hstar, const double *Yg, const double *Tg,
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,

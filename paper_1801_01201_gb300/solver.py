@@ -52,6 +52,15 @@ def lobatto(n_nodes):
     return tau, Q, QI, QE
 
 
+def exp(x, stream=None):
+    """e^x with the FP64 exponential the rate kernels use (misdc_exp); x a device tensor."""
+    lib = L.load()
+    x = x.to(torch.float64).contiguous()
+    y = torch.empty_like(x)
+    L.check(lib.misdc_exp(_ptr(x), _ptr(y), x.numel(), _stream(stream)))
+    return y
+
+
 PDE_STATUS_BITS = {1: "newton_limit", 2: "non_finite", 4: "singular_diffusion"}
 
 
