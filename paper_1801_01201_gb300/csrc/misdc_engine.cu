@@ -844,6 +844,7 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
       s->alloc(&s->thfR, 3 * cs) || s->alloc(&s->iters, cs) || s->alloc(&s->st, 1) ||
       s->alloc(&s->nl.work, 1) ||
       s->alloc(&s->dw.thf, 3 * cs) || s->alloc(&s->dw.invdiag, F * cs) || s->alloc(&s->dw.xa, F * cs) ||
+      s->alloc(&s->dw.cdiag, F * cs) || s->alloc(&s->dw.bdiag, F * cs) ||
       s->alloc(&s->dw.xb, F * cs) || s->alloc(&s->dw.xc, F * cs) ||
       s->alloc(&s->dw.rho_bits, 1) || s->alloc(&s->dw.kdev, 1) || s->alloc(&s->dw.omega, kMaxCheb))
     return bail(fail(MISDC_E_OOM, "work buffers"));

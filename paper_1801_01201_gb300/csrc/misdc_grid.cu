@@ -68,6 +68,7 @@ __global__ void k_lincomb(LinComb lc, size_t n) {
 // F_E (advection of every field + explicit differential diffusion of h) and
 // F_D (implicit diffusion, dominant species closed by minus the sum).
 // ---------------------------------------------------------------------------
+template <int DIM>
 __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restrict__ phi,
                             const double *__restrict__ hsp, const double *__restrict__ thf,
                             const double *__restrict__ vel, double *__restrict__ FE,
@@ -75,48 +76,55 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int cs = g.cells;
   if (c >= cs) return;
-  const int N = m.N, dim = g.dim;
+  const int N = m.N;
   const Nbr nb = neighbours(g, c);
   const double invdx = 1.0 / g.dx, invdx2 = invdx * invdx;
   // fourth-order face values are (7(a+b) - (c+d))/12; the 1/12 is applied once
   // per field with 1/dx (an FP64 division per face would dominate the kernel)
   const double adv = invdx / 12.0;
-  double ulo[3], uhi[3], tlo[3], thi[3];
-  double qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0}, glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
-  for (int d = 0; d < dim; ++d) {
+  double ulo[DIM], uhi[DIM], tlo[DIM], thi[DIM];
+  // differential diffusion of h (eq. enthalpy_equation), per low / high face:
+  //   q = sum_i hbar_i (lambda/cp - rho D_i) grad Y_i  and  G = sum_{i != i0} rho D_i grad Y_i,
+  // accumulated as sq = sum_i (h_a + h_b)(Y_b - Y_a)(alpha0 - D_i) and
+  // sg = sum_{i != i0} D_i (Y_b - Y_a); the face's theta, 1/2 and 1/dx are applied once
+  double sqlo[DIM], sqhi[DIM], sglo[DIM], sghi[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
     ulo[d] = vel[(size_t)d * cs + c];
     uhi[d] = vel[(size_t)d * cs + nb.cp[d]];
     tlo[d] = thf[(size_t)d * cs + c];
     thi[d] = thf[(size_t)d * cs + nb.cp[d]];
+    sqlo[d] = sqhi[d] = sglo[d] = sghi[d] = 0.0;
   }
   double fd_i0 = 0.0, fa_h = 0.0;
   for (int f = 0; f <= N; ++f) {
     const double *x = phi + (size_t)f * cs;
     const double xc = x[c];
+    const bool sp = f < N;
+    const double *hs = hsp + (size_t)f * cs;
+    const double hc = sp ? hs[c] : 0.0;
+    const double wf = sp ? (f != i0 ? m.alpha0 - m.D0[f] : m.alpha0) : 0.0;
+    const double Df = (sp && f != i0) ? m.D0[f] : 0.0;
     double fa = 0.0, fdl = 0.0;
-    for (int d = 0; d < dim; ++d) {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
       const double xm2 = x[nb.cm2[d]], xm = x[nb.cm[d]], xp = x[nb.cp[d]], xp2 = x[nb.cp2[d]];
-      const double lo = 7.0 * (xm + xc) - (xm2 + xp);    // 12 x face value
-      const double hi = 7.0 * (xc + xp) - (xm + xp2);
-      fa += uhi[d] * hi - ulo[d] * lo;
-      fdl += thi[d] * (xp - xc) - tlo[d] * (xc - xm);
-      if (f < N) {
-        const double *hs = hsp + (size_t)f * cs;
-        const double hbl = 0.5 * (hs[nb.cm[d]] + hs[c]);
-        const double hbh = 0.5 * (hs[c] + hs[nb.cp[d]]);
-        const double dyl = (xc - xm) * invdx, dyh = (xp - xc) * invdx;
-        qlo[d] += hbl * m.alpha0 * tlo[d] * dyl;
-        qhi[d] += hbh * m.alpha0 * thi[d] * dyh;
-        if (f != i0) {
-          const double Gl = m.D0[f] * tlo[d] * dyl, Gh = m.D0[f] * thi[d] * dyh;
-          qlo[d] -= hbl * Gl;
-          qhi[d] -= hbh * Gh;
-          glo[d] += Gl;
-          ghi[d] += Gh;
-        }
+      const double lo = fma(7.0, xm + xc, -(xm2 + xp));   // 12 x face value
+      const double hi = fma(7.0, xc + xp, -(xm + xp2));
+      fa = fma(uhi[d], hi, fa);
+      fa = fma(-ulo[d], lo, fa);
+      const double dl = xc - xm, dh = xp - xc;
+      fdl = fma(thi[d], dh, fdl);
+      fdl = fma(-tlo[d], dl, fdl);
+      if (sp) {
+        const double hl = hs[nb.cm[d]] + hc, hh = hc + hs[nb.cp[d]];
+        sqlo[d] = fma(hl * dl, wf, sqlo[d]);
+        sqhi[d] = fma(hh * dh, wf, sqhi[d]);
+        sglo[d] = fma(Df, dl, sglo[d]);
+        sghi[d] = fma(Df, dh, sghi[d]);
       }
     }
-    if (f < N) {
+    if (sp) {
       if (FE) FE[(size_t)f * cs + c] = -fa * adv;
       if (f != i0) {
         const double v = m.D0[f] * fdl * invdx2;
@@ -130,14 +138,17 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
   }
   if (FD) FD[(size_t)i0 * cs + c] = fd_i0;
   if (FE) {
+    // the dominant species' flux is minus the others' (its h weighs -G)
     const double *hs0 = hsp + (size_t)i0 * cs;
+    const double h0 = hs0[c];
     double div = 0.0;
-    for (int d = 0; d < dim; ++d) {
-      const double hbl = 0.5 * (hs0[nb.cm[d]] + hs0[c]);
-      const double hbh = 0.5 * (hs0[c] + hs0[nb.cp[d]]);
-      div += (qhi[d] + hbh * ghi[d]) - (qlo[d] + hbl * glo[d]);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const double hl0 = hs0[nb.cm[d]] + h0, hh0 = h0 + hs0[nb.cp[d]];
+      div = fma(thi[d], fma(hh0, sghi[d], sqhi[d]), div);
+      div = fma(-tlo[d], fma(hl0, sglo[d], sqlo[d]), div);
     }
-    FE[(size_t)N * cs + c] = -fa_h * adv - div * invdx;
+    FE[(size_t)N * cs + c] = -fa_h * adv - 0.5 * div * invdx2;
   }
 }
 
@@ -148,7 +159,7 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
 __global__ void k_face_coef(DevGrid g, FieldMap fm, const double *__restrict__ theta,
                             double *__restrict__ thf, double *__restrict__ invdiag, double cmax,
                             unsigned long long *rho_bits, float *__restrict__ thf32,
-                            float *__restrict__ invdiag32) {
+                            float *__restrict__ invdiag32, double *__restrict__ cdiag) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int cs = g.cells;
   double ratio = 0.0;
@@ -167,6 +178,7 @@ __global__ void k_face_coef(DevGrid g, FieldMap fm, const double *__restrict__ t
       const double di = 1.0 / (1.0 + fm.cf[k] * S);
       invdiag[(size_t)k * cs + c] = di;
       if (invdiag32) invdiag32[(size_t)k * cs + c] = (float)di;
+      if (cdiag) cdiag[(size_t)k * cs + c] = fm.cf[k] * di;
     }
     ratio = cmax * S / (1.0 + cmax * S);
   }
@@ -237,6 +249,7 @@ __global__ void k_refine_residual(DevGrid g, FieldMap fm, const double *__restri
 
 // one FP32 Chebyshev-accelerated Jacobi sweep of A e = r from e = 0 (same method
 // as k_cheb; weights from the FP64 plan of the inner reduction)
+template <int DIM>
 __global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
                          const float *__restrict__ invdiag, const float *__restrict__ rhs,
                          const float *__restrict__ xk, const float *__restrict__ xkm1,
@@ -247,9 +260,10 @@ __global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
   const int cs = g.cells;
   if (c >= cs) return;
   const Nbr nb = neighbours(g, c);
-  float tlo[3], thi[3];
-  int cm[3], cp[3];
-  for (int d = 0; d < g.dim; ++d) {
+  float tlo[DIM], thi[DIM];
+  int cm[DIM], cp[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
     cm[d] = nb.cm[d];
     cp[d] = nb.cp[d];
     tlo[d] = thf[(size_t)d * cs + c];
@@ -267,7 +281,8 @@ __global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
     } else {
       const float *x = xk + off;
       float sx = 0.0f;
-      for (int d = 0; d < g.dim; ++d) sx += thi[d] * x[cp[d]] + tlo[d] * x[cm[d]];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) sx += thi[d] * x[cp[d]] + tlo[d] * x[cm[d]];
       y = (rhs[off + c] + cf * sx) * invdiag[(size_t)k * cs + c];
       const float prev = xkm1 ? xkm1[off + c] : 0.0f;
       xkp1[off + c] = fmaf(om, y - prev, prev);
@@ -290,8 +305,10 @@ __device__ __forceinline__ T lap_theta(const DevGrid &g, const Nbr &nb, int c, i
 // A thread takes one cell and kChebFields fields (neighbour indices and face
 // coefficients loaded once). Sweeps it >= *kdev (the device-planned count) do nothing.
 constexpr int kChebFields = 4;
+template <int DIM>
 __global__ void k_cheb(DevGrid g, FieldMap fm, const double *__restrict__ thf,
-                       const double *__restrict__ invdiag, const double *__restrict__ rhs,
+                       const double *__restrict__ invdiag, const double *__restrict__ cdiag,
+                       double *__restrict__ bdiag, const double *__restrict__ rhs,
                        const double *__restrict__ xk, const double *__restrict__ xkm1,
                        double *__restrict__ xkp1, int it, const int *__restrict__ kdev,
                        const double *__restrict__ omega) {
@@ -300,9 +317,10 @@ __global__ void k_cheb(DevGrid g, FieldMap fm, const double *__restrict__ thf,
   const int cs = g.cells;
   if (c >= cs) return;
   const Nbr nb = neighbours(g, c);
-  double tlo[3], thi[3];
-  int cm[3], cp[3];
-  for (int d = 0; d < g.dim; ++d) {
+  double tlo[DIM], thi[DIM];
+  int cm[DIM], cp[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
     cm[d] = nb.cm[d];
     cp[d] = nb.cp[d];
     tlo[d] = thf[(size_t)d * cs + c];
@@ -311,11 +329,26 @@ __global__ void k_cheb(DevGrid g, FieldMap fm, const double *__restrict__ thf,
   const double om = omega[it];
   const int k0 = blockIdx.y * kChebFields, k1 = min(fm.nfs, k0 + kChebFields);
   for (int k = k0; k < k1; ++k) {
-    const size_t off = (size_t)fm.fld[k] * cs;
+    const size_t off = (size_t)fm.fld[k] * cs, kc = (size_t)k * cs + c;
     const double *x = xk + off;
-    double s = 0.0;
-    for (int d = 0; d < g.dim; ++d) s += thi[d] * x[cp[d]] + tlo[d] * x[cm[d]];
-    const double y = (rhs[off + c] + fm.cf[k] * s) * invdiag[(size_t)k * cs + c];
+    // neighbour sum as one FMA chain (FP64 instructions, not bytes, bound this sweep)
+    double s = thi[0] * x[cp[0]];
+    s = fma(tlo[0], x[cm[0]], s);
+#pragma unroll
+    for (int d = 1; d < DIM; ++d) {
+      s = fma(thi[d], x[cp[d]], s);
+      s = fma(tlo[d], x[cm[d]], s);
+    }
+    // Jacobi value D^{-1} (rhs + c_f s) = b~ + c~ s: c~ = c_f D^{-1} comes with the
+    // diagonal, b~ = D^{-1} rhs is formed by sweep 0 and kept for the later sweeps
+    double bt;
+    if (it == 0) {
+      bt = rhs[off + c] * invdiag[kc];
+      bdiag[kc] = bt;
+    } else {
+      bt = bdiag[kc];
+    }
+    const double y = fma(cdiag[kc], s, bt);
     xkp1[off + c] = (it == 0) ? y : fma(om, y - xkm1[off + c], xkm1[off + c]);
   }
 }
@@ -616,14 +649,20 @@ void launch_lincomb(const LinComb &lc, size_t n, cudaStream_t s) {
 void launch_operators(const DevMech &m, const DevGrid &g, int i0, const double *phi,
                       const double *hsp, const double *theta_face, const double *vel,
                       double *FE, double *FD, cudaStream_t s) {
-  k_operators<<<(g.cells + 127) / 128, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, FE, FD);
+  const int blocks = (g.cells + 127) / 128;
+  if (g.dim == 1)
+    k_operators<1><<<blocks, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, FE, FD);
+  else if (g.dim == 2)
+    k_operators<2><<<blocks, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, FE, FD);
+  else
+    k_operators<3><<<blocks, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, FE, FD);
 }
 
 void launch_theta_faces(const DevGrid &g, const double *theta, double *thf, cudaStream_t s) {
   FieldMap fm;
   fm.nfs = 0;
   k_face_coef<<<(g.cells + 255) / 256, 256, 0, s>>>(g, fm, theta, thf, nullptr, 0.0, nullptr,
-                                                     nullptr, nullptr);
+                                                     nullptr, nullptr, nullptr);
 }
 
 namespace {
@@ -804,7 +843,7 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
   for (int k = 0; k < fm.nfs; ++k) cmax = std::max(cmax, fm.cf[k]);
   cudaMemsetAsync(w.rho_bits, 0, sizeof(unsigned long long), s);
   k_face_coef<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, theta, w.thf, w.invdiag, cmax, w.rho_bits,
-                                               w.thf32, w.invdiag32);
+                                               w.thf32, w.invdiag32, w.cdiag);
   if (w.refine_rounds > 0 && w.levels <= 1) {
     // mixed precision: FP64 residuals, FP32 inner Chebyshev solves (reduction 1e-6
     // each), three rounds, then the same reconstruction and checks as below
@@ -820,8 +859,15 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
       for (int it = 0; it < k32; ++it) {
         const float *ek = w.e32[(it + 2) % 3];
         const float *ekm1 = (it >= 2) ? w.e32[(it + 1) % 3] : nullptr;   // e_0 = 0
-        k_cheb32<<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
-                                     w.e32[it % 3], it, w.kdev32, w.omega32);
+        if (g.dim == 1)
+          k_cheb32<1><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
+                                          w.e32[it % 3], it, w.kdev32, w.omega32);
+        else if (g.dim == 2)
+          k_cheb32<2><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
+                                          w.e32[it % 3], it, w.kdev32, w.omega32);
+        else
+          k_cheb32<3><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
+                                          w.e32[it % 3], it, w.kdev32, w.omega32);
       }
       xin = xo;
     }
@@ -848,8 +894,16 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
   for (int it = 0; it < sweeps; ++it) {
     const double *xk = (it == 0) ? rhs : bufs[(it - 1) % 3];
     const double *xkm1 = (it <= 1) ? rhs : bufs[(it - 2) % 3];
-    k_cheb<<<dim3((cs + tb - 1) / tb, (fm.nfs + kChebFields - 1) / kChebFields), tb, 0, s>>>(
-        g, fm, w.thf, w.invdiag, rhs, xk, xkm1, bufs[it % 3], it, w.kdev, w.omega);
+    const dim3 grid((cs + tb - 1) / tb, (fm.nfs + kChebFields - 1) / kChebFields);
+    if (g.dim == 1)
+      k_cheb<1><<<grid, tb, 0, s>>>(g, fm, w.thf, w.invdiag, w.cdiag, w.bdiag, rhs, xk, xkm1,
+                                    bufs[it % 3], it, w.kdev, w.omega);
+    else if (g.dim == 2)
+      k_cheb<2><<<grid, tb, 0, s>>>(g, fm, w.thf, w.invdiag, w.cdiag, w.bdiag, rhs, xk, xkm1,
+                                    bufs[it % 3], it, w.kdev, w.omega);
+    else
+      k_cheb<3><<<grid, tb, 0, s>>>(g, fm, w.thf, w.invdiag, w.cdiag, w.bdiag, rhs, xk, xkm1,
+                                    bufs[it % 3], it, w.kdev, w.omega);
   }
   const int *kdev = w.kdev;
   const double *xfin = w.xa;

@@ -163,6 +163,7 @@ void prepare_chem_kernels(const DevMech &m);
 struct DiffWork {
   double *thf;       // [dim][cs] face coefficients
   double *invdiag;   // [N+1][cs]
+  double *cdiag, *bdiag;   // [N+1][cs] c_f / diagonal and rhs / diagonal (Chebyshev sweep)
   double *xa, *xb, *xc;   // [N+1][cs] iterates
   double *res;       // [N+1][cs] residual (multigrid)
   unsigned long long *rho_bits;   // measured Gershgorin bound (bit pattern)
