@@ -47,26 +47,31 @@ NEWTON_TRAFFIC_BYTES = {("flame2d_256_n21", "learned_mixed"): 332.12e6 + 30.35e6
 
 def newton_flops(N, R, nnz, stats, mixed=False):
     """Algorithmic FP64 flops (FMA = 2) of the reaction-Newton launches behind
-    `stats`, and their exp/log calls. Every iteration evaluates thermo (34N), the
-    rates of progress (20R) and the residual (2 nnz); an iteration that assembles
-    the Jacobian adds the rate derivatives (10R), the Jacobian (22 nnz + 4N) and,
-    in mixed precision, the row equilibration (n^2); an FP64 factorisation adds
-    2n^3/3 + 2n^2, a reused (chord) factor 2n^2 for the substitutions; every solve
-    ends with thermo and rates at the solution (34N + 14R + 2 nnz), except those
-    certified from the stored reaction term (4n). FP32 LU work of the mixed kernel
-    is not counted."""
+    `stats`, and their exp/log calls. An iteration that evaluates the rates does
+    thermo (34N), the rates of progress (20R), the residual (2 nnz) and the update
+    (6n), with 2R exponentials and one log; an iteration that assembles the
+    Jacobian adds the rate derivatives (10R), the Jacobian (22 nnz + 4N) and, in
+    mixed precision, the row equilibration (n^2) and the kept inverse of the new
+    factor (5n^3/3); an FP64 factorisation adds 2n^3/3 + 2n^2, a kept-inverse
+    chord step 2n^2. Certified solves and first chord steps taken from the stored
+    reaction term evaluate no rate (4n for their residual and test). Every solve
+    that is not certified ends with thermo at the solution (34N, a log and an
+    exponential for theta). FP32 LU work of the mixed kernel is not counted."""
     n = N + 1
     it, jac = stats["newton_iters"], stats.get("newton_jacobians", stats["newton_iters"])
     lu64 = stats.get("newton_lu_fp64", jac) if mixed else it
-    cert = stats.get("newton_certified", 0) if mixed else 0   # no rates, one substitution
+    cert = stats.get("newton_certified", 0) if mixed else 0
+    stored = stats.get("newton_stored_steps", 0) if mixed else 0
+    ev = it - cert - stored
     per_it = 34 * N + 20 * R + 2 * nnz + 6 * n
-    per_jac = 10 * R + 22 * nnz + 4 * N + (n * n if mixed else 0)
+    per_jac = 10 * R + 22 * nnz + 4 * N + ((n * n + (5 * n ** 3) // 3) if mixed else 0)
     per_lu = (2 * n ** 3) // 3 + 2 * n * n
     chord = (it - lu64) * 2 * n * n if mixed else 0
-    fin = 34 * N + 14 * R + 2 * nnz
-    flops = ((it - cert) * per_it + cert * 4 * n + jac * per_jac + lu64 * per_lu + chord
-             + (stats["newton_solves"] - cert) * fin)
-    exps = (it - cert + stats["newton_solves"] - cert) * (2 * R + 1)
+    fin = 34 * N
+    fin_solves = stats["newton_solves"] - cert
+    flops = (ev * per_it + (cert + stored) * 4 * n + jac * per_jac + lu64 * per_lu + chord
+             + fin_solves * fin)
+    exps = ev * (2 * R + 1) + fin_solves * 2
     return flops, exps
 
 class ClockSampler:
@@ -727,6 +732,7 @@ def main():
         ns = max(s_["newton_solves"], 1)
         d["newton_jacobians_per_solve"] = s_["newton_jacobians"] / ns
         d["newton_certified_per_solve"] = s_["newton_certified"] / ns
+        d["newton_stored_steps_per_solve"] = s_["newton_stored_steps"] / ns
         if k == "learned_mixed":
             d["surrogate_used"] = s_["surrogate_used"]
             d["surrogate_rejected"] = s_["surrogate_rejected"]

@@ -136,6 +136,9 @@ typedef struct misdc_stats {
                                    certified from the stored reaction term alone
                                    (counted as one iteration, no rate evaluated) */
   long long nested_iterations;  /* CISDCQ nested iterations run, summed over sweeps */
+  long long newton_stored_steps; /* mixed precision: uncertified solves whose first
+                                    chord step came from the stored reaction term
+                                    (iteration 1 without a rate evaluation) */
 } misdc_stats;
 
 typedef struct misdc_solver misdc_solver;

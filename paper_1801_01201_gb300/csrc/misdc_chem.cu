@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
   double *J = w.J;
   const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
   unsigned long long my_solves = 0, my_iters = 0, my_fail = 0, my_sg = 0, my_rej = 0, my_fb = 0,
-                     my_jac = 0, my_lu64 = 0, my_cert = 0;
+                     my_jac = 0, my_lu64 = 0, my_cert = 0, my_stored = 0;
   int my_max = 0;
   unsigned bits = 0;
 
@@ -531,6 +531,8 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       for (int i = lane; i < nn; i += 32) w.xg[i] = vet ? w.dx[i] : w.xs[i];
       __syncwarp();
     }
+    int it0 = 1;              // first iteration of the loop below
+    double dprev0 = INFINITY;  // size of the step taken before it (none)
     if (MIXED && from_store && !fac32 && !vet && FRp && hspp) {
       // A chord step certified without evaluating any rate: the residual of the
       // guess follows from its stored reaction term, r = b - Y_p + wdt F_p (and
@@ -567,9 +569,33 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         my_max = max(my_max, 1);
         continue;
       }
+      // Not certified, but a step of at most 1e-4 is the chord step the loop's
+      // first iteration would take from x_p (there with the rates evaluated afresh
+      // at x_p instead of the stored reaction term, which agree to the previous
+      // solve's tolerance). Taken here, it is iteration 1 and costs no rate
+      // evaluation; fresh residuals from x_p + step on decide convergence.
+      bool fin = true;
+      double dm = 0.0;
+      for (int i = lane; i < nn; i += 32) {
+        fin = fin && isfinite(w.zd[i]);
+        if (i < N) dm = fmax(dm, fabs(w.zd[i]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+      fin = __all_sync(0xffffffffu, fin);
+      double d0 = 0.0;
+      if (lane == 0) d0 = fmax(dm, fabs(w.zd[N]) / w.xs[N]);
+      d0 = __shfl_sync(0xffffffffu, d0, 0);
+      if (fin && d0 <= 1e-4 && maxit >= 2) {
+        for (int i = lane; i < nn; i += 32) w.xs[i] += w.zd[i];
+        __syncwarp();
+        it0 = 2;
+        dprev0 = d0;
+        ++my_stored;
+      }
     }
     double T = w.xs[N];
-    double dprev = INFINITY;
+    double dprev = dprev0;
     int it, code = 0;
     for (int attempt = 0; attempt < (MIXED ? 2 : 1); ++attempt) {
     if (attempt == 1) {
@@ -580,11 +606,12 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       T = w.xs[N];
       code = 0;
       dprev = INFINITY;
+      it0 = 1;
       have = fresh = from_store = fresh_exact = false;
       exact = no32 = true;
       ++my_fb;
     }
-    for (it = 1; it <= maxit; ++it) {
+    for (it = it0; it <= maxit; ++it) {
       const bool jac = !MIXED || !have || exact;   // this iteration assembles the Jacobian
       // ---- thermo and concentrations (species over lanes). FP64 work is paid per
       // active lane on this part, so warp-uniform scalars are computed by lane 0
@@ -1092,6 +1119,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     if (my_jac) atomicAdd(&st->jacobians, my_jac);
     if (my_lu64) atomicAdd(&st->lu64, my_lu64);
     if (my_cert) atomicAdd(&st->certified, my_cert);
+    if (my_stored) atomicAdd(&st->stored_steps, my_stored);
   }
 }
 

@@ -1045,6 +1045,7 @@ misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
   out->newton_jacobians = (long long)d.jacobians;
   out->newton_lu_fp64 = (long long)d.lu64;
   out->newton_certified = (long long)d.certified;
+  out->newton_stored_steps = (long long)d.stored_steps;
   int st = MISDC_OK;
   if (d.status_bits & kBitTdiag) st = MISDC_E_TDIAG;
   else if (d.status_bits & (kBitNan | kBitSingular)) st = MISDC_E_NAN;
@@ -1876,6 +1877,7 @@ misdc_status misdc_batch_stats(misdc_batch *b, misdc_stats *out, int reset) {
     sum.newton_jacobians += t.newton_jacobians;
     sum.newton_lu_fp64 += t.newton_lu_fp64;
     sum.newton_certified += t.newton_certified;
+    sum.newton_stored_steps += t.newton_stored_steps;
     sum.kernel_launches += t.kernel_launches;   // kernels in conditional bodies
     sum.nested_iterations += t.nested_iterations;
   }

@@ -38,6 +38,7 @@ struct DevStats {
   unsigned long long jacobians;        // Jacobian assemblies of the reaction Newton
   unsigned long long lu64;             // FP64 LU factorisations of the reaction Newton
   unsigned long long certified;        // solves whose guess was certified without rates
+  unsigned long long stored_steps;     // first chord steps taken from the stored reaction term
   unsigned long long body_launches;    // kernels run inside conditional graph bodies
   unsigned long long nested_iters;     // CISDCQ nested iterations run, summed over sweeps
 };
