@@ -49,16 +49,26 @@ __global__ void k_exp(const double *__restrict__ x, double *__restrict__ y, size
     y[i] = exp_tab(x[i]);
 }
 
-__device__ __forceinline__ void species_thermo(const DevMech &m, int i, double T, double lnT,
-                                               double invT, double &hRT, double &gRT,
-                                               double &cpR) {
+// h/RT and g/RT of species i (NASA-7); cp/R separately where it is needed
+__device__ __forceinline__ void species_hg(const DevMech &m, int i, double T, double lnT,
+                                           double invT, double &hRT, double &gRT) {
   const double *a = m.hcoef + 6 * i;
   hRT = fma(a[5], invT, a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4]))));
   const double *s = m.scoef + 6 * i;
   double sR = fma(s[0], lnT, T * (s[1] + T * (s[2] + T * (s[3] + T * s[4])))) + s[5];
   gRT = hRT - sR;
+}
+
+__device__ __forceinline__ double species_cpR(const DevMech &m, int i, double T) {
   const double *c = m.cpcoef + 5 * i;
-  cpR = c[0] + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4])));
+  return c[0] + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4])));
+}
+
+__device__ __forceinline__ void species_thermo(const DevMech &m, int i, double T, double lnT,
+                                               double invT, double &hRT, double &gRT,
+                                               double &cpR) {
+  species_hg(m, i, T, lnT, invT, hRT, gRT);
+  cpR = species_cpR(m, i, T);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -620,21 +630,24 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       if (lane == 0) { lnT = log(T); invT = 1.0 / T; }
       lnT = __shfl_sync(0xffffffffu, lnT, 0);
       invT = __shfl_sync(0xffffffffu, invT, 0);
+      // the mixture cp only scales the temperature row of a new Jacobian: chord
+      // iterations (residual only, with the scale their factor was built with)
+      // skip it
       double sh = 0.0, scp = 0.0;
       for (int i = lane; i < N; i += 32) {
-        double hRT, gRT, cpR;
-        species_thermo(m, i, T, lnT, invT, hRT, gRT, cpR);
+        double hRT, gRT;
+        species_hg(m, i, T, lnT, invT, hRT, gRT);
         const double y = w.xs[i];
         w.c[i] = m.rho * y * m.invW[i];
         w.g[i] = gRT;
         w.hRT[i] = hRT;
-        const double hm = kRu * m.invW[i] * T * hRT, cpm = kRu * m.invW[i] * cpR;
+        const double hm = kRu * m.invW[i] * T * hRT;
         w.hm[i] = hm;
         sh = fma(y, hm, sh);
-        scp = fma(y, cpm, scp);
+        if (jac) scp = fma(y, kRu * m.invW[i] * species_cpR(m, i, T), scp);
       }
       sh = warp_sum(sh);
-      scp = warp_sum(scp);
+      if (jac) scp = warp_sum(scp);
       __syncwarp();
       // ---- rates of progress, dq/dT and slot derivatives (reactions over lanes)
       for (int r = lane; r < R; r += 32) {
@@ -674,8 +687,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         }
       }
       double sT = 0.0;
-      if (lane == 0) sT = invT / scp;
-      sT = __shfl_sync(0xffffffffu, sT, 0);
+      if (jac) {
+        if (lane == 0) sT = invT / scp;
+        sT = __shfl_sync(0xffffffffu, sT, 0);
+      }
       if (!jac) {
         // ---- chord iteration: FP64 residual only, wdot_i = sum_r W_i nu_ri q_r;
         // the temperature row keeps the scaling its stored factor was built with
