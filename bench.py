@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12      # 152 SMs x 2 DFMA/clk x 2 flop 
 # dram__bytes_read.sum + dram__bytes_write.sum of one reaction-Newton launch, per
 # (workload, variant), from the ncu captures summarised under profiles/; a variant
 # missing here has changed since its capture (traffic reported as null).
-NEWTON_TRAFFIC_BYTES = {("flame2d_256_n21", "learned_mixed"): 333.55e6 + 30.60e6}
+NEWTON_TRAFFIC_BYTES = {("flame2d_256_n21", "learned_mixed"): 332.72e6 + 30.85e6}
 
 
 def newton_flops(N, R, nnz, stats, mixed=False):
