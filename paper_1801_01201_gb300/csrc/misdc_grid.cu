@@ -217,33 +217,39 @@ __global__ void k_cheb_plan(const unsigned long long *rho_bits, int kmax, double
 // x_{j+1} = x_j + e_j, A e_j = r_j = b - A x_j solved approximately in FP32 from
 // e_j = 0; r_j and the update in FP64.
 
-// x_out = x_in + e (e: the buffer the last planned inner sweep wrote; none in the
-// first round, where x_in = b), r32 = b - A x_out, for every solved field
+// r32 = b - A x (A = I - c_f L_theta) for every solved field: the FP64 residual
+// of the round's iterate x (the right-hand side itself in the first round),
+// rounded to FP32 for the inner solve
+template <int DIM>
 __global__ void k_refine_residual(DevGrid g, FieldMap fm, const double *__restrict__ thf,
-                                  const double *__restrict__ rhs, const double *x_in,
-                                  const float *e0, const float *e1, const float *e2,
-                                  const int *__restrict__ kdev, double *x_out,
+                                  const double *__restrict__ rhs, const double *__restrict__ x,
                                   float *__restrict__ r32) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int cs = g.cells;
   if (c >= cs) return;
-  const float *e = nullptr;
-  if (e0) {
-    const int sl = (*kdev - 1) % 3;
-    e = sl == 0 ? e0 : (sl == 1 ? e1 : e2);
-  }
   const Nbr nb = neighbours(g, c);
+  double tlo[DIM], thi[DIM];
+  int cm[DIM], cp[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    cm[d] = nb.cm[d];
+    cp[d] = nb.cp[d];
+    tlo[d] = thf[(size_t)d * cs + c];
+    thi[d] = thf[(size_t)d * cs + cp[d]];
+  }
   const int k0 = blockIdx.y * 4, k1 = min(fm.nfs, k0 + 4);
   for (int k = k0; k < k1; ++k) {
     const size_t off = (size_t)fm.fld[k] * cs;
-    // the updated iterate at this cell and its neighbours (x_in + e on the fly)
-    auto xv = [&](int q) -> double { return x_in[off + q] + (e ? (double)e[off + q] : 0.0); };
-    const double xc = xv(c);
-    double L = 0.0;
-    for (int d = 0; d < g.dim; ++d)
-      L += thf[(size_t)d * cs + nb.cp[d]] * (xv(nb.cp[d]) - xc) - thf[(size_t)d * cs + c] * (xc - xv(nb.cm[d]));
-    x_out[off + c] = xc;
-    r32[off + c] = (float)(rhs[off + c] - (xc - fm.cf[k] * L));
+    const double *xf = x + off;
+    const double xc = xf[c];
+    double L = thi[0] * (xf[cp[0]] - xc);
+    L = fma(-tlo[0], xc - xf[cm[0]], L);
+#pragma unroll
+    for (int d = 1; d < DIM; ++d) {
+      L = fma(thi[d], xf[cp[d]] - xc, L);
+      L = fma(-tlo[d], xc - xf[cm[d]], L);
+    }
+    r32[off + c] = (float)(rhs[off + c] - fma(-fm.cf[k], L, xc));
   }
 }
 
@@ -254,8 +260,11 @@ __global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
                          const float *__restrict__ invdiag, const float *__restrict__ rhs,
                          const float *__restrict__ xk, const float *__restrict__ xkm1,
                          float *__restrict__ xkp1, int it, const int *__restrict__ kdev,
-                         const double *__restrict__ omega) {
-  if (it >= *kdev) return;
+                         const double *__restrict__ omega, const double *__restrict__ xbase,
+                         double *__restrict__ xnext) {
+  const int K = *kdev;
+  if (it >= K) return;
+  const bool last = (it == K - 1);   // the last planned sweep also forms x + e in FP64
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int cs = g.cells;
   if (c >= cs) return;
@@ -274,10 +283,10 @@ __global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
   for (int k = k0; k < k1; ++k) {
     const size_t off = (size_t)fm.fld[k] * cs;
     const float cf = (float)fm.cf[k];
-    float y;
+    float y, v;
     if (it == 0) {   // e_0 = 0: the first sweep is D^{-1} r
       y = rhs[off + c] * invdiag[(size_t)k * cs + c];
-      xkp1[off + c] = y;
+      v = y;
     } else {
       const float *x = xk + off;
       float sx = 0.0f;
@@ -285,8 +294,10 @@ __global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
       for (int d = 0; d < DIM; ++d) sx += thi[d] * x[cp[d]] + tlo[d] * x[cm[d]];
       y = (rhs[off + c] + cf * sx) * invdiag[(size_t)k * cs + c];
       const float prev = xkm1 ? xkm1[off + c] : 0.0f;
-      xkp1[off + c] = fmaf(om, y - prev, prev);
+      v = fmaf(om, y - prev, prev);
     }
+    xkp1[off + c] = v;
+    if (last && xnext) xnext[off + c] = xbase[off + c] + (double)v;
   }
 }
 
@@ -850,30 +861,34 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
     const int k32 = std::min(sweeps, chebyshev_sweeps(rho_bound, 1e-6));
     k_cheb_plan<<<1, 32, 0, s>>>(w.rho_bits, k32, 1e-6, w.kdev32, w.omega32, st, w.refine_rounds);
     const dim3 gr4((cs + 255) / 256, (fm.nfs + 3) / 4);
-    const double *xin = rhs;
+    // round r: r32 = b - A x_r in FP64 (x_0 = b), inner FP32 sweeps for e, and the
+    // last planned sweep writes x_{r+1} = x_r + e (the final round into xc)
+    const double *xcur = rhs;
     double *xr[2] = {w.xa, w.xb};
     for (int round = 0; round < w.refine_rounds; ++round) {
-      double *xo = xr[round & 1];
-      k_refine_residual<<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xin, round ? w.e32[0] : nullptr,
-                                            w.e32[1], w.e32[2], w.kdev32, xo, w.r32);
+      double *xnext = (round == w.refine_rounds - 1) ? w.xc : xr[round & 1];
+      if (g.dim == 1)
+        k_refine_residual<1><<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xcur, w.r32);
+      else if (g.dim == 2)
+        k_refine_residual<2><<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xcur, w.r32);
+      else
+        k_refine_residual<3><<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xcur, w.r32);
       for (int it = 0; it < k32; ++it) {
         const float *ek = w.e32[(it + 2) % 3];
         const float *ekm1 = (it >= 2) ? w.e32[(it + 1) % 3] : nullptr;   // e_0 = 0
         if (g.dim == 1)
           k_cheb32<1><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
-                                          w.e32[it % 3], it, w.kdev32, w.omega32);
+                                          w.e32[it % 3], it, w.kdev32, w.omega32, xcur, xnext);
         else if (g.dim == 2)
           k_cheb32<2><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
-                                          w.e32[it % 3], it, w.kdev32, w.omega32);
+                                          w.e32[it % 3], it, w.kdev32, w.omega32, xcur, xnext);
         else
           k_cheb32<3><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
-                                          w.e32[it % 3], it, w.kdev32, w.omega32);
+                                          w.e32[it % 3], it, w.kdev32, w.omega32, xcur, xnext);
       }
-      xin = xo;
+      xcur = xnext;
     }
-    // last update x += e into xc, then the reconstruction and residual check
-    k_refine_residual<<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xin, w.e32[0], w.e32[1], w.e32[2],
-                                          w.kdev32, w.xc, w.r32);
+    // reconstruction and residual check of the final iterate
     k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, w.xc,
                                               w.xc, w.xc, nullptr, out, st);
     return;
