@@ -55,3 +55,31 @@ def test_misdc_needs_more_sweeps_than_misdcq():
     nm = int(np.where(im <= 1e-11)[0][0]) + 1
     nq = int(np.where(iq <= 1e-11)[0][0]) + 1
     assert 1.5 * nq <= nm <= 3 * nq
+
+
+def test_operators_consistent_at_fourth_order_inside_second_at_the_wall():
+    """Consistency of the spatial operators of eq. nonlinear_test_pde (Sec. 5.2).
+
+    With r = 0 and a tiny step, (phi^1 - phi^0)/dt tends to the cell averages of
+    a phi' + d phi'', which for phi = cos(kx) are exact flux differences. The
+    fourth-order face values and Laplacian converge at fourth order away from the
+    walls; next to a wall the ghost averages of the cubic closure are O(h^4)
+    accurate and the Laplacian divides them by h^2, so those cells converge at
+    second order. A wrong ghost weight or stencil coefficient breaks one of the two.
+    """
+    k, a, d, dt = 9 * np.pi / 40, 1.0, 1.0, 1e-8
+    inner, wall = [], []
+    for nx in (50, 100, 200):
+        h = LX / nx
+        xf = np.arange(nx + 1) * h
+        phi0 = (np.sin(k * xf[1:]) - np.sin(k * xf[:-1])) / (k * h)
+        F = (a * (np.cos(k * xf[1:]) - np.cos(k * xf[:-1]))
+             - d * k * (np.sin(k * xf[1:]) - np.sin(k * xf[:-1]))) / h
+        p1, _ = O.pde_step("MISDCQ", 4, 1, 1, dt, phi0, Lx=LX, a=a, d=d, r=0.0,
+                           left=1.0, right=np.cos(k * LX))
+        e = np.abs((p1 - phi0) / dt - F)
+        inner.append(e[3:-3].max())
+        wall.append(max(e[0], e[-1]))
+    for i in range(2):
+        assert inner[i] / inner[i + 1] > 12.0, inner
+        assert 3.0 < wall[i] / wall[i + 1] < 5.0, wall
