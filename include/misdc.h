@@ -243,10 +243,14 @@ misdc_status misdc_exp(const double *x, double *y, size_t n, void *stream);
  * phi_in, phi_out [n][nx] (may alias); incr [n][n_steps][n_sweeps] (may be NULL)
  * receives the sweep increments (1/nx) sum_i |phi^{M,(k+1)}_i - phi^{M,(k)}_i|;
  * status [n] (may be NULL): 0, or bits 1 (Newton limit), 2 (non-finite),
- * 4 (singular diffusion matrix). One block per instance holds all node arrays
- * in shared memory: misdc_pde_smem_bytes gives the need, and a launch whose need
- * exceeds the device's per-block limit returns MISDC_E_INVALID (at 5 nodes about
- * 340 cells, at 3 nodes about 610). nx >= 8. */
+ * 4 (singular diffusion matrix). Below 4096 instances one block per instance
+ * holds all node arrays in shared memory: misdc_pde_smem_bytes gives the need,
+ * and a launch whose need exceeds the device's per-block limit returns
+ * MISDC_E_INVALID (at 5 nodes about 340 cells, at 3 nodes about 610). From 4096
+ * instances on, one thread per instance works on a workspace laid out
+ * [array][cell][instance] (coalesced across a warp), which the call allocates
+ * and frees stream-ordered (cudaMallocAsync / cudaFreeAsync; MISDC_E_OOM when it
+ * does not fit). nx >= 8. */
 misdc_status misdc_pde_step(int scheme, int n_nodes, int n_sweeps, int nu, double dt, int n_steps,
                             int nx, double length, int n, const double *params,
                             const double *phi_in, double *phi_out, double *incr, int *status,

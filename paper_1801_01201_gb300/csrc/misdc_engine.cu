@@ -1249,13 +1249,16 @@ misdc_status misdc_pde_step(int scheme, int n_nodes, int n_sweeps, int nu, doubl
   if (!params || !phi_in || !phi_out) return fail(MISDC_E_INVALID, "pde_step: null array");
   Tables T;
   if (!make_tables(n_nodes, T)) return fail(MISDC_E_INVALID, "pde_step: n_nodes must be in 2..9");
-  int dev = 0, smem_max = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (pde_smem_bytes(T.M, nx) > (size_t)smem_max)
-    return fail(MISDC_E_INVALID, "pde_step: nx too large for one block's shared memory (" +
-                                     std::to_string(pde_smem_bytes(T.M, nx)) + " > " +
-                                     std::to_string(smem_max) + " bytes)");
+  const bool batch = n >= kPdeBatchMin;
+  if (!batch) {
+    int dev = 0, smem_max = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (pde_smem_bytes(T.M, nx) > (size_t)smem_max)
+      return fail(MISDC_E_INVALID, "pde_step: nx too large for one block's shared memory (" +
+                                       std::to_string(pde_smem_bytes(T.M, nx)) + " > " +
+                                       std::to_string(smem_max) + " bytes)");
+  }
   PdeLaunch p;
   memset(&p, 0, sizeof(p));
   p.scheme = scheme; p.M = T.M; p.n_sweeps = n_sweeps; p.nu = nu; p.n_steps = n_steps;
@@ -1266,7 +1269,17 @@ misdc_status misdc_pde_step(int scheme, int n_nodes, int n_sweeps, int nu, doubl
   memcpy(p.QI, T.QI, sizeof(p.QI));
   memcpy(p.QE, T.QE, sizeof(p.QE));
   p.params = params; p.phi_in = phi_in; p.phi_out = phi_out; p.incr = incr; p.status = status;
-  CK(launch_pde_step(p, (cudaStream_t)stream));
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (!batch) {
+    CK(launch_pde_step(p, cs));
+    return MISDC_OK;
+  }
+  // stream-ordered workspace of the batched layout, freed behind the launch
+  double *ws = nullptr;
+  CK(cudaMallocAsync((void **)&ws, pde_batch_bytes(T.M, nx, n), cs));
+  const cudaError_t e = launch_pde_batch(p, ws, cs);
+  cudaFreeAsync(ws, cs);
+  CK(e);
   return MISDC_OK;
 }
 

@@ -252,6 +252,12 @@ struct PdeLaunch {
 };
 size_t pde_smem_bytes(int M, int nx);
 cudaError_t launch_pde_step(const PdeLaunch &p, cudaStream_t s);
+// many instances: one thread each, node arrays in a workspace of pde_batch_bytes
+// laid out [array][cell][instance]
+// (one warp per 32 instances is latency-bound: it pays once several warps share each SM)
+constexpr int kPdeBatchMin = 4096;
+size_t pde_batch_bytes(int M, int nx, int n);
+cudaError_t launch_pde_batch(const PdeLaunch &p, double *ws, cudaStream_t s);
 
 // ---- learned Newton guess: MLP kernels (misdc_mlp.cu) ----
 namespace mlp {

@@ -150,3 +150,32 @@ def test_pde_argument_errors():
     empty = torch.zeros((0, 16), dtype=torch.float64, device="cuda")
     out, incr, st = sv.pde_step(empty, np.zeros((0, 5)), 0.05)
     assert out.shape == (0, 16)
+
+
+@pytest.mark.parametrize("scheme,nu", [("MISDC", 1), ("MISDCQ", 1), ("CISDCQ", 2)])
+def test_many_instances_take_the_batched_layout(scheme, nu):
+    """From 4096 instances on, one thread per instance with the node arrays in a
+    global [array][cell][instance] workspace. Same per-cell arithmetic as one block
+    per instance (run on the same instances in chunks below 4096): states within
+    1e-13, increments within 1e-13 (their cell sums run in another order), and the
+    oracle within the bound on three instances."""
+    rng = np.random.default_rng(13)
+    n = 4096
+    prm = np.stack([rng.uniform(-1, 1, n), rng.uniform(0.5, 16, n), rng.uniform(1, 32, n),
+                    rng.uniform(0.5, 1.0, n), rng.uniform(0.0, 0.5, n)], axis=1)
+    phis = np.stack([prm[i, 3] + (prm[i, 4] - prm[i, 3]) * 0.5 * (1 + np.tanh(2 * X - rng.uniform(8, 30)))
+                     for i in range(n)])
+    kw = dict(scheme=scheme, n_nodes=5, n_sweeps=3, nu=nu, n_steps=2)
+    got, inc, st = gpu(phis, prm, 0.05, **kw)
+    assert np.all(st == 0)
+    parts = [gpu(phis[i:i + 2048], prm[i:i + 2048], 0.05, **kw) for i in (0, 2048)]
+    ref = np.concatenate([q[0] for q in parts])
+    rinc = np.concatenate([q[1] for q in parts])
+    assert np.max(np.abs(got - ref)) <= 1e-13
+    assert np.max(np.abs(inc - rinc)) <= 1e-13
+    for i in (0, 2047, 4095):
+        want = phis[i]
+        for _ in range(2):
+            want, _ = O.pde_step(scheme, 4, 3, nu, 0.05, want, a=prm[i, 0], d=prm[i, 1], r=prm[i, 2],
+                                 left=prm[i, 3], right=prm[i, 4])
+        assert np.max(np.abs(got[i] - want)) <= TOL
