@@ -105,6 +105,7 @@ def _declare(L):
                                      C.c_double, C.c_int]
     L.or_adr_operators.argtypes = [C.POINTER(Mech), C.POINTER(AdrCfg), dp, dp, dp, dp]
     L.or_adr_solve_diff.argtypes = [C.POINTER(Mech), C.POINTER(AdrCfg), C.c_double, dp, dp, dp]
+    L.or_lm_terms.argtypes = [C.POINTER(Mech), C.POINTER(LmCfg), dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
 
 
 def _p(a):
@@ -269,3 +270,62 @@ class ADR:
                 raise RuntimeError("oracle step failed: %r" % st.as_dict())
             phi, out = out, phi
         return phi, st.as_dict()
+
+
+R_U = 8.314462618   # J/(mol K)
+
+
+class LmCfg(C.Structure):
+    _fields_ = [("nx", C.c_int), ("dx", C.c_double), ("U_in", C.c_double), ("Y_in", dp),
+                ("T_in", C.c_double), ("p0", C.c_double), ("i0", C.c_int),
+                ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("dchi", C.c_int)]
+
+
+class LowMach:
+    """Oracle handle of the 1D variable-density low-Mach system (Sec. 2, Sec. 3.3):
+    state q = [rho, rho Y_1..rho Y_N, rho h] per cell, open boundaries (inflow
+    Dirichlet state and velocity at x = 0, zero-gradient outflow at x = L)."""
+
+    def __init__(self, mech, nx, dx, U_in, Y_in, T_in, p0=101325.0, i0=None, newton_rtol=1e-12,
+                 newton_maxit=50, dchi=True):
+        self.mech_py = mech
+        self.N, self.nx = mech.n_species, nx
+        self._keep = dict(
+            W=_f64(mech.W), nasa7=_f64(mech.nasa7), A=_f64(mech.A), beta=_f64(mech.beta),
+            Ea=_f64(mech.Ea), nu_f=np.ascontiguousarray(mech.nu_f, dtype=np.int32),
+            nu_r=np.ascontiguousarray(mech.nu_r, dtype=np.int32), D0=_f64(mech.D0), Y_in=_f64(Y_in))
+        k = self._keep
+        self.m = Mech(mech.n_species, mech.n_reactions, _p(k["W"]), _p(k["nasa7"]), _p(k["A"]),
+                      _p(k["beta"]), _p(k["Ea"]), k["nu_f"].ctypes.data_as(ip),
+                      k["nu_r"].ctypes.data_as(ip), _p(k["D0"]), mech.alpha0, mech.T_ref,
+                      mech.theta_exp, mech.p_ref)
+        if i0 is None:
+            i0 = int(np.argmax(k["Y_in"]))
+        self.cfg = LmCfg(nx, dx, U_in, _p(k["Y_in"]), T_in, p0, i0, newton_rtol, newton_maxit,
+                         1 if dchi else 0)
+        self.p0 = p0
+
+    def state_from_YT(self, Y, T):
+        """q from mass fractions and temperature, with rho from the EOS at p0."""
+        Y = _f64(Y)
+        T = _f64(T)
+        W = _f64(self.mech_py.W)
+        rho = self.p0 / (R_U * T * np.sum(Y / W[:, None], axis=0))
+        h = np.zeros(T.size)
+        lib().or_h_from_T(C.byref(self.m), T.size, _p(np.ascontiguousarray(Y)), _p(T), _p(h))
+        return np.concatenate([rho[None], rho[None] * Y, (rho * h)[None]], axis=0)
+
+    def terms(self, q, dchi=None, U_adv=None, T_guess=None):
+        """(FA, FD, FR, S, U, p_eos, T) of state q (or_lm_terms)."""
+        q = _f64(q)
+        nx, F = self.nx, self.N + 2
+        FA = np.zeros((F, nx)); FD = np.zeros((F, nx)); FR = np.zeros((F, nx))
+        S = np.zeros(nx); U = np.zeros(nx + 1); pe = np.zeros(nx)
+        T = _f64(T_guess).copy() if T_guess is not None else np.full(nx, 1000.0)
+        rc = lib().or_lm_terms(C.byref(self.m), C.byref(self.cfg), _p(q),
+                               _p(_f64(dchi)) if dchi is not None else None,
+                               _p(_f64(U_adv)) if U_adv is not None else None,
+                               _p(FA), _p(FD), _p(FR), _p(S), _p(U), _p(pe), _p(T))
+        if rc:
+            raise RuntimeError("temperature diagnosis failed")
+        return FA, FD, FR, S, U, pe, T

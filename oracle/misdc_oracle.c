@@ -1097,3 +1097,235 @@ int or_adr_solve_diff(const or_mech *mech, const or_adr_cfg *cfg, double wdt,
   adr_ctx a = {mech, cfg, cfg->nx * cfg->ny * cfg->nz, mech->N, NULL};
   return adr_sd(&a, wdt, coef_state, rhs, x);
 }
+
+/* ======================================================================= */
+/* Variable-density low-Mach coupling in 1D (Sec. 2; Sec. 3.3 I3, I4, S2, S6) */
+/* ======================================================================= */
+/*
+ * The paper's own setting (1D, open boundaries): the state is conservative,
+ * [rho, rho Y_1..rho Y_N, rho h] per cell; the velocity lives on the faces and
+ * follows from the divergence constraint div U = S + delta_chi (eqs.
+ * divergence_constraint, S_def) integrated from the inflow face, as the paper
+ * does in 1D (I4). Readings (the paper states none of these closures):
+ *  - inflow at x = 0: Dirichlet state (Y_in, T_in, rho_in from the EOS at p0)
+ *    and velocity U_in; outflow at x = L: zero gradient, no diffusive flux;
+ *  - advection: fourth-order centred face values of the conserved quantity,
+ *    the inflow value on the inflow face and as the ghost of the first face,
+ *    the last cell's value on and beyond the outflow face;
+ *  - diffusion: second-order compact fluxes with harmonic-mean coefficients;
+ *    on the inflow face the gradient to the inflow value half a cell away;
+ *  - the dominant species' flux is minus the sum of the others (Sec. 2);
+ *  - in eq. S_def the flux Gamma_i enters as rho D_i grad Y_i: deriving S from
+ *    the EOS held at p0 along particle paths (D/Dt ln p_EOS = 0 with the
+ *    species and enthalpy equations) gives
+ *      S = (div(lambda grad T) + sum_i rho D_i grad Y_i . grad h_i) / (rho cp T)
+ *          + sum_i (W/W_i) div(rho D_i grad Y_i) / rho
+ *          + sum_i (W/W_i - h_i/(cp T)) wdot_i / rho,
+ *    whereas the text's Gamma_i := -rho D_i grad Y_i would reverse the sign of
+ *    the diffusive expansion;
+ *  - lambda/cp = rho alpha(T) (the same transport model as the periodic ADR
+ *    system), so lambda = rho cp alpha(T); the differential-diffusion flux
+ *    sum_i h_i (rho D_i - lambda/cp) grad Y_i uses face means of h_i.
+ */
+
+typedef struct lm_ctx {
+  const or_mech *m;
+  const or_lm_cfg *g;
+  int nx, N;
+  double rho_in, h_in, T_in;
+  double hsp_in[64];   /* species enthalpies at the inflow state, J/kg */
+} lm_ctx;
+
+static void lm_setup(lm_ctx *c, const or_mech *m, const or_lm_cfg *g) {
+  c->m = m; c->g = g; c->nx = g->nx; c->N = m->N;
+  double sw = 0.0;
+  for (int i = 0; i < m->N; ++i) sw += g->Y_in[i] / m->W[i];
+  c->T_in = g->T_in;
+  c->rho_in = g->p0 / (R_UNIV * g->T_in * sw);
+  c->h_in = mix_h(m, g->Y_in, 1, g->T_in);
+  for (int i = 0; i < m->N; ++i) c->hsp_in[i] = or_species_h(m, i, g->T_in);
+}
+
+static double lm_theta(const or_mech *m, double T) { return pow(T / m->T_ref, m->theta_exp); }
+
+/* primitive variables of every cell: Y [N][nx], h, T [nx]; returns non-zero if a
+ * temperature cannot be diagnosed */
+static int lm_prims(const lm_ctx *c, const double *q, double *Y, double *h, double *T,
+                    const double *Tguess) {
+  const int nx = c->nx, N = c->N;
+  int rc = 0;
+  for (int k = 0; k < nx; ++k) {
+    const double rho = q[k];
+    for (int i = 0; i < N; ++i) Y[(size_t)i * nx + k] = q[(size_t)(1 + i) * nx + k] / rho;
+    h[k] = q[(size_t)(N + 1) * nx + k] / rho;
+    (void)Tguess;
+    rc |= T_of_cell(c->m, Y + k, nx, h[k], &T[k]);
+  }
+  return rc;
+}
+
+/* 12 x the fourth-order face value of field f on face j (j = 1..nx-1), with the
+ * inflow ghost and zero-gradient outflow ghosts */
+static double lm_face4(const lm_ctx *c, const double *f, double fin, int j) {
+  const int nx = c->nx;
+  const double a = (j - 2 >= 0) ? f[j - 2] : fin;
+  const double b = f[j - 1], d = f[j];
+  const double e = (j + 1 < nx) ? f[j + 1] : f[nx - 1];
+  return 7.0 * (b + d) - (a + e);
+}
+
+/* A = -div(U f) for a conserved field f with inflow value fin */
+static void lm_advect(const lm_ctx *c, const double *U, const double *f, double fin, double *out) {
+  const int nx = c->nx;
+  const double inv = 1.0 / c->g->dx;
+  double Fl = U[0] * fin;
+  for (int k = 0; k < nx; ++k) {
+    const double Fr = (k + 1 < nx) ? U[k + 1] * lm_face4(c, f, fin, k + 1) / 12.0 : U[nx] * f[nx - 1];
+    out[k] = -(Fr - Fl) * inv;
+    Fl = Fr;
+  }
+}
+
+/* diffusive fluxes on the nx+1 faces: G[i][j] = rho D_i grad Y_i (dominant
+ * species closed), Q[j] = (lambda/cp) grad h, K[j] = lambda grad T,
+ * gY[i][j] = grad Y_i and the face species enthalpies hf[i][j] */
+typedef struct lm_faces {
+  double *G, *Q, *K, *gY, *hf, *Lc, *gh;   /* Lc: lambda/cp; gh[i][j]: grad h_i */
+} lm_faces;
+
+static void lm_fluxes(const lm_ctx *c, const double *rho, const double *Y, const double *h,
+                      const double *T, const double *hsp, lm_faces *F) {
+  const or_mech *m = c->m;
+  const int nx = c->nx, N = c->N, i0 = c->g->i0;
+  const double dx = c->g->dx;
+  for (int j = 0; j <= nx; ++j) {
+    const int l = j - 1, r = j;
+    double dist, th_l, th_r, rho_l, rho_r, cp_l, cp_r, T_l, T_r, h_l, h_r;
+    if (j == nx) {   /* outflow: no diffusive flux */
+      for (int i = 0; i < N; ++i) {
+        F->G[(size_t)i * (nx + 1) + j] = 0.0;
+        F->gY[(size_t)i * (nx + 1) + j] = 0.0;
+        F->hf[(size_t)i * (nx + 1) + j] = hsp[(size_t)i * nx + nx - 1];
+      }
+      F->Q[j] = 0.0;
+      F->K[j] = 0.0;
+      F->Lc[j] = 0.0;
+      for (int i = 0; i < N; ++i) F->gh[(size_t)i * (nx + 1) + j] = 0.0;
+      continue;
+    }
+    if (j == 0) {    /* inflow: the boundary state half a cell away */
+      dist = 0.5 * dx;
+      rho_l = c->rho_in; T_l = c->T_in; h_l = c->h_in;
+      cp_l = mix_cp(m, c->g->Y_in, 1, c->T_in);
+    } else {
+      dist = dx;
+      rho_l = rho[l]; T_l = T[l]; h_l = h[l];
+      cp_l = mix_cp(m, Y + l, nx, T[l]);
+    }
+    rho_r = rho[r]; T_r = T[r]; h_r = h[r];
+    cp_r = mix_cp(m, Y + r, nx, T[r]);
+    th_l = lm_theta(m, T_l);
+    th_r = lm_theta(m, T_r);
+    /* on the inflow face the coefficients are those of the first cell */
+    const double a_l = (j == 0) ? rho_r * th_r : rho_l * th_l, a_r = rho_r * th_r;
+    const double hm = 2.0 * a_l * a_r / (a_l + a_r);   /* (rho theta) at the face */
+    const double lam_l = (j == 0) ? rho_r * cp_r * m->alpha0 * th_r : rho_l * cp_l * m->alpha0 * th_l;
+    const double lam_r = rho_r * cp_r * m->alpha0 * th_r;
+    F->Lc[j] = m->alpha0 * hm;
+    F->Q[j] = F->Lc[j] * (h_r - h_l) / dist;
+    F->K[j] = (2.0 * lam_l * lam_r / (lam_l + lam_r)) * (T_r - T_l) / dist;
+    double sum = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double yl = (j == 0) ? c->g->Y_in[i] : Y[(size_t)i * nx + l];
+      const double yr = Y[(size_t)i * nx + r];
+      const double g = (yr - yl) / dist;
+      F->gY[(size_t)i * (nx + 1) + j] = g;
+      const double hl = (j == 0) ? c->hsp_in[i] : hsp[(size_t)i * nx + l];
+      F->hf[(size_t)i * (nx + 1) + j] = 0.5 * (hl + hsp[(size_t)i * nx + r]);
+      F->gh[(size_t)i * (nx + 1) + j] = (hsp[(size_t)i * nx + r] - hl) / dist;
+      if (i == i0) continue;
+      const double v = m->D0[i] * hm * g;
+      F->G[(size_t)i * (nx + 1) + j] = v;
+      sum += v;
+    }
+    F->G[(size_t)i0 * (nx + 1) + j] = -sum;
+  }
+}
+
+/* Right-hand sides, S, velocity and thermodynamic pressure of a state
+ * q = [rho, rho Y_1..rho Y_N, rho h] ([N+2][nx]):
+ *  FA = explicit part: -div(U q) for every row, plus the differential
+ *       diffusion of h (eq. enthalpy_equation, explicit as in S4);
+ *  FD = implicit diffusion: div(rho D_i grad Y_i) for the species rows,
+ *       div(lambda/cp grad h) for h, 0 for rho;
+ *  FR = reaction: wdot_i for the species rows, 0 for rho and h;
+ *  S [nx] (eq. S_def), U [nx+1] from div U = S + dchi with U_0 = U_in (I4, S6;
+ *  dchi may be NULL), peos [nx] (eq. p_eos_definition), T [nx] in/out (guess). */
+int or_lm_terms(const or_mech *m, const or_lm_cfg *g, const double *q, const double *dchi,
+                const double *Uadv, double *FA, double *FD, double *FR, double *S, double *U,
+                double *peos, double *T) {
+  lm_ctx c;
+  lm_setup(&c, m, g);
+  const int nx = g->nx, N = m->N, F = N + 2;
+  const double dx = g->dx, inv = 1.0 / dx;
+  double *Y = vec(N * nx), *h = vec(nx), *hsp = vec(N * nx), *wd = vec(N);
+  double *Yc = vec(N);
+  lm_faces Fc;
+  Fc.G = vec(N * (nx + 1)); Fc.gY = vec(N * (nx + 1)); Fc.hf = vec(N * (nx + 1));
+  Fc.gh = vec(N * (nx + 1)); Fc.Q = vec(nx + 1); Fc.K = vec(nx + 1); Fc.Lc = vec(nx + 1);
+  int rc = lm_prims(&c, q, Y, h, T, T);
+  for (int k = 0; k < nx; ++k)
+    for (int i = 0; i < N; ++i) hsp[(size_t)i * nx + k] = or_species_h(m, i, T[k]);
+  lm_fluxes(&c, q, Y, h, T, hsp, &Fc);
+  /* diffusion, reaction and S per cell */
+  for (int k = 0; k < nx; ++k) {
+    const double rho = q[k];
+    for (int i = 0; i < N; ++i) Yc[i] = Y[(size_t)i * nx + k];
+    or_wdot(m, rho, Yc, T[k], wd, NULL);
+    double sw = 0.0;
+    for (int i = 0; i < N; ++i) sw += Yc[i] / m->W[i];
+    const double Wmix = 1.0 / sw, cp = mix_cp(m, Yc, 1, T[k]);
+    double s2 = 0.0, s3 = 0.0, ghl = 0.0, ghr = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double dY = (Fc.G[(size_t)i * (nx + 1) + k + 1] - Fc.G[(size_t)i * (nx + 1) + k]) * inv;
+      if (FD) FD[(size_t)(1 + i) * nx + k] = dY;
+      if (FR) FR[(size_t)(1 + i) * nx + k] = wd[i];
+      s2 += Wmix / m->W[i] * dY;
+      s3 += (Wmix / m->W[i] - hsp[(size_t)i * nx + k] / (cp * T[k])) * wd[i];
+      ghl += Fc.G[(size_t)i * (nx + 1) + k] * Fc.gh[(size_t)i * (nx + 1) + k];
+      ghr += Fc.G[(size_t)i * (nx + 1) + k + 1] * Fc.gh[(size_t)i * (nx + 1) + k + 1];
+    }
+    if (FD) {
+      FD[k] = 0.0;
+      FD[(size_t)(N + 1) * nx + k] = (Fc.Q[k + 1] - Fc.Q[k]) * inv;
+    }
+    if (FR) { FR[k] = 0.0; FR[(size_t)(N + 1) * nx + k] = 0.0; }
+    const double divK = (Fc.K[k + 1] - Fc.K[k]) * inv;
+    S[k] = (divK + 0.5 * (ghl + ghr)) / (rho * cp * T[k]) + s2 / rho + s3 / rho;
+    if (peos) peos[k] = rho * R_UNIV * T[k] * sw;
+  }
+  U[0] = g->U_in;
+  for (int k = 0; k < nx; ++k) U[k + 1] = U[k] + dx * (S[k] + (dchi ? dchi[k] : 0.0));
+  /* advection with the given face velocity (or the one just computed) and the
+   * explicit differential diffusion of h */
+  if (FA) {
+    const double *Ua = Uadv ? Uadv : U;
+    lm_advect(&c, Ua, q, c.rho_in, FA);
+    for (int i = 0; i < N; ++i)
+      lm_advect(&c, Ua, q + (size_t)(1 + i) * nx, c.rho_in * g->Y_in[i], FA + (size_t)(1 + i) * nx);
+    lm_advect(&c, Ua, q + (size_t)(N + 1) * nx, c.rho_in * c.h_in, FA + (size_t)(N + 1) * nx);
+    for (int k = 0; k < nx; ++k) {
+      double fl = 0.0, fr = 0.0;
+      for (int i = 0; i < N; ++i) {
+        const size_t a = (size_t)i * (nx + 1) + k, b = a + 1;
+        fl += Fc.hf[a] * (Fc.G[a] - Fc.Lc[k] * Fc.gY[a]);
+        fr += Fc.hf[b] * (Fc.G[b] - Fc.Lc[k + 1] * Fc.gY[b]);
+      }
+      FA[(size_t)(N + 1) * nx + k] += (fr - fl) * inv;
+    }
+  }
+  (void)F;
+  free(Y); free(h); free(hsp); free(wd); free(Yc);
+  free(Fc.G); free(Fc.gY); free(Fc.hf); free(Fc.gh); free(Fc.Q); free(Fc.K); free(Fc.Lc);
+  return rc;
+}

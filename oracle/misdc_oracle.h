@@ -146,6 +146,24 @@ int or_adr_step_ex(const or_mech *mech, const or_adr_cfg *cfg, int scheme, int M
                    or_adr_stats *stats);
 
 /* pieces, exposed for pins */
+/* ---- variable-density low-Mach coupling, 1D with open boundaries --------- */
+typedef struct or_lm_cfg {
+  int nx;
+  double dx;
+  double U_in;          /* velocity on the inflow face x = 0, m/s */
+  const double *Y_in;   /* [N] inflow mass fractions */
+  double T_in;          /* inflow temperature, K */
+  double p0;            /* ambient thermodynamic pressure, Pa */
+  int i0;               /* dominant species */
+  double newton_rtol;
+  int newton_maxit;
+  int dchi;             /* 1: the volume-discrepancy correction of S6 */
+} or_lm_cfg;
+
+int or_lm_terms(const or_mech *m, const or_lm_cfg *g, const double *q, const double *dchi,
+                const double *Uadv, double *FA, double *FD, double *FR, double *S, double *U,
+                double *peos, double *T);
+
 double or_species_h(const or_mech *m, int i, double T);     /* J/kg */
 double or_species_cp(const or_mech *m, int i, double T);    /* J/(kg K) */
 double or_species_s_R(const or_mech *m, int i, double T);   /* s/R (molar) */
