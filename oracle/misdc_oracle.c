@@ -1329,3 +1329,201 @@ int or_lm_terms(const or_mech *m, const or_lm_cfg *g, const double *q, const dou
   free(Fc.G); free(Fc.gY); free(Fc.hf); free(Fc.gh); free(Fc.Q); free(Fc.K); free(Fc.Lc);
   return rc;
 }
+
+/* (rho theta) on the faces of a state (the diffusion coefficient without its
+ * per-field factor D0_i or alpha0): harmonic means inside, the first cell's value
+ * on the inflow face, 0 on the outflow face (no diffusive flux) */
+static void lm_face_coef(const lm_ctx *c, const double *rho, const double *T, double *hm) {
+  const int nx = c->nx;
+  for (int j = 0; j <= nx; ++j) {
+    if (j == nx) { hm[j] = 0.0; continue; }
+    const double ar = rho[j] * lm_theta(c->m, T[j]);
+    if (j == 0) { hm[j] = ar; continue; }
+    const double al = rho[j - 1] * lm_theta(c->m, T[j - 1]);
+    hm[j] = 2.0 * al * ar / (al + ar);
+  }
+}
+
+/* rho_new x - w div(k grad x) = rhs on the open domain (inflow value xin on the
+ * inflow face, half a cell away; no flux through the outflow face), k = f0 hm;
+ * dense direct solve, then the flux-form reconstruction
+ * rho_new x := rhs + w div(k grad x) (returned in out, conserved exactly) */
+static int lm_solve_diff(const lm_ctx *c, double w, double f0, const double *hm, const double *rho_new,
+                         const double *rhs, double xin, double *x, double *out) {
+  const int nx = c->nx;
+  const double dx = c->g->dx;
+  double *A = vec(nx * nx);
+  for (int k = 0; k < nx; ++k) {
+    const double kl = f0 * hm[k] / ((k == 0 ? 0.5 : 1.0) * dx * dx);
+    const double kr = f0 * hm[k + 1] / (dx * dx);
+    A[k * nx + k] = rho_new[k] + w * (kl + kr);
+    if (k > 0) A[k * nx + k - 1] = -w * kl;
+    if (k + 1 < nx) A[k * nx + k + 1] = -w * kr;
+    x[k] = rhs[k] + (k == 0 ? w * kl * xin : 0.0);
+  }
+  int rc = dense_solve(nx, A, x);
+  free(A);
+  for (int k = 0; k < nx; ++k) {
+    const double fl = f0 * hm[k] * (x[k] - (k == 0 ? xin : x[k - 1])) / ((k == 0 ? 0.5 : 1.0) * dx);
+    const double fr = (k + 1 < nx) ? f0 * hm[k + 1] * (x[k + 1] - x[k]) / dx : 0.0;
+    out[k] = rhs[k] + w * (fr - fl) / dx;
+  }
+  return rc;
+}
+
+/* One time step of CISDCQ-nu (eqs. update_equation_amisdcq_discrete_form_D and
+ * _R_alt, I1-I4, S1-S7) on the low-Mach system: per node, S2 (the density row of
+ * the D update, advection only), S3 and S4 (species and enthalpy diffusion solved
+ * against the new density with coefficients lagged as in eq.
+ * lagged_diffusion_flux; the differential diffusion explicit), S5 (reaction
+ * Newton at the new density, enthalpy fixed), S6 (delta_chi increment and the
+ * velocity from div U = S + delta_chi). Readings beyond the periodic scheme's:
+ * the lag source of iteration 0 at node m is the node's advection-diffusion
+ * state with the velocity of its own S and the current delta_chi; delta_chi of
+ * a sweep starts from the previous sweep's (as S6 writes it).
+ * q_n, q_out: [N+2][nx]; incr[k] (may be NULL): max over cells of
+ * |rho h^{M,(k+1)} - rho h^{M,(k)}| / max |rho h^{M,(k+1)}|; peos_out [nx] (may
+ * be NULL): p_EOS of the result. */
+int or_lm_step(const or_mech *m, const or_lm_cfg *g, int M, int n_sweeps, int nu, double dt,
+               const double *q_n, double *q_out, double *incr, double *peos_out) {
+  sweep_tables Tb;
+  Tb.M = M;
+  if (or_lobatto(M, Tb.tau, Tb.Q, Tb.S, Tb.QI, Tb.QE)) return 1;
+  lm_ctx c;
+  lm_setup(&c, m, g);
+  const int nx = g->nx, N = m->N, F = N + 2, n = F * nx, i0 = g->i0;
+  int rc = 0;
+  enum { KS = 0, XS = 1, CS = 2 };   /* sweep k, iteration l, iteration l+1 */
+  double *q[3][17], *FA[3][17], *FD[3][17], *FR[3][17], *Tn[3][17], *dch[3][17];
+  for (int s = 0; s < 3; ++s)
+    for (int j = 0; j <= M; ++j) {
+      q[s][j] = vec(n); FA[s][j] = vec(n); FD[s][j] = vec(n); FR[s][j] = vec(n);
+      Tn[s][j] = vec(nx); dch[s][j] = vec(nx);
+    }
+  double *qad = vec(n), *lagA = vec(n), *lagD = vec(n), *rhs = vec(n), *b = vec(n);
+  double *S = vec(nx), *U = vec(nx + 1), *pe = vec(nx), *Tad = vec(nx), *hm = vec(nx + 1);
+  double *xs = vec(nx), *ys = vec(nx), *Yc = vec(N + 1), *bc = vec(N);
+  /* I1, I2, I4: every node holds q^n, its terms and the velocity of S^n */
+  for (int k = 0; k < nx; ++k) Tn[KS][0][k] = 1000.0;
+  rc |= or_lm_terms(m, g, q_n, NULL, NULL, FA[KS][0], FD[KS][0], FR[KS][0], S, U, pe, Tn[KS][0]);
+  for (int s = 0; s < 3; ++s)   /* node 0 is fixed: the same in every set */
+    for (int j = 0; j <= M; ++j) {
+      if (s != KS && j != 0) continue;
+      memcpy(q[s][j], q_n, sizeof(double) * n);
+      if (s == KS && j == 0) continue;
+      memcpy(FA[s][j], FA[KS][0], sizeof(double) * n);
+      memcpy(FD[s][j], FD[KS][0], sizeof(double) * n);
+      memcpy(FR[s][j], FR[KS][0], sizeof(double) * n);
+      memcpy(Tn[s][j], Tn[KS][0], sizeof(double) * nx);
+    }
+  int sK = KS, sX = XS, sC = CS;
+  for (int kk = 0; kk < n_sweeps && !rc; ++kk) {
+    for (int l = 0; l < nu && !rc; ++l) {
+      for (int mm = 0; mm < M && !rc; ++mm) {
+        const int t = mm + 1;
+        const double w = dt * QIW(&Tb, t, t), dtm = dt * (Tb.tau[t] - Tb.tau[mm]);
+        /* right-hand side of the D update (generic CISDCQ form on q) */
+        memcpy(rhs, q_n, sizeof(double) * n);
+        for (int j = 0; j <= M; ++j) {
+          const double qw = dt * QW(&Tb, t, j);
+          axpy(n, qw, FA[sK][j], rhs); axpy(n, qw, FD[sK][j], rhs); axpy(n, qw, FR[sK][j], rhs);
+        }
+        for (int j = 1; j <= mm - 1; ++j)
+          for (int i = 0; i < n; ++i)
+            rhs[i] += dt * QEW(&Tb, t, j) * (FA[sC][j][i] - FA[sK][j][i]) +
+                      dt * QIW(&Tb, t, j) * (FD[sC][j][i] - FD[sK][j][i] + FR[sC][j][i] - FR[sK][j][i]);
+        const double *lA = NULL, *lD = NULL, *lRm = NULL;
+        if (mm >= 1) {
+          lA = (l == 0) ? lagA : FA[sX][mm];
+          lD = (l == 0) ? lagD : FD[sX][mm];
+          lRm = (l == 0) ? FR[sK][mm] : FR[sX][mm];
+          for (int i = 0; i < n; ++i)
+            rhs[i] += dt * QEW(&Tb, t, mm) * (lA[i] - FA[sK][mm][i]) +
+                      dt * QIW(&Tb, t, mm) * (lD[i] - FD[sK][mm][i] + lRm[i] - FR[sK][mm][i]);
+        }
+        const double *lRt = (l == 0) ? FR[sK][t] : FR[sX][t];
+        for (int i = 0; i < n; ++i) rhs[i] += w * (-FD[sK][t][i] + lRt[i] - FR[sK][t][i]);
+        /* S2: the density row has no diffusion or reaction */
+        memcpy(qad, rhs, sizeof(double) * nx);
+        /* S3, S4: diffusion against rho_new, coefficients lagged (eq.
+         * lagged_diffusion_flux: sweep k at l = 0, iteration l otherwise) */
+        const double *qc = (l == 0) ? q[sK][t] : q[sX][t];
+        const double *Tc = (l == 0) ? Tn[sK][t] : Tn[sX][t];
+        lm_face_coef(&c, qc, Tc, hm);
+        double *rhoY0 = qad + (size_t)(1 + i0) * nx;
+        for (int k = 0; k < nx; ++k) rhoY0[k] = qad[k];
+        for (int i = 0; i < N; ++i) {
+          if (i == i0) continue;
+          rc |= lm_solve_diff(&c, w, m->D0[i], hm, qad, rhs + (size_t)(1 + i) * nx, g->Y_in[i], xs,
+                              qad + (size_t)(1 + i) * nx);
+          for (int k = 0; k < nx; ++k) rhoY0[k] -= qad[(size_t)(1 + i) * nx + k];
+        }
+        rc |= lm_solve_diff(&c, w, m->alpha0, hm, qad, rhs + (size_t)(N + 1) * nx, c.h_in, xs,
+                            qad + (size_t)(N + 1) * nx);
+        /* S5: rho_new Y - w wdot(Y) = b (R_alt form), enthalpy fixed */
+        memcpy(b, qad, sizeof(double) * n);
+        if (mm >= 1)
+          for (int i = 0; i < n; ++i) b[i] += dt * QIW(&Tb, t, mm) * (FR[sC][mm][i] - lRm[i]);
+        for (int i = 0; i < n; ++i) b[i] -= w * lRt[i];
+        const double *qg = (l == 0) ? q[sK][t] : q[sX][t];
+        const double *Tg = (l == 0) ? Tn[sK][t] : Tn[sX][t];
+        double *qn = q[sC][t];
+        for (int k = 0; k < nx && !rc; ++k) {
+          const double rho = qad[k];
+          for (int i = 0; i < N; ++i) {
+            Yc[i] = qg[(size_t)(1 + i) * nx + k] / qg[k];
+            bc[i] = b[(size_t)(1 + i) * nx + k] / rho;
+          }
+          Yc[N] = Tg[k];
+          const double hst = qad[(size_t)(N + 1) * nx + k] / rho;
+          int it = or_reaction_newton(m, rho, w, bc, hst, Yc, g->newton_rtol, g->newton_maxit);
+          if (it < 0) rc |= 2;
+          qn[k] = rho;
+          for (int i = 0; i < N; ++i) {
+            qn[(size_t)(1 + i) * nx + k] = rho * Yc[i];
+            FR[sC][t][(size_t)(1 + i) * nx + k] = (rho * Yc[i] - b[(size_t)(1 + i) * nx + k]) / w;
+          }
+          FR[sC][t][k] = 0.0;
+          FR[sC][t][(size_t)(N + 1) * nx + k] = 0.0;
+          qn[(size_t)(N + 1) * nx + k] = qad[(size_t)(N + 1) * nx + k];
+          Tn[sC][t][k] = Yc[N];
+        }
+        /* S6: delta_chi from the thermodynamic-pressure discrepancy, velocity and
+         * the advection / diffusion terms at the new state */
+        for (int k = 0; k < nx; ++k) Tad[k] = Tn[sC][t][k];
+        rc |= or_lm_terms(m, g, qn, NULL, NULL, NULL, NULL, NULL, S, U, pe, Tad);
+        for (int k = 0; k < nx; ++k)
+          dch[sC][t][k] = g->dchi ? dch[sK][t][k] + 2.0 / g->p0 * (pe[k] - g->p0) / dtm : 0.0;
+        rc |= or_lm_terms(m, g, qn, dch[sC][t], NULL, FA[sC][t], FD[sC][t], NULL, S, U, pe, Tn[sC][t]);
+        if (l == 0 && t < M) {   /* S4: lag source of the next node */
+          for (int k = 0; k < nx; ++k) Tad[k] = Tn[sC][t][k];
+          rc |= or_lm_terms(m, g, qad, dch[sC][t], NULL, lagA, lagD, NULL, S, U, pe, Tad);
+        }
+      }
+      const int tmp = sX; sX = sC; sC = tmp;   /* iteration l+1 becomes the lag source */
+    }
+    /* S7 and the sweep increment of rho h at node M */
+    if (incr) {
+      double dm = 0.0, sm = 0.0;
+      for (int k = 0; k < nx; ++k) {
+        const double a = q[sX][M][(size_t)(N + 1) * nx + k], bb = q[sK][M][(size_t)(N + 1) * nx + k];
+        dm = fmax(dm, fabs(a - bb));
+        sm = fmax(sm, fabs(a));
+      }
+      incr[kk] = sm > 0.0 ? dm / sm : 0.0;
+    }
+    const int old = sK; sK = sX; sX = old;
+  }
+  memcpy(q_out, q[sK][M], sizeof(double) * n);
+  if (peos_out) {
+    for (int k = 0; k < nx; ++k) Tad[k] = Tn[sK][M][k];
+    rc |= or_lm_terms(m, g, q_out, NULL, NULL, NULL, NULL, NULL, S, U, peos_out, Tad);
+  }
+  for (int s = 0; s < 3; ++s)
+    for (int j = 0; j <= M; ++j) {
+      free(q[s][j]); free(FA[s][j]); free(FD[s][j]); free(FR[s][j]); free(Tn[s][j]); free(dch[s][j]);
+    }
+  free(qad); free(lagA); free(lagD); free(rhs); free(b); free(S); free(U); free(pe); free(Tad); free(hm);
+  free(xs); free(ys); free(Yc); free(bc);
+  return rc;
+}

@@ -84,3 +84,100 @@ def test_velocity_integrates_the_constraint(inert):
     assert U[0] == 0.5
     np.testing.assert_allclose(np.diff(U) / (L_DOMAIN / nx), S + dchi, rtol=1e-12, atol=1e-9)
     assert np.sum(S) > 0.0
+
+
+def test_uniform_state_is_steady_through_a_step(inert):
+    """A full CISDCQ step (S2-S6) keeps the inert inflow state unchanged."""
+    _, Yu, _ = inert
+    mech = I.make_mechanism(1801, 9, 21, logA_range=(-30.0, -29.0))
+    nx = 32
+    lm = O.LowMach(mech, nx, L_DOMAIN / nx, 0.5, Yu, 300.0)
+    q0 = lm.state_from_YT(np.repeat(Yu[:, None], nx, axis=1), np.full(nx, 300.0))
+    q1, pe = lm.step(q0, 1e-5, n_sweeps=3, nu=2)
+    assert np.max(np.abs(q1 - q0) / np.abs(q0).max(axis=1, keepdims=True)) < 1e-14
+    assert np.max(np.abs(pe / 101325.0 - 1.0)) < 1e-14
+
+
+def _front_inert(Yu, Yb, dchi):
+    mech = I.make_mechanism(1801, 9, 21, logA_range=(-30.0, -29.0))
+    nx = 32
+    lm = O.LowMach(mech, nx, L_DOMAIN / nx, 0.5, Yu, 300.0, dchi=dchi)
+    x = (np.arange(nx) + 0.5) * L_DOMAIN / nx
+    s = 0.5 * (1 + np.tanh((x - L_DOMAIN / 2) / (L_DOMAIN / 16)))
+    return lm, lm.state_from_YT(Yu[:, None] * (1 - s) + Yb[:, None] * s, 300 + 1700 * s)
+
+
+def test_each_sweep_adds_one_order_without_the_correction(inert):
+    """Without delta_chi (S6 solves div U = S), 1-4 sweeps give temporal orders
+    1-4 on a front with variable density and velocity (against 8 sweeps at 1/8
+    of the smallest step)."""
+    _, Yu, Yb = inert
+    lm, q = _front_inert(Yu, Yb, dchi=False)
+    t_end = 2e-5
+    ref, _ = lm.step(q, t_end / 64, n_sweeps=8, nu=2, n_steps=64)
+    for sweeps in (1, 2, 3, 4):
+        err = []
+        for k in (2, 4, 8):
+            got, _ = lm.step(q, t_end / k, n_sweeps=sweeps, nu=2, n_steps=k)
+            err.append(np.max(np.abs(got[-1] - ref[-1])) / np.max(np.abs(ref[-1])))
+        orders = [np.log2(err[i] / err[i + 1]) for i in range(2)]
+        assert all(abs(o - sweeps) < 0.25 for o in orders), (sweeps, err, orders)
+
+
+def test_correction_drives_the_thermodynamic_pressure_to_p0(inert):
+    """S6: with delta_chi the sweeps drive p_EOS to p0 (2 -> 16 sweeps: more than
+    1e5 times closer); without it p_EOS drifts by the discretisation error."""
+    _, Yu, Yb = inert
+    lm, q = _front_inert(Yu, Yb, dchi=True)
+    dev = []
+    for sweeps in (2, 8, 16):
+        _, pe = lm.step(q, 5e-6, n_sweeps=sweeps, nu=2, n_steps=2)
+        dev.append(np.max(np.abs(pe / 101325.0 - 1.0)))
+    assert dev[0] > 30 * dev[1] > 30 * 30 * dev[2] and dev[2] < 1e-11, dev
+    lm0, q0 = _front_inert(Yu, Yb, dchi=False)
+    _, pe0 = lm0.step(q0, 5e-6, n_sweeps=16, nu=2, n_steps=2)
+    assert np.max(np.abs(pe0 / 101325.0 - 1.0)) > 1e4 * dev[2]
+
+
+@pytest.mark.parametrize("dchi,bounds", [(False, (2e-10, 2e-11)), (True, (1e-8, 5e-10))])
+def test_uniform_reacting_mixture_is_a_constant_pressure_reactor(inert, dchi, bounds):
+    """A uniform reacting mixture (no inflow through the inflow face: U_in = 0)
+    must follow the textbook constant-pressure adiabatic reactor, dY/dt =
+    wdot(rho, Y, T)/rho with h fixed and rho = p0 W/(R T): in the low-Mach system
+    that takes S (its reaction term), the velocity it induces, the density
+    advection and delta_chi together. Reference: scipy's BDF at rtol 1e-12 on
+    the reactor ODE; cells next to the inflow face (whose Dirichlet state keeps
+    diffusing in) are left out. delta_chi adds the error of its own unconverged
+    iteration; without it the match is closer, and a missing S term shows at once."""
+    from scipy.integrate import solve_ivp
+    _, Yu, _ = inert
+    mech = I.make_mechanism(1801, 9, 21, logA_range=(3.0, 5.0))
+    N, W, p0, T0, nx = mech.n_species, np.asarray(mech.W), 101325.0, 1000.0, 24
+    lm = O.LowMach(mech, nx, 2e-4, 0.0, Yu, T0, dchi=dchi)
+    q0 = lm.state_from_YT(np.repeat(Yu[:, None], nx, axis=1), np.full(nx, T0))
+    h0 = q0[N + 1, 0] / q0[0, 0]
+
+    def temp(Y):
+        T = np.zeros(1)
+        O.lib().or_T_from_h(C.byref(lm.m), 1, O._p(np.ascontiguousarray(Y)), O._p(np.array([h0])), O._p(T))
+        return T[0]
+
+    def rhs(t, Y):
+        T = temp(Y)
+        rho = p0 / (O.R_U * T * np.sum(Y / W))
+        w = np.zeros(N)
+        O.lib().or_wdot(C.byref(lm.m), rho, O._p(np.ascontiguousarray(Y)), T, O._p(w), None)
+        return w / rho
+
+    t_end = 6e-8
+    sol = solve_ivp(rhs, (0.0, t_end), Yu.copy(), method="BDF", rtol=1e-12, atol=1e-15)
+    Yref = sol.y[:, -1]
+    assert np.max(np.abs(Yref - Yu)) > 1e-2   # the mixture reacts noticeably
+    rho_ref = p0 / (O.R_U * temp(Yref) * np.sum(Yref / W))
+    errs = []
+    for n_steps, sweeps in ((8, 6), (16, 8)):
+        q, pe = lm.step(q0, t_end / n_steps, n_sweeps=sweeps, nu=2, n_steps=n_steps)
+        Y = q[1:N + 1] / q[0]
+        errs.append(max(np.max(np.abs(Y[:, 6:] - Yref[:, None])) / np.max(Yref),
+                        np.max(np.abs(q[0, 6:] / rho_ref - 1.0))))
+    assert errs[0] < bounds[0] and errs[1] < bounds[1], errs
