@@ -15,7 +15,11 @@
  *     update_equation_amisdcq_discrete_form_D/R/R_alt,
  *     initial_lagged_values_A/D/R)
  *  - problems: linear model ODE (Sec. 4), nonlinear test PDE (Sec. 5.2),
- *    low-Mach species/enthalpy ADR with prescribed velocity (Sec. 2, 3.3)
+ *    low-Mach species/enthalpy ADR with prescribed velocity (Sec. 2, 3.3),
+ *    and the 1D variable-density low-Mach system with open boundaries, the
+ *    velocity from the divergence constraint and the volume-discrepancy
+ *    correction (Sec. 2, eqs. divergence_constraint and S_def; Sec. 3.3 I3,
+ *    I4, S2-S6)
  */
 #ifndef MISDC_ORACLE_H
 #define MISDC_ORACLE_H
