@@ -107,6 +107,7 @@ def _declare(L):
     L.or_adr_solve_diff.argtypes = [C.POINTER(Mech), C.POINTER(AdrCfg), C.c_double, dp, dp, dp]
     L.or_lm_terms.argtypes = [C.POINTER(Mech), C.POINTER(LmCfg), dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
     L.or_lm_step.argtypes = [C.POINTER(Mech), C.POINTER(LmCfg), C.c_int, C.c_int, C.c_int, C.c_double, dp, dp, dp, dp]
+    L.or_lm_step_ex.argtypes = [C.POINTER(Mech), C.POINTER(LmCfg), C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp, dp, dp, dp]
 
 
 def _p(a):
@@ -331,15 +332,16 @@ class LowMach:
             raise RuntimeError("temperature diagnosis failed")
         return FA, FD, FR, S, U, pe, T
 
-    def step(self, q, dt, M=2, n_sweeps=4, nu=2, n_steps=1, incr_out=None):
-        """Advance q by n_steps CISDCQ-nu steps (or_lm_step); returns (q, p_eos)."""
+    def step(self, q, dt, M=2, n_sweeps=4, nu=2, n_steps=1, incr_out=None, scheme="CISDCQ"):
+        """Advance q by n_steps steps of CISDCQ-nu or MISDCQ (or_lm_step_ex); returns
+        (q, p_eos)."""
         q = _f64(q).copy()
         out = np.zeros_like(q)
         pe = np.zeros(self.nx)
         for _ in range(n_steps):
             incr = np.zeros(max(n_sweeps, 1))
-            rc = lib().or_lm_step(C.byref(self.m), C.byref(self.cfg), M, n_sweeps, nu, dt, _p(q), _p(out),
-                                  _p(incr), _p(pe))
+            rc = lib().or_lm_step_ex(C.byref(self.m), C.byref(self.cfg), SCHEMES.get(scheme, scheme), M,
+                                     n_sweeps, nu, dt, _p(q), _p(out), _p(incr), _p(pe))
             if incr_out is not None:
                 incr_out.append(incr[:n_sweeps].copy())
             if rc:

@@ -1386,6 +1386,18 @@ static int lm_solve_diff(const lm_ctx *c, double w, double f0, const double *hm,
  * be NULL): p_EOS of the result. */
 int or_lm_step(const or_mech *m, const or_lm_cfg *g, int M, int n_sweeps, int nu, double dt,
                const double *q_n, double *q_out, double *incr, double *peos_out) {
+  return or_lm_step_ex(m, g, OR_CISDCQ, M, n_sweeps, nu, dt, q_n, q_out, incr, peos_out);
+}
+
+/* scheme OR_CISDCQ as above, or OR_MISDCQ: the serial sweep of eqs.
+ * update_equation_misdcq_discrete_form_D/_R on the same system (one pass per
+ * sweep, nu ignored), whose D update takes the new values of nodes 1..m and no
+ * reaction correction, and whose R update corrects the reaction terms of nodes
+ * 1..m+1 */
+int or_lm_step_ex(const or_mech *m, const or_lm_cfg *g, int scheme, int M, int n_sweeps, int nu,
+                  double dt, const double *q_n, double *q_out, double *incr, double *peos_out) {
+  if (scheme != OR_CISDCQ && scheme != OR_MISDCQ) return 1;
+  if (scheme == OR_MISDCQ) nu = 1;
   sweep_tables Tb;
   Tb.M = M;
   if (or_lobatto(M, Tb.tau, Tb.Q, Tb.S, Tb.QI, Tb.QE)) return 1;
@@ -1428,12 +1440,19 @@ int or_lm_step(const or_mech *m, const or_lm_cfg *g, int M, int n_sweeps, int nu
           const double qw = dt * QW(&Tb, t, j);
           axpy(n, qw, FA[sK][j], rhs); axpy(n, qw, FD[sK][j], rhs); axpy(n, qw, FR[sK][j], rhs);
         }
-        for (int j = 1; j <= mm - 1; ++j)
+        if (scheme == OR_MISDCQ) {
+          for (int j = 1; j <= mm; ++j)
+            for (int i = 0; i < n; ++i)
+              rhs[i] += dt * QEW(&Tb, t, j) * (FA[sC][j][i] - FA[sK][j][i]) +
+                        dt * QIW(&Tb, t, j) * (FD[sC][j][i] - FD[sK][j][i]);
+          for (int i = 0; i < n; ++i) rhs[i] -= w * FD[sK][t][i];
+        }
+        for (int j = 1; j <= mm - 1 && scheme == OR_CISDCQ; ++j)
           for (int i = 0; i < n; ++i)
             rhs[i] += dt * QEW(&Tb, t, j) * (FA[sC][j][i] - FA[sK][j][i]) +
                       dt * QIW(&Tb, t, j) * (FD[sC][j][i] - FD[sK][j][i] + FR[sC][j][i] - FR[sK][j][i]);
         const double *lA = NULL, *lD = NULL, *lRm = NULL;
-        if (mm >= 1) {
+        if (mm >= 1 && scheme == OR_CISDCQ) {
           lA = (l == 0) ? lagA : FA[sX][mm];
           lD = (l == 0) ? lagD : FD[sX][mm];
           lRm = (l == 0) ? FR[sK][mm] : FR[sX][mm];
@@ -1442,7 +1461,8 @@ int or_lm_step(const or_mech *m, const or_lm_cfg *g, int M, int n_sweeps, int nu
                       dt * QIW(&Tb, t, mm) * (lD[i] - FD[sK][mm][i] + lRm[i] - FR[sK][mm][i]);
         }
         const double *lRt = (l == 0) ? FR[sK][t] : FR[sX][t];
-        for (int i = 0; i < n; ++i) rhs[i] += w * (-FD[sK][t][i] + lRt[i] - FR[sK][t][i]);
+        if (scheme == OR_CISDCQ)
+          for (int i = 0; i < n; ++i) rhs[i] += w * (-FD[sK][t][i] + lRt[i] - FR[sK][t][i]);
         /* S2: the density row has no diffusion or reaction */
         memcpy(qad, rhs, sizeof(double) * nx);
         /* S3, S4: diffusion against rho_new, coefficients lagged (eq.
@@ -1462,8 +1482,12 @@ int or_lm_step(const or_mech *m, const or_lm_cfg *g, int M, int n_sweeps, int nu
                             qad + (size_t)(N + 1) * nx);
         /* S5: rho_new Y - w wdot(Y) = b (R_alt form), enthalpy fixed */
         memcpy(b, qad, sizeof(double) * n);
-        if (mm >= 1)
+        if (scheme == OR_MISDCQ) {
+          for (int j = 1; j <= mm; ++j)
+            for (int i = 0; i < n; ++i) b[i] += dt * QIW(&Tb, t, j) * (FR[sC][j][i] - FR[sK][j][i]);
+        } else if (mm >= 1) {
           for (int i = 0; i < n; ++i) b[i] += dt * QIW(&Tb, t, mm) * (FR[sC][mm][i] - lRm[i]);
+        }
         for (int i = 0; i < n; ++i) b[i] -= w * lRt[i];
         const double *qg = (l == 0) ? q[sK][t] : q[sX][t];
         const double *Tg = (l == 0) ? Tn[sK][t] : Tn[sX][t];
@@ -1495,7 +1519,7 @@ int or_lm_step(const or_mech *m, const or_lm_cfg *g, int M, int n_sweeps, int nu
         for (int k = 0; k < nx; ++k)
           dch[sC][t][k] = g->dchi ? dch[sK][t][k] + 2.0 / g->p0 * (pe[k] - g->p0) / dtm : 0.0;
         rc |= or_lm_terms(m, g, qn, dch[sC][t], NULL, FA[sC][t], FD[sC][t], NULL, S, U, pe, Tn[sC][t]);
-        if (l == 0 && t < M) {   /* S4: lag source of the next node */
+        if (l == 0 && t < M && scheme == OR_CISDCQ) {   /* S4: lag source of the next node */
           for (int k = 0; k < nx; ++k) Tad[k] = Tn[sC][t][k];
           rc |= or_lm_terms(m, g, qad, dch[sC][t], NULL, lagA, lagD, NULL, S, U, pe, Tad);
         }

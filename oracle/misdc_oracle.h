@@ -169,6 +169,8 @@ int or_lm_terms(const or_mech *m, const or_lm_cfg *g, const double *q, const dou
                 double *peos, double *T);
 int or_lm_step(const or_mech *m, const or_lm_cfg *g, int M, int n_sweeps, int nu, double dt,
                const double *q_n, double *q_out, double *incr, double *peos_out);
+int or_lm_step_ex(const or_mech *m, const or_lm_cfg *g, int scheme, int M, int n_sweeps, int nu,
+                  double dt, const double *q_n, double *q_out, double *incr, double *peos_out);
 
 double or_species_h(const or_mech *m, int i, double T);     /* J/kg */
 double or_species_cp(const or_mech *m, int i, double T);    /* J/(kg K) */

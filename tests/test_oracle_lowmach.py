@@ -107,10 +107,11 @@ def _front_inert(Yu, Yb, dchi):
     return lm, lm.state_from_YT(Yu[:, None] * (1 - s) + Yb[:, None] * s, 300 + 1700 * s)
 
 
-def test_each_sweep_adds_one_order_without_the_correction(inert):
+@pytest.mark.parametrize("scheme", ["CISDCQ", "MISDCQ"])
+def test_each_sweep_adds_one_order_without_the_correction(inert, scheme):
     """Without delta_chi (S6 solves div U = S), 1-4 sweeps give temporal orders
-    1-4 on a front with variable density and velocity (against 8 sweeps at 1/8
-    of the smallest step)."""
+    1-4 on a front with variable density and velocity (against 8 CISDCQ sweeps
+    at 1/8 of the smallest step), for the concurrent and the serial scheme."""
     _, Yu, Yb = inert
     lm, q = _front_inert(Yu, Yb, dchi=False)
     t_end = 2e-5
@@ -118,7 +119,7 @@ def test_each_sweep_adds_one_order_without_the_correction(inert):
     for sweeps in (1, 2, 3, 4):
         err = []
         for k in (2, 4, 8):
-            got, _ = lm.step(q, t_end / k, n_sweeps=sweeps, nu=2, n_steps=k)
+            got, _ = lm.step(q, t_end / k, n_sweeps=sweeps, nu=2, n_steps=k, scheme=scheme)
             err.append(np.max(np.abs(got[-1] - ref[-1])) / np.max(np.abs(ref[-1])))
         orders = [np.log2(err[i] / err[i + 1]) for i in range(2)]
         assert all(abs(o - sweeps) < 0.25 for o in orders), (sweeps, err, orders)
@@ -181,3 +182,14 @@ def test_uniform_reacting_mixture_is_a_constant_pressure_reactor(inert, dchi, bo
         errs.append(max(np.max(np.abs(Y[:, 6:] - Yref[:, None])) / np.max(Yref),
                         np.max(np.abs(q[0, 6:] / rho_ref - 1.0))))
     assert errs[0] < bounds[0] and errs[1] < bounds[1], errs
+
+
+@pytest.mark.parametrize("dchi", [False, True])
+def test_serial_and_concurrent_sweeps_share_the_fixed_point(inert, dchi):
+    """MISDCQ and CISDCQ-2 iterate to the same solution of the node equations (the
+    collocation solution; with delta_chi, the one whose nodes satisfy the EOS)."""
+    _, Yu, Yb = inert
+    lm, q = _front_inert(Yu, Yb, dchi=dchi)
+    a, _ = lm.step(q, 1e-5, n_sweeps=30, nu=2, scheme="CISDCQ")
+    b, _ = lm.step(q, 1e-5, n_sweeps=30, scheme="MISDCQ")
+    assert np.max(np.abs(a - b) / np.abs(a).max(axis=1, keepdims=True)) < 1e-12
