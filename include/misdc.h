@@ -139,6 +139,9 @@ typedef struct misdc_stats {
   long long newton_stored_steps; /* mixed precision: uncertified solves whose first
                                     chord step came from the stored reaction term
                                     (iteration 1 without a rate evaluation) */
+  long long newton_floor_stops;  /* exact (FP64) Newton solves that stopped on the
+                                    round-off-floor test: step d <= 1e-8 that no longer
+                                    halves, while still above newton_rtol */
 } misdc_stats;
 
 typedef struct misdc_solver misdc_solver;

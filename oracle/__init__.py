@@ -71,7 +71,7 @@ class NuRule(C.Structure):
 class AdrStats(C.Structure):
     _fields_ = [("newton_solves", C.c_long), ("newton_iters", C.c_long), ("newton_fail", C.c_long),
                 ("newton_maxit_seen", C.c_long), ("lin_solves", C.c_long), ("lin_iters", C.c_long),
-                ("lin_fail", C.c_long), ("tdiag_fail", C.c_long)]
+                ("lin_fail", C.c_long), ("tdiag_fail", C.c_long), ("newton_floor", C.c_long)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,6 +103,8 @@ def _declare(L):
     L.or_wdot_jac.argtypes = [C.POINTER(Mech), C.c_double, dp, C.c_double, dp]
     L.or_reaction_newton.argtypes = [C.POINTER(Mech), C.c_double, C.c_double, dp, C.c_double, dp,
                                      C.c_double, C.c_int]
+    L.or_reaction_newton_ex.argtypes = [C.POINTER(Mech), C.c_double, C.c_double, dp, C.c_double, dp,
+                                        C.c_double, C.c_int, C.POINTER(C.c_int)]
     L.or_adr_operators.argtypes = [C.POINTER(Mech), C.POINTER(AdrCfg), dp, dp, dp, dp]
     L.or_adr_solve_diff.argtypes = [C.POINTER(Mech), C.POINTER(AdrCfg), C.c_double, dp, dp, dp]
     L.or_lm_terms.argtypes = [C.POINTER(Mech), C.POINTER(LmCfg), dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -229,11 +231,16 @@ class ADR:
         lib().or_wdot_jac(C.byref(self.m), self.flame.rho if rho is None else rho, _p(Y), T, _p(J))
         return J
 
-    def reaction_newton(self, wdt, b, hstar, x0, rtol=1e-12, maxit=50, rho=None):
+    def reaction_newton(self, wdt, b, hstar, x0, rtol=1e-12, maxit=50, rho=None, floor_out=None):
+        """Reaction step S5 of one cell; floor_out (a list) receives 1 when the
+        solve ended on the round-off-floor test, else 0."""
         x = _f64(x0).copy()
         b = _f64(b)
-        it = lib().or_reaction_newton(C.byref(self.m), self.flame.rho if rho is None else rho, wdt,
-                                      _p(b), hstar, _p(x), rtol, maxit)
+        fl = C.c_int(0)
+        it = lib().or_reaction_newton_ex(C.byref(self.m), self.flame.rho if rho is None else rho, wdt,
+                                         _p(b), hstar, _p(x), rtol, maxit, C.byref(fl))
+        if floor_out is not None:
+            floor_out.append(fl.value)
         return x, it
 
     # operators ----------------------------------------------------------

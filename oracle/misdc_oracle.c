@@ -826,7 +826,15 @@ void or_wdot_jac(const or_mech *m, double rho, const double *Y, double T, double
  * the step can no longer fall below rtol. */
 int or_reaction_newton(const or_mech *m, double rho, double wdt, const double *b,
                        double hstar, double *x, double rtol, int maxit) {
+  return or_reaction_newton_ex(m, rho, wdt, b, hstar, x, rtol, maxit, NULL);
+}
+
+/* The same solve; *floor_stop (if given) is set to 1 when it ended on the
+ * round-off-floor test (the last step above rtol), else 0. */
+int or_reaction_newton_ex(const or_mech *m, double rho, double wdt, const double *b,
+                          double hstar, double *x, double rtol, int maxit, int *floor_stop) {
   int N = m->N, n = N + 1;
+  if (floor_stop) *floor_stop = 0;
   double J[64 * 64], Jw[64 * 65], r[64], wd[64];   /* n <= 64 */
   if (n > 64) return -1;
   double dprev = INFINITY;
@@ -850,7 +858,11 @@ int or_reaction_newton(const or_mech *m, double rho, double wdt, const double *b
     double d = fabs(r[N]) / x[N];
     if (dmax > d) d = dmax;
     if (!isfinite(d)) return -3;
-    if (d <= rtol || (d <= 1e-8 && d >= 0.5 * dprev)) return it;
+    if (d <= rtol) return it;
+    if (d <= 1e-8 && d >= 0.5 * dprev) {
+      if (floor_stop) *floor_stop = 1;
+      return it;
+    }
     dprev = d;
   }
   return -4;
@@ -1052,9 +1064,12 @@ static int adr_sr(void *cv, double wdt, const double *b, const double *guess, do
     for (int i = 0; i < N; ++i) { xx[i] = guess[(size_t)i * C + c]; bb[i] = b[(size_t)i * C + c]; }
     xx[N] = Tg[c];
     double hstar = b[(size_t)N * C + c];
-    int it = or_reaction_newton(a->m, g->rho, wdt, bb, hstar, xx, g->newton_rtol, g->newton_maxit);
+    int floor_stop = 0;
+    int it = or_reaction_newton_ex(a->m, g->rho, wdt, bb, hstar, xx, g->newton_rtol, g->newton_maxit,
+                                   &floor_stop);
     if (a->st) {
       a->st->newton_solves++;
+      a->st->newton_floor += floor_stop;
       if (it > 0) { a->st->newton_iters += it; if (it > a->st->newton_maxit_seen) a->st->newton_maxit_seen = it; }
       else a->st->newton_fail++;
     }

@@ -138,6 +138,7 @@ typedef struct or_adr_stats {
   long newton_solves, newton_iters, newton_fail, newton_maxit_seen;
   long lin_solves, lin_iters, lin_fail;
   long tdiag_fail;
+  long newton_floor;     /* reaction solves that ended on the round-off-floor test */
 } or_adr_stats;
 
 /* State layout phi[(N+1)][cells]: Y_1..Y_N then h (J/kg). */
@@ -189,6 +190,10 @@ void or_wdot_jac(const or_mech *m, double rho, const double *Y, double T,
  * x[N+1] in: guess (Y,T), out: solution. Returns iterations (<0 failure). */
 int or_reaction_newton(const or_mech *m, double rho, double wdt, const double *b,
                        double hstar, double *x, double rtol, int maxit);
+/* the same; *floor_stop = 1 when the solve ended on the round-off-floor test
+ * (d <= 1e-8 and d >= d_prev / 2 with d > rtol), else 0 (may be NULL) */
+int or_reaction_newton_ex(const or_mech *m, double rho, double wdt, const double *b,
+                          double hstar, double *x, double rtol, int maxit, int *floor_stop);
 /* operators on a full state (for pins) */
 int or_adr_operators(const or_mech *mech, const or_adr_cfg *cfg, const double *phi,
                      double *FE, double *FD, double *FR);

@@ -48,7 +48,7 @@ class Stats(C.Structure):
                 ("surrogate_rejected", C.c_longlong), ("newton_fp64_fallbacks", C.c_longlong),
                 ("newton_jacobians", C.c_longlong), ("newton_lu_fp64", C.c_longlong),
                 ("newton_certified", C.c_longlong), ("nested_iterations", C.c_longlong),
-                ("newton_stored_steps", C.c_longlong)]
+                ("newton_stored_steps", C.c_longlong), ("newton_floor_stops", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

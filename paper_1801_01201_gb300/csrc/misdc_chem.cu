@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
   double *J = w.J;
   const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
   unsigned long long my_solves = 0, my_iters = 0, my_fail = 0, my_sg = 0, my_rej = 0, my_fb = 0,
-                     my_jac = 0, my_lu64 = 0, my_cert = 0, my_stored = 0;
+                     my_jac = 0, my_lu64 = 0, my_cert = 0, my_stored = 0, my_floor = 0;
   int my_max = 0;
   unsigned bits = 0;
 
@@ -1038,7 +1038,11 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       if (!MIXED || exact || (fresh && fresh_exact)) {
         // exact Newton step: stop on the step size, or at the round-off floor of
         // very stiff cells (the step no longer halves below 1e-8)
-        if (d <= rtol || (d <= 1e-8 && d >= 0.5 * dprev)) break;
+        if (d <= rtol) break;
+        if (d <= 1e-8 && d >= 0.5 * dprev) {
+          ++my_floor;
+          break;
+        }
       } else if (fresh) {
         // a step with a new FP32 factor is judged only by the chord steps after it
       } else {
@@ -1135,6 +1139,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     if (my_lu64) atomicAdd(&st->lu64, my_lu64);
     if (my_cert) atomicAdd(&st->certified, my_cert);
     if (my_stored) atomicAdd(&st->stored_steps, my_stored);
+    if (my_floor) atomicAdd(&st->floor_stops, my_floor);
   }
 }
 

@@ -1046,6 +1046,7 @@ misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
   out->newton_lu_fp64 = (long long)d.lu64;
   out->newton_certified = (long long)d.certified;
   out->newton_stored_steps = (long long)d.stored_steps;
+  out->newton_floor_stops = (long long)d.floor_stops;
   int st = MISDC_OK;
   if (d.status_bits & kBitTdiag) st = MISDC_E_TDIAG;
   else if (d.status_bits & (kBitNan | kBitSingular)) st = MISDC_E_NAN;
@@ -1358,8 +1359,11 @@ extern "C" misdc_status misdc_reaction_solve_noalloc(misdc_solver *s, double wdt
   double *theta = base + kNoAllocStatsDoubles;
   double *hsp = theta + n;
   CK(cudaMemsetAsync(stats, 0, sizeof(DevStats), cs));
+  NewtonLaunch nl = s->nl;   // the solver's (autotuned) launch shape, as misdc_reaction_solve
+  nl.dynamic = 0;            // the work counter is solver memory: static cell scheduling here
   launch_newton(s->m, n, n, wdt, s->o.newton_rtol, s->o.newton_maxit, b, hstar, x, x + N * n, x,
-                x + N * n, FR, hsp, theta, iters, stats, cs, s->o.precision == MISDC_PREC_MIXED);
+                x + N * n, FR, hsp, theta, iters, stats, cs, s->o.precision == MISDC_PREC_MIXED,
+                nullptr, 0, nullptr, 0.0, nullptr, nullptr, &nl);
   CK(cudaGetLastError());
   return MISDC_OK;
 }
@@ -1891,6 +1895,7 @@ misdc_status misdc_batch_stats(misdc_batch *b, misdc_stats *out, int reset) {
     sum.newton_lu_fp64 += t.newton_lu_fp64;
     sum.newton_certified += t.newton_certified;
     sum.newton_stored_steps += t.newton_stored_steps;
+    sum.newton_floor_stops += t.newton_floor_stops;
     sum.kernel_launches += t.kernel_launches;   // kernels in conditional bodies
     sum.nested_iterations += t.nested_iterations;
   }

@@ -41,6 +41,7 @@ struct DevStats {
   unsigned long long stored_steps;     // first chord steps taken from the stored reaction term
   unsigned long long body_launches;    // kernels run inside conditional graph bodies
   unsigned long long nested_iters;     // CISDCQ nested iterations run, summed over sweeps
+  unsigned long long floor_stops;      // exact Newton solves that ended on the round-off-floor test
 };
 
 // Mechanism tables in device memory (built by the engine from misdc_mech_desc).

@@ -356,3 +356,138 @@ def test_each_sweep_adds_one_order_in_time_on_the_adr_system():
             err.append(np.max(np.abs(got[:N] - ref[:N])))
         orders = [np.log2(err[i] / err[i + 1]) for i in range(2)]
         assert all(abs(o - sweeps) < 0.2 for o in orders), (sweeps, err, orders)
+
+
+# ---------------------------------------------------------------------------
+# The reaction Newton (S5) against roots computed in 40-digit arithmetic, and
+# its round-off-floor stop
+# ---------------------------------------------------------------------------
+def _mp_residual(mp, mech, rho, wdt, b, hstar, x):
+    """Residual of S5 written out from the mass-action law and the NASA-7
+    polynomials in mpmath arithmetic: r_Y = Y - wdt wdot(Y, T)/rho - b,
+    r_T = sum_i Y_i h_i(T) - h*, with c_i = rho Y_i / W_i,
+    q_r = k_f prod c^nu' - k_r prod c^nu'', k_f = A T^beta exp(-Ea/(R T)),
+    K_c = exp(-sum nu g/(R T)) (p_ref/(R T))^(sum nu), wdot_i = W_i sum_r nu_ri q_r."""
+    N = mech.n_species
+    Ru = mp.mpf("8.314462618")
+    T = x[N]
+    lnT = mp.log(T)
+    a = [[mp.mpf(float(v)) for v in row] for row in mech.nasa7]
+    hRT = [a[i][0] + a[i][1] * T / 2 + a[i][2] * T ** 2 / 3 + a[i][3] * T ** 3 / 4 + a[i][4] * T ** 4 / 5
+           + a[i][5] / T for i in range(N)]
+    sR = [a[i][0] * lnT + a[i][1] * T + a[i][2] * T ** 2 / 2 + a[i][3] * T ** 3 / 3 + a[i][4] * T ** 4 / 4
+          + a[i][6] for i in range(N)]
+    W = [mp.mpf(float(w)) for w in mech.W]
+    c = [rho * x[i] / W[i] for i in range(N)]
+    wd = [mp.mpf(0)] * N
+    for r in range(mech.n_reactions):
+        nf, nr = mech.nu_f[r], mech.nu_r[r]
+        nu = nr - nf
+        kf = (mp.mpf(float(mech.A[r])) * T ** mp.mpf(float(mech.beta[r]))
+              * mp.exp(-mp.mpf(float(mech.Ea[r])) / (Ru * T)))
+        dg = sum(int(nu[i]) * (hRT[i] - sR[i]) for i in range(N))
+        Kc = mp.exp(-dg) * (mp.mpf(float(mech.p_ref)) / (Ru * T)) ** int(nu.sum())
+        Ff, Fr = mp.mpf(1), mp.mpf(1)
+        for i in range(N):
+            if nf[i]:
+                Ff *= c[i] ** int(nf[i])
+            if nr[i]:
+                Fr *= c[i] ** int(nr[i])
+        q = kf * Ff - kf / Kc * Fr
+        for i in range(N):
+            if nu[i]:
+                wd[i] += W[i] * int(nu[i]) * q
+    res = [x[i] - wdt * wd[i] / rho - b[i] for i in range(N)]
+    res.append(sum(x[i] * Ru * T * hRT[i] / W[i] for i in range(N)) - hstar)
+    return res
+
+
+def _mp_root(mp, mech, rho, wdt, b, hstar, x0):
+    """The root of the 40-digit residual next to x0: chord iterations (the
+    forward-difference Jacobian at x0, 1e-25 relative steps) until the step is
+    below 1e-30. From an x0 within ~1e-12 of the root each chord step gains
+    about 12 digits."""
+    N = mech.n_species
+    n = N + 1
+    rho, wdt, hstar = mp.mpf(float(rho)), mp.mpf(float(wdt)), mp.mpf(float(hstar))
+    b = [mp.mpf(float(v)) for v in b]
+    x = [mp.mpf(float(v)) for v in x0]
+    r = _mp_residual(mp, mech, rho, wdt, b, hstar, x)
+    J = mp.matrix(n, n)
+    for j in range(n):
+        h = mp.mpf(10) ** -25 * (abs(x[j]) if x[j] != 0 else 1)
+        xp = list(x)
+        xp[j] += h
+        rp = _mp_residual(mp, mech, rho, wdt, b, hstar, xp)
+        for i in range(n):
+            J[i, j] = (rp[i] - r[i]) / h
+    for _ in range(12):
+        dx = mp.lu_solve(J, mp.matrix([-v for v in r]))
+        x = [x[i] + dx[i] for i in range(n)]
+        if max(max(abs(dx[i]) for i in range(N)), abs(dx[N]) / x[N]) < mp.mpf(10) ** -30:
+            return np.array([float(v) for v in x])
+        r = _mp_residual(mp, mech, rho, wdt, b, hstar, x)
+    raise AssertionError("40-digit chord iteration did not converge")
+
+
+@pytest.mark.parametrize("key,cells,wdts", [((1801, 9, 21), (6, 10, 14, 16, 20), (1e-6, 1e-4, 1e-2)),
+                                            ((1802, 21, 84), (6, 14, 16), (1e-6, 1e-4, 1e-2)),
+                                            ((1803, 53, 325), (14,), (1e-2,))])
+def test_reaction_newton_matches_40_digit_root(key, cells, wdts):
+    """The FP64 root of S5 equals the root found in 40-digit arithmetic to a few
+    ulps (max |dY| and |dT|/T below 1e-14) on front cells, from mild to very stiff
+    weights (wdt = 1e-6 to 1e-2 s, pre-exponential factors up to 1e14): the
+    oracle's answer is converged far below the 1e-10 parity bound."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    mech = I.make_mechanism(*key)
+    fl = I.flame_1d(mech, 0, nx=32, dx=1e-4)
+    ad = O.ADR(mech, fl)
+    N = mech.n_species
+    rng = np.random.default_rng(4)
+    for wdt in wdts:
+        for c in cells:
+            Y, T = fl.Y[:, c], fl.T[c]
+            b = Y * (1 + 0.01 * rng.standard_normal(N))
+            hstar = ad.h_from_T(Y[:, None], np.array([T]))[0]
+            fo = []
+            x, it = ad.reaction_newton(wdt, b, hstar, np.r_[Y, T], floor_out=fo)
+            assert it > 0 and fo == [0]
+            xm = _mp_root(mp, mech, fl.rho, wdt, b, hstar, x)
+            err = max(np.max(np.abs(x[:N] - xm[:N])), abs(x[N] - xm[N]) / xm[N])
+            assert err < 1e-14, (key, wdt, c, err)
+
+
+def test_newton_floor_stop_never_fires():
+    """The reaction Newton stops on its step (d <= 1e-12) or, as a guard, once a step
+    d <= 1e-8 no longer halves (a round-off floor). On every workload sample -- the
+    1D slab (full and A <= 1e11 chemistry, 20 steps), the 2D 21/84 and 53/325
+    flames, the batch's mechanisms -- and on stand-alone solves up to wdt = 1e-2 s,
+    the guard never fires: every root is converged to the step tolerance."""
+    samples = [(I.make_mechanism(1801, 9, 21), None, 1e-5, 20),
+               (I.make_mechanism(1801, 9, 21, logA_range=(8.0, 11.0)), None, 1e-5, 20),
+               (I.make_mechanism(1802, 21, 84), 24, 5e-6, 1),
+               (I.make_mechanism(1803, 53, 325), 10, 5e-6, 1)]
+    for mech, n, dt, steps in samples:
+        if n is None:
+            fl = I.flame_1d(mech, 1801, nx=128, dx=1e-4)
+        else:
+            fl = I.flame_2d(mech, 0, n=n, dx=4e-5, radius=n * 4e-5 / 4, delta=2 * 4e-5)
+        ad = O.ADR(mech, fl)
+        _, st = ad.step(ad.state_from_YT(fl.Y, fl.T), dt, "CISDCQ", 2, 4, 2, n_steps=steps)
+        assert st["newton_solves"] > 0 and st["newton_fail"] == 0
+        assert st["newton_floor"] == 0, (mech.n_species, st)
+    rng = np.random.default_rng(3)
+    for key in ((1801, 9, 21), (1802, 21, 84), (1803, 53, 325)):
+        mech = I.make_mechanism(*key)
+        fl = I.flame_1d(mech, 0, nx=32, dx=1e-4)
+        ad = O.ADR(mech, fl)
+        N = mech.n_species
+        for wdt in (1e-6, 1e-4, 1e-2):
+            for c in range(32):
+                Y, T = fl.Y[:, c], fl.T[c]
+                b = Y * (1 + 0.01 * rng.standard_normal(N))
+                hstar = ad.h_from_T(Y[:, None], np.array([T]))[0]
+                fo = []
+                _, it = ad.reaction_newton(wdt, b, hstar, np.r_[Y, T], floor_out=fo)
+                assert it > 0 and fo == [0], (key, wdt, c, it)

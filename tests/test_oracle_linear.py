@@ -86,7 +86,7 @@ def sweeps_to(scheme, nu, d, r, tol=1e-14, kmax=800):
     return int(idx[0]) + 1
 
 
-# Entries of Tables 1-2 that the equations as printed do not reproduce (see DESIGN):
+# Entries of Tables 1-2 that the equations as printed do not reproduce:
 # (-5,-5) nu=1 prints 2.1 where the sweep counts give 1.2 (and the text states that
 # CISDCQ-1 converges slower than MISDCQ there); the two nu=3 entries at r=-4 and r=-20.
 TABLE_EXCEPTIONS = {("-5", "-5", 1), ("-2", "-4", 3), ("-10", "-20", 3)}

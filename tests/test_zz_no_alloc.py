@@ -65,9 +65,25 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     fl = I.flame_1d(mech, 0, nx=16, dx=1e-4)
     sv = Solver(mech, fl)
     lib = L.load()
-    n = (1 << 19) // (mech.n_species + 1) + 1       # one cell too many for 4 MiB
+    N = mech.n_species
+    # the array holds 2^19 doubles: 32 for the counters and N + 1 per cell
+    n_max = ((1 << 19) - 32) // (N + 1)
+    assert n_max == 23829
     dummy = torch.zeros(1, dtype=torch.float64, device="cuda")
-    rc = lib.misdc_reaction_solve_noalloc(sv.handle, 1e-6, _p(dummy), _p(dummy), _p(dummy), None, None, n,
-                                          C.c_void_p(0))
+    rc = lib.misdc_reaction_solve_noalloc(sv.handle, 1e-6, _p(dummy), _p(dummy), _p(dummy), None, None,
+                                          n_max + 1, C.c_void_p(0))
     assert rc == L.E_INVALID
     assert b"no-allocation scratch" in lib.misdc_last_error()
+    assert b"at most %d cells" % n_max in lib.misdc_last_error()
+    # exactly at the limit the call is accepted and solves every cell
+    fl2 = I.flame_1d(mech, 0, nx=n_max, dx=1e-4)
+    sv2 = Solver(mech, fl2)
+    b = torch.as_tensor(fl2.Y, device="cuda").contiguous()
+    hstar = sv2.enthalpy(fl2.Y, fl2.T)
+    x = torch.as_tensor(np.concatenate([fl2.Y, fl2.T[None, :]], axis=0), device="cuda").contiguous()
+    it = torch.zeros(n_max, dtype=torch.int32, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.check(lib.misdc_reaction_solve_noalloc(sv2.handle, 1e-7, _p(b), _p(hstar), _p(x), None, _p(it), n_max,
+                                             stream))
+    torch.cuda.synchronize()
+    assert bool((it > 0).all())
