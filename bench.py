@@ -1,10 +1,12 @@
 """Benchmark: MISDC cell-updates/s, learned + mixed-precision concurrent MISDC
 against the plain FP64 sweep, at 1e-8 relative error.
 
-Workload (default): 2D periodic 256x256 flame, synthetic 21-species/84-reaction
-mechanism, Taylor-Green velocity (2 m/s), circular tanh kernel of radius 2 mm,
-3 Gauss-Lobatto nodes, 4 sweeps, nu = 2, dt = 5e-6 s. One "step" = one time
-step of every cell (all nodes, sweeps and nested iterations).
+Workload (default): 3D periodic 128^3 flame (2,097,152 cells), synthetic
+21-species/84-reaction mechanism, random-phase solenoidal velocity of rms 3 m/s,
+spherical tanh kernel of radius 2 mm, 3 Gauss-Lobatto nodes, 4 sweeps, nu = 2,
+dt = 5e-6 s: the learned form's configuration, the largest that runs on one
+GPU. One "step" = one time step of every cell (all nodes, sweeps and nested
+iterations).
 
 Three variants of the same workload are timed back to back, each from the same
 initial state: the plain FP64 sweep, the mixed-precision sweep, and the learned
@@ -13,8 +15,14 @@ the library's own kernels, on solves recorded from a different flame of the
 same mechanism; training is setup, outside the timed region. The headline's
 error against the FP64 sweep after the same steps is reported per field.
 
-Other workloads: --workload flame2d_512_n53 | flame3d_128_n21 | flame1d_128_n9 |
+Other workloads: --workload flame2d_256_n21 | flame2d_512_n53 | flame1d_128_n9 |
 batch64_2d (64 independent flames, one graph launch per step, autotuned).
+
+Roofline of the reaction Newton (the step's dominant kernel): algorithmic FP64
+flops per launch from the device counters with the per cell-iteration counts
+thermo 15N, rates R(10 + 4 nubar), Jacobian 2 R nubar^2, LU 2n^3/3 and one
+solve 2n^2 (n = N + 1, nubar = molecules per reaction), against the FP64 FMA
+throughput measured at start-up by the library's probe kernel.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank advances its own copy of the workload (weak scaling,
@@ -38,7 +46,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MISDC cell-updates/s, learned+mixed vs plain FP64 sweep, at 1e-8 rel err"
 UNIT = "cell-updates/s"
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12      # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_NOMINAL_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 # dram__bytes_read.sum + dram__bytes_write.sum of one reaction-Newton launch, per
 # (workload, variant), from the ncu captures summarised under profiles/; a variant
 # missing here has changed since its capture (traffic reported as null).
@@ -73,6 +81,56 @@ def newton_flops(N, R, nnz, stats, mixed=False):
              + fin_solves * fin)
     exps = ev * (2 * R + 1) + fin_solves * 2
     return flops, exps
+
+def mean_molecules(mech):
+    """nubar: reactant plus product molecules per reaction, averaged."""
+    return float(np.mean(mech.nu_f.sum(axis=1) + mech.nu_r.sum(axis=1)))
+
+
+def newton_flops_counted(N, R, nubar, stats, mixed=False):
+    """Algorithmic FP64 flops of the reaction-Newton launches behind `stats` with
+    per cell-iteration counts: an iteration that evaluates the rates does thermo
+    (15N) and the rates (R(10 + 4 nubar)); a Jacobian assembly adds 2 R nubar^2
+    and its LU 2n^3/3 (in either precision); every iteration, and every solve
+    that a kept factor certifies or starts from the stored reaction term, does
+    one solve (2n^2: a product with the kept inverse, or two substitutions)."""
+    n = N + 1
+    it = stats["newton_iters"]
+    jac = stats.get("newton_jacobians", it) if mixed else it
+    cert = stats.get("newton_certified", 0) if mixed else 0
+    stored = stats.get("newton_stored_steps", 0) if mixed else 0
+    ev = it - cert - stored
+    per_ev = 15 * N + R * (10 + 4 * nubar)
+    per_jac = 2 * R * nubar ** 2 + 2.0 * n ** 3 / 3
+    flops = ev * per_ev + jac * per_jac + (ev + cert + stored) * 2 * n * n
+    return flops, {"rate_iterations": ev, "jacobians": jac, "certified": cert, "stored_steps": stored,
+                   "N": N, "R": R, "nubar": nubar,
+                   "per_rate_iteration": per_ev, "per_jacobian": per_jac, "per_solve": 2 * n * n}
+
+
+def measure_fp_peaks(dev, reps=5):
+    """Best-of-`reps` throughput (TFLOP/s) of the library's FP64 FMA, FP64
+    tensor-core MMA and FP32 FMA probes over every SM (CUDA events around each
+    launch, after one warm-up launch)."""
+    import torch
+    from paper_1801_01201_gb300 import solver as SV
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    st = torch.cuda.current_stream()
+    out = {}
+    for kind, iters in (("dfma", 20000), ("dmma", 4000), ("ffma", 200000)):
+        blocks = sms * 8
+        SV.probe_flops(kind, blocks, iters // 10, stream=st)
+        best = 0.0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fl, _ = SV.probe_flops(kind, blocks, iters, stream=st)
+            b.record(st)
+            b.synchronize()
+            best = max(best, fl / (a.elapsed_time(b) / 1e3) / 1e12)
+        out[kind] = best
+    return out
+
 
 class ClockSampler:
     def __init__(self, gpu_index=0):
@@ -528,6 +586,7 @@ def pde_bench(args, dev, rank):
     err = float(np.max(np.abs(one[0].cpu().numpy() - want)))
     t = statistics.median(ms) / 1e3
     rate = n * nx / t
+    peak = measure_fp_peaks(dev)["dfma"]
     # algorithmic FP64 flops per cell and node stage (an FMA counts 2): right-hand
     # side 8(M+1) + 6(M-1), band substitutions 14, Newton 3 x 14, F_A and F_D 24,
     # reaction term 3; per cell and step sweeps x nu x M stages + 40 at phi^n
@@ -538,8 +597,9 @@ def pde_bench(args, dev, rank):
                                 "5 nodes, CISDCQ-%d, %d sweeps, dt %.2g" % (n, nx, nu, sweeps, dt),
                     "value": rate, "unit": "cell-updates/s", "ms_per_step": t * 1e3, "status_ok": ok,
                     "max_abs_err_vs_oracle": err,
-                    "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                                 "unit": "TFLOP/s", "frac": achieved / peak,
+                                 "peak_source": "measured: FP64 FMA probe (misdc_probe_flops), of measured",
                                  "flops_per_cell_update": flops / (n * nx)},
                     "cpu_baseline": {"value": nx / cpu_s, "unit": "cell-updates/s", "cores": 1,
                                      "kind": "oracle", "sample": "one instance, one step"}},
@@ -555,7 +615,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="flame2d_256_n21")
+    ap.add_argument("--workload", default="flame3d_128_n21")
     ap.add_argument("--scheme", default="CISDCQ")
     ap.add_argument("--headline", default="learned_mixed", choices=["learned_mixed", "mixed", "fp64"])
     ap.add_argument("--autotune", type=int, default=-1, help="1/0; default: on for batches")
@@ -614,6 +674,7 @@ def main():
         return nu_compare(entries, w, args, dev, rank)
     tune = (len(entries) > 1) if args.autotune < 0 else bool(args.autotune)
     stream = torch.cuda.current_stream()
+    peaks = measure_fp_peaks(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     # plain FP64 sweep
@@ -696,20 +757,28 @@ def main():
         mech = entries[0][0]
         nnz = int(np.count_nonzero(mech.nu_r - mech.nu_f))
         mixedk = args.headline != "fp64"
-        flops64, exps = newton_flops(mech.n_species, mech.n_reactions, nnz, st, mixedk)
-        per_launch = flops64 / r_head["newton_launches"]
-        avg_s = r_head["newton_ms"] / 1e3 / r_head["newton_launches"]
-        achieved = per_launch / avg_s / 1e12
+        launches = r_head["newton_launches"]
+        avg_s = r_head["newton_ms"] / 1e3 / launches
+        flops, counters = newton_flops_counted(mech.n_species, mech.n_reactions, mean_molecules(mech), st, mixedk)
+        achieved = flops / launches / avg_s / 1e12
+        kflops, exps = newton_flops(mech.n_species, mech.n_reactions, nnz, st, mixedk)
+        kach = kflops / launches / avg_s / 1e12
+        peak = peaks["dfma"]
         roofline = {"kernel": "k_newton2<%s> (reaction Newton, warp per cell)" % ("mixed" if mixedk else "fp64"),
-                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NEWTON_TRAFFIC_BYTES.get(
-                        (name, args.headline)),
-                    "peak_source": "FP64 nominal from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                    "flops_counted": "FP64 algorithmic flops from the device counters (iterations, Jacobians, FP64 factorisations); FP32 LU work excluded",
+                    "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": NEWTON_TRAFFIC_BYTES.get((name, args.headline)),
+                    "peak_source": "measured: FP64 FMA probe over every SM (misdc_probe_flops), of measured",
+                    "flops_counted": "per cell-iteration: thermo 15N, rates R(10+4 nubar), Jacobian 2R nubar^2, "
+                                     "LU 2n^3/3, solve 2n^2; counters of the timed steps",
+                    "counters": counters, "launches": launches,
+                    "flops_per_launch": flops / launches,
+                    "kernel_instruction_model": {"achieved": kach, "frac": kach / peak,
+                                                 "flops_per_launch": kflops / launches},
                     "newton_ms_per_step": r_head["newton_ms"] / args.steps,
                     "diffusion_ms_per_step": r_head["diffusion_ms"] / args.steps,
                     "newton_launch_ms": avg_s * 1e3,
-                    "exp_log_calls_per_launch": exps / r_head["newton_launches"],
+                    "exp_log_calls_per_launch": exps / launches,
+                    "newton_floor_stops": st["newton_floor_stops"],
                     "newton_jacobians_per_solve": st["newton_jacobians"] / max(st["newton_solves"], 1)}
     cpu = None
     if not args.no_cpu_baseline:
@@ -762,6 +831,7 @@ def main():
             "data": "synthetic", "config": cfg, "clocks": r_head["clocks"],
             "gpu_launches": st["kernel_launches"], "e2e": e2e, "roofline": roofline,
             "cpu_baseline": cpu, "status": st["status_name"],
+            "measured_peaks_tflops": {k: v for k, v in peaks.items()},
             "accuracy_vs_fp64_ok": acc_ok,
             "variants": {k: summary(k) for k in variants},
             "speedup_vs_plain_fp64": value / summary("fp64")["value"] / world}

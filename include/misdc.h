@@ -230,6 +230,18 @@ misdc_status misdc_lincomb(int n_out, int n_in, double *const *out, const double
  * arguments outside (-700, 700) fall back to the CUDA exp. */
 misdc_status misdc_exp(const double *x, double *y, size_t n, void *stream);
 
+/* Arithmetic-throughput probe, the measured denominator of the roofline
+ * fractions of the FP64-bound kernels. The paper has no counterpart (it reports
+ * no hardware figures). kind 0: FP64 FMA, 8 independent chains per thread;
+ * kind 1: FP64 tensor-core MMA (m8n8k4, 512 flops each), 4 independent
+ * accumulators per warp; kind 2: FP32 FMA, 8 chains per thread. Launches
+ * `blocks` blocks of 256 threads running `iters` iterations each, stream-ordered;
+ * out: device [blocks * 256] doubles (results, so nothing is optimised away);
+ * *flops (host) receives the flops the launch performs (an FMA counts 2). The
+ * caller times the launch. MISDC_E_INVALID for a bad kind or size. */
+misdc_status misdc_probe_flops(int kind, int blocks, int iters, double *out, double *flops,
+                               void *stream);
+
 /* ---- nonlinear scalar test PDE (Sec. 5.2, eq. nonlinear_test_pde) ---------
  * phi_t = a phi_x + d phi_xx + r phi (phi - 1)(phi - 1/2) on [0, length] with
  * phi(0) = left, phi(length) = right, in nx uniform cells: fourth-order advective

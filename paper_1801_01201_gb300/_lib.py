@@ -76,7 +76,7 @@ EXPORTS = ["misdc_default_opts", "misdc_create", "misdc_destroy", "misdc_step", 
            "misdc_surrogate_features", "misdc_surrogate_forward", "misdc_surrogate_gradient",
            "misdc_surrogate_train_batch", "misdc_surrogate_forward_layers", "misdc_surrogate_guess", "misdc_autotune", "misdc_get_tuning", "misdc_set_tuning",
            "misdc_batch_create", "misdc_batch_destroy", "misdc_batch_step", "misdc_batch_stats",
-           "misdc_pde_step", "misdc_pde_smem_bytes", "misdc_exp"]
+           "misdc_pde_step", "misdc_pde_smem_bytes", "misdc_exp", "misdc_probe_flops"]
 
 _lib = None
 
@@ -143,6 +143,7 @@ def load(build_if_missing: bool = True):
     L.misdc_pde_step.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
                                  C.c_double, C.c_int, vp, vp, vp, vp, vp, vp]
     L.misdc_exp.argtypes = [vp, vp, C.c_size_t, vp]
+    L.misdc_probe_flops.argtypes = [C.c_int, C.c_int, C.c_int, vp, dp, vp]
     L.misdc_pde_smem_bytes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_size_t)]
     L.misdc_last_error.restype = C.c_char_p
     L.misdc_last_error.argtypes = []

@@ -61,6 +61,19 @@ def exp(x, stream=None):
     return y
 
 
+PROBE_KINDS = {"dfma": 0, "dmma": 1, "ffma": 2}
+
+
+def probe_flops(kind, blocks, iters, stream=None):
+    """Launch the arithmetic-throughput probe (misdc_probe_flops) on `stream`;
+    returns (the flops the launch performs, its output tensor)."""
+    lib = L.load()
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    fl = C.c_double()
+    L.check(lib.misdc_probe_flops(PROBE_KINDS[kind], blocks, iters, _ptr(out), C.byref(fl), _stream(stream)))
+    return fl.value, out
+
+
 PDE_STATUS_BITS = {1: "newton_limit", 2: "non_finite", 4: "singular_diffusion"}
 
 

@@ -135,3 +135,63 @@ def test_batch_mixed_precision_bitwise_and_accurate():
     g = got[0].cpu().numpy()
     N = m.n_species
     assert np.max(np.abs(g[:N] - want[:N])) / np.max(np.abs(want[:N])) < 1e-8
+
+
+def _small_batch(n_flames=64, seed=4242):
+    """64 flames like the benchmark batch but on 16^2..32^2 grids: side
+    U{16..32}, the three mechanisms with their full rate ranges (taken in turn),
+    dt ~ U[1e-6, 1e-5] s, kernel centre uniform, radius 0.3 L, front width L/8."""
+    rng = np.random.default_rng(seed)
+    mechs = [I.make_mechanism(*k) for k in ((1801, 9, 21), (1802, 21, 84), (1803, 53, 325))]
+    out = []
+    for f in range(n_flames):
+        side = int(rng.integers(16, 33))
+        mech = mechs[f % 3]
+        dt = float(rng.uniform(1e-6, 1e-5))
+        L = side * 4e-5
+        centre = (float(rng.uniform(0, L)), float(rng.uniform(0, L)))
+        fl = I.flame_2d(mech, seed + f, n=side, dx=4e-5, amp=2.0, radius=0.3 * L, delta=L / 8, centre=centre)
+        out.append((mech, fl, dt))
+    return out
+
+
+def test_batch_of_64_small_flames_autotuned():
+    """64 uneven flames (16^2..32^2, 9/21, 21/84 and 53/325 species/reactions,
+    each its own dt) in one autotuned batch equal stepping each flame alone with
+    default launch shapes bit for bit, and three of them (one per mechanism)
+    match the oracle within max(1e-10, 2 S) per field."""
+    from oracle.parallel import StepPool
+    from parity_util import record, tol_from
+    fl = _small_batch()
+    picks = [0, 1, 2]
+    with StepPool() as pool:
+        handles = []
+        for k in picks:
+            m, f, dt = fl[k]
+            ad = O.ADR(m, f)
+            handles.append(pool.step(m, f, ad.state_from_YT(f.Y, f.T), dt, "CISDCQ", 2, 4, 2, 1, perturb=4))
+        single = [S().Solver(m, f) for m, f, _ in fl]
+        batched = [S().Solver(m, f) for m, f, _ in fl]
+        states = [_state(s, f) for s, (_, f, _) in zip(single, fl)]
+        shapes = set()
+        for s, x, (_, f, dt) in zip(batched, states, fl):
+            t = s.autotune(x, torch.as_tensor(f.T, device="cuda").contiguous(), dt)
+            shapes.add((t["newton_warps_per_block"], t["newton_blocks_per_sm"], t["newton_dynamic"],
+                        t["cheb_block"]))
+        ref = [x.clone() for x in states]
+        for s, x, (_, _, dt) in zip(single, ref, fl):
+            s.step(x, dt, 1)
+        got = [x.clone() for x in states]
+        B = S().Batch(batched)
+        B.step(got, [dt for _, _, dt in fl], 1)
+        st = B.stats()
+        assert st["status_name"] == "OK", st
+        assert st["newton_floor_stops"] == 0
+        for k, (x, y) in enumerate(zip(ref, got)):
+            assert torch.equal(x, y), k
+        for k, h in zip(picks, handles):
+            want, _, sens = pool.sensitivity(h)
+            err = relerr(got[k].cpu().numpy(), want)
+            record("batch64_small[%d:%d species]" % (k, fl[k][0].n_species), err=err, S=sens,
+                   shapes=len(shapes))
+            assert np.all(err <= tol_from(sens)), (k, err, sens)

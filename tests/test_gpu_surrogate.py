@@ -311,6 +311,11 @@ def test_trained_guess_gain():
     for f in range(A.shape[0]):
         assert nrel(B[f], A[f]) < 1e-10, f
     assert learned["status"] == 0 and plain["status"] == 0
+    from parity_util import record
+    record("trained_guess_gain", plain_iters=plain["newton_iters"], plain_solves=plain["newton_solves"],
+           learned_iters=learned["newton_iters"], learned_solves=learned["newton_solves"],
+           used=learned["surrogate_used"], rejected=learned["surrogate_rejected"], rows=rows,
+           loss_first=float(curve[:10].mean()), loss_last=float(curve[-50:].mean()))
     print("\nplain iters/solve %.4f  learned iters/solve %.4f  used %d rejected %d  loss %.3g -> %.3g"
           % (plain["newton_iters"] / plain["newton_solves"],
              learned["newton_iters"] / learned["newton_solves"], learned["surrogate_used"],
