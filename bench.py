@@ -245,13 +245,17 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def entries_for(name):
-    """[(mechanism, flame, dt)] and the time-integration settings of a workload."""
+def entries_for(name, grid=0):
+    """[(mechanism, flame, dt)] and the time-integration settings of a workload;
+    grid > 0 replaces the cells per side of a single-flame 2D or 3D workload (a
+    smaller case of the same recipe, for profiling)."""
     from paper_1801_01201_gb300 import inputs as I
     if name in I.BATCHES:
         b = I.BATCHES[name]
         return I.build_batch(name), b
-    mech, fl, w = I.build_workload(name)
+    w = I.WORKLOADS[name]
+    over = {"n": grid} if grid > 0 and w["dim"] > 1 else None
+    mech, fl, w = I.build_workload(name, over)
     return [(mech, fl, w["dt"])], w
 
 
@@ -355,8 +359,9 @@ def whole_job_rate(world, cells, steps, total_ms):
     return world * cells * steps / (total_ms / 1e3)
 
 
-def timed(runner, args, flush, stream, dist=None, clocks=None):
-    """W untimed steps, then K steps timed with CUDA events (L2 flushed between)."""
+def timed(runner, args, flush, stream, dist=None, clocks=None, label="timed"):
+    """W untimed steps, then K steps timed with CUDA events (L2 flushed between).
+    The timed steps sit in an NVTX range named `label` (a profiler can select them)."""
     import torch
     for _ in range(args.warmup):
         runner.step()
@@ -368,6 +373,7 @@ def timed(runner, args, flush, stream, dist=None, clocks=None):
         clocks.start()
     torch.cuda.synchronize()
     ms, newton_ms, newton_n, diff_ms = [], 0.0, 0, 0.0
+    torch.cuda.nvtx.range_push(label)
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -382,6 +388,7 @@ def timed(runner, args, flush, stream, dist=None, clocks=None):
             newton_ms += t["newton_ms"]
             newton_n += t["newton_launches"]
             diff_ms += t["diffusion_ms"]
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
     if dist:
@@ -541,6 +548,100 @@ def nu_compare(entries, w, args, dev, rank):
     return 0
 
 
+def concurrency_compare(entries, w, args, dev, rank):
+    """The paper's cost question on this GPU (Sec. 3.2.2, eq. simple_parallel_speedup),
+    measured on the first flame in FP64. Arms: serial MISDCQ; CISDCQ-nu with the
+    diffusion and reaction stages on one stream and on two streams; CISDCQ with
+    adaptive nested iterations (cap nu + 2) on two streams. For every arm and every
+    sweep count k = 1..K (one solver each): the device time of one time step
+    (CUDA events, median of --steps after --warmup, L2 flushed), the measured stage
+    costs Upsilon_AD (one diffusion solve of all fields) and Upsilon_R (one
+    reaction-Newton launch), and the state after the step, which gives the sweep
+    increment inc(k) = max over fields of ||phi^{M,(k)} - phi^{M,(k-1)}||_1 /
+    ||phi^{M,(k-1)}||_1 (phi^{M,(0)} = phi^n). As in the paper's Tables 3 and 5,
+    N_M = K MISDCQ sweeps set the target eps = inc_MISDCQ(K), and N_C is the first
+    sweep of an arm with inc <= eps. Reported per arm: N_C, the measured ratio
+    t_MISDCQ(N_M) / t_arm(N_C), and the paper's model
+    R_nu = (N_M / N_C) alpha M / (alpha nu + M - 1), alpha = (U_AD + U_R) / max(U_AD, U_R)
+    from the measured stage costs (nu: the mean nested iterations per sweep)."""
+    import torch
+    from paper_1801_01201_gb300.solver import Solver
+    K = args.concurrency
+    mech, fl, dt = entries[0]
+    nu, M = w["nu"], w["nodes"] - 1
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    arms = [("misdcq", dict(scheme="MISDCQ", nu=1, two_streams=False)),
+            ("cisdcq_nu%d_one_stream" % nu, dict(scheme="CISDCQ", nu=nu, two_streams=False)),
+            ("cisdcq_nu%d_two_streams" % nu, dict(scheme="CISDCQ", nu=nu, two_streams=True)),
+            ("cisdcq_adaptive_max%d_two_streams" % (nu + 2),
+             dict(scheme="CISDCQ", nu=nu + 2, two_streams=True, nu_rule=(0.02, 0.9)))]
+    x0 = None
+    out = {}
+    for name, kw in arms:
+        res = {"ms_per_step": [], "inc": [], "U_AD_ms": [], "U_R_ms": [], "nested_per_sweep": []}
+        prev = None
+        for k in range(1, K + 1):
+            sv = Solver(mech, fl, n_sweeps=k, n_nodes=w["nodes"], profile=True, device=dev, **kw)
+            if x0 is None:
+                x0 = sv.state_from_YT(fl.Y, fl.T)
+                prev0 = x0.clone()
+            x = x0.clone()
+            for _ in range(max(args.warmup, 1)):
+                x.copy_(x0)
+                sv.step(x, dt, 1, stream=st)
+            sv.stats()
+            ms, uad, ur = [], [], []
+            for _ in range(max(args.steps, 1)):
+                x.copy_(x0)
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                sv.step(x, dt, 1, stream=st)
+                b.record(st)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+                t = sv.stage_times()
+                uad.append(t["diffusion_ms"] / max(t["diffusion_launches"], 1))
+                ur.append(t["newton_ms"] / max(t["newton_launches"], 1))
+            stt = sv.stats()
+            assert stt["status_name"] == "OK", stt
+            ref = prev0 if prev is None else prev
+            d = (x - ref).abs().sum(dim=1) / ref.abs().sum(dim=1).clamp_min(1e-300)
+            res["inc"].append(float(d.max()))
+            res["ms_per_step"].append(statistics.median(ms))
+            res["U_AD_ms"].append(statistics.median(uad))
+            res["U_R_ms"].append(statistics.median(ur))
+            res["nested_per_sweep"].append(stt["nested_iterations"] / max(args.steps, 1) / k
+                                           if kw["scheme"] == "CISDCQ" else 1.0)
+            prev = x.clone()
+            sv.close()
+            del sv
+            torch.cuda.synchronize()
+        out[name] = res
+    mis = out["misdcq"]
+    eps = mis["inc"][K - 1]
+    for name, res in out.items():
+        nc = next((k + 1 for k, v in enumerate(res["inc"]) if v <= eps), None)
+        res["N_C"] = nc
+        if nc is None or name == "misdcq":
+            continue
+        uad, ur = res["U_AD_ms"][nc - 1], res["U_R_ms"][nc - 1]
+        alpha = (uad + ur) / max(uad, ur)
+        nub = res["nested_per_sweep"][nc - 1]
+        res["alpha"] = alpha
+        res["R_nu_model"] = (K / nc) * alpha * M / (alpha * nub + M - 1)
+        res["R_nu_measured"] = mis["ms_per_step"][K - 1] / res["ms_per_step"][nc - 1]
+    line = {"concurrency": out, "N_M": K, "eps": eps, "nodes": w["nodes"], "nu": nu, "workload": args.workload,
+            "cells": fl.cells, "species": mech.n_species, "dt": dt, "steps": args.steps, "warmup": args.warmup,
+            "two_stream_gain_at_%d_sweeps" % min(K, w["sweeps"]):
+                out["cisdcq_nu%d_one_stream" % nu]["ms_per_step"][min(K, w["sweeps"]) - 1]
+                / out["cisdcq_nu%d_two_streams" % nu]["ms_per_step"][min(K, w["sweeps"]) - 1]}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def pde_bench(args, dev, rank):
     """The nonlinear test PDE of Sec. 5.2 (n_x = 200 on [0, 20], a = 1, 5 Gauss-Lobatto
     nodes, dt = 0.05, CISDCQ-3, 10 sweeps) on INSTANCES independent instances in one
@@ -616,6 +717,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="flame3d_128_n21")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="cells per side of a 2D/3D single-flame workload (default: the workload's)")
     ap.add_argument("--scheme", default="CISDCQ")
     ap.add_argument("--headline", default="learned_mixed", choices=["learned_mixed", "mixed", "fp64"])
     ap.add_argument("--autotune", type=int, default=-1, help="1/0; default: on for batches")
@@ -643,6 +746,10 @@ def main():
     ap.add_argument("--pde", type=int, default=0, metavar="INSTANCES",
                     help="instead of the step: the nonlinear test PDE of Sec. 5.2 on INSTANCES "
                          "independent 200-cell instances, one launch per step")
+    ap.add_argument("--concurrency", type=int, default=0, metavar="K",
+                    help="instead of the headline: serial MISDCQ against CISDCQ-nu on one and on two "
+                         "streams and with adaptive nu, sweeps 1..K each: step times, stage costs, "
+                         "sweep increments, sweeps to the MISDCQ tolerance, measured and modelled R_nu")
     ap.add_argument("--rates-compare", action="store_true",
                     help="instead of the step: time the production-rate kernel, sparse FP64 FMA "
                          "against FP64 tensor cores, on the workload's initial state")
@@ -665,13 +772,15 @@ def main():
         return pde_bench(args, dev, rank)
 
     name = args.workload
-    entries, w = entries_for(name)
+    entries, w = entries_for(name, args.grid)
     if args.rates_compare:
         return rates_compare(entries, args, dev, rank)
     if args.diffusion_compare > 0:
         return diffusion_compare(entries, args, dev, rank)
     if args.nu_compare:
         return nu_compare(entries, w, args, dev, rank)
+    if args.concurrency > 0:
+        return concurrency_compare(entries, w, args, dev, rank)
     tune = (len(entries) > 1) if args.autotune < 0 else bool(args.autotune)
     stream = torch.cuda.current_stream()
     peaks = measure_fp_peaks(dev)
@@ -700,7 +809,7 @@ def main():
     # the headline again with the clock sampler running (its own timed region)
     clocks = ClockSampler(local) if rank == 0 else None
     head.states = [x.clone() for x in head.states0]
-    r_head = timed(head, args, flush, stream, dist, clocks)
+    r_head = timed(head, args, flush, stream, dist, clocks, label="headline")
     cells = head.cells
     value = whole_job_rate(world, cells, args.steps, r_head["total_ms"])
 
@@ -810,7 +919,8 @@ def main():
         return d
 
     dtype = {"fp64": "f64", "mixed": "f64+f32", "learned_mixed": "f64+f32, bf16 MLP"}[args.headline]
-    cfg = {"workload": name, "flames": len(entries), "cells": cells, "nodes": w["nodes"],
+    cfg = {"workload": name if not args.grid else "%s at %d cells per side" % (name, args.grid),
+           "flames": len(entries), "cells": cells, "nodes": w["nodes"],
            "sweeps": w["sweeps"], "nu": w["nu"], "scheme": args.scheme, "variant": args.headline,
            "autotuned": tune, "l2": "flushed between steps (256 MB write)",
            "rates": "fp64 tensor cores" if args.rates_mma else "sparse fp64 fma",
