@@ -377,16 +377,18 @@ __device__ __forceinline__ NW carve2(double *p, int N, int R, int ld, bool mixed
 // matrix-vector product (nn FMA warp instructions) instead of a forward and a
 // back substitution (about 3 nn, each on a shrinking set of lanes).
 //
-// invert_kept: Z = U^{-1} L^{-1} P D in place of the factor in J (L unit lower
-// below the diagonal, U on and above it, piv = 1/U_kk, row exchanges sw taken in
-// order k = 0..nn-1, row scales res), the inverse of the unscaled Jacobian. Steps:
-// U^{-1} column by column; then, from the last column to the first, the columns of
-// U^{-1} L^{-1} from those to their right; then the column exchanges in reverse
-// order and the column scaling by D.
-__device__ void invert_kept(const NW &w, double *J, int ld, int nn, int lane) {
+// invert_lu: Z = U^{-1} L^{-1} P in place of the factor in J (L unit lower below
+// the diagonal, U on and above it, piv = 1/U_kk, row exchanges sw taken in order
+// k = 0..nn-1): the inverse of the factored matrix. Steps: U^{-1} column by
+// column; then, from the last column to the first, the columns of U^{-1} L^{-1}
+// from those to their right; then the column exchanges in reverse order. T is
+// the precision of the factor (an FP32 factor is inverted in FP32: it carries
+// no more accuracy than that, and the FP32 pipe is 60x faster). z: nn scratch.
+template <class T>
+__device__ void invert_lu(T *J, int ld, int nn, int lane, const T *piv, T *z, const int *sw) {
   for (int j = 0; j < nn; ++j) {   // U^{-1}: X[0:j, j] = -X[j][j] X[0:j, 0:j] U[0:j, j]
-    const double xjj = w.piv[j];
-    double t0 = 0.0, t1 = 0.0;
+    const T xjj = piv[j];
+    T t0 = 0, t1 = 0;
     if (lane < j)
       for (int k = lane; k < j; ++k) t0 = fma(J[(size_t)lane * ld + k], J[(size_t)k * ld + j], t0);
     if (lane + 32 < j)
@@ -399,29 +401,26 @@ __device__ void invert_kept(const NW &w, double *J, int ld, int nn, int lane) {
   }
   for (int j = nn - 2; j >= 0; --j) {   // X[:, j] -= X[:, j+1:] L[j+1:, j]
     for (int i = j + 1 + lane; i < nn; i += 32) {
-      w.zd[i] = J[(size_t)i * ld + j];
-      J[(size_t)i * ld + j] = 0.0;
+      z[i] = J[(size_t)i * ld + j];
+      J[(size_t)i * ld + j] = 0;
     }
     __syncwarp();
     for (int i = lane; i < nn; i += 32) {
-      double s = J[(size_t)i * ld + j];
-      for (int k = j + 1; k < nn; ++k) s = fma(-J[(size_t)i * ld + k], w.zd[k], s);
+      T s = J[(size_t)i * ld + j];
+      for (int k = j + 1; k < nn; ++k) s = fma(-J[(size_t)i * ld + k], z[k], s);
       J[(size_t)i * ld + j] = s;
     }
     __syncwarp();
   }
   for (int j = nn - 2; j >= 0; --j) {   // column exchanges, last first
-    const int jp = w.sw[j];
+    const int jp = sw[j];
     if (jp != j)
       for (int i = lane; i < nn; i += 32) {
-        const double t = J[(size_t)i * ld + j];
+        const T t = J[(size_t)i * ld + j];
         J[(size_t)i * ld + j] = J[(size_t)i * ld + jp];
         J[(size_t)i * ld + jp] = t;
       }
   }
-  __syncwarp();
-  for (int i = lane; i < nn; i += 32)   // right-multiply by D
-    for (int j = 0; j < nn; ++j) J[(size_t)i * ld + j] *= w.res[j];
   __syncwarp();
 }
 
@@ -460,6 +459,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
   NW w = carve2(smem + (size_t)wib * per_warp, N, R, ld, MIXED);
   double *J = w.J;
   const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
+  // per-launch constants (an FP64 division is a long instruction sequence on this
+  // part: formed once, not per cell)
+  const double invw = (wdt > 0.0) ? 1.0 / wdt : 0.0;
+  const double wr = wdt / m.rho;
   unsigned long long my_solves = 0, my_iters = 0, my_fail = 0, my_sg = 0, my_rej = 0, my_fb = 0,
                      my_jac = 0, my_lu64 = 0, my_cert = 0, my_stored = 0, my_floor = 0;
   int my_max = 0;
@@ -509,11 +512,13 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     bool exact = false;   // retry: plain FP64 Newton, no factor reuse
     double sTf = 0.0;
     if (MIXED && cst.valid) no32 = (cst.valid[cell] & 2) != 0;   // FP32 factors failed this cell
+    bool stored = false;   // a kept factor of this cell's node, built near its guess
+    const double *src = nullptr;
     if (MIXED && cst.valid && (cst.valid[cell] & 1)) {
       // a stored factor is used only while the cell stays within 1e-4 (Y, and T
       // relative) of the state it was built at: a stale factor of a stiffer
       // Jacobian would shrink the chord step and fake convergence
-      const double *src = cst.f + (size_t)cell * cst.fs;
+      src = cst.f + (size_t)cell * cst.fs;
       const double *xf = src + nn * nn + 2 * nn + 2;
       bool near = true;   // compared without dividing by T
       for (int i = lane; i < nn; i += 32) {
@@ -521,46 +526,66 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         near = near && fabs(xi - xf[i]) <= ((i < N) ? 1e-4 : 1e-4 * xi);
       }
       if (__all_sync(0xffffffffu, near)) {
-        for (int e = lane; e < nn * nn; e += 32) {
-          const int i = e / nn, j = e - i * nn;
-          J[(size_t)i * ld + j] = src[e];
-        }
-        for (int i = lane; i < nn; i += 32) {
-          w.piv[i] = src[nn * nn + i];
-          w.res[i] = src[nn * nn + nn + i];
-          w.sw[i] = cst.sw[(size_t)cell * cst.swld + i];
-        }
+        stored = true;
         sTf = src[nn * nn + 2 * nn];
         fac32 = src[nn * nn + 2 * nn + 1] != 0.0;
-        have = true;
-        from_store = true;
+      }
+    }
+    // copy the kept FP64 inverse into shared memory (chord steps use it)
+    auto load_stored = [&]() {
+      for (int e = lane; e < nn * nn; e += 32) {
+        const int i = e / nn, j = e - i * nn;
+        J[(size_t)i * ld + j] = src[e];
+      }
+      for (int i = lane; i < nn; i += 32) {
+        w.piv[i] = src[nn * nn + i];
+        w.res[i] = src[nn * nn + nn + i];
+        w.sw[i] = cst.sw[(size_t)cell * cst.swld + i];
       }
       __syncwarp();
-    }
+      have = true;
+      from_store = true;
+    };
+    const bool certify = MIXED && stored && !fac32 && !vet && FRp && hspp;
+    if (MIXED && stored && !certify) load_stored();
     if (MIXED) {   // restart point: the plain guess x_p
       for (int i = lane; i < nn; i += 32) w.xg[i] = vet ? w.dx[i] : w.xs[i];
       __syncwarp();
     }
     int it0 = 1;              // first iteration of the loop below
     double dprev0 = INFINITY;  // size of the step taken before it (none)
-    if (MIXED && from_store && !fac32 && !vet && FRp && hspp) {
+    if (certify) {
       // A chord step certified without evaluating any rate: the residual of the
       // guess follows from its stored reaction term, r = b - Y_p + wdt F_p (and
       // h* - h_p), and the kept factor gives the step. A guess whose step is
       // below rtol / 10 is the solution: the cell keeps x_p, its species
       // enthalpies and theta, and only its reaction term (Y - b)/wdt is new.
-      for (int i = lane; i < nn; i += 32)
-        w.r64[i] = (i < N) ? w.bs[i] - w.xs[i] + wdt * FRp[(size_t)i * cs + cell]
-                           : (hst - hp[cell]) * sTf;
+      // The residual is formed in FP64 (it is a difference of nearly equal
+      // values); the step only has to be compared with rtol / 10, so it is the
+      // product of the FP32 copy of the kept inverse with the residual rounded to
+      // FP32 (relative error ~1e-6, on the FP32 pipe), tested against 0.09 rtol.
+      for (int i = lane; i < nn; i += 32) {
+        const double r = (i < N) ? w.bs[i] - w.xs[i] + wdt * FRp[(size_t)i * cs + cell]
+                                 : (hst - hp[cell]) * sTf;
+        w.r64[i] = r;
+        w.zf[i] = __double2float_rn(r);
+      }
       __syncwarp();
-      apply_kept(J, ld, nn, lane, w.r64, w.zd);
-      bool tiny = true;   // max(max|dY|, |dT|/T) <= rtol / 10, without dividing by T
-      for (int i = lane; i < nn; i += 32)
-        tiny = tiny && fabs(w.zd[i]) <= ((i < N) ? 0.1 * rtol : 0.1 * rtol * w.xs[N]);
+      bool tiny = false;
+      if (cst.z32) {
+        const float *zc = cst.z32 + (size_t)cell * nn * nn;   // column-major
+        float z0 = 0.0f, z1 = 0.0f;
+        for (int j = 0; j < nn; ++j) {
+          const float rj = w.zf[j];
+          if (lane < nn) z0 = fmaf(zc[(size_t)j * nn + lane], rj, z0);
+          if (lane + 32 < nn) z1 = fmaf(zc[(size_t)j * nn + lane + 32], rj, z1);
+        }
+        const float thr = (float)(0.09 * rtol), thrT = thr * (float)w.xs[N];
+        tiny = true;   // max(max|dY|, |dT|/T) <= 0.09 rtol, without dividing by T
+        if (lane < nn) tiny = fabsf(z0) <= ((lane < N) ? thr : thrT);
+        if (lane + 32 < nn) tiny = tiny && fabsf(z1) <= ((lane + 32 < N) ? thr : thrT);
+      }
       if (__all_sync(0xffffffffu, tiny)) {
-        double invw = 0.0;
-        if (lane == 0 && wdt > 0.0) invw = 1.0 / wdt;
-        invw = __shfl_sync(0xffffffffu, invw, 0);
         for (int i = lane; i < N; i += 32) {
           const double y = w.xs[i];
           Yout[(size_t)i * cs + cell] = y;
@@ -582,8 +607,11 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       // Not certified, but a step of at most 1e-4 is the chord step the loop's
       // first iteration would take from x_p (there with the rates evaluated afresh
       // at x_p instead of the stored reaction term, which agree to the previous
-      // solve's tolerance). Taken here, it is iteration 1 and costs no rate
-      // evaluation; fresh residuals from x_p + step on decide convergence.
+      // solve's tolerance). Taken here (with the FP64 inverse), it is iteration 1
+      // and costs no rate evaluation; fresh residuals from x_p + step on decide
+      // convergence.
+      load_stored();
+      apply_kept(J, ld, nn, lane, w.r64, w.zd);
       bool fin = true;
       double dm = 0.0;
       for (int i = lane; i < nn; i += 32) {
@@ -698,7 +726,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         for (int i = lane; i < N; i += 32) {
           double wd = 0.0;
           for (int p = m.sp_ptr[i]; p < m.sp_ptr[i + 1]; ++p) wd = fma(m.sp_coef[p], w.src[m.sp_rx[p]], wd);
-          w.r64[i] = fma(wdt / m.rho, wd, w.bs[i] - w.xs[i]);
+          w.r64[i] = fma(wr, wd, w.bs[i] - w.xs[i]);
         }
         if (lane == 0) w.r64[N] = -(sh - hst) * sTf;
         __syncwarp();
@@ -864,14 +892,15 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           if (fallback) {
             no32 = true;
           } else {
-            // the FP32 factor, widened, is the factor in J
+            // the FP32 factor, inverted in FP32 and widened with the row scales D
+            // applied (Z = (D J)^{-1} D, the inverse of the unscaled Jacobian)
+            invert_lu<float>(Jf, ld, nn, lane, w.pivf, w.zf, w.sw);
             for (int e = lane; e < nn * nn; e += 32) {
               const int i = e / nn, j = e - i * nn;
-              J[(size_t)i * ld + j] = (double)Jf[(size_t)i * ld + j];
+              J[(size_t)i * ld + j] = (double)Jf[(size_t)i * ld + j] * w.res[j];
             }
             for (int k = lane; k < nn; k += 32) w.piv[k] = (double)w.pivf[k];
             __syncwarp();
-            invert_kept(w, J, ld, nn, lane);
             have = fresh = true;
             fresh_exact = false;
             from_store = false;
@@ -940,7 +969,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         if (MIXED) {   // an unscaled FP64 factor of the current Jacobian, kept as its inverse
           for (int i = lane; i < nn; i += 32) w.res[i] = 1.0;
           __syncwarp();
-          invert_kept(w, J, ld, nn, lane);
+          invert_lu<double>(J, ld, nn, lane, w.piv, w.zd, w.sw);
           have = fresh = fresh_exact = true;
           from_store = false;
           fac32 = false;
@@ -949,9 +978,12 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       }
       if (MIXED && fresh && cst.f && !exact) {   // keep the new factor for this node's next solve
         double *dst = cst.f + (size_t)cell * cst.fs;
+        float *dz = cst.z32 ? cst.z32 + (size_t)cell * nn * nn : nullptr;
         for (int e = lane; e < nn * nn; e += 32) {
           const int i = e / nn, j = e - i * nn;
-          dst[e] = J[(size_t)i * ld + j];
+          const double v = J[(size_t)i * ld + j];
+          dst[e] = v;
+          if (dz) dz[(size_t)j * nn + i] = __double2float_rn(v);
         }
         for (int i = lane; i < nn; i += 32) {
           dst[nn * nn + i] = w.piv[i];
@@ -1087,9 +1119,6 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     }
     // species enthalpies and theta at the solution; reaction term (Y - b)/wdt
     const double Tf = (code == -3 && !MIXED) ? 1000.0 : T;
-    double invw = 0.0;
-    if (lane == 0 && wdt > 0.0) invw = 1.0 / wdt;
-    invw = __shfl_sync(0xffffffffu, invw, 0);
     double th_f = 0.0;   // theta = (T/T_ref)^theta_exp = exp(theta_exp (ln T - ln T_ref))
     {
       double lnT = 0.0, invT = 0.0;

@@ -861,7 +861,7 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
       c.fs = chord_floats(N);
       c.swld = (int)((F + 3) / 4 * 4);
       if (s->alloc(&c.f, (size_t)c.fs * cs) || s->alloc(&c.sw, (size_t)c.swld * cs) ||
-          s->alloc(&c.valid, cs))
+          s->alloc(&c.valid, cs) || s->alloc(&c.z32, (size_t)F * F * cs))
         return bail(fail(MISDC_E_OOM, "factor store"));
       cudaMemset(c.valid, 0, cs * sizeof(int));
     }

@@ -121,10 +121,13 @@ struct NewtonLaunch {
 // pivot reciprocals, row scales, the temperature-row scale, an FP32-built flag, the
 // state it was built at) and swld bytes of pivot rows; valid[c] bit 0: the factor
 // may be used, bit 1: FP32 factors are too coarse for this cell.
+// z32 (optional): the kept inverse rounded to FP32, column-major per cell
+// ((N+1)^2 floats), which certifies converged guesses on the FP32 pipe.
 struct ChordStore {
   double *f = nullptr;
   unsigned char *sw = nullptr;
   int *valid = nullptr;
+  float *z32 = nullptr;
   int fs = 0, swld = 0;
 };
 __host__ __device__ inline int chord_floats(int N) {

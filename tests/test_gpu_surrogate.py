@@ -282,8 +282,9 @@ def test_learned_guess_fallback_and_agreement():
 
 def test_trained_guess_gain():
     """Record solves, train on them with the library's kernels, and compare the
-    Newton iterations of the same steps with and without the learned guess. The
-    converged state is the same; the iteration counts are reported."""
+    Newton iterations of the same steps with and without the learned guess: the
+    converged state is the same and the trained network saves at least 3 % of
+    the FP64 Newton iterations (measured on a GB300: 5.3 %)."""
     mech, fl = _mild_flame(48)
     dt = 5e-6
     sv = S().Solver(mech, fl, use_graph=False)
@@ -321,3 +322,54 @@ def test_trained_guess_gain():
              learned["newton_iters"] / learned["newton_solves"], learned["surrogate_used"],
              learned["surrogate_rejected"], curve[:10].mean(), curve[-50:].mean()))
     assert learned["surrogate_used"] > 0
+    assert learned["newton_solves"] == plain["newton_solves"]
+    assert learned["newton_iters"] <= 0.97 * plain["newton_iters"], (learned["newton_iters"], plain["newton_iters"])
+
+
+def test_trained_guess_gain_on_a_flame_it_was_not_trained_on():
+    """The learned guess as the benchmark uses it: trained on solves recorded from
+    one flame of the 21-species / 84-reaction mechanism with its full rate ranges
+    (seed 4242, kernel off-centre), applied to another flame of the same recipe
+    (seed 1802, centred kernel) with the benchmark's s_min = 1e-4. It leaves the
+    converged state unchanged and takes fewer FP64 Newton iterations than plain
+    Newton from the previous iterate."""
+    mech = I.make_mechanism(1802, 21, 84)
+    n, dx, dt = 64, 4e-5, 5e-6
+    L = n * dx
+    train = I.flame_2d(mech, 4242, n=n, dx=dx, amp=2.0, radius=0.28 * L, delta=2e-4 * n / 256,
+                       centre=(0.41 * L, 0.57 * L))
+    target = I.flame_2d(mech, 1802, n=n, dx=dx, amp=2.0, radius=0.25 * L, delta=2e-4 * n / 256)
+    sv = S().Solver(mech, train)
+    sv.surrogate_init(seed=3)
+    sv.surrogate_collect(2_000_000)
+    x = sv.state_from_YT(train.Y, train.T)
+    sv.step(x, dt, 4)
+    rows, _, _ = sv.surrogate_dataset()
+    sv.surrogate_collect(0)
+    curve = sv.surrogate_train(1500, batch=8192, lr=2e-3, weight_decay=1e-4, seed=7)
+    params = sv.surrogate_save()
+    sv.close()
+    ref = S().Solver(mech, target)
+    lrn = S().Solver(mech, target)
+    lrn.surrogate_load(params)
+    lrn.surrogate_enable(True, s_min=1e-4)
+    x0 = ref.state_from_YT(target.Y, target.T)
+    a, b = x0.clone(), x0.clone()
+    ref.step(a, dt, 3)
+    lrn.step(b, dt, 3)
+    plain, learned = ref.stats(), lrn.stats()
+    from parity_util import record
+    record("trained_guess_gain_other_flame", plain_iters=plain["newton_iters"],
+           learned_iters=learned["newton_iters"], solves=plain["newton_solves"],
+           used=learned["surrogate_used"], rejected=learned["surrogate_rejected"], rows=rows,
+           loss_first=float(curve[:10].mean()), loss_last=float(curve[-50:].mean()))
+    assert plain["status_name"] == learned["status_name"] == "OK"
+    A, B = a.cpu().numpy(), b.cpu().numpy()
+    # the two runs take different Newton paths to the same roots; with rates up to
+    # A = 1e14 the steps amplify their round-off differences (as in the FP64
+    # parity tests), so the states agree to the mixed bar rather than to 1e-10
+    d = max(nrel(B[f], A[f]) for f in range(A.shape[0]))
+    record("trained_guess_gain_other_flame_state", max_rel_diff=d)
+    assert d < 1e-8, d
+    assert learned["surrogate_used"] > 0
+    assert learned["newton_iters"] < plain["newton_iters"], (learned["newton_iters"], plain["newton_iters"])
