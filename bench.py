@@ -254,7 +254,12 @@ def entries_for(name, grid=0):
         b = I.BATCHES[name]
         return I.build_batch(name), b
     w = I.WORKLOADS[name]
-    over = {"n": grid} if grid > 0 and w["dim"] > 1 else None
+    over = None
+    if grid > 0 and w["dim"] > 1:
+        # the kernel radius scales with the box (same burnt fraction); the front
+        # keeps its width in cells
+        full = w["grid"].get("n", 128 if w["dim"] == 3 else 256)
+        over = {"n": grid, "radius": 2e-3 * grid / full}
     mech, fl, w = I.build_workload(name, over)
     return [(mech, fl, w["dt"])], w
 

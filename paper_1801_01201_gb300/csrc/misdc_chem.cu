@@ -338,8 +338,8 @@ struct NW {
 // doubles of shared memory one warp needs
 __host__ __device__ inline size_t newton_warp_doubles(int N, int R, int ld, bool mixed) {
   const size_t nn = N + 1;
-  size_t d = nn * ld + 8 * (size_t)R + 6 * (size_t)N + 3 * nn;
-  if (mixed) d += (nn * ld + 1) / 2 + 4 * nn + (3 * nn + 1) / 2 + 1;
+  size_t d = nn * ld + 8 * (size_t)R + 6 * (size_t)N + 4 * nn;
+  if (mixed) d += (nn * ld + 1) / 2 + 3 * nn + (3 * nn + 1) / 2 + 1;
   return d;
 }
 
@@ -357,17 +357,17 @@ __device__ __forceinline__ NW carve2(double *p, int N, int R, int ld, bool mixed
   w.cpm = p; p += N;
   w.piv = p; p += nn;
   w.dx = p; p += nn;
+  w.xg = p; p += nn;
   if (mixed) {
     w.r64 = p; p += nn;
     w.res = p; p += nn;
-    w.xg = p; p += nn;
     w.zd = p; p += nn;
     w.Jf = reinterpret_cast<float *>(p); p += ((size_t)nn * ld + 1) / 2;
     float *f = reinterpret_cast<float *>(p);
     w.zf = f; w.pivf = f + nn;
     w.sw = reinterpret_cast<int *>(f + 2 * nn);
   } else {
-    w.r64 = w.res = w.xg = w.zd = nullptr; w.Jf = w.zf = w.pivf = nullptr; w.sw = nullptr;
+    w.r64 = w.res = w.zd = nullptr; w.Jf = w.zf = w.pivf = nullptr; w.sw = nullptr;
   }
   return w;
 }
@@ -499,7 +499,8 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       for (int i = lane; i < nn; i += 32) {
         const double xp = w.xs[i];
         w.dx[i] = xp;
-        const double f = s0 * (double)pc[i];
+        // the output in the range of the training targets
+        const double f = s0 * fmin(fmax((double)pc[i], -8.0), 8.0);
         w.xs[i] = (i < N) ? xp + f : xp * (1.0 + fmin(fmax(f, -0.5), 0.5));
       }
       __syncwarp();
@@ -548,10 +549,14 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     };
     const bool certify = MIXED && stored && !fac32 && !vet && FRp && hspp;
     if (MIXED && stored && !certify) load_stored();
-    if (MIXED) {   // restart point: the plain guess x_p
+    {   // restart point: the plain guess x_p
       for (int i = lane; i < nn; i += 32) w.xg[i] = vet ? w.dx[i] : w.xs[i];
       __syncwarp();
     }
+    // the solve started from an accepted learned guess: its root must lie near the
+    // plain guess (within 100 times the scale s of the residual there), otherwise
+    // the solve is repeated from x_p, whose root is the one the plain method finds
+    bool guessed = false;
     int it0 = 1;              // first iteration of the loop below
     double dprev0 = INFINITY;  // size of the step taken before it (none)
     if (certify) {
@@ -635,9 +640,10 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
     double T = w.xs[N];
     double dprev = dprev0;
     int it, code = 0;
-    for (int attempt = 0; attempt < (MIXED ? 2 : 1); ++attempt) {
+    for (int attempt = 0; attempt < ((MIXED || guessed) ? 2 : 1); ++attempt) {
     if (attempt == 1) {
-      // the mixed iteration failed: plain FP64 Newton from the same start
+      // the mixed iteration (or a solve from a learned guess) failed: plain FP64
+      // Newton from the plain guess
       if (code == 0) break;
       for (int i = lane; i < nn; i += 32) w.xs[i] = w.xg[i];
       __syncwarp();
@@ -812,6 +818,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           continue;
         }
         ++my_sg;
+        guessed = true;
       }
       bool singular = false, fallback = false;
       if (MIXED) {
@@ -1021,6 +1028,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
         }
         if (d0 < dp) {
           ++my_sg;
+          guessed = true;
         } else {
           for (int i = lane; i < nn; i += 32) {
             w.xs[i] = w.xg[i];
@@ -1109,6 +1117,18 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       dprev = d;
     }
     if (code == 0 && it > maxit) code = -1;
+    if (attempt == 0 && guessed && code == 0) {
+      double far = 0.0;
+      for (int i = lane; i < nn; i += 32)
+        far = fmax(far, (i < N) ? fabs(w.xs[i] - w.xg[i]) : fabs(w.xs[i] - w.xg[i]) / w.xg[i]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) far = fmax(far, __shfl_xor_sync(0xffffffffu, far, o));
+      if (!(far <= 100.0 * s0 + 1e-10)) code = -4;   // another root: solve again from x_p
+    }
+    if (!MIXED && attempt == 0 && guessed && code) {
+      ++my_rej;   // counted as a rejected guess
+      --my_sg;
+    }
     }   // attempt
     if (MIXED && code) {
       // both attempts failed: the cell keeps its finite starting point (the

@@ -174,11 +174,18 @@ __global__ void k_face_coef(DevGrid g, FieldMap fm, const double *__restrict__ t
       if (thf32) thf32[(size_t)d * cs + c] = (float)lo;
       S += lo + hi;
     }
-    for (int k = 0; k < fm.nfs; ++k) {
-      const double di = 1.0 / (1.0 + fm.cf[k] * S);
-      invdiag[(size_t)k * cs + c] = di;
-      if (invdiag32) invdiag32[(size_t)k * cs + c] = (float)di;
-      if (cdiag) cdiag[(size_t)k * cs + c] = fm.cf[k] * di;
+    if (invdiag) {
+      for (int k = 0; k < fm.nfs; ++k) {
+        const double di = 1.0 / (1.0 + fm.cf[k] * S);
+        invdiag[(size_t)k * cs + c] = di;
+        if (invdiag32) invdiag32[(size_t)k * cs + c] = (float)di;
+        if (cdiag) cdiag[(size_t)k * cs + c] = fm.cf[k] * di;
+      }
+    } else if (invdiag32) {
+      // FP32 inner solves only (mixed precision): the diagonal in FP32
+      const float Sf = (float)S;
+      for (int k = 0; k < fm.nfs; ++k)
+        invdiag32[(size_t)k * cs + c] = 1.0f / fmaf((float)fm.cf[k], Sf, 1.0f);
     }
     ratio = cmax * S / (1.0 + cmax * S);
   }
@@ -853,9 +860,11 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
   double cmax = 0.0;
   for (int k = 0; k < fm.nfs; ++k) cmax = std::max(cmax, fm.cf[k]);
   cudaMemsetAsync(w.rho_bits, 0, sizeof(unsigned long long), s);
-  k_face_coef<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, theta, w.thf, w.invdiag, cmax, w.rho_bits,
-                                               w.thf32, w.invdiag32, w.cdiag);
-  if (w.refine_rounds > 0 && w.levels <= 1) {
+  const bool refine = w.refine_rounds > 0 && w.levels <= 1;   // FP32 inner Chebyshev solves
+  k_face_coef<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, theta, w.thf, refine ? nullptr : w.invdiag, cmax,
+                                               w.rho_bits, w.thf32, w.invdiag32,
+                                               refine ? nullptr : w.cdiag);
+  if (refine) {
     // mixed precision: FP64 residuals, FP32 inner Chebyshev solves (reduction 1e-6
     // each), three rounds, then the same reconstruction and checks as below
     const int k32 = std::min(sweeps, chebyshev_sweeps(rho_bound, 1e-6));
