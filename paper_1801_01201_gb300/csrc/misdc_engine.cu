@@ -243,7 +243,7 @@ void copy_node(misdc_solver *s, NodeBuf &d, const NodeBuf &a, cudaStream_t st) {
 // F_E and F_D of a node state whose theta and hsp are current
 void node_operators(misdc_solver *s, NodeBuf &b, double *thf, cudaStream_t st) {
   launch_theta_faces(s->g, b.theta, thf, st);
-  launch_operators(s->m, s->g, s->i0, b.phi, b.hsp, thf, s->vel, b.FE, b.FD, st);
+  launch_operators(s->m, s->g, s->i0, b.phi, b.hsp, thf, s->vel, b.FE, b.FD, thf + 3 * s->cs, st);
 }
 
 double rho_bound_for(misdc_solver *s, double wdt_max) {
@@ -840,8 +840,10 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     if (op->scheme == MISDC_SCHEME_CISDCQ && op->nu > 1 && (st = alloc_node(s, s->Y[j]))) return bail(st);
     if (s->alloc(&s->B[j], F * cs)) return bail(fail(MISDC_E_OOM, "B"));
   }
-  if (s->alloc(&s->rhsD, F * cs) || s->alloc(&s->bR, F * cs) || s->alloc(&s->thfD, 3 * cs) ||
-      s->alloc(&s->thfR, 3 * cs) || s->alloc(&s->iters, cs) || s->alloc(&s->st, 1) ||
+  // per stream: theta on the faces [3][cs], then the operators' face fluxes
+  const size_t thf_n = 3 * cs + operator_face_doubles(s->g, s->N);
+  if (s->alloc(&s->rhsD, F * cs) || s->alloc(&s->bR, F * cs) || s->alloc(&s->thfD, thf_n) ||
+      s->alloc(&s->thfR, thf_n) || s->alloc(&s->iters, cs) || s->alloc(&s->st, 1) ||
       s->alloc(&s->nl.work, 1) ||
       s->alloc(&s->dw.thf, 3 * cs) || s->alloc(&s->dw.invdiag, F * cs) || s->alloc(&s->dw.xa, F * cs) ||
       s->alloc(&s->dw.cdiag, F * cs) || s->alloc(&s->dw.bdiag, F * cs) ||
@@ -1141,7 +1143,8 @@ misdc_status misdc_operators(misdc_solver *s, const double *state, double *FE, d
   launch_temperature(s->m, s->cs, s->cs, b.phi, b.phi + (size_t)s->N * cs, nullptr, b.T, b.theta,
                      b.hsp, s->st, st);
   launch_theta_faces(s->g, b.theta, s->thfD, st);
-  if (FE || FD) launch_operators(s->m, s->g, s->i0, b.phi, b.hsp, s->thfD, s->vel, FE, FD, st);
+  if (FE || FD)
+    launch_operators(s->m, s->g, s->i0, b.phi, b.hsp, s->thfD, s->vel, FE, FD, s->thfD + 3 * cs, st);
   if (FR) {
     launch_rates(s->m, s->cs, s->cs, b.phi, b.T, FR, st, s->o.rates_mma != 0);
     CK(cudaMemsetAsync(FR + (size_t)s->N * cs, 0, cs * sizeof(double), st));

@@ -66,37 +66,39 @@ __global__ void k_lincomb(LinComb lc, size_t n) {
 
 // ---------------------------------------------------------------------------
 // F_E (advection of every field + explicit differential diffusion of h) and
-// F_D (implicit diffusion, dominant species closed by minus the sum).
+// F_D (implicit diffusion, dominant species closed by minus the sum), in two
+// passes so that every face is evaluated once (FP64 instructions bound these
+// kernels): k_faces writes, for the low face of every cell along every used
+// direction, the advective flux, the diffusive flux and the differential-diffusion
+// flux of h; k_divergence differences them.
+//
+// Face buffer (per direction d, quantity q, cell c at fb[(d * (2N+3) + q) * cs + c]):
+//   q = f (0..N):       A_f = u (7 (x_{c-1} + x_c) - (x_{c-2} + x_{c+1}))   (12 x the
+//                        fourth-order face value times the face velocity)
+//   q = N + 1 + f:      D_f = theta_face (x_c - x_{c-1})                  (f != i0)
+//   q = 2N + 2:         Q = theta_face (hbar0 G + q), the differential diffusion of h
+//                        of eq. enthalpy_equation with the dominant species' flux
+//                        minus the others':  q = sum_i (h_i,l + h_i,r)(Y_i,r - Y_i,l)
+//                        (alpha0 - D_i) (D_i -> 0 for i0), G = sum_{i != i0} D_i
+//                        (Y_i,r - Y_i,l), hbar0 = h_i0,l + h_i0,r
+// The 1/12, 1/dx, 1/dx^2, 1/2 and the per-field D0 are applied in k_divergence.
 // ---------------------------------------------------------------------------
 template <int DIM>
-__global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restrict__ phi,
-                            const double *__restrict__ hsp, const double *__restrict__ thf,
-                            const double *__restrict__ vel, double *__restrict__ FE,
-                            double *__restrict__ FD) {
+__global__ void k_faces(DevMech m, DevGrid g, int i0, const double *__restrict__ phi,
+                        const double *__restrict__ hsp, const double *__restrict__ thf,
+                        const double *__restrict__ vel, double *__restrict__ fb) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int cs = g.cells;
   if (c >= cs) return;
-  const int N = m.N;
+  const int N = m.N, FB = 2 * N + 3;
   const Nbr nb = neighbours(g, c);
-  const double invdx = 1.0 / g.dx, invdx2 = invdx * invdx;
-  // fourth-order face values are (7(a+b) - (c+d))/12; the 1/12 is applied once
-  // per field with 1/dx (an FP64 division per face would dominate the kernel)
-  const double adv = invdx / 12.0;
-  double ulo[DIM], uhi[DIM], tlo[DIM], thi[DIM];
-  // differential diffusion of h (eq. enthalpy_equation), per low / high face:
-  //   q = sum_i hbar_i (lambda/cp - rho D_i) grad Y_i  and  G = sum_{i != i0} rho D_i grad Y_i,
-  // accumulated as sq = sum_i (h_a + h_b)(Y_b - Y_a)(alpha0 - D_i) and
-  // sg = sum_{i != i0} D_i (Y_b - Y_a); the face's theta, 1/2 and 1/dx are applied once
-  double sqlo[DIM], sqhi[DIM], sglo[DIM], sghi[DIM];
+  double u[DIM], th[DIM], sq[DIM], sg[DIM];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    ulo[d] = vel[(size_t)d * cs + c];
-    uhi[d] = vel[(size_t)d * cs + nb.cp[d]];
-    tlo[d] = thf[(size_t)d * cs + c];
-    thi[d] = thf[(size_t)d * cs + nb.cp[d]];
-    sqlo[d] = sqhi[d] = sglo[d] = sghi[d] = 0.0;
+    u[d] = vel[(size_t)d * cs + c];
+    th[d] = thf[(size_t)d * cs + c];
+    sq[d] = sg[d] = 0.0;
   }
-  double fd_i0 = 0.0, fa_h = 0.0;
   for (int f = 0; f <= N; ++f) {
     const double *x = phi + (size_t)f * cs;
     const double xc = x[c];
@@ -105,51 +107,67 @@ __global__ void k_operators(DevMech m, DevGrid g, int i0, const double *__restri
     const double hc = sp ? hs[c] : 0.0;
     const double wf = sp ? (f != i0 ? m.alpha0 - m.D0[f] : m.alpha0) : 0.0;
     const double Df = (sp && f != i0) ? m.D0[f] : 0.0;
-    double fa = 0.0, fdl = 0.0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      const double xm2 = x[nb.cm2[d]], xm = x[nb.cm[d]], xp = x[nb.cp[d]], xp2 = x[nb.cp2[d]];
-      const double lo = fma(7.0, xm + xc, -(xm2 + xp));   // 12 x face value
-      const double hi = fma(7.0, xc + xp, -(xm + xp2));
-      fa = fma(uhi[d], hi, fa);
-      fa = fma(-ulo[d], lo, fa);
-      const double dl = xc - xm, dh = xp - xc;
-      fdl = fma(thi[d], dh, fdl);
-      fdl = fma(-tlo[d], dl, fdl);
+      const int cm = nb.cm[d];
+      const double xm = x[cm];
+      const double face12 = fma(7.0, xm + xc, -(x[nb.cm2[d]] + x[nb.cp[d]]));
+      double *o = fb + (size_t)d * FB * cs + c;
+      o[(size_t)f * cs] = u[d] * face12;
+      const double dl = xc - xm;
+      if (f != i0) o[(size_t)(N + 1 + f) * cs] = th[d] * dl;
       if (sp) {
-        const double hl = hs[nb.cm[d]] + hc, hh = hc + hs[nb.cp[d]];
-        sqlo[d] = fma(hl * dl, wf, sqlo[d]);
-        sqhi[d] = fma(hh * dh, wf, sqhi[d]);
-        sglo[d] = fma(Df, dl, sglo[d]);
-        sghi[d] = fma(Df, dh, sghi[d]);
+        sq[d] = fma((hs[cm] + hc) * dl, wf, sq[d]);
+        sg[d] = fma(Df, dl, sg[d]);
       }
     }
-    if (sp) {
+  }
+  const double *hs0 = hsp + (size_t)i0 * cs;
+  const double h0 = hs0[c];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d)
+    fb[((size_t)d * FB + 2 * N + 2) * cs + c] = th[d] * fma(hs0[nb.cm[d]] + h0, sg[d], sq[d]);
+}
+
+template <int DIM>
+__global__ void k_divergence(DevMech m, DevGrid g, int i0, const double *__restrict__ fb,
+                             double *__restrict__ FE, double *__restrict__ FD) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cs = g.cells;
+  if (c >= cs) return;
+  const int N = m.N, FB = 2 * N + 3;
+  const Nbr nb = neighbours(g, c);
+  const double invdx = 1.0 / g.dx, invdx2 = invdx * invdx;
+  const double adv = invdx / 12.0;
+  int cp[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) cp[d] = nb.cp[d];
+  // sum over directions of (value at the high face) - (value at the low face)
+  auto div = [&](int q) {
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const double *a = fb + ((size_t)d * FB + q) * cs;
+      s += a[cp[d]] - a[c];
+    }
+    return s;
+  };
+  double fd_i0 = 0.0;
+  for (int f = 0; f <= N; ++f) {
+    const double fa = div(f);
+    if (f < N) {
       if (FE) FE[(size_t)f * cs + c] = -fa * adv;
       if (f != i0) {
-        const double v = m.D0[f] * fdl * invdx2;
+        const double v = m.D0[f] * div(N + 1 + f) * invdx2;
         if (FD) FD[(size_t)f * cs + c] = v;
         fd_i0 -= v;
       }
     } else {
-      fa_h = fa;
-      if (FD) FD[(size_t)N * cs + c] = m.alpha0 * fdl * invdx2;
+      if (FD) FD[(size_t)N * cs + c] = m.alpha0 * div(N + 1 + N) * invdx2;
+      if (FE) FE[(size_t)N * cs + c] = -fa * adv - 0.5 * div(2 * N + 2) * invdx2;
     }
   }
   if (FD) FD[(size_t)i0 * cs + c] = fd_i0;
-  if (FE) {
-    // the dominant species' flux is minus the others' (its h weighs -G)
-    const double *hs0 = hsp + (size_t)i0 * cs;
-    const double h0 = hs0[c];
-    double div = 0.0;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const double hl0 = hs0[nb.cm[d]] + h0, hh0 = h0 + hs0[nb.cp[d]];
-      div = fma(thi[d], fma(hh0, sghi[d], sqhi[d]), div);
-      div = fma(-tlo[d], fma(hl0, sglo[d], sqlo[d]), div);
-    }
-    FE[(size_t)N * cs + c] = -fa_h * adv - 0.5 * div * invdx2;
-  }
 }
 
 // theta at cells -> harmonic mean at the low face of each cell; inverse
@@ -664,16 +682,24 @@ void launch_lincomb(const LinComb &lc, size_t n, cudaStream_t s) {
   k_lincomb<<<(unsigned)blocks, 256, 0, s>>>(lc, n);
 }
 
+size_t operator_face_doubles(const DevGrid &g, int N) {
+  return (size_t)g.dim * (2 * N + 3) * g.cells;
+}
+
 void launch_operators(const DevMech &m, const DevGrid &g, int i0, const double *phi,
                       const double *hsp, const double *theta_face, const double *vel,
-                      double *FE, double *FD, cudaStream_t s) {
+                      double *FE, double *FD, double *faces, cudaStream_t s) {
   const int blocks = (g.cells + 127) / 128;
-  if (g.dim == 1)
-    k_operators<1><<<blocks, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, FE, FD);
-  else if (g.dim == 2)
-    k_operators<2><<<blocks, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, FE, FD);
-  else
-    k_operators<3><<<blocks, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, FE, FD);
+  if (g.dim == 1) {
+    k_faces<1><<<blocks, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, faces);
+    k_divergence<1><<<blocks, 128, 0, s>>>(m, g, i0, faces, FE, FD);
+  } else if (g.dim == 2) {
+    k_faces<2><<<blocks, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, faces);
+    k_divergence<2><<<blocks, 128, 0, s>>>(m, g, i0, faces, FE, FD);
+  } else {
+    k_faces<3><<<blocks, 128, 0, s>>>(m, g, i0, phi, hsp, theta_face, vel, faces);
+    k_divergence<3><<<blocks, 128, 0, s>>>(m, g, i0, faces, FE, FD);
+  }
 }
 
 void launch_theta_faces(const DevGrid &g, const double *theta, double *thf, cudaStream_t s) {

@@ -157,9 +157,12 @@ struct LinComb {
   double w[8][16];
 };
 void launch_lincomb(const LinComb &lc, size_t n, cudaStream_t s);
+// faces: scratch of operator_face_doubles(g, N) doubles (the face fluxes of the
+// two-pass operator kernels)
+size_t operator_face_doubles(const DevGrid &g, int N);
 void launch_operators(const DevMech &m, const DevGrid &g, int i0, const double *phi,
                       const double *hsp, const double *theta_face, const double *vel,
-                      double *FE, double *FD, cudaStream_t s);
+                      double *FE, double *FD, double *faces, cudaStream_t s);
 // theta at cells -> theta at the low face of every cell (harmonic mean)
 void launch_theta_faces(const DevGrid &g, const double *theta, double *thf, cudaStream_t s);
 void prepare_chem_kernels(const DevMech &m);
