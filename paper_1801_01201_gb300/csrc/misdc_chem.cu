@@ -435,6 +435,90 @@ __device__ __forceinline__ void apply_kept(const double *J, int ld, int nn, int 
   __syncwarp();
 }
 
+// Certification of converged guesses, one thread per cell (mixed precision with
+// kept factors). A cell whose guess x_p has a kept FP64-built factor, built within
+// 1e-4 of x_p, is solved when the step through that factor's inverse Z of the
+// residual r = b - Y_p + wdt F_p (and (h* - h_p) times the temperature-row scale),
+// formed from the stored reaction term F_p without evaluating any rate, is below
+// 0.09 rtol (|dY|, |dT|/T). r is formed in FP64 (a difference of nearly equal
+// values), rounded to FP32 and multiplied by the FP32 copy of Z on the FP32 pipe
+// (the product only has to be compared with the threshold). A certified cell keeps
+// x_p, its species enthalpies and theta; its reaction term is (Y - b)/wdt. Every
+// other cell (no usable factor, a learned guess to vet, a step above the
+// threshold) is appended to `list` for the warp-per-cell Newton kernel.
+__global__ void __launch_bounds__(256) k_certify(DevMech m, int n, int cs, double wdt, double rtol,
+                                                 const double *__restrict__ b,
+                                                 const double *__restrict__ hstar,
+                                                 const double *__restrict__ Yg,
+                                                 const double *__restrict__ Tg,
+                                                 double *__restrict__ Yout, double *__restrict__ Tout,
+                                                 double *__restrict__ FR, double *__restrict__ hsp,
+                                                 double *__restrict__ theta, int *__restrict__ iters,
+                                                 DevStats *st, const double *__restrict__ sc,
+                                                 double s_min, const int *__restrict__ prow,
+                                                 const double *__restrict__ FRp,
+                                                 const double *__restrict__ hp, ChordStore cst,
+                                                 const double *__restrict__ hspp,
+                                                 const double *__restrict__ thp,
+                                                 int *__restrict__ list, int *__restrict__ list_n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = m.N, nn = N + 1;
+  bool done = false;
+  if (c < n) {
+    bool ok = (cst.valid[c] & 1) != 0;
+    if (ok && sc) {   // a learned guess goes to the Newton kernel, which vets it
+      const int prw = prow ? prow[c] : c;
+      const double s0 = sc[c];
+      ok = !(prw >= 0 && s0 > s_min && isfinite(s0));
+    }
+    const double *src = cst.f + (size_t)c * cst.fs;
+    if (ok) ok = src[nn * nn + 2 * nn + 1] == 0.0;   // FP64-built factors only
+    const double T = Tg[c];
+    if (ok) {   // the factor was built near x_p (without dividing by T)
+      const double *xf = src + nn * nn + 2 * nn + 2;
+      for (int i = 0; i < N && ok; ++i) ok = fabs(Yg[(size_t)i * cs + c] - xf[i]) <= 1e-4;
+      ok = ok && fabs(T - xf[N]) <= 1e-4 * T;
+    }
+    if (ok) {
+      float r32[kMaxSpecies + 1];
+      for (int i = 0; i < N; ++i)
+        r32[i] = __double2float_rn(b[(size_t)i * cs + c] - Yg[(size_t)i * cs + c] +
+                                   wdt * FRp[(size_t)i * cs + c]);
+      r32[N] = __double2float_rn((hstar[c] - hp[c]) * src[nn * nn + 2 * nn]);
+      const float thr = (float)(0.09 * rtol), thrT = thr * (float)T;
+      for (int i = 0; i < nn && ok; ++i) {
+        float z = 0.0f;
+        for (int j = 0; j < nn; ++j) z = fmaf(cst.z32[((size_t)j * nn + i) * cs + c], r32[j], z);
+        ok = fabsf(z) <= (i < N ? thr : thrT);
+      }
+    }
+    if (ok) {
+      const double invw = (wdt > 0.0) ? 1.0 / wdt : 0.0;
+      for (int i = 0; i < N; ++i) {
+        const double y = Yg[(size_t)i * cs + c];
+        Yout[(size_t)i * cs + c] = y;
+        if (FR) FR[(size_t)i * cs + c] = (y - b[(size_t)i * cs + c]) * invw;
+        if (hsp) hsp[(size_t)i * cs + c] = hspp[(size_t)i * cs + c];
+      }
+      Tout[c] = T;
+      if (theta) theta[c] = thp[c];
+      if (iters) iters[c] = 1;
+      done = true;
+    } else {
+      list[atomicAdd(list_n, 1)] = c;
+    }
+  }
+  // statistics: one atomic per warp
+  const unsigned cert = __ballot_sync(0xffffffffu, done);
+  if ((threadIdx.x & 31) == 0 && cert) {
+    const unsigned long long k = __popc(cert);
+    atomicAdd(&st->newton_solves, k);
+    atomicAdd(&st->newton_iters, k);
+    atomicAdd(&st->certified, k);
+    atomicMax(&st->newton_max, 1);
+  }
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, double wdt, double rtol,
                                                  int maxit, int ld, const double *__restrict__ b,
@@ -451,7 +535,9 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
                                                  int *__restrict__ work, ChordStore cst,
                                                  const int *__restrict__ prow,
                                                  const double *__restrict__ hspp,
-                                                 const double *__restrict__ thp) {
+                                                 const double *__restrict__ thp,
+                                                 const int *__restrict__ list,
+                                                 const int *__restrict__ list_n) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int N = m.N, R = m.R, nn = N + 1, na = nn + 1;   // na: columns of the augmented matrix
@@ -470,13 +556,19 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
 
   // cells: a fixed grid-stride share per warp, or (work != NULL) the next free cell
   // from a global counter, which balances the per-cell iteration counts
-  auto next_cell = [&](int cur) -> int {
+  // work items: a fixed grid-stride share per warp, or (work != NULL) the next
+  // free item from a global counter, which balances the per-cell iteration counts;
+  // an item is a cell, or with `list` the list's entry (the cells that the
+  // certification kernel left)
+  auto next_item = [&](int cur) -> int {
     if (!work) return cur < 0 ? blockIdx.x * wpb + wib : cur + gridDim.x * wpb;
     int c = 0;
     if (lane == 0) c = atomicAdd(work, 1);
     return __shfl_sync(0xffffffffu, c, 0);
   };
-  for (int cell = next_cell(-1); cell < n; cell = next_cell(cell)) {
+  const int items = list ? *list_n : n;
+  for (int item = next_item(-1); item < items; item = next_item(item)) {
+    const int cell = list ? list[item] : item;
     for (int i = lane; i < N; i += 32) {
       w.xs[i] = Yg[(size_t)i * cs + cell];
       w.bs[i] = b[(size_t)i * cs + cell];
@@ -577,13 +669,12 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       }
       __syncwarp();
       bool tiny = false;
-      if (cst.z32) {
-        const float *zc = cst.z32 + (size_t)cell * nn * nn;   // column-major
+      if (cst.z32 && !list) {   // (with a list the certification kernel has tested it)
         float z0 = 0.0f, z1 = 0.0f;
         for (int j = 0; j < nn; ++j) {
           const float rj = w.zf[j];
-          if (lane < nn) z0 = fmaf(zc[(size_t)j * nn + lane], rj, z0);
-          if (lane + 32 < nn) z1 = fmaf(zc[(size_t)j * nn + lane + 32], rj, z1);
+          if (lane < nn) z0 = fmaf(cst.z32[((size_t)j * nn + lane) * cs + cell], rj, z0);
+          if (lane + 32 < nn) z1 = fmaf(cst.z32[((size_t)j * nn + lane + 32) * cs + cell], rj, z1);
         }
         const float thr = (float)(0.09 * rtol), thrT = thr * (float)w.xs[N];
         tiny = true;   // max(max|dY|, |dT|/T) <= 0.09 rtol, without dividing by T
@@ -985,12 +1076,11 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       }
       if (MIXED && fresh && cst.f && !exact) {   // keep the new factor for this node's next solve
         double *dst = cst.f + (size_t)cell * cst.fs;
-        float *dz = cst.z32 ? cst.z32 + (size_t)cell * nn * nn : nullptr;
         for (int e = lane; e < nn * nn; e += 32) {
           const int i = e / nn, j = e - i * nn;
           const double v = J[(size_t)i * ld + j];
           dst[e] = v;
-          if (dz) dz[(size_t)j * nn + i] = __double2float_rn(v);
+          if (cst.z32) cst.z32[((size_t)j * nn + i) * cs + cell] = __double2float_rn(v);
         }
         for (int i = lane; i < nn; i += 32) {
           dst[nn * nn + i] = w.piv[i];
@@ -1290,14 +1380,28 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
   if (work) cudaMemsetAsync(work, 0, sizeof(int), s);
   ChordStore cst{};
   if (mixed && store) cst = *store;
+  // mixed precision with kept factors and the stored reaction terms of the
+  // guesses: certification first (one thread per cell), then the warp-per-cell
+  // Newton on the cells it left
+  const bool split = mixed && cst.f && cst.valid && cst.z32 && FRp && hspp && hp && thp && cfg &&
+                     cfg->list && cfg->list_n;
+  const int *list = split ? cfg->list : nullptr, *list_n = split ? cfg->list_n : nullptr;
+  if (split) {
+    cudaMemsetAsync(cfg->list_n, 0, sizeof(int), s);
+    k_certify<<<(n + 255) / 256, 256, 0, s>>>(m, n, cs, wdt, rtol, b, hstar, Yg, Tg, Y, T, FR, hsp,
+                                              theta, iters, st, pred ? sc : nullptr, s_min, prow, FRp,
+                                              hp, cst, hspp, thp, cfg->list, cfg->list_n);
+  }
   if (mixed)
     k_newton2<true><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
                                                FR, hsp, theta, iters, st, pred, ldp, sc,
-                                               s_min, FRp, hp, work, cst, prow, hspp, thp);
+                                               s_min, FRp, hp, work, cst, prow, hspp, thp, list,
+                                               list_n);
   else
     k_newton2<false><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
                                                 FR, hsp, theta, iters, st, pred, ldp, sc,
-                                                s_min, FRp, hp, work, cst, prow, hspp, thp);
+                                                s_min, FRp, hp, work, cst, prow, hspp, thp, nullptr,
+                                                nullptr);
 }
 
 

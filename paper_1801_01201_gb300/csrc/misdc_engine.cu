@@ -844,7 +844,7 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   const size_t thf_n = 3 * cs + operator_face_doubles(s->g, s->N);
   if (s->alloc(&s->rhsD, F * cs) || s->alloc(&s->bR, F * cs) || s->alloc(&s->thfD, thf_n) ||
       s->alloc(&s->thfR, thf_n) || s->alloc(&s->iters, cs) || s->alloc(&s->st, 1) ||
-      s->alloc(&s->nl.work, 1) ||
+      s->alloc(&s->nl.work, 1) || s->alloc(&s->nl.list, cs) || s->alloc(&s->nl.list_n, 1) ||
       s->alloc(&s->dw.thf, 3 * cs) || s->alloc(&s->dw.invdiag, F * cs) || s->alloc(&s->dw.xa, F * cs) ||
       s->alloc(&s->dw.cdiag, F * cs) || s->alloc(&s->dw.bdiag, F * cs) ||
       s->alloc(&s->dw.xb, F * cs) || s->alloc(&s->dw.xc, F * cs) ||
@@ -1123,6 +1123,7 @@ misdc_status misdc_reaction_solve(misdc_solver *s, double wdt, const double *b, 
   CK(cudaMallocAsync(&th, n * sizeof(double), (cudaStream_t)stream));
   NewtonLaunch nl = s->nl;
   nl.dynamic = 0;   // the counter belongs to the step's stream
+  nl.list = nl.list_n = nullptr;
   launch_newton(s->m, n, n, wdt, s->o.newton_rtol, s->o.newton_maxit, b, hstar, x, x + N * n, x,
                 x + N * n, FR, hsp, th, iters, s->st, (cudaStream_t)stream,
                 s->o.precision == MISDC_PREC_MIXED, nullptr, 0, nullptr, 0.0, nullptr, nullptr, &nl);
@@ -1364,6 +1365,7 @@ extern "C" misdc_status misdc_reaction_solve_noalloc(misdc_solver *s, double wdt
   CK(cudaMemsetAsync(stats, 0, sizeof(DevStats), cs));
   NewtonLaunch nl = s->nl;   // the solver's (autotuned) launch shape, as misdc_reaction_solve
   nl.dynamic = 0;            // the work counter is solver memory: static cell scheduling here
+  nl.list = nl.list_n = nullptr;
   launch_newton(s->m, n, n, wdt, s->o.newton_rtol, s->o.newton_maxit, b, hstar, x, x + N * n, x,
                 x + N * n, FR, hsp, theta, iters, stats, cs, s->o.precision == MISDC_PREC_MIXED,
                 nullptr, 0, nullptr, 0.0, nullptr, nullptr, &nl);

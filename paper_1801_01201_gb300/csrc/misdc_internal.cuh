@@ -112,17 +112,21 @@ void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double
 // Launch shape of the reaction Newton (chosen by the autotuner): warps per block
 // (0: largest that fits), resident-block cap per SM (0: default), and dynamic
 // cell scheduling through the device counter `work`.
+// list / list_n (mixed precision with kept factors): scratch of cs + 1 ints for the
+// cells a kept factor did not certify, which the warp-per-cell kernel then takes.
 struct NewtonLaunch {
   int wpb = 0, blocks_per_sm = 0, dynamic = 0;
   int *work = nullptr;
+  int *list = nullptr, *list_n = nullptr;
 };
 // Mixed precision: per-cell Jacobian factors kept between the solves of one SDC
 // node. Per cell: fs doubles (row-major LU of the (row-scaled) (N+1)^2 Jacobian,
 // pivot reciprocals, row scales, the temperature-row scale, an FP32-built flag, the
 // state it was built at) and swld bytes of pivot rows; valid[c] bit 0: the factor
 // may be used, bit 1: FP32 factors are too coarse for this cell.
-// z32 (optional): the kept inverse rounded to FP32, column-major per cell
-// ((N+1)^2 floats), which certifies converged guesses on the FP32 pipe.
+// z32 (optional): the kept inverse rounded to FP32, element-major ([e][cs] with
+// e = j (N+1) + i for entry (i, j)), which certifies converged guesses on the FP32
+// pipe, one thread per cell.
 struct ChordStore {
   double *f = nullptr;
   unsigned char *sw = nullptr;
