@@ -272,6 +272,45 @@ misdc_status misdc_pde_step(int scheme, int n_nodes, int n_sweeps, int nu, doubl
                             void *stream);
 misdc_status misdc_pde_smem_bytes(int n_nodes, int nx, size_t *bytes);
 
+/* ---- variable-density low-Mach coupling, independent 1D flames -------------
+ * The paper's own setting (Sec. 2: eqs. continuity_equation, species_equation,
+ * enthalpy_equation, p_eos_definition, divergence_constraint and S_def; Sec. 3.3:
+ * steps I1-I4 and S1-S7 with S2 the density update, S3-S4 the species and
+ * enthalpy diffusion solved against the new density, S5 the reaction Newton at
+ * the new density with h fixed, S6 the volume-discrepancy correction delta_chi
+ * and the velocity from div U = S + delta_chi): one time step of CISDCQ-nu (or
+ * the serial MISDCQ) for n independent flames on the solver's 1D grid, one thread
+ * block per flame. State per flame q = [rho, rho Y_1..rho Y_N, rho h], [N+2][nx].
+ * Open boundaries: at x = 0 an inflow Dirichlet state (Y_in, T_in, density from
+ * the EOS at p0) and face velocity U_in; at x = nx dx zero-gradient outflow with
+ * no diffusive flux. Advection: fourth-order centred face values of q (inflow
+ * value on the inflow face and as the first face's outer ghost, the last cell
+ * beyond the outflow); diffusion: second-order fluxes with harmonic-mean
+ * rho theta(T) coefficients (the inflow face takes the first cell's, with the
+ * gradient to the inflow value half a cell away), dominant species closed by
+ * minus the others' flux, differential diffusion of h explicit; S with
+ * Gamma_i = rho D_i grad Y_i; delta_chi per cell and node, incremented each sweep
+ * by (2/p0)(p_EOS - p0)/dt_m (d->dchi = 0: no correction). The implicit diffusion
+ * systems are tridiagonal and solved directly; S5 is Newton with the analytic
+ * Jacobian (newton_rtol, newton_maxit of the solver's options).
+ * The solver (created on a 1D grid) supplies the mechanism, nx, dx, n_nodes,
+ * n_sweeps, nu, scheme and dominant_species. Device arrays, stream-ordered:
+ * q_in, q_out [n][N+2][nx] (may alias); peos [n][nx] (may be NULL): p_EOS of the
+ * result; status [n] (may be NULL): 0, or bits 1 (Newton limit), 2 (temperature
+ * outside [50, 6000] K), 4 (non-finite or singular). The workspace (about
+ * 8 ((M+1)(12 (N+2) + 6) + 30 N + (N+1)^2) nx bytes per flame) is allocated and freed
+ * stream-ordered (MISDC_E_OOM when it does not fit). */
+typedef struct misdc_lowmach_desc {
+  double U_in;          /* velocity on the inflow face, m/s   */
+  double T_in;          /* inflow temperature, K              */
+  double p0;            /* thermodynamic pressure, Pa         */
+  const double *Y_in;   /* [N] host: inflow mass fractions    */
+  int dchi;             /* 1: the delta_chi correction of S6  */
+} misdc_lowmach_desc;
+misdc_status misdc_lowmach_step(misdc_solver *s, const misdc_lowmach_desc *d, double dt, int n,
+                                const double *q_in, double *q_out, double *peos, int *status,
+                                void *stream);
+
 /* Reaction solve that allocates nothing. The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory during the call (host
  * callbacks, memory-pool-restricted or real-time processes, plugins whose host

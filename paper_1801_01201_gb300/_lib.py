@@ -56,6 +56,11 @@ class Stats(C.Structure):
         return d
 
 
+class LowMachDesc(C.Structure):
+    _fields_ = [("U_in", C.c_double), ("T_in", C.c_double), ("p0", C.c_double), ("Y_in", dp),
+                ("dchi", C.c_int)]
+
+
 class Tuning(C.Structure):
     _fields_ = [("newton_warps_per_block", C.c_int), ("newton_blocks_per_sm", C.c_int),
                 ("newton_dynamic", C.c_int), ("cheb_block", C.c_int),
@@ -76,7 +81,8 @@ EXPORTS = ["misdc_default_opts", "misdc_create", "misdc_destroy", "misdc_step", 
            "misdc_surrogate_features", "misdc_surrogate_forward", "misdc_surrogate_gradient",
            "misdc_surrogate_train_batch", "misdc_surrogate_forward_layers", "misdc_surrogate_guess", "misdc_autotune", "misdc_get_tuning", "misdc_set_tuning",
            "misdc_batch_create", "misdc_batch_destroy", "misdc_batch_step", "misdc_batch_stats",
-           "misdc_pde_step", "misdc_pde_smem_bytes", "misdc_exp", "misdc_probe_flops"]
+           "misdc_pde_step", "misdc_pde_smem_bytes", "misdc_exp", "misdc_probe_flops",
+           "misdc_lowmach_step"]
 
 _lib = None
 
@@ -144,6 +150,7 @@ def load(build_if_missing: bool = True):
                                  C.c_double, C.c_int, vp, vp, vp, vp, vp, vp]
     L.misdc_exp.argtypes = [vp, vp, C.c_size_t, vp]
     L.misdc_probe_flops.argtypes = [C.c_int, C.c_int, C.c_int, vp, dp, vp]
+    L.misdc_lowmach_step.argtypes = [vp, C.POINTER(LowMachDesc), C.c_double, C.c_int, vp, vp, vp, vp, vp]
     L.misdc_pde_smem_bytes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_size_t)]
     L.misdc_last_error.restype = C.c_char_p
     L.misdc_last_error.argtypes = []

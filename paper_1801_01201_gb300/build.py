@@ -12,7 +12,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libmisdc.so")
 SOURCES = ["misdc_chem.cu", "misdc_grid.cu", "misdc_engine.cu", "misdc_mlp.cu", "misdc_pde.cu",
-           "misdc_probe.cu"]
+           "misdc_probe.cu", "misdc_lowmach.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -1288,6 +1288,32 @@ misdc_status misdc_pde_step(int scheme, int n_nodes, int n_sweeps, int nu, doubl
   return MISDC_OK;
 }
 
+misdc_status misdc_lowmach_step(misdc_solver *s, const misdc_lowmach_desc *d, double dt, int n,
+                                const double *q_in, double *q_out, double *peos, int *status,
+                                void *stream) {
+  if (!s || !d || !d->Y_in) return fail(MISDC_E_INVALID, "lowmach_step: null argument");
+  if (s->g.dim != 1 || s->g.nx < 4)
+    return fail(MISDC_E_INVALID, "lowmach_step: the solver's grid must be 1D with at least 4 cells");
+  if (s->o.scheme != MISDC_SCHEME_CISDCQ && s->o.scheme != MISDC_SCHEME_MISDCQ)
+    return fail(MISDC_E_INVALID, "lowmach_step: the scheme must be CISDCQ or MISDCQ");
+  if (!(dt > 0.0) || n < 0 || !(d->p0 > 0.0) || !(d->T_in > 0.0))
+    return fail(MISDC_E_INVALID, "lowmach_step: dt, p0 and T_in must be positive, n >= 0");
+  if (n == 0) return MISDC_OK;
+  if (!q_in || !q_out) return fail(MISDC_E_INVALID, "lowmach_step: null state");
+  cudaStream_t cs = (cudaStream_t)stream;
+  const int nx = s->g.nx, M = s->tab.M;
+  double *ws = nullptr;
+  const cudaError_t ea = cudaMallocAsync((void **)&ws, lowmach_work_bytes(s->N, nx, M, n), cs);
+  if (ea != cudaSuccess) return fail(MISDC_E_OOM, "lowmach_step: workspace");
+  const cudaError_t e = launch_lowmach(s->m, nx, s->g.dx, M, s->tab.tau, s->tab.Q, s->tab.QI, s->tab.QE,
+                                       s->o.scheme, s->o.n_sweeps, s->o.nu, s->i0, s->o.newton_rtol,
+                                       s->o.newton_maxit, dt, d->U_in, d->T_in, d->p0, d->dchi ? 1 : 0,
+                                       d->Y_in, n, q_in, q_out, peos, status, ws, cs);
+  cudaFreeAsync(ws, cs);
+  CK(e);
+  return MISDC_OK;
+}
+
 }  // extern "C"
 
 // ===========================================================================

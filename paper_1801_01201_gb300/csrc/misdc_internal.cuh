@@ -270,6 +270,16 @@ constexpr int kPdeBatchMin = 4096;
 size_t pde_batch_bytes(int M, int nx, int n);
 cudaError_t launch_pde_batch(const PdeLaunch &p, double *ws, cudaStream_t s);
 
+// ---- variable-density low-Mach step of independent 1D flames (misdc_lowmach.cu) ----
+size_t lowmach_work_bytes(int N, int nx, int M, int n);
+cudaError_t launch_lowmach(const DevMech &m, int nx, double dx, int M, const double *tau,
+                           const double (*Q)[kMaxNodes + 1], const double (*QI)[kMaxNodes],
+                           const double (*QE)[kMaxNodes], int scheme, int n_sweeps, int nu,
+                           int i0, double rtol, int maxit, double dt, double U_in, double T_in,
+                           double p0, int dchi, const double *Y_in_host, int n,
+                           const double *q_in, double *q_out, double *peos, int *status,
+                           double *ws, cudaStream_t s);
+
 // ---- learned Newton guess: MLP kernels (misdc_mlp.cu) ----
 namespace mlp {
 // BF16 operand: element (r, k) at p[r * sm + k * sk]; rows >= rows read as zero

@@ -227,6 +227,30 @@ class Solver:
         return dict(newton_ms=tn.value, newton_launches=nn.value, diffusion_ms=td.value,
                     diffusion_launches=nd.value)
 
+    # -- variable-density low-Mach step of independent 1D flames -------------
+    def lowmach_step(self, q, dt, Y_in, T_in, U_in, p0=101325.0, dchi=True, n_steps=1, stream=None):
+        """Advance the 1D low-Mach states q ([n, N+2, nx] or [N+2, nx], device or
+        host) n_steps steps (misdc_lowmach_step, one call per step); returns
+        (q, p_eos, status) as device tensors."""
+        one = q.dim() == 2 if isinstance(q, torch.Tensor) else np.ndim(q) == 2
+        q = _dev(q, self.device)
+        if one:
+            q = q[None]
+        q = q.contiguous().clone()
+        n, nx = q.shape[0], q.shape[2]
+        y_in = np.ascontiguousarray(Y_in, dtype=np.float64)
+        d = L.LowMachDesc(float(U_in), float(T_in), float(p0), y_in.ctypes.data_as(L.dp), 1 if dchi else 0)
+        pe = torch.empty((n, nx), dtype=torch.float64, device=self.device)
+        status = torch.zeros(n, dtype=torch.int32, device=self.device)
+        st = torch.zeros_like(status)
+        for _ in range(n_steps):
+            L.check(self.lib.misdc_lowmach_step(self.handle, C.byref(d), float(dt), n, _ptr(q), _ptr(q),
+                                                _ptr(pe), _ptr(st), _stream(stream)))
+            status |= st
+        if one:
+            return q[0], pe[0], status[0]
+        return q, pe, status
+
     # -- row-level entry points --------------------------------------------
     def production_rates(self, Y, T, stream=None):
         Y = _dev(Y, self.device)
