@@ -573,12 +573,17 @@ def concurrency_compare(entries, w, args, dev, rank):
     from paper_1801_01201_gb300.solver import Solver
     K = args.concurrency
     mech, fl, dt = entries[0]
+    w = dict(w)
+    if args.nodes:
+        w["nodes"] = args.nodes
     nu, M = w["nu"], w["nodes"] - 1
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
     arms = [("misdcq", dict(scheme="MISDCQ", nu=1, two_streams=False)),
             ("cisdcq_nu%d_one_stream" % nu, dict(scheme="CISDCQ", nu=nu, two_streams=False)),
             ("cisdcq_nu%d_two_streams" % nu, dict(scheme="CISDCQ", nu=nu, two_streams=True)),
+            ("cisdcq_nu%d_%d_stream_pairs" % (nu, nu), dict(scheme="CISDCQ", nu=nu, two_streams=True,
+                                                           lanes=nu)),
             ("cisdcq_adaptive_max%d_two_streams" % (nu + 2),
              dict(scheme="CISDCQ", nu=nu + 2, two_streams=True, nu_rule=(0.02, 0.9)))]
     x0 = None
@@ -638,6 +643,9 @@ def concurrency_compare(entries, w, args, dev, rank):
         res["R_nu_model"] = (K / nc) * alpha * M / (alpha * nub + M - 1)
         res["R_nu_measured"] = mis["ms_per_step"][K - 1] / res["ms_per_step"][nc - 1]
     line = {"concurrency": out, "N_M": K, "eps": eps, "nodes": w["nodes"], "nu": nu, "workload": args.workload,
+            "pipelined_gain_at_%d_sweeps" % min(K, w["sweeps"]):
+                out["cisdcq_nu%d_two_streams" % nu]["ms_per_step"][min(K, w["sweeps"]) - 1]
+                / out["cisdcq_nu%d_%d_stream_pairs" % (nu, nu)]["ms_per_step"][min(K, w["sweeps"]) - 1],
             "cells": fl.cells, "species": mech.n_species, "dt": dt, "steps": args.steps, "warmup": args.warmup,
             "two_stream_gain_at_%d_sweeps" % min(K, w["sweeps"]):
                 out["cisdcq_nu%d_one_stream" % nu]["ms_per_step"][min(K, w["sweeps"]) - 1]
@@ -755,6 +763,8 @@ def main():
                     help="instead of the headline: serial MISDCQ against CISDCQ-nu on one and on two "
                          "streams and with adaptive nu, sweeps 1..K each: step times, stage costs, "
                          "sweep increments, sweeps to the MISDCQ tolerance, measured and modelled R_nu")
+    ap.add_argument("--nodes", type=int, default=0,
+                    help="--concurrency: Gauss-Lobatto nodes (default: the workload's)")
     ap.add_argument("--rates-compare", action="store_true",
                     help="instead of the step: time the production-rate kernel, sparse FP64 FMA "
                          "against FP64 tensor cores, on the workload's initial state")

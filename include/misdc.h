@@ -114,6 +114,15 @@ typedef struct misdc_opts {
                              Captured steps decide on the device (IF graph nodes);
                              eager steps read the decision on the host.           */
   double nu_rho_stall;    /* the contraction bound of that rule (> 0 when nu_eta > 0) */
+  int lanes;              /* CISDCQ on two streams: stream pairs for the nested
+                             iterations, 1..min(nu, 4). With lanes > 1, iteration l
+                             runs its diffusion and reaction steps on pair l mod lanes,
+                             so iteration l+1 starts at a node as soon as iteration l
+                             has passed the next one (the pipelining of up to 2 nu
+                             tasks of Sec. 3.2.2, Fig. 2); results are bitwise those of
+                             one pair. Each further pair has its own stage buffers.
+                             Multigrid solves, the learned guess and the adaptive rule
+                             use one pair. Default 1. */
 } misdc_opts;
 
 typedef struct misdc_stats {

@@ -37,7 +37,7 @@ class Opts(C.Structure):
                 ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("lin_rtol", C.c_double),
                 ("mg_levels", C.c_int), ("two_streams", C.c_int), ("use_graph", C.c_int),
                 ("profile", C.c_int), ("rates_mma", C.c_int), ("nu_eta", C.c_double),
-                ("nu_rho_stall", C.c_double)]
+                ("nu_rho_stall", C.c_double), ("lanes", C.c_int)]
 
 
 class Stats(C.Structure):

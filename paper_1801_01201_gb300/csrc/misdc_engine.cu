@@ -195,6 +195,18 @@ struct misdc_solver {
   double *dout = nullptr;
   double *g_state = nullptr, *g_T = nullptr;
   double g_dt = 0.0;
+  // further stream pairs for the nested iterations of CISDCQ (opts.lanes > 1):
+  // iteration l runs on pair l mod lanes, pair 0 being (sD, sR) with the solver's
+  // own stage scratch; pairs 1.. have their own
+  struct Lane {
+    double *rhsD = nullptr, *bR = nullptr, *thfD = nullptr, *thfR = nullptr;
+    int *iters = nullptr;
+    NewtonLaunch nl{};
+    DiffWork dw{};
+    cudaStream_t sD = nullptr, sR = nullptr;
+  };
+  int lanes = 1;
+  Lane lane[kMaxLanes];
   int cheb_sweeps = 0;
   double rho_bound = 0.0, rho_dt = -1.0;
   long long kernels_per_step = 0, kernels_launched = 0;
@@ -333,24 +345,33 @@ void prepare_node0(misdc_solver *s, const double *state, const double *Tin, cuda
 }
 
 // diffusion step at node t: rhs already in s->rhsD; writes AD[t]
+// stage scratch of stream pair p (0: the solver's own)
+double *lane_rhsD(misdc_solver *s, int p) { return p ? s->lane[p].rhsD : s->rhsD; }
+double *lane_bR(misdc_solver *s, int p) { return p ? s->lane[p].bR : s->bR; }
+double *lane_thfD(misdc_solver *s, int p) { return p ? s->lane[p].thfD : s->thfD; }
+double *lane_thfR(misdc_solver *s, int p) { return p ? s->lane[p].thfR : s->thfR; }
+int *lane_iters(misdc_solver *s, int p) { return p ? s->lane[p].iters : s->iters; }
+NewtonLaunch *lane_nl(misdc_solver *s, int p) { return p ? &s->lane[p].nl : &s->nl; }
+DiffWork &lane_dw(misdc_solver *s, int p) { return p ? s->lane[p].dw : s->dw; }
+
 void d_stage(misdc_solver *s, int t, const double *theta_coef, double wdt, bool lag_source,
-             const NodeBuf *Tguess, cudaStream_t st) {
+             const NodeBuf *Tguess, cudaStream_t st, int p = 0) {
   NodeBuf &ad = s->AD[t];
   const bool prof = s->o.profile && !s->in_body && 2 * (s->d_used + 1) <= (int)s->prof_d.size();
   if (prof) cudaEventRecordWithFlags(s->prof_d[2 * s->d_used], st, cudaEventRecordExternal);
-  diffusion_solve(s->m, s->g, s->i0, wdt, theta_coef, s->rhsD, ad.phi, s->dw, s->cheb_sweeps,
-                  s->rho_bound, s->o.lin_rtol, s->st, st);
+  diffusion_solve(s->m, s->g, s->i0, wdt, theta_coef, lane_rhsD(s, p), ad.phi, lane_dw(s, p),
+                  s->cheb_sweeps, s->rho_bound, s->o.lin_rtol, s->st, st);
   if (prof) cudaEventRecordWithFlags(s->prof_d[2 * s->d_used++ + 1], st, cudaEventRecordExternal);
   if (lag_source) {
     launch_temperature(s->m, s->cs, s->cs, ad.phi, ad.phi + (size_t)s->N * s->cs, Tguess->T, ad.T,
                        ad.theta, ad.hsp, s->st, st);
-    node_operators(s, ad, s->thfD, st);
+    node_operators(s, ad, lane_thfD(s, p), st);
   }
 }
 
 // reaction step at node t: b already in s->bR; writes out (phi, T, theta, hsp, F's)
 void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &out,
-             cudaStream_t st) {
+             cudaStream_t st, int p = 0) {
   const size_t cs = s->cs, N = s->N;
   const NodeBuf &ad = s->AD[t];
   const bool prof = s->o.profile && !s->in_body && 2 * (s->n_used + 1) <= (int)s->prof_n.size();
@@ -373,10 +394,10 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
                       nullptr, sg->Xi, s->cs, sg->Oi, st, sg->inf_count);
     pred = sg->Oi;
   }
-  launch_newton(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, s->bR,
+  launch_newton(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, lane_bR(s, p),
                 ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR, out.hsp, out.theta,
-                s->iters, s->st, st, s->o.precision == MISDC_PREC_MIXED, pred, sg ? sg->ldo : 0,
-                sg ? sg->scale : nullptr, s->sg_smin, guess.FR, guess.phi + N * cs, &s->nl,
+                lane_iters(s, p), s->st, st, s->o.precision == MISDC_PREC_MIXED, pred, sg ? sg->ldo : 0,
+                sg ? sg->scale : nullptr, s->sg_smin, guess.FR, guess.phi + N * cs, lane_nl(s, p),
                 s->keep_factors ? &s->cst[t] : nullptr, pred ? sg->rowmap : nullptr, guess.hsp,
                 guess.theta);
   if (sg && s->sg_collect)
@@ -384,7 +405,7 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
                 sg->ldo, sg->DT, st);
   if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used++ + 1], st, cudaEventRecordExternal);
   cudaMemcpyAsync(out.phi + N * cs, ad.phi + N * cs, cs * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  node_operators(s, out, s->thfR, st);
+  node_operators(s, out, lane_thfR(s, p), st);
 }
 
 // Enqueue one full time step on s->sD (and s->sR).
@@ -395,12 +416,19 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
   const bool two = s->o.two_streams && sch == MISDC_SCHEME_CISDCQ;
   cudaStream_t sD = s->sD, sR = two ? s->sR : s->sD;
   s->n_used = s->d_used = 0;
+  // stream pairs for the nested iterations (the learned guess and the adaptive rule
+  // keep one pair: their scratch and decisions are per solver)
+  const int lanes = (two && s->nu_bits == nullptr && !(s->sg && (s->sg_on || s->sg_collect))) ? s->lanes : 1;
 
   prepare_node0(s, state, Tio, sD);
   for (int m = 1; m <= M; ++m) copy_node(s, s->K[m], s->node0, sD);   // I1-I2
   if (two) {
     cudaEventRecord(s->evFork, sD);
     cudaStreamWaitEvent(sR, s->evFork, 0);
+    for (int p = 1; p < lanes; ++p) {
+      cudaStreamWaitEvent(s->lane[p].sD, s->evFork, 0);
+      cudaStreamWaitEvent(s->lane[p].sR, s->evFork, 0);
+    }
   }
   for (int k = 0; k < s->o.n_sweeps; ++k) {
     sweep_quadrature(s, dt, sD);
@@ -408,7 +436,7 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
       // one nested iteration l on streams qD (diffusion) and qR (reaction); `fresh`:
       // everything of iteration l-1 is complete before the first node starts (an
       // adaptive iteration that starts after the decision), so no waits on it
-      auto iteration = [&](int l, cudaStream_t qD, cudaStream_t qR, bool fresh, bool join) {
+      auto iteration = [&](int l, cudaStream_t qD, cudaStream_t qR, bool fresh, bool join, int lp = 0) {
         const bool dual = qD != qR;
         NodeBuf *C = (l % 2 == 0) ? s->X : s->Y;
         NodeBuf *P = (l == 0) ? s->K : ((l % 2 == 1) ? s->X : s->Y);
@@ -418,9 +446,13 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
           if (dual && l >= 1 && !fresh) {
             if (m >= 1) cudaStreamWaitEvent(qD, s->eR(m, l - 1), 0);
             cudaStreamWaitEvent(qD, s->eR(t, l - 1), 0);
+            // on its own stream pair iteration l overtakes l-1: before this node's
+            // buffers (those of iteration l-2) are rewritten, iteration l-1 must have
+            // read them, its last reader being the reaction step at node t+1
+            if (lanes > 1 && t < M) cudaStreamWaitEvent(qD, s->eR(t + 1, l - 1), 0);
           }
           if (dual) for (int j = 1; j <= m - 1; ++j) cudaStreamWaitEvent(qD, s->eR(j, l), 0);
-          LC r(s->rhsD);
+          LC r(lane_rhsD(s, lp));
           r.add(s->B[t], 1.0);
           for (int j = 1; j <= m - 1; ++j) {
             r.add(C[j].FE, dt * T.QE[t - 1][j - 1]);
@@ -440,11 +472,11 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
           launch_lincomb(r.lc, n, qD);
           const double wdt = dt * T.QI[t - 1][t - 1];
           const double *coef = (l == 0) ? s->K[t].theta : P[t].theta;
-          d_stage(s, t, coef, wdt, l == 0 && t < M, &s->K[t], qD);
+          d_stage(s, t, coef, wdt, l == 0 && t < M, &s->K[t], qD, lp);
           if (dual) cudaEventRecord(s->eD(t, l), qD);
           // ---- reaction step at node t (R_alt form) ----
           if (dual) cudaStreamWaitEvent(qR, s->eD(t, l), 0);
-          LC b(s->bR);
+          LC b(lane_bR(s, lp));
           b.add(s->AD[t].phi, 1.0);
           if (m >= 1) {
             const double *lagRm = (l == 0) ? s->K[m].FR : P[m].FR;
@@ -453,7 +485,7 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
           }
           b.add(lagR1, -dt * T.QI[t - 1][t - 1]);
           launch_lincomb(b.lc, n, qR);
-          r_stage(s, t, wdt, P[t], C[t], qR);
+          r_stage(s, t, wdt, P[t], C[t], qR, lp);
           if (dual) cudaEventRecord(s->eR(t, l), qR);
         }
         if (dual && join) cudaStreamWaitEvent(qD, s->eR(M, l), 0);   // the iteration ends on qD
@@ -471,7 +503,12 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
       };
       const bool adapt = s->nu_bits != nullptr;
       if (!adapt) {
-        for (int l = 0; l < nu; ++l) iteration(l, sD, sR, false, l == nu - 1);
+        for (int l = 0; l < nu; ++l) {
+          const int lp = l % lanes;
+          iteration(l, lp ? s->lane[lp].sD : sD, lp ? s->lane[lp].sR : sR, false, l == nu - 1, lp);
+        }
+        // the sweep's last reaction step follows every other stage of the sweep
+        if (lanes > 1) cudaStreamWaitEvent(sD, s->eR(M, nu - 1), 0);
       } else {
         // iterations 0 and 1 always run; iteration l >= 2 runs inside an IF graph
         // node (nested in the body of l-1) that the decision after l-1 sets, or, in
@@ -639,6 +676,7 @@ void misdc_default_opts(misdc_opts *o) {
   o->lin_rtol = 1e-14;
   o->mg_levels = 1;
   o->two_streams = 1;
+  o->lanes = 1;
   o->use_graph = 1;
 }
 
@@ -907,6 +945,36 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   if (cudaStreamCreateWithFlags(&s->sD, cudaStreamNonBlocking) ||
       cudaStreamCreateWithFlags(&s->sR, cudaStreamNonBlocking))
     return bail(fail(MISDC_E_CUDA, "stream creation failed"));
+  // further stream pairs of the nested iterations: CISDCQ on two streams with the
+  // Chebyshev diffusion solve (multigrid keeps one pair: its loop state is shared)
+  s->lanes = 1;
+  if (op->lanes > 1 && op->scheme == MISDC_SCHEME_CISDCQ && op->two_streams && op->nu > 1 &&
+      s->dw.levels <= 1)
+    s->lanes = std::min(std::min(op->lanes, op->nu), kMaxLanes);
+  for (int p = 1; p < s->lanes; ++p) {
+    misdc_solver::Lane &L = s->lane[p];
+    DiffWork &w = L.dw;
+    w = s->dw;   // options and sizes; the arrays below are the lane's own
+    const size_t thf_n = 3 * cs + operator_face_doubles(s->g, s->N);
+    if (s->alloc(&L.rhsD, F * cs) || s->alloc(&L.bR, F * cs) || s->alloc(&L.thfD, thf_n) ||
+        s->alloc(&L.thfR, thf_n) || s->alloc(&L.iters, cs) || s->alloc(&L.nl.work, 1) ||
+        s->alloc(&L.nl.list, cs) || s->alloc(&L.nl.list_n, 1) || s->alloc(&w.thf, 3 * cs) ||
+        s->alloc(&w.invdiag, F * cs) || s->alloc(&w.cdiag, F * cs) || s->alloc(&w.bdiag, F * cs) ||
+        s->alloc(&w.xa, F * cs) || s->alloc(&w.xb, F * cs) || s->alloc(&w.xc, F * cs) ||
+        s->alloc(&w.rho_bits, 1) || s->alloc(&w.kdev, 1) || s->alloc(&w.omega, kMaxCheb))
+      return bail(fail(MISDC_E_OOM, "stream-pair buffers"));
+    if (s->o.precision == MISDC_PREC_MIXED &&
+        (s->alloc(&w.thf32, 3 * cs) || s->alloc(&w.invdiag32, F * cs) || s->alloc(&w.r32, F * cs) ||
+         s->alloc(&w.e32[0], F * cs) || s->alloc(&w.e32[1], F * cs) || s->alloc(&w.e32[2], F * cs) ||
+         s->alloc(&w.kdev32, 1) || s->alloc(&w.omega32, kMaxCheb)))
+      return bail(fail(MISDC_E_OOM, "stream-pair buffers"));
+    L.nl.wpb = s->nl.wpb;
+    L.nl.blocks_per_sm = s->nl.blocks_per_sm;
+    L.nl.dynamic = s->nl.dynamic;
+    if (cudaStreamCreateWithFlags(&L.sD, cudaStreamNonBlocking) ||
+        cudaStreamCreateWithFlags(&L.sR, cudaStreamNonBlocking))
+      return bail(fail(MISDC_E_CUDA, "stream creation failed"));
+  }
   s->evD.assign((size_t)(M + 1) * op->nu, nullptr);
   s->evR.assign((size_t)(M + 1) * op->nu, nullptr);
   for (auto *v : {&s->evD, &s->evR})
@@ -943,6 +1011,10 @@ void misdc_destroy(misdc_solver *s) {
   if (!s) return;
   if (s->sD) cudaStreamSynchronize(s->sD);
   if (s->sR) cudaStreamSynchronize(s->sR);
+  for (int p = 1; p < kMaxLanes; ++p) {
+    if (s->lane[p].sD) cudaStreamSynchronize(s->lane[p].sD);
+    if (s->lane[p].sR) cudaStreamSynchronize(s->lane[p].sR);
+  }
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   if (s->dgexec) cudaGraphExecDestroy(s->dgexec);
   for (auto *v : {&s->evD, &s->evR})
@@ -952,6 +1024,10 @@ void misdc_destroy(misdc_solver *s) {
     for (auto &ev : *v) if (ev) cudaEventDestroy(ev);
   if (s->sD) cudaStreamDestroy(s->sD);
   if (s->sR) cudaStreamDestroy(s->sR);
+  for (int p = 1; p < kMaxLanes; ++p) {
+    if (s->lane[p].sD) cudaStreamDestroy(s->lane[p].sD);
+    if (s->lane[p].sR) cudaStreamDestroy(s->lane[p].sR);
+  }
   if (s->dw.mg_stream) cudaStreamDestroy(s->dw.mg_stream);
   for (cudaStream_t q : s->body_streams) if (q) cudaStreamDestroy(q);
   for (cudaEvent_t e : s->evBody) if (e) cudaEventDestroy(e);

@@ -18,6 +18,7 @@ constexpr int kMaxSlots = 3;               // molecules per reaction side
 constexpr int kMaxSpecies = 63;
 constexpr int kMaxNodes = 9;
 constexpr int kMaxCheb = 512;   // cap on Chebyshev sweeps per diffusion solve
+constexpr int kMaxLanes = 4;    // stream pairs for the nested iterations of CISDCQ
 
 // Device status bits (OR-ed into DevStats::status_bits); mapped to misdc_status
 enum : unsigned {

@@ -129,7 +129,7 @@ class Solver:
     def __init__(self, mech, flame, *, n_nodes=3, n_sweeps=4, nu=2, scheme="CISDCQ",
                  precision="fp64", newton_rtol=1e-12, newton_maxit=50, lin_rtol=1e-14,
                  mg_levels=1, two_streams=True, use_graph=True, profile=False, rates_mma=False,
-                 nu_rule=None, device="cuda"):
+                 nu_rule=None, lanes=1, device="cuda"):
         self.lib = L.load()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -160,6 +160,7 @@ class Solver:
         o.two_streams, o.use_graph = int(two_streams), int(use_graph)
         o.profile = int(profile)
         o.rates_mma = int(rates_mma)
+        o.lanes = int(lanes)
         if nu_rule is not None:   # (eta, rho_stall): adaptive nested iterations, nu the cap
             o.nu_eta, o.nu_rho_stall = float(nu_rule[0]), float(nu_rule[1])
         self.opts = o

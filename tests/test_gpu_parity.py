@@ -348,6 +348,27 @@ def test_stream_graph_variants_are_bitwise_identical():
         assert np.array_equal(o, outs[0])
 
 
+@pytest.mark.parametrize("nodes,nu,lanes,precision", [(5, 2, 2, "fp64"), (5, 3, 3, "fp64"), (3, 2, 2, "fp64"),
+                                                      (5, 2, 2, "mixed")])
+def test_stream_pairs_for_nested_iterations_are_bitwise_identical(nodes, nu, lanes, precision):
+    """Iteration l of a CISDCQ sweep on stream pair l mod lanes (the pipelined
+    schedule of Sec. 3.2.2 with up to 2 nu concurrent tasks) computes exactly what
+    one stream pair computes; captured and eager steps alike."""
+    mech, fl = small_2d(n=24)
+    ad = O.ADR(mech, fl)
+    phi0 = ad.state_from_YT(fl.Y, fl.T)
+    outs = []
+    for ln, graph in ((1, True), (lanes, True), (lanes, False)):
+        sv = S().Solver(mech, fl, n_nodes=nodes, nu=nu, lanes=ln, use_graph=graph, precision=precision)
+        st = torch.as_tensor(phi0, device="cuda").contiguous()
+        sv.step(st, 5e-6, 2)
+        torch.cuda.synchronize()
+        assert sv.stats()["status_name"] == "OK"
+        outs.append(st.cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
 def test_multigrid_levels_agree(pool):
     mech, fl = small_2d(n=32, logA=MILD)
     a = _run_both(mech, fl, 5e-6, 1, mg_levels=1, pool=pool)[0]
