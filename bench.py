@@ -316,11 +316,13 @@ class Runner:
         for mech, fl, dt in entries:
             sv = Solver(mech, fl, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"],
                         scheme=args.scheme, precision=precision, profile=len(entries) == 1,
-                        mg_levels=args.mg_levels, rates_mma=bool(args.rates_mma), device=dev)
+                        mg_levels=args.mg_levels, rates_mma=bool(args.rates_mma),
+                        lin_rounds=args.lin_rounds, device=dev)
             st = sv.state_from_YT(fl.Y, fl.T)
             if params is not None:
                 sv.surrogate_load(params[id(mech)])
                 sv.surrogate_enable(True, s_min=args.s_min)
+                sv.surrogate_sweeps(args.sg_sweeps)
             if tune:
                 T = torch.as_tensor(fl.T, device=dev).contiguous()
                 sv.autotune(st, T, dt)
@@ -745,6 +747,8 @@ def main():
     ap.add_argument("--train-batch", type=int, default=8192)
     ap.add_argument("--train-lr", type=float, default=2e-3)
     ap.add_argument("--s-min", type=float, default=1e-4)
+    ap.add_argument("--sg-sweeps", type=int, default=0,
+                    help="learned guess in the first SG_SWEEPS sweeps of a step only (0: all)")
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--rates-mma", type=int, default=0,
                     help="1: production rates on the FP64 tensor cores (all variants)")
@@ -763,6 +767,9 @@ def main():
                     help="instead of the headline: serial MISDCQ against CISDCQ-nu on one and on two "
                          "streams and with adaptive nu, sweeps 1..K each: step times, stage costs, "
                          "sweep increments, sweeps to the MISDCQ tolerance, measured and modelled R_nu")
+    ap.add_argument("--lin-rounds", type=int, default=0,
+                    help="mixed precision: FP64-residual refinement rounds of the diffusion solve "
+                         "(0: the library's default)")
     ap.add_argument("--nodes", type=int, default=0,
                     help="--concurrency: Gauss-Lobatto nodes (default: the workload's)")
     ap.add_argument("--rates-compare", action="store_true",
@@ -919,7 +926,7 @@ def main():
         d = {"value": whole_job_rate(world, rn.cells, args.steps, r["total_ms"]), "unit": UNIT,
              "ms_per_step": r["total_ms"] / args.steps,
              "newton_iters_per_solve": s_["newton_iters"] / max(s_["newton_solves"], 1),
-             "status": s_["status_name"]}
+             "status": s_["status_name"], "lin_resid_max": s_["lin_resid_max"]}
         if r["newton_launches"]:
             d["newton_ms_per_step"] = r["newton_ms"] / args.steps
         ns = max(s_["newton_solves"], 1)
@@ -938,6 +945,7 @@ def main():
            "flames": len(entries), "cells": cells, "nodes": w["nodes"],
            "sweeps": w["sweeps"], "nu": w["nu"], "scheme": args.scheme, "variant": args.headline,
            "autotuned": tune, "l2": "flushed between steps (256 MB write)",
+           "learned_sweeps": args.sg_sweeps or w["sweeps"], "lin_rounds": args.lin_rounds or 3,
            "rates": "fp64 tensor cores" if args.rates_mma else "sparse fp64 fma",
            "diffusion": "multigrid %d levels" % args.mg_levels if args.mg_levels > 1 else "chebyshev"}
     if len(entries) == 1:

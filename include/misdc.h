@@ -123,6 +123,9 @@ typedef struct misdc_opts {
                              one pair. Each further pair has its own stage buffers.
                              Multigrid solves, the learned guess and the adaptive rule
                              use one pair. Default 1. */
+  int lin_rounds;         /* mixed precision, Chebyshev diffusion solve: FP64-residual
+                             refinement rounds around the FP32 inner solves (each
+                             reduces the residual by about 1e-6); 0: 3 rounds      */
 } misdc_opts;
 
 typedef struct misdc_stats {
@@ -364,6 +367,11 @@ misdc_status misdc_surrogate_save(misdc_solver *s, float *params, size_t n_param
 /* on = 1: later misdc_step calls start each reaction Newton from the learned guess
  * (needs parameters). s_min: cells with s <= s_min keep x_p. */
 misdc_status misdc_surrogate_enable(misdc_solver *s, int on, double s_min);
+/* The learned guess serves only the first n_sweeps sweeps of every time step
+ * (0, the default: all). Later sweeps start from iterates that the previous
+ * sweep has already converged, where plain Newton (or a kept factor's
+ * certification) needs no help and the network's inference is overhead. */
+misdc_status misdc_surrogate_sweeps(misdc_solver *s, int n_sweeps);
 /* capacity > 0: later misdc_step calls record (features, target) rows of every
  * reaction solve with s > s_min (plain Newton from x_p) until capacity rows are
  * held; a larger capacity starts a new, empty dataset. 0 stops recording. */

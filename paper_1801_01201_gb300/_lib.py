@@ -37,7 +37,8 @@ class Opts(C.Structure):
                 ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("lin_rtol", C.c_double),
                 ("mg_levels", C.c_int), ("two_streams", C.c_int), ("use_graph", C.c_int),
                 ("profile", C.c_int), ("rates_mma", C.c_int), ("nu_eta", C.c_double),
-                ("nu_rho_stall", C.c_double), ("lanes", C.c_int)]
+                ("nu_rho_stall", C.c_double), ("lanes", C.c_int),
+                ("lin_rounds", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -82,7 +83,7 @@ EXPORTS = ["misdc_default_opts", "misdc_create", "misdc_destroy", "misdc_step", 
            "misdc_surrogate_train_batch", "misdc_surrogate_forward_layers", "misdc_surrogate_guess", "misdc_autotune", "misdc_get_tuning", "misdc_set_tuning",
            "misdc_batch_create", "misdc_batch_destroy", "misdc_batch_step", "misdc_batch_stats",
            "misdc_pde_step", "misdc_pde_smem_bytes", "misdc_exp", "misdc_probe_flops",
-           "misdc_lowmach_step"]
+           "misdc_lowmach_step", "misdc_surrogate_sweeps"]
 
 _lib = None
 
@@ -129,6 +130,7 @@ def load(build_if_missing: bool = True):
     L.misdc_surrogate_load.argtypes = [vp, fp, C.c_size_t]
     L.misdc_surrogate_save.argtypes = [vp, fp, C.c_size_t]
     L.misdc_surrogate_enable.argtypes = [vp, C.c_int, C.c_double]
+    L.misdc_surrogate_sweeps.argtypes = [vp, C.c_int]
     L.misdc_surrogate_collect.argtypes = [vp, C.c_longlong]
     L.misdc_surrogate_dataset.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(vp), C.POINTER(vp)]
     L.misdc_surrogate_train.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_ulonglong, fp]

@@ -465,26 +465,24 @@ __global__ void __launch_bounds__(256) k_certify(DevMech m, int n, int cs, doubl
   const int N = m.N, nn = N + 1;
   bool done = false;
   if (c < n) {
-    bool ok = (cst.valid[c] & 1) != 0;
+    const int v = cst.valid[c];
+    bool ok = (v & 1) != 0 && (v & 4) == 0;   // a kept factor, built in FP64
     if (ok && sc) {   // a learned guess goes to the Newton kernel, which vets it
       const int prw = prow ? prow[c] : c;
       const double s0 = sc[c];
       ok = !(prw >= 0 && s0 > s_min && isfinite(s0));
     }
-    const double *src = cst.f + (size_t)c * cst.fs;
-    if (ok) ok = src[nn * nn + 2 * nn + 1] == 0.0;   // FP64-built factors only
     const double T = Tg[c];
     if (ok) {   // the factor was built near x_p (without dividing by T)
-      const double *xf = src + nn * nn + 2 * nn + 2;
-      for (int i = 0; i < N && ok; ++i) ok = fabs(Yg[(size_t)i * cs + c] - xf[i]) <= 1e-4;
-      ok = ok && fabs(T - xf[N]) <= 1e-4 * T;
+      for (int i = 0; i < N && ok; ++i) ok = fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]) <= 1e-4;
+      ok = ok && fabs(T - cst.xc[(size_t)N * cs + c]) <= 1e-4 * T;
     }
     if (ok) {
       float r32[kMaxSpecies + 1];
       for (int i = 0; i < N; ++i)
         r32[i] = __double2float_rn(b[(size_t)i * cs + c] - Yg[(size_t)i * cs + c] +
                                    wdt * FRp[(size_t)i * cs + c]);
-      r32[N] = __double2float_rn((hstar[c] - hp[c]) * src[nn * nn + 2 * nn]);
+      r32[N] = __double2float_rn((hstar[c] - hp[c]) * cst.sT[c]);
       const float thr = (float)(0.09 * rtol), thrT = thr * (float)T;
       for (int i = 0; i < nn && ok; ++i) {
         float z = 0.0f;
@@ -1087,10 +1085,12 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
           dst[nn * nn + nn + i] = w.res[i];
           dst[nn * nn + 2 * nn + 2 + i] = w.xs[i];
           cst.sw[(size_t)cell * cst.swld + i] = (unsigned char)w.sw[i];
+          if (cst.xc) cst.xc[(size_t)i * cs + cell] = w.xs[i];
         }
         if (lane == 0) {
           dst[nn * nn + 2 * nn] = sT;
           dst[nn * nn + 2 * nn + 1] = fac32 ? 1.0 : 0.0;
+          if (cst.sT) cst.sT[cell] = sT;
         }
       }
       if (MIXED && vet && !singular) {
@@ -1249,7 +1249,7 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
       }
     }
     if (MIXED && cst.valid && lane == 0)
-      cst.valid[cell] = ((have && code == 0 && !exact) ? 1 : 0) | (no32 ? 2 : 0);
+      cst.valid[cell] = ((have && code == 0 && !exact) ? 1 : 0) | (no32 ? 2 : 0) | (fac32 ? 4 : 0);
     if (lane == 0) {
       Tout[cell] = T;
       if (theta) theta[cell] = th_f;
@@ -1383,8 +1383,8 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
   // mixed precision with kept factors and the stored reaction terms of the
   // guesses: certification first (one thread per cell), then the warp-per-cell
   // Newton on the cells it left
-  const bool split = mixed && cst.f && cst.valid && cst.z32 && FRp && hspp && hp && thp && cfg &&
-                     cfg->list && cfg->list_n;
+  const bool split = mixed && cst.f && cst.valid && cst.z32 && cst.xc && cst.sT && FRp && hspp && hp &&
+                     thp && cfg && cfg->list && cfg->list_n;
   const int *list = split ? cfg->list : nullptr, *list_n = split ? cfg->list_n : nullptr;
   if (split) {
     cudaMemsetAsync(cfg->list_n, 0, sizeof(int), s);

@@ -164,6 +164,8 @@ struct misdc_solver {
   // learned Newton guess (created on first use)
   Surrogate *sg = nullptr;
   bool sg_on = false, sg_collect = false;
+  int sg_sweeps = 0;        // the learned guess serves sweeps k < sg_sweeps (0: all)
+  bool sg_this_sweep = true;  // set per sweep while a step is enqueued
   double sg_smin = 1e-8;
   // reaction-Newton launch shape (autotuned)
   NewtonLaunch nl{};
@@ -383,7 +385,7 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
     mlp_features(s->m, s->cs, s->cs, wdt, s->bR, ad.phi + N * cs, guess.phi, guess.T, guess.FR,
                  guess.phi + N * cs, sg->ldx, sg->DX, sg->scale, s->sg_smin, sg->ds_count,
                  sg->ds_cap, sg->rowmap, st);
-  } else if (sg && s->sg_on) {
+  } else if (sg && s->sg_on && s->sg_this_sweep) {
     // learned guess: features of the cells worth it (s > s_min) gathered into
     // compact rows, then the four layers in one fused kernel over those rows
     cudaMemsetAsync(sg->inf_count, 0, sizeof(unsigned long long), st);
@@ -431,6 +433,7 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
     }
   }
   for (int k = 0; k < s->o.n_sweeps; ++k) {
+    s->sg_this_sweep = s->sg_sweeps <= 0 || k < s->sg_sweeps;
     sweep_quadrature(s, dt, sD);
     if (sch == MISDC_SCHEME_CISDCQ) {
       // one nested iteration l on streams qD (diffusion) and qR (reaction); `fresh`:
@@ -677,6 +680,7 @@ void misdc_default_opts(misdc_opts *o) {
   o->mg_levels = 1;
   o->two_streams = 1;
   o->lanes = 1;
+  o->lin_rounds = 0;
   o->use_graph = 1;
 }
 
@@ -895,13 +899,14 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
         s->alloc(&w.e32[0], F * cs) || s->alloc(&w.e32[1], F * cs) || s->alloc(&w.e32[2], F * cs) ||
         s->alloc(&w.kdev32, 1) || s->alloc(&w.omega32, kMaxCheb))
       return bail(fail(MISDC_E_OOM, "mixed diffusion buffers"));
-    w.refine_rounds = 3;
+    w.refine_rounds = (s->o.lin_rounds > 0) ? std::min(s->o.lin_rounds, 8) : 3;
     for (int j = 1; j <= M; ++j) {
       ChordStore &c = s->cst[j];
       c.fs = chord_floats(N);
       c.swld = (int)((F + 3) / 4 * 4);
       if (s->alloc(&c.f, (size_t)c.fs * cs) || s->alloc(&c.sw, (size_t)c.swld * cs) ||
-          s->alloc(&c.valid, cs) || s->alloc(&c.z32, (size_t)F * F * cs))
+          s->alloc(&c.valid, cs) || s->alloc(&c.z32, (size_t)F * F * cs) ||
+          s->alloc(&c.xc, (size_t)F * cs) || s->alloc(&c.sT, cs))
         return bail(fail(MISDC_E_OOM, "factor store"));
       cudaMemset(c.valid, 0, cs * sizeof(int));
     }
@@ -1566,6 +1571,13 @@ misdc_status misdc_surrogate_save(misdc_solver *s, float *params, size_t n_param
   CK(cudaStreamSynchronize(s->sD));
   CK(cudaStreamSynchronize(s->sR));
   CK(cudaMemcpy(params, s->sg->P, n_params * sizeof(float), cudaMemcpyDeviceToHost));
+  return MISDC_OK;
+}
+
+misdc_status misdc_surrogate_sweeps(misdc_solver *s, int n_sweeps) {
+  if (!s || n_sweeps < 0) return fail(MISDC_E_INVALID, "surrogate_sweeps: bad argument");
+  drop_graph(s);
+  s->sg_sweeps = n_sweeps;
   return MISDC_OK;
 }
 

@@ -128,11 +128,15 @@ struct NewtonLaunch {
 // z32 (optional): the kept inverse rounded to FP32, element-major ([e][cs] with
 // e = j (N+1) + i for entry (i, j)), which certifies converged guesses on the FP32
 // pipe, one thread per cell.
+// xc [N+1][cs] and sT [cs] (optional, element-major): the state each factor was
+// built at and its temperature-row scale, for the certification kernel; valid bit
+// 2 marks a factor built in FP32.
 struct ChordStore {
   double *f = nullptr;
   unsigned char *sw = nullptr;
   int *valid = nullptr;
   float *z32 = nullptr;
+  double *xc = nullptr, *sT = nullptr;
   int fs = 0, swld = 0;
 };
 __host__ __device__ inline int chord_floats(int N) {

@@ -129,7 +129,7 @@ class Solver:
     def __init__(self, mech, flame, *, n_nodes=3, n_sweeps=4, nu=2, scheme="CISDCQ",
                  precision="fp64", newton_rtol=1e-12, newton_maxit=50, lin_rtol=1e-14,
                  mg_levels=1, two_streams=True, use_graph=True, profile=False, rates_mma=False,
-                 nu_rule=None, lanes=1, device="cuda"):
+                 nu_rule=None, lanes=1, lin_rounds=0, device="cuda"):
         self.lib = L.load()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -161,6 +161,7 @@ class Solver:
         o.profile = int(profile)
         o.rates_mma = int(rates_mma)
         o.lanes = int(lanes)
+        o.lin_rounds = int(lin_rounds)
         if nu_rule is not None:   # (eta, rho_stall): adaptive nested iterations, nu the cap
             o.nu_eta, o.nu_rho_stall = float(nu_rule[0]), float(nu_rule[1])
         self.opts = o
@@ -329,6 +330,10 @@ class Solver:
 
     def surrogate_enable(self, on=True, s_min=1e-8):
         L.check(self.lib.misdc_surrogate_enable(self.handle, int(bool(on)), float(s_min)))
+
+    def surrogate_sweeps(self, n_sweeps):
+        """Use the learned guess only in the first n_sweeps sweeps of a step (0: all)."""
+        L.check(self.lib.misdc_surrogate_sweeps(self.handle, int(n_sweeps)))
 
     def surrogate_collect(self, capacity):
         L.check(self.lib.misdc_surrogate_collect(self.handle, int(capacity)))
