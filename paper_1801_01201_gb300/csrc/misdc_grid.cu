@@ -45,6 +45,27 @@ __device__ __forceinline__ Nbr neighbours(const DevGrid &g, int c) {
 }
 
 // ---------------------------------------------------------------------------
+// out[o][e] = sum_k w[o][k] in[k][e] with the input and output counts fixed at
+// compile time (NI inputs, NO outputs): exactly NI x NO FMAs and NI loads per
+// element, every load of a thread issued before its first FMA
+template <int NO, int NI>
+__global__ void __launch_bounds__(256) k_lincomb_t(LinComb lc, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double v[NI];
+#pragma unroll
+    for (int k = 0; k < NI; ++k) v[k] = lc.in[k][e];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < NI; ++k) acc = fma(lc.w[o][k], v[k], acc);
+      lc.out[o][e] = acc;
+    }
+  }
+}
+
+// any other count (at most 8 outputs, 16 inputs)
 __global__ void k_lincomb(LinComb lc, size_t n) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -675,11 +696,27 @@ int chebyshev_sweeps(double rho_bound, double reduction) {
   return std::max(1, (int)ceil(need / a));
 }
 
+namespace {
+template <int NO, int NI>
+bool lincomb_fixed(const LinComb &lc, size_t n, unsigned blocks, cudaStream_t s) {
+  if (lc.n_in == NI) {
+    k_lincomb_t<NO, NI><<<blocks, 256, 0, s>>>(lc, n);
+    return true;
+  }
+  if constexpr (NI > 1) return lincomb_fixed<NO, NI - 1>(lc, n, blocks, s);
+  return false;
+}
+}  // namespace
+
 void launch_lincomb(const LinComb &lc, size_t n, cudaStream_t s) {
   if (!n) return;
   size_t blocks = (n + 255) / 256;
   if (blocks > 65535 * 8) blocks = 65535 * 8;
-  k_lincomb<<<(unsigned)blocks, 256, 0, s>>>(lc, n);
+  const unsigned b = (unsigned)blocks;
+  bool done = false;
+  if (lc.n_out == 1) done = lincomb_fixed<1, 12>(lc, n, b, s);
+  else if (lc.n_out == 2) done = lincomb_fixed<2, 12>(lc, n, b, s);
+  if (!done) k_lincomb<<<b, 256, 0, s>>>(lc, n);
 }
 
 size_t operator_face_doubles(const DevGrid &g, int N) {
