@@ -416,6 +416,7 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
 
 // Residual check, flux-form reconstruction x := rhs + c_f L x, and closure of
 // the dominant species. Writes the advection-diffusion state.
+template <int DIM>
 __global__ void k_finish(DevGrid g, FieldMap fm, int N, int i0, double tol,
                          const double *__restrict__ thf, const double *__restrict__ rhs,
                          const double *x0, const double *x1, const double *x2,
@@ -430,18 +431,35 @@ __global__ void k_finish(DevGrid g, FieldMap fm, int N, int i0, double tol,
     x = sl == 0 ? x0 : (sl == 1 ? x1 : x2);
   }
   if (c < cs) {
-    const Nbr nb = neighbours(g, c);
+    // neighbour indices and face coefficients once per cell (not per field)
+    int cm[DIM], cp[DIM];
+    double tlo[DIM], thi[DIM];
+    {
+      const Nbr nb = neighbours(g, c);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        cm[d] = nb.cm[d];
+        cp[d] = nb.cp[d];
+        tlo[d] = thf[(size_t)d * cs + c];
+        thi[d] = thf[(size_t)d * cs + cp[d]];
+      }
+    }
     double sum = 0.0;
     for (int k = 0; k < fm.nfs; ++k) {
       const int f = fm.fld[k];
       const size_t off = (size_t)f * cs;
-      const double L = lap_theta(g, nb, c, cs, thf, x + off);
+      const double *xf = x + off;
+      const double xc = xf[c];
+      double L = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) L += thi[d] * (xf[cp[d]] - xc) - tlo[d] * (xc - xf[cm[d]]);
       const double b = rhs[off + c];
-      const double scale = fabs(b) + fabs(fm.cf[k] * L) + fabs(x[off + c]) + 1e-300;
-      const double r = b - (x[off + c] - fm.cf[k] * L);
+      const double cl = fm.cf[k] * L;
+      const double scale = fabs(b) + fabs(cl) + fabs(xc) + 1e-300;
+      const double r = b - (xc - cl);
       // diagnostic ratio in FP32 (FP64 divisions are scarce on this part)
       rmax = fmax(rmax, (double)(__double2float_ru(fabs(r)) / fmaxf(__double2float_rd(scale), 1e-30f)));
-      const double v = b + fm.cf[k] * L;
+      const double v = b + cl;
       out[off + c] = v;
       if (f < N) sum += v;
     }
@@ -453,6 +471,18 @@ __global__ void k_finish(DevGrid g, FieldMap fm, int N, int i0, double tol,
     atomicMax(&st->lin_resid_bits, dbits(rmax));
     if (!(rmax <= tol)) atomicOr(&st->status_bits, kBitMG);
   }
+}
+
+void launch_finish(const DevGrid &g, const FieldMap &fm, int N, int i0, double tol, const double *thf,
+                   const double *rhs, const double *x0, const double *x1, const double *x2,
+                   const int *kdev, double *out, DevStats *st, cudaStream_t s) {
+  const int blocks = (g.cells + 255) / 256;
+  if (g.dim == 1)
+    k_finish<1><<<blocks, 256, 0, s>>>(g, fm, N, i0, tol, thf, rhs, x0, x1, x2, kdev, out, st);
+  else if (g.dim == 2)
+    k_finish<2><<<blocks, 256, 0, s>>>(g, fm, N, i0, tol, thf, rhs, x0, x1, x2, kdev, out, st);
+  else
+    k_finish<3><<<blocks, 256, 0, s>>>(g, fm, N, i0, tol, thf, rhs, x0, x1, x2, kdev, out, st);
 }
 
 // ---- multigrid (cell-centred, coarsening by 2 in every used direction) on
@@ -961,14 +991,12 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
       xcur = xnext;
     }
     // reconstruction and residual check of the final iterate
-    k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, w.xc,
-                                              w.xc, w.xc, nullptr, out, st);
+    launch_finish(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, w.xc, w.xc, w.xc, nullptr, out, st, s);
     return;
   }
   if (w.levels > 1) {
     multigrid_solve(g, fm, rhs, w, lin_rtol, st, s);
-    k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, w.xa,
-                                              w.xb, w.xc, nullptr, out, st);
+    launch_finish(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, w.xa, w.xb, w.xc, nullptr, out, st, s);
     return;
   }
   // sweeps: planned on the device from the measured Gershgorin bound, at most
@@ -994,8 +1022,7 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
   }
   const int *kdev = w.kdev;
   const double *xfin = w.xa;
-  k_finish<<<(cs + 255) / 256, 256, 0, s>>>(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, xfin, w.xb,
-                                            w.xc, kdev, out, st);
+  launch_finish(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, xfin, w.xb, w.xc, kdev, out, st, s);
 }
 
 void launch_nu_decide(int F, int cs, int M, NodePtrs now, NodePtrs before, int l, int nu,
