@@ -633,12 +633,15 @@ def concurrency_compare(entries, w, args, dev, rank):
         out[name] = res
     mis = out["misdcq"]
     eps = mis["inc"][K - 1]
+    # the model's stage costs are those of a stage running alone (the one-stream
+    # arm): on two streams the events around a stage also time its neighbour's work
+    iso = out["cisdcq_nu%d_one_stream" % nu]
     for name, res in out.items():
         nc = next((k + 1 for k, v in enumerate(res["inc"]) if v <= eps), None)
         res["N_C"] = nc
         if nc is None or name == "misdcq":
             continue
-        uad, ur = res["U_AD_ms"][nc - 1], res["U_R_ms"][nc - 1]
+        uad, ur = iso["U_AD_ms"][nc - 1], iso["U_R_ms"][nc - 1]
         alpha = (uad + ur) / max(uad, ur)
         nub = res["nested_per_sweep"][nc - 1]
         res["alpha"] = alpha
@@ -741,13 +744,13 @@ def main():
     ap.add_argument("--cpu-side", type=int, default=64)
     ap.add_argument("--ref-side", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--collect-steps", type=int, default=3)
-    ap.add_argument("--train-rows", type=int, default=4_000_000)
-    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--collect-steps", type=int, default=13)
+    ap.add_argument("--train-rows", type=int, default=10_000_000)
+    ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--train-batch", type=int, default=8192)
     ap.add_argument("--train-lr", type=float, default=2e-3)
     ap.add_argument("--s-min", type=float, default=1e-4)
-    ap.add_argument("--sg-sweeps", type=int, default=0,
+    ap.add_argument("--sg-sweeps", type=int, default=1,
                     help="learned guess in the first SG_SWEEPS sweeps of a step only (0: all)")
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--rates-mma", type=int, default=0,
@@ -767,9 +770,10 @@ def main():
                     help="instead of the headline: serial MISDCQ against CISDCQ-nu on one and on two "
                          "streams and with adaptive nu, sweeps 1..K each: step times, stage costs, "
                          "sweep increments, sweeps to the MISDCQ tolerance, measured and modelled R_nu")
-    ap.add_argument("--lin-rounds", type=int, default=0,
+    ap.add_argument("--lin-rounds", type=int, default=2,
                     help="mixed precision: FP64-residual refinement rounds of the diffusion solve "
-                         "(0: the library's default)")
+                         "(0: the library's default, 3); the line reports the residual and the "
+                         "error against the FP64 sweep")
     ap.add_argument("--nodes", type=int, default=0,
                     help="--concurrency: Gauss-Lobatto nodes (default: the workload's)")
     ap.add_argument("--rates-compare", action="store_true",

@@ -315,6 +315,19 @@ def test_step_parity_full_chemistry_multid(case, pool):
     assert np.all(err <= tol_from(sens)), (err, sens)
 
 
+def test_mixed_step_with_two_refinement_rounds_meets_accuracy_bar(pool):
+    """The benchmark's mixed diffusion setting (two FP64-residual refinement rounds
+    around the FP32 inner solves instead of three) on full chemistry: the mixed
+    bar against the oracle and a final diffusion residual below 1e-12."""
+    mech, fl = small_2d(n=32)
+    got, T, want, ad, st, sens = _run_both(mech, fl, 5e-6, 2, precision="mixed", lin_rounds=2,
+                                           sensitivity=True, pool=pool, case="mixed_2rounds_2d_n21")
+    N = mech.n_species
+    mixed_bar(got, want, sens, N)
+    assert relerr(T, ad.T_from_h(want[:N], want[N])) <= 1e-6
+    assert st["lin_resid_max"] < 1e-12, st["lin_resid_max"]
+
+
 @pytest.mark.parametrize("case", ["2d_n21", "2d_n53", "3d_n21"])
 def test_step_mixed_precision_meets_accuracy_bar(case, pool):
     """Mixed mode against the FP64 oracle: each species (above Y_FLOOR) within
