@@ -1386,7 +1386,7 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
   const bool split = mixed && cst.f && cst.valid && cst.z32 && cst.xc && cst.sT && FRp && hspp && hp &&
                      thp && cfg && cfg->list && cfg->list_n;
   const int *list = split ? cfg->list : nullptr, *list_n = split ? cfg->list_n : nullptr;
-  if (split) {
+  if (split && !cfg->precertified) {
     cudaMemsetAsync(cfg->list_n, 0, sizeof(int), s);
     k_certify<<<(n + 255) / 256, 256, 0, s>>>(m, n, cs, wdt, rtol, b, hstar, Yg, Tg, Y, T, FR, hsp,
                                               theta, iters, st, pred ? sc : nullptr, s_min, prow, FRp,
@@ -1404,6 +1404,23 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                                                 nullptr);
 }
 
+
+bool launch_certify(const DevMech &m, int n, int cs, double wdt, double rtol, const double *b,
+                    const double *hstar, const double *Yg, const double *Tg, double *Y, double *T,
+                    double *FR, double *hsp, double *theta, int *iters, DevStats *st,
+                    const double *FRp, const double *hp, const ChordStore *store,
+                    const double *hspp, const double *thp, const NewtonLaunch *cfg, cudaStream_t s) {
+  if (n <= 0 || !store) return false;
+  const ChordStore &cst = *store;
+  if (!(cst.f && cst.valid && cst.z32 && cst.xc && cst.sT && FRp && hspp && hp && thp && cfg &&
+        cfg->list && cfg->list_n))
+    return false;
+  cudaMemsetAsync(cfg->list_n, 0, sizeof(int), s);
+  k_certify<<<(n + 255) / 256, 256, 0, s>>>(m, n, cs, wdt, rtol, b, hstar, Yg, Tg, Y, T, FR, hsp, theta,
+                                            iters, st, nullptr, 0.0, nullptr, FRp, hp, cst, hspp, thp,
+                                            cfg->list, cfg->list_n);
+  return true;
+}
 
 cudaError_t init_exp_table() {
   static std::mutex mu;

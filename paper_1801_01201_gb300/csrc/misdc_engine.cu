@@ -380,18 +380,28 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
   if (prof) cudaEventRecordWithFlags(s->prof_n[2 * s->n_used], st, cudaEventRecordExternal);
   Surrogate *sg = s->sg;
   const float *pred = nullptr;
+  NewtonLaunch nlc = *lane_nl(s, p);
   if (sg && s->sg_collect) {
     // record the features of every solve worth learning (plain Newton follows)
-    mlp_features(s->m, s->cs, s->cs, wdt, s->bR, ad.phi + N * cs, guess.phi, guess.T, guess.FR,
+    mlp_features(s->m, s->cs, s->cs, wdt, lane_bR(s, p), ad.phi + N * cs, guess.phi, guess.T, guess.FR,
                  guess.phi + N * cs, sg->ldx, sg->DX, sg->scale, s->sg_smin, sg->ds_count,
                  sg->ds_cap, sg->rowmap, st);
   } else if (sg && s->sg_on && s->sg_this_sweep) {
+    // mixed precision with kept factors: certification first, so that the learned
+    // guess is computed only for the cells it leaves (a certified guess is
+    // converged and needs none)
+    const bool pre = s->o.precision == MISDC_PREC_MIXED && s->keep_factors &&
+                     launch_certify(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, lane_bR(s, p),
+                                    ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR,
+                                    out.hsp, out.theta, lane_iters(s, p), s->st, guess.FR,
+                                    guess.phi + N * cs, &s->cst[t], guess.hsp, guess.theta, &nlc, st);
+    nlc.precertified = pre;
     // learned guess: features of the cells worth it (s > s_min) gathered into
     // compact rows, then the four layers in one fused kernel over those rows
     cudaMemsetAsync(sg->inf_count, 0, sizeof(unsigned long long), st);
-    mlp_features(s->m, s->cs, s->cs, wdt, s->bR, ad.phi + N * cs, guess.phi, guess.T, guess.FR,
+    mlp_features(s->m, s->cs, s->cs, wdt, lane_bR(s, p), ad.phi + N * cs, guess.phi, guess.T, guess.FR,
                  guess.phi + N * cs, sg->ldx, sg->Xi, sg->scale, s->sg_smin, sg->inf_count, s->cs,
-                 sg->rowmap, st);
+                 sg->rowmap, st, pre ? nlc.list : nullptr, pre ? nlc.list_n : nullptr);
     mlp_fused_forward(*sg, nullptr, 0, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                       nullptr, sg->Xi, s->cs, sg->Oi, st, sg->inf_count);
     pred = sg->Oi;
@@ -399,7 +409,7 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
   launch_newton(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, lane_bR(s, p),
                 ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR, out.hsp, out.theta,
                 lane_iters(s, p), s->st, st, s->o.precision == MISDC_PREC_MIXED, pred, sg ? sg->ldo : 0,
-                sg ? sg->scale : nullptr, s->sg_smin, guess.FR, guess.phi + N * cs, lane_nl(s, p),
+                sg ? sg->scale : nullptr, s->sg_smin, guess.FR, guess.phi + N * cs, &nlc,
                 s->keep_factors ? &s->cst[t] : nullptr, pred ? sg->rowmap : nullptr, guess.hsp,
                 guess.theta);
   if (sg && s->sg_collect)

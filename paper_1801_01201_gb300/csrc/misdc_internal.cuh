@@ -119,6 +119,7 @@ struct NewtonLaunch {
   int wpb = 0, blocks_per_sm = 0, dynamic = 0;
   int *work = nullptr;
   int *list = nullptr, *list_n = nullptr;
+  bool precertified = false;   // launch_certify has run: the Newton kernel takes the list
 };
 // Mixed precision: per-cell Jacobian factors kept between the solves of one SDC
 // node. Per cell: fs doubles (row-major LU of the (row-scaled) (N+1)^2 Jacobian,
@@ -157,6 +158,14 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                    const int *prow = nullptr, const double *hspp = nullptr,
                    const double *thp = nullptr);
 int newton_max_wpb(const DevMech &m, bool mixed);
+// The certification pass of a mixed reaction step alone (the cells it leaves in
+// cfg->list / cfg->list_n); launch_newton with cfg->precertified then takes the list.
+// Returns false (and launches nothing) when the step has no kept factors to certify from.
+bool launch_certify(const DevMech &m, int n, int cs, double wdt, double rtol, const double *b,
+                    const double *hstar, const double *Yg, const double *Tg, double *Y, double *T,
+                    double *FR, double *hsp, double *theta, int *iters, DevStats *st,
+                    const double *FRp, const double *hp, const ChordStore *store,
+                    const double *hspp, const double *thp, const NewtonLaunch *cfg, cudaStream_t s);
 
 // ---- grid kernels (misdc_grid.cu) ----
 struct LinComb {
@@ -324,7 +333,8 @@ void mlp_fused_forward(const Surrogate &g, const DevMech *m, int cs, double wdt,
 void mlp_features(const DevMech &m, int n, int cs, double wdt, const double *b,
                   const double *hstar, const double *Yp, const double *Tp, const double *FRp,
                   const double *hp, int ldx, __nv_bfloat16 *X, double *scale, double s_min,
-                  unsigned long long *counter, long long cap, int *rowmap, cudaStream_t s);
+                  unsigned long long *counter, long long cap, int *rowmap, cudaStream_t s,
+                  const int *list = nullptr, const int *list_n = nullptr);
 void mlp_targets(int N, int n, int cs, const double *Yp, const double *Tp, const double *Ys,
                  const double *Ts, const double *scale, const int *rowmap, int ldt, float *tgt,
                  cudaStream_t s);

@@ -266,9 +266,11 @@ __global__ void k_features(DevMech m, int n, int cs, double wdt, const double *_
                            const double *__restrict__ hp, int ldx, __nv_bfloat16 *__restrict__ X,
                            double *__restrict__ scale, double s_min,
                            unsigned long long *__restrict__ counter, long long cap,
-                           int *__restrict__ rowmap) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
+                           int *__restrict__ rowmap, const int *__restrict__ list,
+                           const int *__restrict__ list_n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (list ? *list_n : n)) return;
+  const int c = list ? list[k] : k;
   const int N = m.N;
   const double T = Tp[c];
   double cp = 0.0, rmax = 0.0;
@@ -690,10 +692,11 @@ void mlp_gemm(const Operand &A, const Operand &Bt, int M, int N, int K, int spli
 void mlp_features(const DevMech &m, int n, int cs, double wdt, const double *b,
                   const double *hstar, const double *Yp, const double *Tp, const double *FRp,
                   const double *hp, int ldx, __nv_bfloat16 *X, double *scale, double s_min,
-                  unsigned long long *counter, long long cap, int *rowmap, cudaStream_t s) {
+                  unsigned long long *counter, long long cap, int *rowmap, cudaStream_t s,
+                  const int *list, const int *list_n) {
   if (n <= 0) return;
   k_features<<<(n + 127) / 128, 128, 0, s>>>(m, n, cs, wdt, b, hstar, Yp, Tp, FRp, hp, ldx, X,
-                                             scale, s_min, counter, cap, rowmap);
+                                             scale, s_min, counter, cap, rowmap, list, list_n);
 }
 
 void mlp_targets(int N, int n, int cs, const double *Yp, const double *Tp, const double *Ys,
