@@ -292,12 +292,14 @@ def train_params(Solver, mech, fl, dt, w, dev, args):
     sv.step(x, dt, args.collect_steps)
     rows, _, _ = sv.surrogate_dataset()
     sv.surrogate_collect(0)
+    collect_status = sv.stats()["status_name"]
     curve = sv.surrogate_train(args.train_steps, batch=args.train_batch, lr=args.train_lr,
                                weight_decay=1e-4, seed=args.seed)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     p = sv.surrogate_save()
-    info = {"rows": rows, "train_steps": args.train_steps, "batch": args.train_batch,
+    info = {"rows": rows, "collect_steps": args.collect_steps, "collect_status": collect_status,
+            "train_steps": args.train_steps, "batch": args.train_batch,
             "loss_first": float(curve[:10].mean()), "loss_last": float(curve[-50:].mean()),
             "seconds": el, "flame_cells": tf.cells}
     sv.close()

@@ -289,7 +289,8 @@ __global__ void k_features(DevMech m, int n, int cs, double wdt, const double *_
   long long row = c;
   if (counter) {
     row = -1;
-    if (s > s_min) {
+    // a cell whose state is not finite (a failed solve upstream) gives no row
+    if (s > s_min && isfinite(s) && isfinite(T) && T > 0.0) {
       row = (long long)atomicAdd(counter, 1ull);
       if (row >= cap) row = -1;
     }
@@ -322,6 +323,10 @@ __global__ void k_targets(int N, int n, int cs, const double *__restrict__ Yp,
   const double s = scale[c];
   const double inv = (s > 0.0) ? 1.0 / s : 0.0;
   float *t = tgt + (size_t)row * ldt;
+  if (!isfinite(Ts[c]) || !(Ts[c] > 0.0)) {   // the solve failed: a zero step, not a NaN
+    for (int j = 0; j < ldt; ++j) t[j] = 0.0f;
+    return;
+  }
   for (int i = 0; i < N; ++i) {
     const double d = (Ys[(size_t)i * cs + c] - Yp[(size_t)i * cs + c]) * inv;
     t[i] = (float)fmin(fmax(d, -(double)kTargetClip), (double)kTargetClip);

@@ -316,12 +316,17 @@ def test_step_parity_full_chemistry_multid(case, pool):
 
 
 def test_mixed_step_with_two_refinement_rounds_meets_accuracy_bar(pool):
-    """The benchmark's mixed diffusion setting (two FP64-residual refinement rounds
-    around the FP32 inner solves instead of three) on full chemistry: the mixed
-    bar against the oracle and a final diffusion residual below 1e-12."""
-    mech, fl = small_2d(n=32)
+    """The benchmark's mixed diffusion setting on its 3D workload (two FP64-residual
+    refinement rounds around the FP32 inner solves instead of three), on a 12^3
+    box of the same recipe (dx = 1e-4 m, the random-phase field, full chemistry):
+    the mixed bar against the oracle and a final diffusion residual below 1e-12.
+    (On the 2D flames, dx = 4e-5 m, the operator is 6x stiffer; there an FP32
+    inner solve reduces the residual by only about 1e-6 per round, two rounds miss
+    the 1e-12 check, and the library's default stays three.)"""
+    mech = I.make_mechanism(1802, 21, 84)
+    fl = I.flame_3d(mech, 1802, n=12, dx=1e-4, urms=3.0, radius=0.3 * 12 * 1e-4, delta=2e-4)
     got, T, want, ad, st, sens = _run_both(mech, fl, 5e-6, 2, precision="mixed", lin_rounds=2,
-                                           sensitivity=True, pool=pool, case="mixed_2rounds_2d_n21")
+                                           sensitivity=True, pool=pool, case="mixed_2rounds_3d_n21")
     N = mech.n_species
     mixed_bar(got, want, sens, N)
     assert relerr(T, ad.T_from_h(want[:N], want[N])) <= 1e-6
