@@ -274,12 +274,14 @@ __global__ void k_features(DevMech m, int n, int cs, double wdt, const double *_
   const int N = m.N;
   const double T = Tp[c];
   double cp = 0.0, rmax = 0.0;
+  bool finite = isfinite(T) && T > 0.0;
   for (int i = 0; i < N; ++i) {
     const double *a = m.cpcoef + 5 * i;
     const double cpR = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
     const double y = Yp[(size_t)i * cs + c];
     cp = fma(y, kRu * m.invW[i] * cpR, cp);
     const double r = b[(size_t)i * cs + c] - y + wdt * FRp[(size_t)i * cs + c];
+    finite = finite && isfinite(y) && isfinite(r);   // (fmax below would drop a NaN)
     rmax = fmax(rmax, fabs(r));
   }
   const double rT = (hstar[c] - hp[c]) / (cp * T);
@@ -290,7 +292,7 @@ __global__ void k_features(DevMech m, int n, int cs, double wdt, const double *_
   if (counter) {
     row = -1;
     // a cell whose state is not finite (a failed solve upstream) gives no row
-    if (s > s_min && isfinite(s) && isfinite(T) && T > 0.0) {
+    if (s > s_min && isfinite(s) && finite) {
       row = (long long)atomicAdd(counter, 1ull);
       if (row >= cap) row = -1;
     }
@@ -323,7 +325,9 @@ __global__ void k_targets(int N, int n, int cs, const double *__restrict__ Yp,
   const double s = scale[c];
   const double inv = (s > 0.0) ? 1.0 / s : 0.0;
   float *t = tgt + (size_t)row * ldt;
-  if (!isfinite(Ts[c]) || !(Ts[c] > 0.0)) {   // the solve failed: a zero step, not a NaN
+  bool finite = isfinite(Ts[c]) && Ts[c] > 0.0;
+  for (int i = 0; i < N; ++i) finite = finite && isfinite(Ys[(size_t)i * cs + c]);
+  if (!finite) {   // the solve failed: a zero step, not a NaN
     for (int j = 0; j < ldt; ++j) t[j] = 0.0f;
     return;
   }
