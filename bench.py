@@ -264,42 +264,58 @@ def entries_for(name, grid=0):
     return [(mech, fl, w["dt"])], w
 
 
-def training_flame(mech, fl):
+def training_flame(mech, fl, radius_frac=0.28):
     """A different flame of the same mechanism for recording training solves:
-    another seed and kernel, at most 128^2 (48^3) cells."""
+    another seed and kernel (radius radius_frac x the box), at most 128^2 (48^3)
+    cells."""
     from paper_1801_01201_gb300 import inputs as I
     if fl.dim == 2:
         n = min(fl.nx, 128)
         L = n * fl.dx
-        return I.flame_2d(mech, 4242, n=n, dx=fl.dx, amp=2.0, radius=0.28 * L,
+        return I.flame_2d(mech, 4242, n=n, dx=fl.dx, amp=2.0, radius=radius_frac * L,
                           delta=min(2e-4, L / 16), centre=(0.41 * L, 0.57 * L))
     if fl.dim == 3:
         n = min(fl.nx, 48)
-        return I.flame_3d(mech, 4242, n=n, dx=fl.dx, urms=3.0, radius=0.28 * n * fl.dx)
+        return I.flame_3d(mech, 4242, n=n, dx=fl.dx, urms=3.0, radius=radius_frac * n * fl.dx)
     return I.flame_1d(mech, 4242, nx=fl.nx, dx=fl.dx)
 
 
+# kernel radii (fractions of the training box) of the recording restarts
+TRAIN_RADII = (0.28, 0.36, 0.22, 0.40, 0.32, 0.25)
+
+
 def train_params(Solver, mech, fl, dt, w, dev, args):
-    """Record solves on a training flame, train the MLP, return (params, info)."""
+    """Record solves on a training flame, train the MLP, return (params, info).
+
+    The recording runs COLLECT_RESTARTS short runs of COLLECT_STEPS steps, each
+    from a fresh kernel of another radius in the same velocity field: the
+    fourth-order centred advection of a front a few cells wide leaves small
+    undershoots behind it once the front has moved a few cells, and on the small
+    training box (stronger strain) they grow within about ten steps; short runs
+    from fresh states keep every recorded solve in the physical range."""
     import torch
-    tf = training_flame(mech, fl)
-    sv = Solver(mech, tf, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"], scheme=args.scheme,
-                precision="fp64", device=dev)
-    sv.surrogate_init(seed=args.seed)
-    x = sv.state_from_YT(tf.Y, tf.T)
-    sv.surrogate_collect(args.train_rows)
+    sv = None
+    statuses = []
     t0 = time.perf_counter()
-    sv.step(x, dt, args.collect_steps)
+    for k in range(args.collect_restarts):
+        tf = training_flame(mech, fl, TRAIN_RADII[k % len(TRAIN_RADII)])
+        if sv is None:
+            sv = Solver(mech, tf, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"],
+                        scheme=args.scheme, precision="fp64", device=dev)
+            sv.surrogate_init(seed=args.seed)
+            sv.surrogate_collect(args.train_rows)
+        x = sv.state_from_YT(tf.Y, tf.T)
+        sv.step(x, dt, args.collect_steps)
+        statuses.append(sv.stats()["status_name"])
     rows, _, _ = sv.surrogate_dataset()
     sv.surrogate_collect(0)
-    collect_status = sv.stats()["status_name"]
     curve = sv.surrogate_train(args.train_steps, batch=args.train_batch, lr=args.train_lr,
                                weight_decay=1e-4, seed=args.seed)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     p = sv.surrogate_save()
-    info = {"rows": rows, "collect_steps": args.collect_steps, "collect_status": collect_status,
-            "train_steps": args.train_steps, "batch": args.train_batch,
+    info = {"rows": rows, "collect_restarts": args.collect_restarts, "collect_steps": args.collect_steps,
+            "collect_status": statuses, "train_steps": args.train_steps, "batch": args.train_batch,
             "loss_first": float(curve[:10].mean()), "loss_last": float(curve[-50:].mean()),
             "seconds": el, "flame_cells": tf.cells}
     sv.close()
@@ -332,10 +348,24 @@ class Runner:
             self.states0.append(st)
         self.dts = [dt for _, _, dt in entries]
         self.batch = Batch(self.solvers) if len(entries) > 1 else None
-        self.states = [x.clone() for x in self.states0]
+        self.run_steps = w["steps"]
         self.cells = sum(fl.cells for _, fl, _ in entries)
+        self.reset()
+
+    def reset(self):
+        self.states = [x.clone() for x in self.states0]
+        self.taken = 0
 
     def step(self, stream=None):
+        if self.taken == self.run_steps:
+            # the workload is a run of run_steps steps from its initial state:
+            # start it again (a device copy, on the stream the step is timed on)
+            import torch
+            with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream()):
+                for x, x0 in zip(self.states, self.states0):
+                    x.copy_(x0)
+            self.taken = 0
+        self.taken += 1
         if self.batch is not None:
             self.batch.step(self.states, self.dts, 1, stream=stream)
         else:
@@ -746,7 +776,10 @@ def main():
     ap.add_argument("--cpu-side", type=int, default=64)
     ap.add_argument("--ref-side", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--collect-steps", type=int, default=13)
+    ap.add_argument("--collect-steps", type=int, default=4,
+                    help="steps of each recording run of the training flame")
+    ap.add_argument("--collect-restarts", type=int, default=4,
+                    help="recording runs, each from a fresh kernel of another radius")
     ap.add_argument("--train-rows", type=int, default=10_000_000)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--train-batch", type=int, default=8192)
@@ -836,7 +869,7 @@ def main():
     head, r_head = variants[args.headline]
     # the headline again with the clock sampler running (its own timed region)
     clocks = ClockSampler(local) if rank == 0 else None
-    head.states = [x.clone() for x in head.states0]
+    head.reset()
     r_head = timed(head, args, flush, stream, dist, clocks, label="headline")
     cells = head.cells
     value = whole_job_rate(world, cells, args.steps, r_head["total_ms"])
@@ -882,6 +915,23 @@ def main():
         nbytes = sum(x.numel() * 8 for x in head.states0)
         e2e = {"value": world * cells * len(tms) / sum(tms) if tms else None, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # batches: the same variant with one reaction launch per flame and stage (the
+    # reaction steps not grouped across flames), its own timed region
+    batch_forms = None
+    if head.batch is not None:
+        gl, gs = head.batch.grouping()
+        head.batch.set_grouping(False)
+        head.reset()
+        r_sep = timed(head, args, flush, stream, dist, label="separate")
+        head.batch.set_grouping(True)
+        batch_forms = {
+            "grouped": {"value": value, "grouped_newton_launches_per_step": gl,
+                        "flame_reaction_steps_grouped_per_step": gs,
+                        "kernel_launches_per_step": r_head["stats"]["kernel_launches"] / args.steps},
+            "separate": {"value": whole_job_rate(world, cells, args.steps, r_sep["total_ms"]),
+                         "kernel_launches_per_step": r_sep["stats"]["kernel_launches"] / args.steps,
+                         "status": r_sep["stats"]["status_name"]}}
 
     if rank != 0:
         if dist:
@@ -951,6 +1001,8 @@ def main():
            "flames": len(entries), "cells": cells, "nodes": w["nodes"],
            "sweeps": w["sweeps"], "nu": w["nu"], "scheme": args.scheme, "variant": args.headline,
            "autotuned": tune, "l2": "flushed between steps (256 MB write)",
+           "run": "%d-step runs from the initial state, repeated (restart copy inside the timed region)"
+                  % w["steps"],
            "learned_sweeps": args.sg_sweeps or w["sweeps"], "lin_rounds": args.lin_rounds or 3,
            "rates": "fp64 tensor cores" if args.rates_mma else "sparse fp64 fma",
            "diffusion": "multigrid %d levels" % args.mg_levels if args.mg_levels > 1 else "chebyshev"}
@@ -960,6 +1012,9 @@ def main():
                     "reactions": mech.n_reactions, "dt": dt})
     else:
         cfg["mechanisms"] = sorted({"%d/%d" % (m.n_species, m.n_reactions) for m, _, _ in entries})
+    # the state the errors are taken on: steps since the run's start, smallest mass fraction
+    cfg["compared_after_steps"] = plain.taken
+    cfg["Y_min"] = min(float(x[:m.n_species].min().item()) for x, (m, _, _) in zip(head.states, entries))
     acc_ok = None
     if args.headline in errs:
         e = errs[args.headline]
@@ -976,6 +1031,8 @@ def main():
             "speedup_vs_plain_fp64": value / summary("fp64")["value"] / world}
     if train_info:
         line["training"] = train_info
+    if batch_forms:
+        line["batch_forms"] = batch_forms
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
