@@ -446,7 +446,17 @@ misdc_status misdc_set_tuning(misdc_solver *s, const misdc_tuning *t);
  * small grids fill the GPU together. The graph is captured on the first call and
  * again whenever a state or T pointer or a dt changes. states[i] / T[i]
  * (T may be NULL, or hold NULL entries) are device arrays of solver i; dts[i]
- * its time step. The solvers must not record solves while batched. */
+ * its time step. The solvers must not record solves while batched.
+ *
+ * Reaction steps (Sec. 3.3, S5) of the flames are grouped by default: the k-th
+ * reaction step of every flame whose mechanism has the same species and reaction
+ * counts and whose launch has the same shape becomes one persistent launch over
+ * the cells of all of them, fed from one work counter (a warp takes the next free
+ * cell of any of the flames), so uneven per-cell Newton work is balanced across
+ * flames; each flame's stage waits for that launch. Grouping needs every flame to
+ * have the same number of reaction steps per time step, each flame's steps in one
+ * sequence (one stream pair, a fixed nu); otherwise, or with grouping off, every
+ * flame keeps its own launches. Results are bitwise the same either way. */
 typedef struct misdc_batch misdc_batch;
 misdc_status misdc_batch_create(misdc_solver *const *solvers, int n, misdc_batch **out);
 void misdc_batch_destroy(misdc_batch *b);
@@ -454,6 +464,13 @@ misdc_status misdc_batch_step(misdc_batch *b, double *const *states, double *con
                               const double *dts, int n_steps, void *stream);
 /* Statistics summed over the batch's solvers (synchronises). */
 misdc_status misdc_batch_stats(misdc_batch *b, misdc_stats *out, int reset);
+/* Grouping of the flames' reaction steps (on = 1, the default, or 0); takes
+ * effect at the next capture (a change drops the current graph). */
+misdc_status misdc_batch_set_grouping(misdc_batch *b, int on);
+/* Of the current graph (zeros before the first step, or without grouping): the
+ * grouped reaction launches per time step and the per-flame reaction steps they
+ * replace. */
+misdc_status misdc_batch_grouping(misdc_batch *b, int *grouped_launches, int *grouped_solves);
 
 const char *misdc_last_error(void);
 

@@ -82,6 +82,7 @@ EXPORTS = ["misdc_default_opts", "misdc_create", "misdc_destroy", "misdc_step", 
            "misdc_surrogate_features", "misdc_surrogate_forward", "misdc_surrogate_gradient",
            "misdc_surrogate_train_batch", "misdc_surrogate_forward_layers", "misdc_surrogate_guess", "misdc_autotune", "misdc_get_tuning", "misdc_set_tuning",
            "misdc_batch_create", "misdc_batch_destroy", "misdc_batch_step", "misdc_batch_stats",
+           "misdc_batch_set_grouping", "misdc_batch_grouping",
            "misdc_pde_step", "misdc_pde_smem_bytes", "misdc_exp", "misdc_probe_flops",
            "misdc_lowmach_step", "misdc_surrogate_sweeps"]
 
@@ -148,6 +149,8 @@ def load(build_if_missing: bool = True):
     L.misdc_batch_destroy.restype = None
     L.misdc_batch_step.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), dp, C.c_int, vp]
     L.misdc_batch_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
+    L.misdc_batch_set_grouping.argtypes = [vp, C.c_int]
+    L.misdc_batch_grouping.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.misdc_pde_step.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
                                  C.c_double, C.c_int, vp, vp, vp, vp, vp, vp]
     L.misdc_exp.argtypes = [vp, vp, C.c_size_t, vp]

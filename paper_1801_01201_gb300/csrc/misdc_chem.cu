@@ -517,30 +517,37 @@ __global__ void __launch_bounds__(256) k_certify(DevMech m, int n, int cs, doubl
   }
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, double wdt, double rtol,
-                                                 int maxit, int ld, const double *__restrict__ b,
-                                                 const double *__restrict__ hstar,
-                                                 const double *Yg, const double *Tg, double *Yout,
-                                                 double *Tout, double *__restrict__ FR,
-                                                 double *__restrict__ hsp,
-                                                 double *__restrict__ theta,
-                                                 int *__restrict__ iters, DevStats *st,
-                                                 const float *__restrict__ pred, int ldp,
-                                                 const double *__restrict__ sc, double s_min,
-                                                 const double *__restrict__ FRp,
-                                                 const double *__restrict__ hp,
-                                                 int *__restrict__ work, ChordStore cst,
-                                                 const int *__restrict__ prow,
-                                                 const double *__restrict__ hspp,
-                                                 const double *__restrict__ thp,
-                                                 const int *__restrict__ list,
-                                                 const int *__restrict__ list_n) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+// The reaction Newton of a run of work items of one solve (one warp per cell);
+// `first` is the warp's first item, next(item) its next one (>= items ends the
+// run). wsm: the warp's shared-memory scratch. Per-warp counters go to A.st at the
+// end of the run.
+template <bool MIXED, class Next>
+__device__ __forceinline__ void newton_items(const NewtonArgs &A, double *wsm, int first, int items,
+                                             Next next_item) {
+  const DevMech &m = A.m;
+  const int cs = A.cs, maxit = A.maxit, ld = A.ld, ldp = A.ldp;
+  const double wdt = A.wdt, rtol = A.rtol, s_min = A.s_min;
+  const double *__restrict__ b = A.b;
+  const double *__restrict__ hstar = A.hstar;
+  const double *Yg = A.Yg, *Tg = A.Tg;
+  double *Yout = A.Yout, *Tout = A.Tout;
+  double *__restrict__ FR = A.FR;
+  double *__restrict__ hsp = A.hsp;
+  double *__restrict__ theta = A.theta;
+  int *__restrict__ iters = A.iters;
+  DevStats *st = A.st;
+  const float *__restrict__ pred = A.pred;
+  const double *__restrict__ sc = A.sc;
+  const double *__restrict__ FRp = A.FRp;
+  const double *__restrict__ hp = A.hp;
+  const ChordStore &cst = A.cst;
+  const int *__restrict__ prow = A.prow;
+  const double *__restrict__ hspp = A.hspp;
+  const double *__restrict__ thp = A.thp;
+  const int *__restrict__ list = A.list;
+  const int lane = threadIdx.x & 31;
   const int N = m.N, R = m.R, nn = N + 1, na = nn + 1;   // na: columns of the augmented matrix
-  const size_t per_warp = newton_warp_doubles(N, R, ld, MIXED);
-  NW w = carve2(smem + (size_t)wib * per_warp, N, R, ld, MIXED);
+  NW w = carve2(wsm, N, R, ld, MIXED);
   double *J = w.J;
   const int seg0 = m.jc_seg[lane], seg1 = m.jc_seg[lane + 1];
   // per-launch constants (an FP64 division is a long instruction sequence on this
@@ -552,20 +559,9 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
   int my_max = 0;
   unsigned bits = 0;
 
-  // cells: a fixed grid-stride share per warp, or (work != NULL) the next free cell
-  // from a global counter, which balances the per-cell iteration counts
-  // work items: a fixed grid-stride share per warp, or (work != NULL) the next
-  // free item from a global counter, which balances the per-cell iteration counts;
   // an item is a cell, or with `list` the list's entry (the cells that the
   // certification kernel left)
-  auto next_item = [&](int cur) -> int {
-    if (!work) return cur < 0 ? blockIdx.x * wpb + wib : cur + gridDim.x * wpb;
-    int c = 0;
-    if (lane == 0) c = atomicAdd(work, 1);
-    return __shfl_sync(0xffffffffu, c, 0);
-  };
-  const int items = list ? *list_n : n;
-  for (int item = next_item(-1); item < items; item = next_item(item)) {
+  for (int item = first; item < items; item = next_item(item)) {
     const int cell = list ? list[item] : item;
     for (int i = lane; i < N; i += 32) {
       w.xs[i] = Yg[(size_t)i * cs + cell];
@@ -1282,6 +1278,70 @@ __global__ void __launch_bounds__(128, 4) k_newton2(DevMech m, int n, int cs, do
   }
 }
 
+// One solve: work items are a fixed grid-stride share per warp, or (A.work !=
+// NULL) the next free item from a global counter, which balances the per-cell
+// iteration counts.
+template <bool MIXED>
+__global__ void __launch_bounds__(128, 4) k_newton2(NewtonArgs A) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const size_t per_warp = newton_warp_doubles(A.m.N, A.m.R, A.ld, MIXED);
+  int *work = A.work;
+  auto next_item = [&](int cur) -> int {
+    if (!work) return cur < 0 ? blockIdx.x * wpb + wib : cur + gridDim.x * wpb;
+    int c = 0;
+    if (lane == 0) c = atomicAdd(work, 1);
+    return __shfl_sync(0xffffffffu, c, 0);
+  };
+  const int items = A.list ? *A.list_n : A.n;
+  newton_items<MIXED>(A, smem + (size_t)wib * per_warp, next_item(-1), items, next_item);
+}
+
+// Several solves of one mechanism shape (independent flames at the same stage)
+// in one persistent launch: their items are numbered one after another and each
+// warp takes the next free number from one counter, so the per-cell iteration
+// counts are balanced across the solves. A warp runs the items of a solve until
+// the number it draws belongs to the next one.
+template <bool MIXED>
+__global__ void __launch_bounds__(128, 4) k_newton2_group(const NewtonArgs *__restrict__ jobs, int njobs,
+                                                          int *__restrict__ work) {
+  extern __shared__ double smem[];
+  __shared__ int first_item[kMaxGroupJobs + 1];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int j = 0; j < njobs; ++j) {
+      first_item[j] = acc;
+      acc += jobs[j].list ? *jobs[j].list_n : jobs[j].n;
+    }
+    first_item[njobs] = acc;
+  }
+  __syncthreads();
+  const int total = first_item[njobs];
+  const size_t per_warp = newton_warp_doubles(jobs[0].m.N, jobs[0].m.R, jobs[0].ld, MIXED);
+  double *wsm = smem + (size_t)wib * per_warp;
+  auto draw = [&]() -> int {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(work, 1);
+    return __shfl_sync(0xffffffffu, c, 0);
+  };
+  int g = draw();
+  while (g < total) {
+    int f = 0;
+    while (first_item[f + 1] <= g) ++f;   // the solve that item g belongs to
+    const int lo = first_item[f], hi = first_item[f + 1];
+    int after = total;   // the first drawn item past this solve
+    auto next_item = [&](int) -> int {
+      const int c = draw();
+      if (c < hi) return c - lo;
+      after = c;
+      return hi - lo;
+    };
+    newton_items<MIXED>(jobs[f], wsm, g - lo, hi - lo, next_item);
+    g = after;
+  }
+}
+
 int sm_count() {
   static int n = 0;
   if (!n) {
@@ -1392,16 +1452,63 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                                               theta, iters, st, pred ? sc : nullptr, s_min, prow, FRp,
                                               hp, cst, hspp, thp, cfg->list, cfg->list_n);
   }
+  NewtonArgs A;
+  A.m = m;
+  A.n = n;
+  A.cs = cs;
+  A.wdt = wdt;
+  A.rtol = rtol;
+  A.maxit = maxit;
+  A.ld = ld;
+  A.b = b;
+  A.hstar = hstar;
+  A.Yg = Yg;
+  A.Tg = Tg;
+  A.Yout = Y;
+  A.Tout = T;
+  A.FR = FR;
+  A.hsp = hsp;
+  A.theta = theta;
+  A.iters = iters;
+  A.st = st;
+  A.pred = pred;
+  A.ldp = ldp;
+  A.sc = sc;
+  A.s_min = s_min;
+  A.FRp = FRp;
+  A.hp = hp;
+  A.work = work;
+  A.cst = cst;
+  A.prow = prow;
+  A.hspp = hspp;
+  A.thp = thp;
+  A.list = mixed ? list : nullptr;
+  A.list_n = mixed ? list_n : nullptr;
   if (mixed)
-    k_newton2<true><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
-                                               FR, hsp, theta, iters, st, pred, ldp, sc,
-                                               s_min, FRp, hp, work, cst, prow, hspp, thp, list,
-                                               list_n);
+    k_newton2<true><<<grid, wpb * 32, sm, s>>>(A);
   else
-    k_newton2<false><<<grid, wpb * 32, sm, s>>>(m, n, cs, wdt, rtol, maxit, ld, b, hstar, Yg, Tg, Y, T,
-                                                FR, hsp, theta, iters, st, pred, ldp, sc,
-                                                s_min, FRp, hp, work, cst, prow, hspp, thp, nullptr,
-                                                nullptr);
+    k_newton2<false><<<grid, wpb * 32, sm, s>>>(A);
+}
+
+bool newton_kernel_args(const void *func, void **params, NewtonArgs *out, bool *mixed) {
+  if (func == (const void *)k_newton2<true>) *mixed = true;
+  else if (func == (const void *)k_newton2<false>) *mixed = false;
+  else return false;
+  *out = *(const NewtonArgs *)params[0];
+  return true;
+}
+
+const void *newton_group_kernel(bool mixed) {
+  return mixed ? (const void *)k_newton2_group<true> : (const void *)k_newton2_group<false>;
+}
+
+int newton_group_grid(bool mixed, int wpb, size_t smem, int items) {
+  const int blocks = (items + wpb - 1) / wpb;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_group_kernel(mixed), wpb * 32, smem);
+  if (per_sm <= 0) per_sm = 1;
+  const int cap = sm_count() * per_sm;
+  return blocks < 1 ? 1 : (blocks < cap ? blocks : cap);
 }
 
 

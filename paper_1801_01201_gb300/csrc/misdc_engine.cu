@@ -21,6 +21,7 @@
 #include <mutex>
 #include <string>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include "misdc_internal.cuh"
@@ -420,6 +421,13 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
   node_operators(s, out, lane_thfR(s, p), st);
 }
 
+// stream pairs a step uses for its nested iterations (the learned guess and the
+// adaptive rule keep one pair: their scratch and decisions are per solver)
+int step_lanes(const misdc_solver *s) {
+  const bool two = s->o.two_streams && s->o.scheme == MISDC_SCHEME_CISDCQ;
+  return (two && s->nu_bits == nullptr && !(s->sg && (s->sg_on || s->sg_collect))) ? s->lanes : 1;
+}
+
 // Enqueue one full time step on s->sD (and s->sR).
 void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
   const Tables &T = s->tab;
@@ -428,9 +436,7 @@ void enqueue_step(misdc_solver *s, double *state, double *Tio, double dt) {
   const bool two = s->o.two_streams && sch == MISDC_SCHEME_CISDCQ;
   cudaStream_t sD = s->sD, sR = two ? s->sR : s->sD;
   s->n_used = s->d_used = 0;
-  // stream pairs for the nested iterations (the learned guess and the adaptive rule
-  // keep one pair: their scratch and decisions are per solver)
-  const int lanes = (two && s->nu_bits == nullptr && !(s->sg && (s->sg_on || s->sg_collect))) ? s->lanes : 1;
+  const int lanes = step_lanes(s);
 
   prepare_node0(s, state, Tio, sD);
   for (int m = 1; m <= M; ++m) copy_node(s, s->K[m], s->node0, sD);   // I1-I2
@@ -1784,7 +1790,193 @@ struct misdc_batch {
   std::vector<double *> g_state, g_T;
   std::vector<double> g_dt;
   long long kernels_per_step = 0, kernels_launched = 0;
+  // grouped reaction steps: the job tables and work counters of the current graph
+  bool group = true;
+  int grouped_launches = 0, grouped_solves = 0;
+  NewtonArgs *d_jobs = nullptr;
+  int *d_counters = nullptr;
 };
+
+namespace {
+
+void free_groups(misdc_batch *b) {
+  if (b->d_jobs) cudaFree(b->d_jobs);
+  if (b->d_counters) cudaFree(b->d_counters);
+  b->d_jobs = nullptr;
+  b->d_counters = nullptr;
+  b->grouped_launches = b->grouped_solves = 0;
+}
+
+// Nodes of g in a topological order (empty if g has a cycle or cannot be read).
+std::vector<cudaGraphNode_t> topo_order(cudaGraph_t g) {
+  size_t nn = 0, ne = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) return {};
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) return {};
+  if (cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &ne) != cudaSuccess) return {};
+  std::vector<cudaGraphNode_t> from(ne), to(ne);
+  if (ne && cudaGraphGetEdges(g, from.data(), to.data(), nullptr, &ne) != cudaSuccess) return {};
+  std::unordered_map<cudaGraphNode_t, int> id;
+  for (size_t i = 0; i < nn; ++i) id[nodes[i]] = (int)i;
+  std::vector<int> indeg(nn, 0), head(nn, -1), nxt(ne), dst(ne);
+  for (size_t e = 0; e < ne; ++e) {
+    const int a = id[from[e]], c = id[to[e]];
+    dst[e] = c;
+    nxt[e] = head[a];
+    head[a] = (int)e;
+    ++indeg[c];
+  }
+  std::vector<int> queue;
+  for (size_t i = 0; i < nn; ++i)
+    if (!indeg[i]) queue.push_back((int)i);
+  std::vector<cudaGraphNode_t> out;
+  for (size_t q = 0; q < queue.size(); ++q) {
+    const int a = queue[q];
+    out.push_back(nodes[a]);
+    for (int e = head[a]; e >= 0; e = nxt[e])
+      if (--indeg[dst[e]] == 0) queue.push_back(dst[e]);
+  }
+  if (out.size() != nn) out.clear();
+  return out;
+}
+
+// Replace the k-th reaction-Newton launch of every flame by one grouped launch
+// per mechanism shape (k_newton2_group). Returns false, with g unchanged, when the
+// flames do not qualify; an error after g was changed is reported as such.
+misdc_status group_newton(misdc_batch *b, cudaGraph_t g, bool *changed) {
+  *changed = false;
+  const int n = (int)b->sv.size();
+  if (n < 2) return MISDC_OK;
+  for (misdc_solver *s : b->sv)
+    if (s->nu_bits || step_lanes(s) != 1) return MISDC_OK;   // steps not in one sequence
+  std::vector<cudaGraphNode_t> order = topo_order(g);
+  if (order.empty()) return MISDC_OK;
+  struct Member {
+    cudaGraphNode_t node;
+    NewtonArgs a;
+    bool mixed;
+    cudaKernelNodeParams p;
+  };
+  std::vector<std::vector<Member>> per(n);
+  for (cudaGraphNode_t nd : order) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams p{};
+    if (cudaGraphKernelNodeGetParams(nd, &p) != cudaSuccess || !p.kernelParams) continue;
+    Member mb{nd, NewtonArgs{}, false, p};
+    if (!newton_kernel_args(p.func, p.kernelParams, &mb.a, &mb.mixed)) continue;
+    int f = -1;
+    for (int i = 0; i < n && f < 0; ++i)
+      if (b->sv[i]->st == mb.a.st) f = i;
+    if (f < 0) return MISDC_OK;
+    per[f].push_back(mb);
+  }
+  const size_t K = per[0].size();
+  for (int i = 1; i < n; ++i)
+    if (per[i].size() != K) return MISDC_OK;
+  if (K == 0) return MISDC_OK;
+  // the groups: per stage, flames of one key (kernel, N, R, ld, block, shared memory)
+  std::vector<std::vector<int>> groups;   // member flames
+  std::vector<size_t> stage_of;
+  for (size_t k = 0; k < K; ++k) {
+    std::vector<bool> used(n, false);
+    for (int i = 0; i < n; ++i) {
+      if (used[i]) continue;
+      const Member &x = per[i][k];
+      std::vector<int> grp{i};
+      used[i] = true;
+      for (int j = i + 1; j < n; ++j) {
+        const Member &y = per[j][k];
+        if (!used[j] && y.mixed == x.mixed && y.a.m.N == x.a.m.N && y.a.m.R == x.a.m.R &&
+            y.a.ld == x.a.ld && y.p.blockDim.x == x.p.blockDim.x &&
+            y.p.sharedMemBytes == x.p.sharedMemBytes && (int)grp.size() < kMaxGroupJobs) {
+          grp.push_back(j);
+          used[j] = true;
+        }
+      }
+      if (grp.size() >= 2) {
+        groups.push_back(grp);
+        stage_of.push_back(k);
+      }
+    }
+  }
+  if (groups.empty()) return MISDC_OK;
+  size_t jobs = 0;
+  for (auto &gr : groups) jobs += gr.size();
+  if (cudaMalloc(&b->d_jobs, jobs * sizeof(NewtonArgs)) != cudaSuccess ||
+      cudaMalloc(&b->d_counters, groups.size() * sizeof(int)) != cudaSuccess) {
+    free_groups(b);
+    return fail(MISDC_E_OOM, "grouped reaction steps: job tables");
+  }
+  std::vector<NewtonArgs> host(jobs);
+  size_t j0 = 0;
+  *changed = true;
+  for (size_t q = 0; q < groups.size(); ++q) {
+    const std::vector<int> &gr = groups[q];
+    const size_t k = stage_of[q];
+    const Member &x = per[gr[0]][k];
+    std::vector<cudaGraphNode_t> deps, outs;
+    long long items = 0;
+    for (size_t t = 0; t < gr.size(); ++t) {
+      const Member &mb = per[gr[t]][k];
+      host[j0 + t] = mb.a;
+      items += mb.a.n;
+      size_t nd = 0, no = 0;
+      cudaGraphNodeGetDependencies(mb.node, nullptr, nullptr, &nd);
+      cudaGraphNodeGetDependentNodes(mb.node, nullptr, nullptr, &no);
+      std::vector<cudaGraphNode_t> d(nd), o(no);
+      if ((nd && cudaGraphNodeGetDependencies(mb.node, d.data(), nullptr, &nd) != cudaSuccess) ||
+          (no && cudaGraphNodeGetDependentNodes(mb.node, o.data(), nullptr, &no) != cudaSuccess))
+        return fail(MISDC_E_CUDA, "grouped reaction steps: graph edges");
+      deps.insert(deps.end(), d.begin(), d.end());
+      outs.insert(outs.end(), o.begin(), o.end());
+    }
+    std::sort(deps.begin(), deps.end());
+    deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
+    std::sort(outs.begin(), outs.end());
+    outs.erase(std::unique(outs.begin(), outs.end()), outs.end());
+    for (int f : gr)
+      if (cudaGraphDestroyNode(per[f][k].node) != cudaSuccess)
+        return fail(MISDC_E_CUDA, "grouped reaction steps: removing a launch");
+    cudaMemsetParams ms{};
+    ms.dst = b->d_counters + q;
+    ms.value = 0;
+    ms.elementSize = sizeof(int);
+    ms.width = 1;
+    ms.height = 1;
+    cudaGraphNode_t mnode, knode;
+    if (cudaGraphAddMemsetNode(&mnode, g, deps.data(), deps.size(), &ms) != cudaSuccess)
+      return fail(MISDC_E_CUDA, "grouped reaction steps: counter reset");
+    const size_t smem = x.p.sharedMemBytes;
+    const void *fn = newton_group_kernel(x.mixed);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    NewtonArgs *jp = b->d_jobs + j0;
+    int nj = (int)gr.size();
+    int *cp = b->d_counters + q;
+    void *args[3] = {&jp, &nj, &cp};
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)fn;
+    kp.blockDim = x.p.blockDim;
+    kp.gridDim = dim3(newton_group_grid(x.mixed, (int)(x.p.blockDim.x / 32), smem,
+                                        (int)std::min<long long>(items, 1 << 30)));
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    if (cudaGraphAddKernelNode(&knode, g, &mnode, 1, &kp) != cudaSuccess)
+      return fail(MISDC_E_CUDA, "grouped reaction steps: grouped launch");
+    for (cudaGraphNode_t o : outs)
+      if (cudaGraphAddDependencies(g, &knode, &o, nullptr, 1) != cudaSuccess)
+        return fail(MISDC_E_CUDA, "grouped reaction steps: graph edges");
+    j0 += gr.size();
+    b->grouped_launches += 1;
+    b->grouped_solves += (int)gr.size();
+  }
+  if (cudaMemcpy(b->d_jobs, host.data(), jobs * sizeof(NewtonArgs), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(MISDC_E_CUDA, "grouped reaction steps: job tables");
+  if (topo_order(g).empty()) return fail(MISDC_E_CUDA, "grouped reaction steps: the graph has a cycle");
+  return MISDC_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1934,6 +2126,7 @@ void misdc_batch_destroy(misdc_batch *b) {
   if (!b) return;
   if (b->cs) cudaStreamSynchronize(b->cs);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  free_groups(b);
   for (cudaEvent_t e : b->evDone) if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : {b->evIn, b->evOut, b->evFork}) if (e) cudaEventDestroy(e);
   if (b->cs) cudaStreamDestroy(b->cs);
@@ -1954,6 +2147,7 @@ misdc_status misdc_batch_step(misdc_batch *b, double *const *states, double *con
     stale = b->g_state[i] != states[i] || b->g_T[i] != (T ? T[i] : nullptr) || b->g_dt[i] != dts[i];
   if (stale) {
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    free_groups(b);
     for (int i = 0; i < n; ++i) configure_dt(b->sv[i], dts[i]);
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
@@ -1968,6 +2162,15 @@ misdc_status misdc_batch_step(misdc_batch *b, double *const *states, double *con
     }
     cudaError_t ec = cudaStreamEndCapture(b->cs, &graph);
     if (ec != cudaSuccess) return fail(MISDC_E_CUDA, std::string("batch capture: ") + cudaGetErrorString(ec));
+    if (b->group) {
+      bool changed = false;
+      const misdc_status gs = group_newton(b, graph, &changed);
+      if (gs != MISDC_OK) {
+        cudaGraphDestroy(graph);
+        free_groups(b);
+        return gs;
+      }
+    }
     size_t nn = 0;
     cudaGraphGetNodes(graph, nullptr, &nn);
     std::vector<cudaGraphNode_t> nodes(nn);
@@ -1998,6 +2201,24 @@ misdc_status misdc_batch_step(misdc_batch *b, double *const *states, double *con
   b->kernels_launched += b->kernels_per_step * n_steps;
   CK(cudaEventRecord(b->evOut, b->cs));
   CK(cudaStreamWaitEvent(us, b->evOut, 0));
+  return MISDC_OK;
+}
+
+misdc_status misdc_batch_set_grouping(misdc_batch *b, int on) {
+  if (!b) return fail(MISDC_E_INVALID, "null batch");
+  if ((on != 0) != b->group) {
+    if (b->cs) CK(cudaStreamSynchronize(b->cs));
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    free_groups(b);
+    b->group = on != 0;
+  }
+  return MISDC_OK;
+}
+
+misdc_status misdc_batch_grouping(misdc_batch *b, int *grouped_launches, int *grouped_solves) {
+  if (!b) return fail(MISDC_E_INVALID, "null batch");
+  if (grouped_launches) *grouped_launches = b->grouped_launches;
+  if (grouped_solves) *grouped_solves = b->grouped_solves;
   return MISDC_OK;
 }
 

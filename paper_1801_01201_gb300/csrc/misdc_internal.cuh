@@ -140,6 +140,34 @@ struct ChordStore {
   double *xc = nullptr, *sT = nullptr;
   int fs = 0, swld = 0;
 };
+// Arguments of one reaction-Newton solve over n cells (k_newton2): the
+// right-hand side b, the enthalpy h*, the guesses (Yg, Tg) and their stored
+// reaction terms, species enthalpies and theta (FRp, hp, hspp, thp), the outputs,
+// the learned guess (pred rows ldp apart, scale sc, threshold s_min, row map prow),
+// the kept factors, the work counter and the list of cells the certification pass
+// left (list, *list_n).
+struct NewtonArgs {
+  DevMech m;
+  int n, cs;
+  double wdt, rtol;
+  int maxit, ld;
+  const double *b, *hstar, *Yg, *Tg;
+  double *Yout, *Tout, *FR, *hsp, *theta;
+  int *iters;
+  DevStats *st;
+  const float *pred;
+  int ldp;
+  const double *sc;
+  double s_min;
+  const double *FRp, *hp;
+  int *work;
+  ChordStore cst;
+  const int *prow;
+  const double *hspp, *thp;
+  const int *list, *list_n;
+};
+// solves one grouped Newton launch takes at most
+constexpr int kMaxGroupJobs = 256;
 __host__ __device__ inline int chord_floats(int N) {
   const int nn = N + 1;
   return (nn * nn + 3 * nn + 2 + 1) / 2 * 2;
@@ -166,6 +194,14 @@ bool launch_certify(const DevMech &m, int n, int cs, double wdt, double rtol, co
                     double *FR, double *hsp, double *theta, int *iters, DevStats *st,
                     const double *FRp, const double *hp, const ChordStore *store,
                     const double *hspp, const double *thp, const NewtonLaunch *cfg, cudaStream_t s);
+
+// Grouped reaction Newton (k_newton2_group): newton_kernel_args reads the
+// arguments of a captured k_newton2 launch (false for any other kernel);
+// newton_group_kernel is the grouped kernel; newton_group_grid its persistent grid
+// for `items` work items at wpb warps per block and `smem` dynamic bytes.
+bool newton_kernel_args(const void *func, void **params, NewtonArgs *out, bool *mixed);
+const void *newton_group_kernel(bool mixed);
+int newton_group_grid(bool mixed, int wpb, size_t smem, int items);
 
 // ---- grid kernels (misdc_grid.cu) ----
 struct LinComb {

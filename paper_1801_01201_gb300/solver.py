@@ -416,15 +416,29 @@ class Solver:
 
 
 class Batch:
-    """Independent flames advanced together, one CUDA graph launch per step."""
+    """Independent flames advanced together, one CUDA graph launch per step;
+    `grouping` (default on) merges the flames' k-th reaction steps of one
+    mechanism shape into one load-balanced launch (misdc_batch_set_grouping)."""
 
-    def __init__(self, solvers):
+    def __init__(self, solvers, grouping=True):
         self.lib = L.load()
         self.solvers = list(solvers)
         arr = (C.c_void_p * len(self.solvers))(*[s.handle.value for s in self.solvers])
         h = C.c_void_p()
         L.check(self.lib.misdc_batch_create(arr, len(self.solvers), C.byref(h)))
         self.handle = h
+        if not grouping:
+            self.set_grouping(False)
+
+    def set_grouping(self, on):
+        L.check(self.lib.misdc_batch_set_grouping(self.handle, 1 if on else 0))
+
+    def grouping(self):
+        """(grouped reaction launches per step, per-flame reaction steps they replace)
+        of the current graph."""
+        a, b = C.c_int(), C.c_int()
+        L.check(self.lib.misdc_batch_grouping(self.handle, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def close(self):
         if getattr(self, "handle", None):

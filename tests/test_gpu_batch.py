@@ -195,3 +195,40 @@ def test_batch_of_64_small_flames_autotuned():
             record("batch64_small[%d:%d species]" % (k, fl[k][0].n_species), err=err, S=sens,
                    shapes=len(shapes))
             assert np.all(err <= tol_from(sens)), (k, err, sens)
+
+
+@pytest.mark.parametrize("precision,learned", [("fp64", False), ("mixed", False), ("mixed", True)])
+def test_grouped_reaction_steps_bitwise_equal_separate_launches(precision, learned):
+    """Grouping the flames' reaction steps (one persistent, load-balanced Newton
+    launch per stage and mechanism shape) changes scheduling only: twelve uneven
+    flames (four per mechanism) give the same states and Newton counts bit for bit
+    as the batch with one launch per flame, with fewer kernel launches."""
+    fl = _small_batch(n_flames=12, seed=777)
+    dts = [dt for _, _, dt in fl]
+    out, counts, launches = [], [], []
+    for grouping in (True, False):
+        svs = [S().Solver(m, f, precision=precision) for m, f, _ in fl]
+        if learned:
+            for s in svs:
+                s.surrogate_init(seed=3)
+                s.surrogate_enable(True, s_min=1e-4)
+        states = [_state(s, f) for s, (_, f, _) in zip(svs, fl)]
+        B = S().Batch(svs, grouping=grouping)
+        B.step(states, dts, 2)
+        B.step(states, dts, 1)   # graph replay
+        st = B.stats()
+        assert st["status_name"] == "OK", st
+        g_launches, g_solves = B.grouping()
+        if grouping:
+            # 3 mechanism shapes x reaction steps per time step (2 nodes x nu 2 x 4 sweeps)
+            assert g_launches == 3 * 16 and g_solves == 12 * 16, (g_launches, g_solves)
+        else:
+            assert (g_launches, g_solves) == (0, 0)
+        out.append(states)
+        counts.append((st["newton_solves"], st["newton_iters"], st["newton_jacobians"],
+                       st["newton_certified"], st["surrogate_used"]))
+        launches.append(st["kernel_launches"])
+    for k, (x, y) in enumerate(zip(*out)):
+        assert torch.equal(x, y), k
+    assert counts[0] == counts[1], counts
+    assert launches[0] < launches[1], launches
