@@ -1949,7 +1949,7 @@ misdc_status group_newton(misdc_batch *b, cudaGraph_t g, bool *changed) {
       return fail(MISDC_E_CUDA, "grouped reaction steps: counter reset");
     const size_t smem = x.p.sharedMemBytes;
     const void *fn = newton_group_kernel(x.mixed);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    newton_group_reserve_smem(x.mixed, smem);
     NewtonArgs *jp = b->d_jobs + j0;
     int nj = (int)gr.size();
     int *cp = b->d_counters + q;

@@ -25,6 +25,10 @@ struct Nbr {
   int cm2[3], cm[3], cp[3], cp2[3];
 };
 
+__device__ __forceinline__ unsigned long long dbits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 __device__ __forceinline__ Nbr neighbours(const DevGrid &g, int c) {
@@ -264,12 +268,13 @@ __global__ void k_cheb_plan(const unsigned long long *rho_bits, int kmax, double
 // e_j = 0; r_j and the update in FP64.
 
 // r32 = b - A x (A = I - c_f L_theta) for every solved field: the FP64 residual
-// of the round's iterate x (the right-hand side itself in the first round),
-// rounded to FP32 for the inner solve
+// of the round's iterate x, rounded to FP32 for the inner solve. In the last
+// round (q != NULL) also q = b + c_f L_theta x in FP64: the flux-form
+// reconstruction of x, to which the finish adds that of the round's correction.
 template <int DIM>
 __global__ void k_refine_residual(DevGrid g, FieldMap fm, const double *__restrict__ thf,
                                   const double *__restrict__ rhs, const double *__restrict__ x,
-                                  float *__restrict__ r32) {
+                                  float *__restrict__ r32, double *__restrict__ q) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int cs = g.cells;
   if (c >= cs) return;
@@ -295,7 +300,9 @@ __global__ void k_refine_residual(DevGrid g, FieldMap fm, const double *__restri
       L = fma(thi[d], xf[cp[d]] - xc, L);
       L = fma(-tlo[d], xc - xf[cm[d]], L);
     }
-    r32[off + c] = (float)(rhs[off + c] - fma(-fm.cf[k], L, xc));
+    const double qv = fma(fm.cf[k], L, rhs[off + c]);
+    r32[off + c] = (float)(qv - xc);
+    if (q) q[off + c] = qv;
   }
 }
 
@@ -344,6 +351,112 @@ __global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
     }
     xkp1[off + c] = v;
     if (last && xnext) xnext[off + c] = xbase[off + c] + (double)v;
+  }
+}
+
+// First sweep of the first refinement round, whose iterate is the right-hand
+// side itself: its residual b - A b = c_f L_theta b is formed here in FP32 (from
+// b rounded to FP32; the inner solve's own reduction is 1e-6, and the FP64
+// residual of the next round corrects both), stored for the later sweeps, and
+// the sweep from e_0 = 0 is e_1 = D^{-1} r. A single planned sweep also writes
+// x + e in FP64.
+template <int DIM>
+__global__ void k_cheb32_first(DevGrid g, FieldMap fm, const float *__restrict__ thf,
+                               const float *__restrict__ invdiag, const double *__restrict__ b,
+                               float *__restrict__ r32, float *__restrict__ e1,
+                               const int *__restrict__ kdev, double *__restrict__ xnext) {
+  const bool last = (*kdev == 1);
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cs = g.cells;
+  if (c >= cs) return;
+  const Nbr nb = neighbours(g, c);
+  float tlo[DIM], thi[DIM];
+  int cm[DIM], cp[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    cm[d] = nb.cm[d];
+    cp[d] = nb.cp[d];
+    tlo[d] = thf[(size_t)d * cs + c];
+    thi[d] = thf[(size_t)d * cs + cp[d]];
+  }
+  const int k0 = blockIdx.y * 4, k1 = min(fm.nfs, k0 + 4);
+  for (int k = k0; k < k1; ++k) {
+    const size_t off = (size_t)fm.fld[k] * cs;
+    const double *x = b + off;
+    const double xd = x[c];
+    const float xc = (float)xd;
+    float L = 0.0f;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      L = fmaf(thi[d], (float)x[cp[d]] - xc, L);
+      L = fmaf(-tlo[d], xc - (float)x[cm[d]], L);
+    }
+    const float r = (float)fm.cf[k] * L;
+    r32[off + c] = r;
+    const float v = r * invdiag[(size_t)k * cs + c];
+    e1[off + c] = v;
+    if (last && xnext) xnext[off + c] = xd + (double)v;
+  }
+}
+
+// Finish of the mixed-precision solve: with the last round's iterate x_r, its
+// reconstruction q = b + c_f L x_r (FP64) and the round's correction e (FP32,
+// the buffer of the last planned sweep), the solution x = x_r + e is
+// reconstructed in flux form as v = q + c_f L e (L e in FP32: e is the small
+// correction of an FP32 inner solve), its residual r = v - x checked against
+// |b| + |c_f L x| + |x|, and the dominant species closed by 1 - sum.
+template <int DIM>
+__global__ void k_finish32(DevGrid g, FieldMap fm, int N, int i0, double tol,
+                           const float *__restrict__ thf, const double *__restrict__ rhs,
+                           const double *__restrict__ q, const double *__restrict__ xr,
+                           const float *e0, const float *e1, const float *e2,
+                           const int *__restrict__ kdev, double *__restrict__ out, DevStats *st) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cs = g.cells;
+  const int sl = (*kdev - 1) % 3;
+  const float *e = sl == 0 ? e0 : (sl == 1 ? e1 : e2);
+  float rmax = 0.0f;
+  if (c < cs) {
+    int cm[DIM], cp[DIM];
+    float tlo[DIM], thi[DIM];
+    {
+      const Nbr nb = neighbours(g, c);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        cm[d] = nb.cm[d];
+        cp[d] = nb.cp[d];
+        tlo[d] = thf[(size_t)d * cs + c];
+        thi[d] = thf[(size_t)d * cs + cp[d]];
+      }
+    }
+    double sum = 0.0;
+    for (int k = 0; k < fm.nfs; ++k) {
+      const int f = fm.fld[k];
+      const size_t off = (size_t)f * cs;
+      const float *ef = e + off;
+      const float ec = ef[c];
+      float Le = 0.0f;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        Le = fmaf(thi[d], ef[cp[d]] - ec, Le);
+        Le = fmaf(-tlo[d], ec - ef[cm[d]], Le);
+      }
+      const double v = q[off + c] + (double)((float)fm.cf[k] * Le);
+      const double x = xr[off + c] + (double)ec;
+      const double b = rhs[off + c];
+      const double r = v - x;
+      const double scale = fabs(b) + fabs(v - b) + fabs(x) + 1e-300;
+      rmax = fmaxf(rmax, __double2float_ru(fabs(r)) / fmaxf(__double2float_rd(scale), 1e-30f));
+      out[off + c] = v;
+      if (f < N) sum += v;
+    }
+    out[(size_t)i0 * cs + c] = 1.0 - sum;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  if ((threadIdx.x & 31) == 0 && rmax > 0.0f) {
+    atomicMax(&st->lin_resid_bits, dbits((double)rmax));
+    if (!((double)rmax <= tol)) atomicOr(&st->status_bits, kBitMG);
   }
 }
 
@@ -410,9 +523,6 @@ __global__ void k_cheb(DevGrid g, FieldMap fm, const double *__restrict__ thf,
   }
 }
 
-__device__ __forceinline__ unsigned long long dbits(double v) {
-  return (unsigned long long)__double_as_longlong(v);
-}
 
 // Residual check, flux-form reconstruction x := rhs + c_f L x, and closure of
 // the dominant species. Writes the advection-diffusion state.
@@ -958,27 +1068,46 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
                                                w.rho_bits, w.thf32, w.invdiag32,
                                                refine ? nullptr : w.cdiag);
   if (refine) {
-    // mixed precision: FP64 residuals, FP32 inner Chebyshev solves (reduction 1e-6
-    // each), three rounds, then the same reconstruction and checks as below
+    // mixed precision: FP32 inner Chebyshev solves (reduction 1e-6 each) of the
+    // residual of each round's iterate; the first round's residual (of x_0 = b)
+    // in FP32 inside its first sweep, the later rounds' in FP64
     const int k32 = std::min(sweeps, chebyshev_sweeps(rho_bound, 1e-6));
-    k_cheb_plan<<<1, 32, 0, s>>>(w.rho_bits, k32, 1e-6, w.kdev32, w.omega32, st, w.refine_rounds);
+    const int R = w.refine_rounds;
+    k_cheb_plan<<<1, 32, 0, s>>>(w.rho_bits, k32, 1e-6, w.kdev32, w.omega32, st, R);
     const dim3 gr4((cs + 255) / 256, (fm.nfs + 3) / 4);
-    // round r: r32 = b - A x_r in FP64 (x_0 = b), inner FP32 sweeps for e, and the
-    // last planned sweep writes x_{r+1} = x_r + e (the final round into xc)
+    // round r: the residual of x_r, the inner sweeps for e, and (all but the last
+    // round) x_{r+1} = x_r + e written by the last planned sweep; the last round's
+    // residual pass also stores its reconstruction q in xc, and the finish forms
+    // the solution from x_r, q and e
     const double *xcur = rhs;
     double *xr[2] = {w.xa, w.xb};
-    for (int round = 0; round < w.refine_rounds; ++round) {
-      double *xnext = (round == w.refine_rounds - 1) ? w.xc : xr[round & 1];
-      if (g.dim == 1)
-        k_refine_residual<1><<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xcur, w.r32);
-      else if (g.dim == 2)
-        k_refine_residual<2><<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xcur, w.r32);
-      else
-        k_refine_residual<3><<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xcur, w.r32);
+    for (int round = 0; round < R; ++round) {
+      const bool lastr = round == R - 1;
+      double *xnext = lastr ? nullptr : xr[round & 1];
+      double *q = lastr ? w.xc : nullptr;
+      const bool fused = round == 0 && !lastr;
+      if (!fused) {
+        if (g.dim == 1)
+          k_refine_residual<1><<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xcur, w.r32, q);
+        else if (g.dim == 2)
+          k_refine_residual<2><<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xcur, w.r32, q);
+        else
+          k_refine_residual<3><<<gr4, 256, 0, s>>>(g, fm, w.thf, rhs, xcur, w.r32, q);
+      }
       for (int it = 0; it < k32; ++it) {
         const float *ek = w.e32[(it + 2) % 3];
         const float *ekm1 = (it >= 2) ? w.e32[(it + 1) % 3] : nullptr;   // e_0 = 0
-        if (g.dim == 1)
+        if (fused && it == 0) {
+          if (g.dim == 1)
+            k_cheb32_first<1><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, rhs, w.r32, w.e32[0],
+                                                  w.kdev32, xnext);
+          else if (g.dim == 2)
+            k_cheb32_first<2><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, rhs, w.r32, w.e32[0],
+                                                  w.kdev32, xnext);
+          else
+            k_cheb32_first<3><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, rhs, w.r32, w.e32[0],
+                                                  w.kdev32, xnext);
+        } else if (g.dim == 1)
           k_cheb32<1><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
                                           w.e32[it % 3], it, w.kdev32, w.omega32, xcur, xnext);
         else if (g.dim == 2)
@@ -988,10 +1117,20 @@ void diffusion_solve(const DevMech &m, const DevGrid &g, int i0, double wdt, con
           k_cheb32<3><<<gr4, 256, 0, s>>>(g, fm, w.thf32, w.invdiag32, w.r32, ek, ekm1,
                                           w.e32[it % 3], it, w.kdev32, w.omega32, xcur, xnext);
       }
-      xcur = xnext;
+      if (!lastr) xcur = xnext;
     }
-    // reconstruction and residual check of the final iterate
-    launch_finish(g, fm, m.N, i0, lin_rtol * 100.0, w.thf, rhs, w.xc, w.xc, w.xc, nullptr, out, st, s);
+    // solution, reconstruction and residual check from x_r, q and the last e
+    const int blocks = (cs + 255) / 256;
+    const double tol = lin_rtol * 100.0;
+    if (g.dim == 1)
+      k_finish32<1><<<blocks, 256, 0, s>>>(g, fm, m.N, i0, tol, w.thf32, rhs, w.xc, xcur, w.e32[0],
+                                           w.e32[1], w.e32[2], w.kdev32, out, st);
+    else if (g.dim == 2)
+      k_finish32<2><<<blocks, 256, 0, s>>>(g, fm, m.N, i0, tol, w.thf32, rhs, w.xc, xcur, w.e32[0],
+                                           w.e32[1], w.e32[2], w.kdev32, out, st);
+    else
+      k_finish32<3><<<blocks, 256, 0, s>>>(g, fm, m.N, i0, tol, w.thf32, rhs, w.xc, xcur, w.e32[0],
+                                           w.e32[1], w.e32[2], w.kdev32, out, st);
     return;
   }
   if (w.levels > 1) {

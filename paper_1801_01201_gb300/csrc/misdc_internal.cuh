@@ -202,6 +202,8 @@ bool launch_certify(const DevMech &m, int n, int cs, double wdt, double rtol, co
 bool newton_kernel_args(const void *func, void **params, NewtonArgs *out, bool *mixed);
 const void *newton_group_kernel(bool mixed);
 int newton_group_grid(bool mixed, int wpb, size_t smem, int items);
+// raise the grouped kernel's dynamic shared-memory limit to at least smem (never lowers it)
+void newton_group_reserve_smem(bool mixed, size_t smem);
 
 // ---- grid kernels (misdc_grid.cu) ----
 struct LinComb {
