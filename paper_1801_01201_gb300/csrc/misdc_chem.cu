@@ -725,10 +725,14 @@ __device__ __forceinline__ void newton_items(const NewtonArgs &A, double *wsm, i
     double T = w.xs[N];
     double dprev = dprev0;
     int it, code = 0;
-    for (int attempt = 0; attempt < ((MIXED || guessed) ? 2 : 1); ++attempt) {
-    if (attempt == 1) {
-      // the mixed iteration (or a solve from a learned guess) failed: plain FP64
-      // Newton from the plain guess
+    // attempts: the solve itself; after a failure in mixed precision, plain FP64
+    // Newton from x_p; and, before that, after a failed solve from an accepted
+    // learned guess, the iteration the plain guess alone would have run (mixed:
+    // from x_p with a fresh factor), so that a guess never leaves a cell worse
+    // off than no guess
+    int attempts = MIXED ? 2 : 1;
+    for (int attempt = 0; attempt < attempts; ++attempt) {
+    if (attempt >= 1) {
       if (code == 0) break;
       for (int i = lane; i < nn; i += 32) w.xs[i] = w.xg[i];
       __syncwarp();
@@ -737,8 +741,11 @@ __device__ __forceinline__ void newton_items(const NewtonArgs &A, double *wsm, i
       dprev = INFINITY;
       it0 = 1;
       have = fresh = from_store = fresh_exact = false;
-      exact = no32 = true;
-      ++my_fb;
+      vet = false;
+      if (!(MIXED && attempt == 1 && attempts == 3)) {
+        exact = no32 = true;
+        ++my_fb;
+      }
     }
     for (it = it0; it <= maxit; ++it) {
       const bool jac = !MIXED || !have || exact;   // this iteration assembles the Jacobian
@@ -864,13 +871,16 @@ __device__ __forceinline__ void newton_items(const NewtonArgs &A, double *wsm, i
         __syncwarp();
       }
       }   // jac
-      if (!MIXED && vet) {
+      if (vet) {
         // Accept the learned guess only if the residual drops, measured in the
         // Jacobi-scaled max-norm max_i |r_i / J_ii| (species rows; the temperature
         // row as the relative temperature change) with the Jacobian at the guess
         // (a diagonal stand-in for the natural norm |J^{-1} r| of Newton's method,
-        // which a plain residual norm would overweight along stiff directions).
-        // The residual at x_p comes from the stored reaction term of x_p.
+        // which a plain residual norm would overweight along stiff directions;
+        // MIXED: the row scales of its factor). The residual at x_p comes from the
+        // stored reaction term of x_p. (A comparison of the two steps through the
+        // factor at hand is no test when that factor was just built at a poor
+        // guess: it accepted guesses that led to other roots.)
         vet = false;
         double rm = 0.0, rp = 0.0;
         for (int i = lane; i < nn; i += 32) {
@@ -904,6 +914,7 @@ __device__ __forceinline__ void newton_items(const NewtonArgs &A, double *wsm, i
         }
         ++my_sg;
         guessed = true;
+        attempts = MIXED ? 3 : 2;
       }
       bool singular = false, fallback = false;
       if (MIXED) {
@@ -1089,42 +1100,6 @@ __device__ __forceinline__ void newton_items(const NewtonArgs &A, double *wsm, i
           if (cst.sT) cst.sT[cell] = sT;
         }
       }
-      if (MIXED && vet && !singular) {
-        // Mixed precision tests the learned guess x0 in Newton's natural norm: the
-        // step J^{-1} r(x0) just computed against J^{-1} r(x_p) through the same
-        // factor, r(x_p) from the stored reaction term of x_p. A rejected guess
-        // continues from x_p with that second step (no rate evaluation is lost).
-        vet = false;
-        for (int i = lane; i < nn; i += 32)
-          w.r64[i] = (i < N) ? w.bs[i] - w.xg[i] + wdt * FRp[(size_t)i * cs + cell]
-                             : (hst - hp[cell]) * sTf;
-        __syncwarp();
-        apply_kept(J, ld, nn, lane, w.r64, w.zd);
-        double d0 = 0.0, dp = 0.0;
-        for (int i = lane; i < nn; i += 32) {
-          const double s0i = (i < N) ? 1.0 : 1.0 / w.xs[N];
-          const double spi = (i < N) ? 1.0 : 1.0 / w.xg[N];
-          d0 = fmax(d0, fabs(w.dx[i]) * s0i);
-          dp = fmax(dp, fabs(w.zd[i]) * spi);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          d0 = fmax(d0, __shfl_xor_sync(0xffffffffu, d0, o));
-          dp = fmax(dp, __shfl_xor_sync(0xffffffffu, dp, o));
-        }
-        if (d0 < dp) {
-          ++my_sg;
-          guessed = true;
-        } else {
-          for (int i = lane; i < nn; i += 32) {
-            w.xs[i] = w.xg[i];
-            w.dx[i] = w.zd[i];
-          }
-          __syncwarp();
-          T = w.xs[N];
-          ++my_rej;
-        }
-      }
       // ---- update and convergence on d = max(max|dY|, |dT|/T)
       if (MIXED && exact) {
         // the restart of a failed mixed solve limits its steps to |dT| <= T/2 and
@@ -1204,14 +1179,28 @@ __device__ __forceinline__ void newton_items(const NewtonArgs &A, double *wsm, i
     }
     if (code == 0 && it > maxit) code = -1;
     if (attempt == 0 && guessed && code == 0) {
-      double far = 0.0;
-      for (int i = lane; i < nn; i += 32)
+      // the root reached from a learned guess must be the one the plain guess
+      // leads to: near x_p (within 100 times the residual scale s there), and
+      // without a mass fraction below the smallest of x_p (or 0) by more than
+      // 1e-9 (a backward step of mass-action chemistry has one non-negative root)
+      double far = 0.0, ymin = INFINITY, ypmin = 0.0;
+      for (int i = lane; i < nn; i += 32) {
         far = fmax(far, (i < N) ? fabs(w.xs[i] - w.xg[i]) : fabs(w.xs[i] - w.xg[i]) / w.xg[i]);
+        if (i < N) {
+          ymin = fmin(ymin, w.xs[i]);
+          ypmin = fmin(ypmin, w.xg[i]);
+        }
+      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) far = fmax(far, __shfl_xor_sync(0xffffffffu, far, o));
-      if (!(far <= 100.0 * s0 + 1e-10)) code = -4;   // another root: solve again from x_p
+      for (int o = 16; o > 0; o >>= 1) {
+        far = fmax(far, __shfl_xor_sync(0xffffffffu, far, o));
+        ymin = fmin(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+        ypmin = fmin(ypmin, __shfl_xor_sync(0xffffffffu, ypmin, o));
+      }
+      if (!(far <= 100.0 * s0 + 1e-10) || !(ymin >= ypmin - 1e-9))
+        code = -4;   // another root: solve again from x_p
     }
-    if (!MIXED && attempt == 0 && guessed && code) {
+    if (attempt == 0 && guessed && code) {
       ++my_rej;   // counted as a rejected guess
       --my_sg;
     }
@@ -1376,21 +1365,26 @@ static size_t rates_mma_smem(const DevMech &m) {
 }
 
 // The shared-memory limit is an attribute of the kernel, not of a launch: every
-// solver in the process shares it, so it only ever grows to the largest need.
+// solver and every grouped launch in the process shares it, so it only ever grows
+// to the largest need (a grouped launch already in a graph keeps its room).
+static std::mutex g_smem_mu;
+static size_t g_smem_have[6] = {0, 0, 0, 0, 0, 0};
+
+static void reserve_smem(int k, const void *fn, size_t need) {
+  if (need > g_smem_have[k]) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    g_smem_have[k] = need;
+  }
+}
+
 void prepare_chem_kernels(const DevMech &m) {
-  static std::mutex mu;
-  static size_t have[4] = {0, 0, 0, 0};
-  std::lock_guard<std::mutex> lock(mu);
+  std::lock_guard<std::mutex> lock(g_smem_mu);
   int ld, wpb;
   const size_t need[4] = {newton_smem(m, false, ld, wpb), newton_smem(m, true, ld, wpb),
                           (size_t)4 * (5 * m.N + 4 * m.R) * sizeof(double), rates_mma_smem(m)};
   const void *fn[4] = {(const void *)k_newton2<false>, (const void *)k_newton2<true>,
                        (const void *)k_rates, (const void *)k_rates_mma};
-  for (int k = 0; k < 4; ++k)
-    if (need[k] > have[k]) {
-      cudaFuncSetAttribute(fn[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need[k]);
-      have[k] = need[k];
-    }
+  for (int k = 0; k < 4; ++k) reserve_smem(k, fn[k], need[k]);
 }
 
 void launch_temperature(const DevMech &m, int n, int cs, const double *Y, const double *h,
@@ -1500,6 +1494,11 @@ bool newton_kernel_args(const void *func, void **params, NewtonArgs *out, bool *
 
 const void *newton_group_kernel(bool mixed) {
   return mixed ? (const void *)k_newton2_group<true> : (const void *)k_newton2_group<false>;
+}
+
+void newton_group_reserve_smem(bool mixed, size_t smem) {
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  reserve_smem(mixed ? 5 : 4, newton_group_kernel(mixed), smem);
 }
 
 int newton_group_grid(bool mixed, int wpb, size_t smem, int items) {
