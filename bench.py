@@ -989,6 +989,7 @@ def main():
         d["newton_jacobians_per_solve"] = s_["newton_jacobians"] / ns
         d["newton_certified_per_solve"] = s_["newton_certified"] / ns
         d["newton_stored_steps_per_solve"] = s_["newton_stored_steps"] / ns
+        d["newton_chord_cells_per_solve"] = s_.get("newton_chord_cells", 0) / ns
         if k == "learned_mixed":
             d["surrogate_used"] = s_["surrogate_used"]
             d["surrogate_rejected"] = s_["surrogate_rejected"]

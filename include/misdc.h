@@ -154,6 +154,9 @@ typedef struct misdc_stats {
   long long newton_floor_stops;  /* exact (FP64) Newton solves that stopped on the
                                     round-off-floor test: step d <= 1e-8 that no longer
                                     halves, while still above newton_rtol */
+  long long newton_chord_cells;  /* mixed precision: uncertified solves finished by the
+                                    thread-per-cell chord pass (stored first step, then
+                                    chord iterations through the kept inverse) */
 } misdc_stats;
 
 typedef struct misdc_solver misdc_solver;
@@ -427,6 +430,12 @@ typedef struct misdc_tuning {
   int newton_keep_factors;      /* mixed precision: 1 (default) keeps each cell's FP32
                                    Jacobian factor between the solves of an SDC node,
                                    0 rebuilds it in every solve */
+  int newton_chord_iters;       /* mixed precision with kept factors: chord iterations a
+                                   cell may take in the thread-per-cell pass after
+                                   certification before it goes to the warp-per-cell
+                                   Newton (0: certification only); default 4. Unlike the
+                                   other fields this changes which kernel solves a cell,
+                                   so results move within the solver tolerance */
   double newton_ms;             /* autotune: best time of the probe reaction solve */
   double cheb_ms;               /* autotune: best time of the probe diffusion solve */
 } misdc_tuning;

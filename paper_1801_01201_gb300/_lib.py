@@ -49,7 +49,8 @@ class Stats(C.Structure):
                 ("surrogate_rejected", C.c_longlong), ("newton_fp64_fallbacks", C.c_longlong),
                 ("newton_jacobians", C.c_longlong), ("newton_lu_fp64", C.c_longlong),
                 ("newton_certified", C.c_longlong), ("nested_iterations", C.c_longlong),
-                ("newton_stored_steps", C.c_longlong), ("newton_floor_stops", C.c_longlong)]
+                ("newton_stored_steps", C.c_longlong), ("newton_floor_stops", C.c_longlong),
+                ("newton_chord_cells", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,7 +66,8 @@ class LowMachDesc(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("newton_warps_per_block", C.c_int), ("newton_blocks_per_sm", C.c_int),
                 ("newton_dynamic", C.c_int), ("cheb_block", C.c_int),
-                ("newton_keep_factors", C.c_int), ("newton_ms", C.c_double),
+                ("newton_keep_factors", C.c_int), ("newton_chord_iters", C.c_int),
+                ("newton_ms", C.c_double),
                 ("cheb_ms", C.c_double)]
 
     def as_dict(self):

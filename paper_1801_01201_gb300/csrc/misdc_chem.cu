@@ -517,6 +517,199 @@ __global__ void __launch_bounds__(256) k_certify(DevMech m, int n, int cs, doubl
   }
 }
 
+// Chord iterations, one thread per cell, over the cells certification left
+// (in_list; mixed precision with kept factors), persistent blocks taking rounds of
+// them. A cell with a usable FP64-built factor whose step through the kept
+// inverse is at most 1e-4 (certification found it above 0.09 rtol) takes that step (iteration 1, from
+// the stored reaction term, as the warp kernel's stored first step) and then up to
+// max_chord chord iterations: the FP64 residual r = b - Y + (wdt/rho) W nu^T q at
+// the iterate (every rate of progress evaluated by the cell's own thread) and the
+// step Z r through the kept FP64 inverse, as in the warp kernel (the FP32 copy that
+// certification uses is too coarse a chord inverse for stiff cells: its rounding
+// misled the stopping test by up to 1e-5 on the 9-species flames). It stops like
+// the warp kernel's
+// chord iteration: with th = d/d_prev < 0.1 and d th / (1 - th) <= rtol. A step
+// above 1e-4, a contraction of less than 10 or a non-finite value hands the cell,
+// from its original guess, to the warp-per-cell Newton kernel through `list`, as do
+// the cells certification cannot take (no usable FP64-built factor, a learned guess
+// to vet). Per-thread arrays live in shared memory as [element][thread].
+__global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double wdt, double rtol,
+                                              int maxit, int max_chord,
+                                              const double *__restrict__ b,
+                                              const double *__restrict__ hstar,
+                                              const double *__restrict__ Yg,
+                                              const double *__restrict__ Tg,
+                                              double *__restrict__ Yout, double *__restrict__ Tout,
+                                              double *__restrict__ FR, double *__restrict__ hsp,
+                                              double *__restrict__ theta, int *__restrict__ iters,
+                                              DevStats *st, const double *__restrict__ sc,
+                                              double s_min, const int *__restrict__ prow,
+                                              const double *__restrict__ FRp,
+                                              const double *__restrict__ hp, ChordStore cst,
+                                              const double *__restrict__ hspp,
+                                              const double *__restrict__ thp,
+                                              const int *__restrict__ in_list,
+                                              const int *__restrict__ in_n,
+                                              int *__restrict__ list, int *__restrict__ list_n) {
+  extern __shared__ double chord_sm[];
+  const int B = blockDim.x, tid = threadIdx.x;
+  const int N = m.N, nn = N + 1, R = m.R;
+  const int total = *in_n;
+  double *xs = chord_sm;                         // [nn][B] iterate
+  double *cc = xs + (size_t)nn * B;              // [N][B]  concentrations
+  double *gg = cc + (size_t)N * B;               // [N][B]  g/RT
+  double *wd = gg + (size_t)N * B;               // [N][B]  sum_r nu_ri q_r
+  double *rr = wd + (size_t)N * B;              // [nn][B] residual
+  double *dx = rr + (size_t)nn * B;              // [nn][B] step
+#define TH(a, k) a[(size_t)(k) * B + tid]
+  // rounds of B items per block (uniform per block, so the statistics below see
+  // every lane of a warp)
+  for (int base = blockIdx.x * B; base < total; base += gridDim.x * B) {
+  const int item = base + tid;
+  const int c = item < total ? in_list[item] : -1;
+  bool conv = false;
+  int it = 0;
+  if (c >= 0) {
+    const int v = cst.valid[c];
+    bool ok = (v & 1) != 0 && (v & 4) == 0;   // a kept factor, built in FP64
+    if (ok && sc) {   // a learned guess goes to the Newton kernel, which vets it
+      const int prw = prow ? prow[c] : c;
+      const double s0 = sc[c];
+      ok = !(prw >= 0 && s0 > s_min && isfinite(s0));
+    }
+    const double T0 = Tg[c];
+    if (ok) {   // the factor was built near x_p (without dividing by T)
+      for (int i = 0; i < N && ok; ++i) ok = fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]) <= 1e-4;
+      ok = ok && fabs(T0 - cst.xc[(size_t)N * cs + c]) <= 1e-4 * T0;
+    }
+    const double sT = ok ? cst.sT[c] : 0.0;
+    const double hst = hstar[c];
+    // the step Z r through the kept FP64 inverse (row-major, the cell's own block
+    // of the factor store); d = max(max|dY|, |dT|/T)
+    const double *Zc = cst.f + (size_t)c * cst.fs;
+    auto step = [&](double T, double &d, bool &fin) {
+      double dm = 0.0, dT = 0.0;
+      fin = true;
+      for (int i = 0; i < nn; ++i) {
+        const double *Zi = Zc + (size_t)i * nn;
+        double z = 0.0;
+        for (int j = 0; j < nn; ++j) z = fma(Zi[j], TH(rr, j), z);
+        TH(dx, i) = z;
+        fin = fin && isfinite(z);
+        if (i < N) dm = fmax(dm, fabs(z));
+        else dT = fabs(z);
+      }
+      d = fmax(dm, dT / T);
+    };
+    if (ok) {
+      for (int i = 0; i < N; ++i) {
+        const double y = Yg[(size_t)i * cs + c];
+        TH(xs, i) = y;
+        TH(rr, i) = b[(size_t)i * cs + c] - y + wdt * FRp[(size_t)i * cs + c];
+      }
+      TH(xs, N) = T0;
+      TH(rr, N) = (hst - hp[c]) * sT;
+      double d0;
+      bool fin;
+      step(T0, d0, fin);
+      if (fin && max_chord > 0 && maxit >= 2 && d0 <= 1e-4) {
+        // iteration 1: the step from the stored reaction term
+        for (int i = 0; i < nn; ++i) TH(xs, i) += TH(dx, i);
+        double dprev = d0;
+        it = 1;
+        const double wr = wdt / m.rho;
+        while (it < maxit && it <= max_chord) {
+          ++it;
+          const double T = TH(xs, N);
+          if (!(T > 0.0)) break;
+          const double lnT = log(T), invT = 1.0 / T;
+          double sh = 0.0;
+          for (int i = 0; i < N; ++i) {
+            double hRT, gRT;
+            species_hg(m, i, T, lnT, invT, hRT, gRT);
+            const double y = TH(xs, i);
+            TH(cc, i) = m.rho * y * m.invW[i];
+            TH(gg, i) = gRT;
+            TH(wd, i) = 0.0;
+            sh = fma(y, kRu * m.invW[i] * T * hRT, sh);
+          }
+          for (int r = 0; r < R; ++r) {
+            const signed char *fs = m.fwd + kMaxSlots * r, *rs = m.rev + kMaxSlots * r;
+            double dg = 0.0, Ff = 1.0, Fr = 1.0;
+#pragma unroll
+            for (int q = 0; q < kMaxSlots; ++q) {
+              const int sf = fs[q], sr = rs[q];
+              if (sf >= 0) { dg -= TH(gg, sf); Ff *= TH(cc, sf); }
+              if (sr >= 0) { dg += TH(gg, sr); Fr *= TH(cc, sr); }
+            }
+            const double lnkf = m.lnA[r] + m.beta[r] * lnT - m.TA[r] * invT;
+            const double lnKc = -dg + m.dn[r] * (m.ln_p_over_R - lnT);
+            const double qr = exp_tab(lnkf) * Ff - exp_tab(lnkf - lnKc) * Fr;
+#pragma unroll
+            for (int q = 0; q < kMaxSlots; ++q) {
+              const int sf = fs[q], sr = rs[q];
+              if (sf >= 0) TH(wd, sf) -= qr;
+              if (sr >= 0) TH(wd, sr) += qr;
+            }
+          }
+          for (int i = 0; i < N; ++i)
+            TH(rr, i) = fma(wr, m.W[i] * TH(wd, i), b[(size_t)i * cs + c] - TH(xs, i));
+          TH(rr, N) = -(sh - hst) * sT;
+          double d;
+          step(T, d, fin);
+          if (!fin) break;
+          for (int i = 0; i < nn; ++i) TH(xs, i) += TH(dx, i);
+          if (d > 1e-4 || !(d < 0.1 * dprev)) break;   // not contracting: a new factor is due
+          if (d * d <= rtol * (dprev - d)) { conv = true; break; }
+          dprev = d;
+        }
+      }
+    }
+    if (conv) {
+      // species enthalpies and theta at the solution; reaction term (Y - b)/wdt
+      const double invw = (wdt > 0.0) ? 1.0 / wdt : 0.0;
+      const double T = TH(xs, N), lnT = log(T), invT = 1.0 / T;
+      for (int i = 0; i < N; ++i) {
+        double hRT, gRT;
+        species_hg(m, i, T, lnT, invT, hRT, gRT);
+        const double y = TH(xs, i);
+        Yout[(size_t)i * cs + c] = y;
+        if (FR) FR[(size_t)i * cs + c] = (y - b[(size_t)i * cs + c]) * invw;
+        if (hsp) hsp[(size_t)i * cs + c] = kRu * m.invW[i] * T * hRT;
+      }
+      Tout[c] = T;
+      if (theta) theta[c] = exp_tab(m.theta_exp * (lnT - m.ln_Tref));
+      if (iters) iters[c] = it;
+    } else {
+      list[atomicAdd(list_n, 1)] = c;
+    }
+  }
+  // statistics: one atomic per warp and counter
+  const unsigned vb = __ballot_sync(0xffffffffu, conv);
+  int itv = conv ? it : 0;
+  unsigned mx = conv ? (unsigned)it : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    itv += __shfl_xor_sync(0xffffffffu, itv, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0 && vb) {
+    const unsigned long long kv = __popc(vb);
+    atomicAdd(&st->newton_solves, kv);
+    atomicAdd(&st->newton_iters, (unsigned long long)itv);
+    atomicAdd(&st->stored_steps, kv);
+    atomicAdd(&st->chord_cells, kv);
+    atomicMax(&st->newton_max, (int)mx);
+  }
+  }   // rounds
+#undef TH
+}
+
+size_t chord_smem_bytes(int N, int threads) {
+  const size_t nn = N + 1;
+  return (size_t)threads * (3 * nn + 3 * (size_t)N) * sizeof(double);
+}
+
 // The reaction Newton of a run of work items of one solve (one warp per cell);
 // `first` is the warp's first item, next(item) its next one (>= items ends the
 // run). wsm: the warp's shared-memory scratch. Per-warp counters go to A.st at the
@@ -1368,7 +1561,7 @@ static size_t rates_mma_smem(const DevMech &m) {
 // solver and every grouped launch in the process shares it, so it only ever grows
 // to the largest need (a grouped launch already in a graph keeps its room).
 static std::mutex g_smem_mu;
-static size_t g_smem_have[6] = {0, 0, 0, 0, 0, 0};
+static size_t g_smem_have[7] = {0, 0, 0, 0, 0, 0, 0};
 
 static void reserve_smem(int k, const void *fn, size_t need) {
   if (need > g_smem_have[k]) {
@@ -1385,6 +1578,8 @@ void prepare_chem_kernels(const DevMech &m) {
   const void *fn[4] = {(const void *)k_newton2<false>, (const void *)k_newton2<true>,
                        (const void *)k_rates, (const void *)k_rates_mma};
   for (int k = 0; k < 4; ++k) reserve_smem(k, fn[k], need[k]);
+  const size_t chord = chord_smem_bytes(m.N, 64);
+  if (chord <= 200 * 1024) reserve_smem(6, (const void *)k_chord, chord);
 }
 
 void launch_temperature(const DevMech &m, int n, int cs, const double *Y, const double *h,
@@ -1416,6 +1611,36 @@ void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double
   k_rates<<<grid, wpb * 32, sm, s>>>(m, n, cs, Y, T, FR);
 }
 
+// Certification (k_certify, thread per cell, into `list`) and, where enabled and its
+// shared-memory arrays fit, the thread-per-cell chord pass over the cells it left
+// (k_chord, persistent, into `list2`). Returns the list the warp-per-cell Newton
+// is to take.
+static void launch_chord_pass(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit,
+                              const NewtonLaunch &cfg, const double *b, const double *hstar,
+                              const double *Yg, const double *Tg, double *Y, double *T, double *FR,
+                              double *hsp, double *theta, int *iters, DevStats *st, const double *sc,
+                              double s_min, const int *prow, const double *FRp, const double *hp,
+                              const ChordStore &cst, const double *hspp, const double *thp,
+                              int **out_list, int **out_n, cudaStream_t s) {
+  cudaMemsetAsync(cfg.list_n, 0, sizeof(int), s);
+  k_certify<<<(n + 255) / 256, 256, 0, s>>>(m, n, cs, wdt, rtol, b, hstar, Yg, Tg, Y, T, FR, hsp, theta,
+                                            iters, st, sc, s_min, prow, FRp, hp, cst, hspp, thp, cfg.list,
+                                            cfg.list_n);
+  *out_list = cfg.list;
+  *out_n = cfg.list_n;
+  const size_t smem = chord_smem_bytes(m.N, 64);
+  if (cfg.chord_iters <= 0 || !cfg.list2 || !cfg.list2_n || smem > g_smem_have[6]) return;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_chord, 64, smem);
+  const int grid = std::max(1, std::min((n + 63) / 64, sm_count() * std::max(per_sm, 1)));
+  cudaMemsetAsync(cfg.list2_n, 0, sizeof(int), s);
+  k_chord<<<grid, 64, smem, s>>>(m, n, cs, wdt, rtol, maxit, cfg.chord_iters, b, hstar, Yg, Tg, Y, T, FR,
+                                 hsp, theta, iters, st, sc, s_min, prow, FRp, hp, cst, hspp, thp, cfg.list,
+                                 cfg.list_n, cfg.list2, cfg.list2_n);
+  *out_list = cfg.list2;
+  *out_n = cfg.list2_n;
+}
+
 void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit,
                    const double *b, const double *hstar, const double *Yg, const double *Tg,
                    double *Y, double *T, double *FR, double *hsp, double *theta, int *iters,
@@ -1441,10 +1666,11 @@ void launch_newton(const DevMech &m, int n, int cs, double wdt, double rtol, int
                      thp && cfg && cfg->list && cfg->list_n;
   const int *list = split ? cfg->list : nullptr, *list_n = split ? cfg->list_n : nullptr;
   if (split && !cfg->precertified) {
-    cudaMemsetAsync(cfg->list_n, 0, sizeof(int), s);
-    k_certify<<<(n + 255) / 256, 256, 0, s>>>(m, n, cs, wdt, rtol, b, hstar, Yg, Tg, Y, T, FR, hsp,
-                                              theta, iters, st, pred ? sc : nullptr, s_min, prow, FRp,
-                                              hp, cst, hspp, thp, cfg->list, cfg->list_n);
+    int *l = nullptr, *ln = nullptr;
+    launch_chord_pass(m, n, cs, wdt, rtol, maxit, *cfg, b, hstar, Yg, Tg, Y, T, FR, hsp, theta, iters, st,
+                      pred ? sc : nullptr, s_min, prow, FRp, hp, cst, hspp, thp, &l, &ln, s);
+    list = l;
+    list_n = ln;
   }
   NewtonArgs A;
   A.m = m;
@@ -1511,20 +1737,21 @@ int newton_group_grid(bool mixed, int wpb, size_t smem, int items) {
 }
 
 
-bool launch_certify(const DevMech &m, int n, int cs, double wdt, double rtol, const double *b,
+bool launch_certify(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit, const double *b,
                     const double *hstar, const double *Yg, const double *Tg, double *Y, double *T,
                     double *FR, double *hsp, double *theta, int *iters, DevStats *st,
                     const double *FRp, const double *hp, const ChordStore *store,
-                    const double *hspp, const double *thp, const NewtonLaunch *cfg, cudaStream_t s) {
+                    const double *hspp, const double *thp, NewtonLaunch *cfg, cudaStream_t s) {
   if (n <= 0 || !store) return false;
   const ChordStore &cst = *store;
   if (!(cst.f && cst.valid && cst.z32 && cst.xc && cst.sT && FRp && hspp && hp && thp && cfg &&
         cfg->list && cfg->list_n))
     return false;
-  cudaMemsetAsync(cfg->list_n, 0, sizeof(int), s);
-  k_certify<<<(n + 255) / 256, 256, 0, s>>>(m, n, cs, wdt, rtol, b, hstar, Yg, Tg, Y, T, FR, hsp, theta,
-                                            iters, st, nullptr, 0.0, nullptr, FRp, hp, cst, hspp, thp,
-                                            cfg->list, cfg->list_n);
+  int *l = nullptr, *ln = nullptr;
+  launch_chord_pass(m, n, cs, wdt, rtol, maxit, *cfg, b, hstar, Yg, Tg, Y, T, FR, hsp, theta, iters, st,
+                    nullptr, 0.0, nullptr, FRp, hp, cst, hspp, thp, &l, &ln, s);
+  cfg->list = l;      // the cells left for the learned guess and the warp-per-cell Newton
+  cfg->list_n = ln;
   return true;
 }
 

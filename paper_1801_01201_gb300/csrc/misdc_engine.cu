@@ -392,7 +392,7 @@ void r_stage(misdc_solver *s, int t, double wdt, const NodeBuf &guess, NodeBuf &
     // guess is computed only for the cells it leaves (a certified guess is
     // converged and needs none)
     const bool pre = s->o.precision == MISDC_PREC_MIXED && s->keep_factors &&
-                     launch_certify(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, lane_bR(s, p),
+                     launch_certify(s->m, s->cs, s->cs, wdt, s->o.newton_rtol, s->o.newton_maxit, lane_bR(s, p),
                                     ad.phi + N * cs, guess.phi, guess.T, out.phi, out.T, out.FR,
                                     out.hsp, out.theta, lane_iters(s, p), s->st, guess.FR,
                                     guess.phi + N * cs, &s->cst[t], guess.hsp, guess.theta, &nlc, st);
@@ -861,11 +861,11 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     if (e != cudaSuccess) return e;
     return cudaMemcpy((void *)*dst, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice);
   };
-  std::vector<double> D0v(md->D0, md->D0 + N);
-  double *p_invW, *p_hc, *p_sc, *p_cpc, *p_D0, *p_lnA, *p_beta, *p_TA, *p_dn, *p_spc, *p_jcw, *p_mb;
+  std::vector<double> D0v(md->D0, md->D0 + N), Wv(md->W, md->W + N);
+  double *p_W, *p_invW, *p_hc, *p_sc, *p_cpc, *p_D0, *p_lnA, *p_beta, *p_TA, *p_dn, *p_spc, *p_jcw, *p_mb;
   signed char *p_fwd, *p_rev;
   int *p_spp, *p_spr, *p_jcp, *p_jcs, *p_mp, *p_mk;
-  if (up(invW, &p_invW) || up(hc, &p_hc) || up(sc, &p_sc) || up(cpc, &p_cpc) || up(D0v, &p_D0) ||
+  if (up(Wv, &p_W) || up(invW, &p_invW) || up(hc, &p_hc) || up(sc, &p_sc) || up(cpc, &p_cpc) || up(D0v, &p_D0) ||
       up(lnA, &p_lnA) || up(beta, &p_beta) || up(TA, &p_TA) || up(dn, &p_dn) || up(fwd, &p_fwd) ||
       up(rev, &p_rev) || up(sp_ptr, &p_spp) || up(sp_rx, &p_spr) || up(sp_coef, &p_spc) ||
       up(jc_pack, &p_jcp) || up(jc_w, &p_jcw) || up(jc_seg, &p_jcs) || up(mma_b, &p_mb) ||
@@ -874,7 +874,7 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   DevMech &m = s->m;
   m.N = N; m.R = R; m.rho = op->rho; m.T_ref = md->T_ref; m.theta_exp = md->theta_exp;
   m.alpha0 = md->alpha0; m.ln_p_over_R = log(md->p_ref / kRu); m.ln_Tref = log(md->T_ref);
-  m.invW = p_invW; m.hcoef = p_hc; m.scoef = p_sc; m.cpcoef = p_cpc; m.D0 = p_D0;
+  m.W = p_W; m.invW = p_invW; m.hcoef = p_hc; m.scoef = p_sc; m.cpcoef = p_cpc; m.D0 = p_D0;
   m.lnA = p_lnA; m.beta = p_beta; m.TA = p_TA; m.dn = p_dn; m.fwd = p_fwd; m.rev = p_rev;
   m.sp_ptr = p_spp; m.sp_rx = p_spr; m.sp_coef = p_spc;
   m.D0_host = s->D0h.data();
@@ -903,6 +903,7 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
   if (s->alloc(&s->rhsD, F * cs) || s->alloc(&s->bR, F * cs) || s->alloc(&s->thfD, thf_n) ||
       s->alloc(&s->thfR, thf_n) || s->alloc(&s->iters, cs) || s->alloc(&s->st, 1) ||
       s->alloc(&s->nl.work, 1) || s->alloc(&s->nl.list, cs) || s->alloc(&s->nl.list_n, 1) ||
+      s->alloc(&s->nl.list2, cs) || s->alloc(&s->nl.list2_n, 1) ||
       s->alloc(&s->dw.thf, 3 * cs) || s->alloc(&s->dw.invdiag, F * cs) || s->alloc(&s->dw.xa, F * cs) ||
       s->alloc(&s->dw.cdiag, F * cs) || s->alloc(&s->dw.bdiag, F * cs) ||
       s->alloc(&s->dw.xb, F * cs) || s->alloc(&s->dw.xc, F * cs) ||
@@ -979,7 +980,8 @@ misdc_status misdc_create(const misdc_mech_desc *md, const misdc_grid_desc *gd,
     const size_t thf_n = 3 * cs + operator_face_doubles(s->g, s->N);
     if (s->alloc(&L.rhsD, F * cs) || s->alloc(&L.bR, F * cs) || s->alloc(&L.thfD, thf_n) ||
         s->alloc(&L.thfR, thf_n) || s->alloc(&L.iters, cs) || s->alloc(&L.nl.work, 1) ||
-        s->alloc(&L.nl.list, cs) || s->alloc(&L.nl.list_n, 1) || s->alloc(&w.thf, 3 * cs) ||
+        s->alloc(&L.nl.list, cs) || s->alloc(&L.nl.list_n, 1) ||
+        s->alloc(&L.nl.list2, cs) || s->alloc(&L.nl.list2_n, 1) || s->alloc(&w.thf, 3 * cs) ||
         s->alloc(&w.invdiag, F * cs) || s->alloc(&w.cdiag, F * cs) || s->alloc(&w.bdiag, F * cs) ||
         s->alloc(&w.xa, F * cs) || s->alloc(&w.xb, F * cs) || s->alloc(&w.xc, F * cs) ||
         s->alloc(&w.rho_bits, 1) || s->alloc(&w.kdev, 1) || s->alloc(&w.omega, kMaxCheb))
@@ -1146,6 +1148,7 @@ misdc_status misdc_get_stats(misdc_solver *s, misdc_stats *out, int reset) {
   out->newton_certified = (long long)d.certified;
   out->newton_stored_steps = (long long)d.stored_steps;
   out->newton_floor_stops = (long long)d.floor_stops;
+  out->newton_chord_cells = (long long)d.chord_cells;
   int st = MISDC_OK;
   if (d.status_bits & kBitTdiag) st = MISDC_E_TDIAG;
   else if (d.status_bits & (kBitNan | kBitSingular)) st = MISDC_E_NAN;
@@ -1988,13 +1991,15 @@ misdc_status misdc_get_tuning(misdc_solver *s, misdc_tuning *t) {
   t->newton_dynamic = s->nl.dynamic;
   t->cheb_block = s->dw.cheb_block;
   t->newton_keep_factors = s->keep_factors ? 1 : 0;
+  t->newton_chord_iters = s->nl.chord_iters;
   return MISDC_OK;
 }
 
 misdc_status misdc_set_tuning(misdc_solver *s, const misdc_tuning *t) {
   if (!s || !t) return fail(MISDC_E_INVALID, "null argument");
   if (t->newton_warps_per_block < 0 || t->newton_warps_per_block > 4 || t->newton_blocks_per_sm < 0 ||
-      t->newton_blocks_per_sm > 32 || (t->cheb_block && (t->cheb_block < 32 || t->cheb_block > 1024 ||
+      t->newton_blocks_per_sm > 32 || t->newton_chord_iters < 0 || t->newton_chord_iters > 16 ||
+      (t->cheb_block && (t->cheb_block < 32 || t->cheb_block > 1024 ||
                                                          t->cheb_block % 32)))
     return fail(MISDC_E_INVALID, "tuning out of range");
   drop_graph(s);
@@ -2002,6 +2007,8 @@ misdc_status misdc_set_tuning(misdc_solver *s, const misdc_tuning *t) {
   s->nl.blocks_per_sm = t->newton_blocks_per_sm;
   s->nl.dynamic = t->newton_dynamic ? 1 : 0;
   s->dw.cheb_block = t->cheb_block;
+  s->nl.chord_iters = t->newton_chord_iters;
+  for (auto &L : s->lane) L.nl.chord_iters = t->newton_chord_iters;
   if (s->keep_factors != (t->newton_keep_factors != 0)) {
     s->keep_factors = t->newton_keep_factors != 0;
     for (int j = 1; j <= s->tab.M; ++j)
@@ -2246,6 +2253,7 @@ misdc_status misdc_batch_stats(misdc_batch *b, misdc_stats *out, int reset) {
     sum.newton_certified += t.newton_certified;
     sum.newton_stored_steps += t.newton_stored_steps;
     sum.newton_floor_stops += t.newton_floor_stops;
+    sum.newton_chord_cells += t.newton_chord_cells;
     sum.kernel_launches += t.kernel_launches;   // kernels in conditional bodies
     sum.nested_iterations += t.nested_iterations;
   }

@@ -43,6 +43,7 @@ struct DevStats {
   unsigned long long body_launches;    // kernels run inside conditional graph bodies
   unsigned long long nested_iters;     // CISDCQ nested iterations run, summed over sweeps
   unsigned long long floor_stops;      // exact Newton solves that ended on the round-off-floor test
+  unsigned long long chord_cells;      // solves finished by the thread-per-cell chord pass
 };
 
 // Mechanism tables in device memory (built by the engine from misdc_mech_desc).
@@ -50,6 +51,7 @@ struct DevMech {
   int N, R;
   double rho, T_ref, theta_exp, alpha0, ln_p_over_R, ln_Tref;
   const double *invW;      // [N] 1/W
+  const double *W;         // [N] W (kg/mol)
   const double *hcoef;     // [N][6]  a1, a2/2, a3/3, a4/4, a5/5, a6      (h/RT = poly + a6/T)
   const double *scoef;     // [N][6]  a1, a2, a3/2, a4/3, a5/4, a7        (s/R = a1 lnT + poly + a7)
   const double *cpcoef;    // [N][5]  a1..a5                                (cp/R)
@@ -120,6 +122,8 @@ struct NewtonLaunch {
   int *work = nullptr;
   int *list = nullptr, *list_n = nullptr;
   bool precertified = false;   // launch_certify has run: the Newton kernel takes the list
+  int chord_iters = 4;         // chord iterations of the thread-per-cell pass (0: certification only)
+  int *list2 = nullptr, *list2_n = nullptr;   // the cells the chord pass leaves
 };
 // Mixed precision: per-cell Jacobian factors kept between the solves of one SDC
 // node. Per cell: fs doubles (row-major LU of the (row-scaled) (N+1)^2 Jacobian,
@@ -189,11 +193,11 @@ int newton_max_wpb(const DevMech &m, bool mixed);
 // The certification pass of a mixed reaction step alone (the cells it leaves in
 // cfg->list / cfg->list_n); launch_newton with cfg->precertified then takes the list.
 // Returns false (and launches nothing) when the step has no kept factors to certify from.
-bool launch_certify(const DevMech &m, int n, int cs, double wdt, double rtol, const double *b,
+bool launch_certify(const DevMech &m, int n, int cs, double wdt, double rtol, int maxit, const double *b,
                     const double *hstar, const double *Yg, const double *Tg, double *Y, double *T,
                     double *FR, double *hsp, double *theta, int *iters, DevStats *st,
                     const double *FRp, const double *hp, const ChordStore *store,
-                    const double *hspp, const double *thp, const NewtonLaunch *cfg, cudaStream_t s);
+                    const double *hspp, const double *thp, NewtonLaunch *cfg, cudaStream_t s);
 
 // Grouped reaction Newton (k_newton2_group): newton_kernel_args reads the
 // arguments of a captured k_newton2 launch (false for any other kernel);

@@ -351,6 +351,38 @@ def test_step_mixed_precision_meets_accuracy_bar(case, pool):
     assert relerr(T, ad.T_from_h(want[:N], want[N])) <= 1e-6
 
 
+@pytest.mark.parametrize("case", ["2d_n21", "2d_n9", "2d_n53"])
+def test_thread_per_cell_chord_pass_matches_warp_newton(case):
+    """The thread-per-cell chord pass after certification (stored first step, then
+    chord iterations with rates evaluated per thread and steps through the FP32 copy
+    of the kept inverse) against the same mixed steps with certification only, where
+    the warp-per-cell Newton solves every uncertified cell: states within the mixed
+    bar (each species within 1e-8 of its largest value, h within 1e-10), the pass
+    takes most of the uncertified cells, and no solve fails."""
+    key = {"2d_n21": (1802, 21, 84), "2d_n9": (1801, 9, 21), "2d_n53": (1803, 53, 325)}[case]
+    mech, fl = small_2d(key, n=32 if key[1] < 53 else 16)
+    N = mech.n_species
+    out, st = [], []
+    for chord in (4, 0):
+        sv = S().Solver(mech, fl, precision="mixed")
+        sv.set_tuning(newton_chord_iters=chord)
+        x = torch.as_tensor(O.ADR(mech, fl).state_from_YT(fl.Y, fl.T), device="cuda").contiguous()
+        sv.step(x, 5e-6, 3)
+        torch.cuda.synchronize()
+        s_ = sv.stats()
+        assert s_["status_name"] == "OK", s_
+        out.append(x.cpu().numpy())
+        st.append(s_)
+    rel = np.max(np.abs(out[0] - out[1]), axis=1) / np.max(np.abs(out[1]), axis=1)
+    assert np.all(rel[:N] <= 1e-8), rel
+    assert rel[N] <= 1e-10, rel
+    assert st[1]["newton_chord_cells"] == 0
+    uncert = st[1]["newton_solves"] - st[1]["newton_certified"]
+    print("%s: chord pass took %d of %d uncertified solves, worst difference %.1e"
+          % (case, st[0]["newton_chord_cells"], uncert, rel.max()))
+    assert st[0]["newton_chord_cells"] > 0.5 * uncert, (st[0]["newton_chord_cells"], uncert)
+
+
 def test_stream_graph_variants_are_bitwise_identical():
     mech, fl = small_2d(n=32)
     ad = O.ADR(mech, fl)
