@@ -951,7 +951,9 @@ def main():
         kflops, exps = newton_flops(mech.n_species, mech.n_reactions, nnz, st, mixedk)
         kach = kflops / launches / avg_s / 1e12
         peak = peaks["dfma"]
-        roofline = {"kernel": "k_newton2<%s> (reaction Newton, warp per cell)" % ("mixed" if mixedk else "fp64"),
+        kname = ("reaction step: k_certify + k_chord (thread per cell) + k_newton2<mixed> (warp per cell)"
+                 if mixedk else "k_newton2<fp64> (reaction Newton, warp per cell)")
+        roofline = {"kernel": kname,
                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": NEWTON_TRAFFIC_BYTES.get((name, args.headline)),
                     "peak_source": "measured: FP64 FMA probe over every SM (misdc_probe_flops), of measured",

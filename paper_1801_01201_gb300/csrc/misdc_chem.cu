@@ -473,9 +473,11 @@ __global__ void __launch_bounds__(256) k_certify(DevMech m, int n, int cs, doubl
       ok = !(prw >= 0 && s0 > s_min && isfinite(s0));
     }
     const double T = Tg[c];
-    if (ok) {   // the factor was built near x_p (without dividing by T)
-      for (int i = 0; i < N && ok; ++i) ok = fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]) <= 1e-4;
-      ok = ok && fabs(T - cst.xc[(size_t)N * cs + c]) <= 1e-4 * T;
+    if (ok) {   // the factor was built near x_p (without dividing by T); no early
+                // exit, so that the loads of all species are in flight together
+      double dev = 0.0;
+      for (int i = 0; i < N; ++i) dev = fmax(dev, fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]));
+      ok = dev <= 1e-4 && fabs(T - cst.xc[(size_t)N * cs + c]) <= 1e-4 * T;
     }
     if (ok) {
       float r32[kMaxSpecies + 1];
@@ -483,12 +485,16 @@ __global__ void __launch_bounds__(256) k_certify(DevMech m, int n, int cs, doubl
         r32[i] = __double2float_rn(b[(size_t)i * cs + c] - Yg[(size_t)i * cs + c] +
                                    wdt * FRp[(size_t)i * cs + c]);
       r32[N] = __double2float_rn((hstar[c] - hp[c]) * cst.sT[c]);
+      // every row (most cells are certified and need them all): the rows' loads
+      // are independent of the earlier rows' outcome
       const float thr = (float)(0.09 * rtol), thrT = thr * (float)T;
-      for (int i = 0; i < nn && ok; ++i) {
+      bool small = true;
+      for (int i = 0; i < nn; ++i) {
         float z = 0.0f;
         for (int j = 0; j < nn; ++j) z = fmaf(cst.z32[((size_t)j * nn + i) * cs + c], r32[j], z);
-        ok = fabsf(z) <= (i < N ? thr : thrT);
+        small = small && fabsf(z) <= (i < N ? thr : thrT);
       }
+      ok = small;
     }
     if (ok) {
       const double invw = (wdt > 0.0) ? 1.0 / wdt : 0.0;
@@ -579,8 +585,9 @@ __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double w
     }
     const double T0 = Tg[c];
     if (ok) {   // the factor was built near x_p (without dividing by T)
-      for (int i = 0; i < N && ok; ++i) ok = fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]) <= 1e-4;
-      ok = ok && fabs(T0 - cst.xc[(size_t)N * cs + c]) <= 1e-4 * T0;
+      double dev = 0.0;
+      for (int i = 0; i < N; ++i) dev = fmax(dev, fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]));
+      ok = dev <= 1e-4 && fabs(T0 - cst.xc[(size_t)N * cs + c]) <= 1e-4 * T0;
     }
     const double sT = ok ? cst.sT[c] : 0.0;
     const double hst = hstar[c];
