@@ -476,7 +476,10 @@ __global__ void __launch_bounds__(256) k_certify(DevMech m, int n, int cs, doubl
     if (ok) {   // the factor was built near x_p (without dividing by T); no early
                 // exit, so that the loads of all species are in flight together
       double dev = 0.0;
-      for (int i = 0; i < N; ++i) dev = fmax(dev, fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]));
+      for (int i = 0; i < N; ++i) {
+        const double e = fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]);
+        dev = (e <= dev) ? dev : e;   // a NaN deviation propagates (fmax would drop it)
+      }
       ok = dev <= 1e-4 && fabs(T - cst.xc[(size_t)N * cs + c]) <= 1e-4 * T;
     }
     if (ok) {
@@ -586,7 +589,10 @@ __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double w
     const double T0 = Tg[c];
     if (ok) {   // the factor was built near x_p (without dividing by T)
       double dev = 0.0;
-      for (int i = 0; i < N; ++i) dev = fmax(dev, fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]));
+      for (int i = 0; i < N; ++i) {
+        const double e = fabs(Yg[(size_t)i * cs + c] - cst.xc[(size_t)i * cs + c]);
+        dev = (e <= dev) ? dev : e;   // a NaN deviation propagates (fmax would drop it)
+      }
       ok = dev <= 1e-4 && fabs(T0 - cst.xc[(size_t)N * cs + c]) <= 1e-4 * T0;
     }
     const double sT = ok ? cst.sT[c] : 0.0;
