@@ -221,31 +221,6 @@ __device__ void eval_chem(const DevMech &m, const WarpChem &w, int lane, double 
   __syncwarp();
 }
 
-// wdot_i = sum_r W_i nu_ri q_r for the species rows a lane owns
-__device__ __forceinline__ double species_wdot(const DevMech &m, const WarpChem &w, int i) {
-  double s = 0.0;
-  for (int p = m.sp_ptr[i]; p < m.sp_ptr[i + 1]; ++p) s = fma(m.sp_coef[p], w.q[m.sp_rx[p]], s);
-  return s;
-}
-
-__global__ void __launch_bounds__(128) k_rates(DevMech m, int n, int cs,
-                                               const double *__restrict__ Y,
-                                               const double *__restrict__ T,
-                                               double *__restrict__ FR) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int N = m.N, R = m.R;
-  WarpChem w = carve(smem + (size_t)wib * (5 * N + 4 * R), N, R);
-  const double invrho = 1.0 / m.rho;
-  for (int cell = blockIdx.x * wpb + wib; cell < n; cell += gridDim.x * wpb) {
-    for (int i = lane; i < N; i += 32) w.c[i] = m.rho * Y[(size_t)i * cs + cell] * m.invW[i];
-    __syncwarp();
-    eval_chem(m, w, lane, T[cell], false);
-    for (int i = lane; i < N; i += 32) FR[(size_t)i * cs + cell] = species_wdot(m, w, i) * invrho;
-    __syncwarp();
-  }
-}
-
 // Production rates with the contraction wdot = diag(W) nu^T q on the FP64 tensor
 // cores. A block takes 32 cells at a time: each warp evaluates the reaction
 // rates q of 8 cells (lanes over reactions, as above) into a [32][qld] tile in
@@ -526,6 +501,57 @@ __global__ void __launch_bounds__(256) k_certify(DevMech m, int n, int cs, doubl
   }
 }
 
+// One thread's rates of progress q_r = k_f prod c^nu' - k_r prod c^nu'' of its
+// cell, scattered into wd_i += (nu''_ri - nu'_ri) q_r (wd zeroed by the caller).
+// Per-thread arrays in shared memory as [species][thread] (B threads): cc the
+// concentrations, gg g/RT, wd the sums.
+__device__ __forceinline__ void thread_rates(const DevMech &m, double lnT, double invT,
+                                             const double *cc, const double *gg, double *wd, int B,
+                                             int tid) {
+  for (int r = 0; r < m.R; ++r) {
+    const signed char *fs = m.fwd + kMaxSlots * r, *rs = m.rev + kMaxSlots * r;
+    double dg = 0.0, Ff = 1.0, Fr = 1.0;
+#pragma unroll
+    for (int q = 0; q < kMaxSlots; ++q) {
+      const int sf = fs[q], sr = rs[q];
+      if (sf >= 0) { dg -= gg[(size_t)sf * B + tid]; Ff *= cc[(size_t)sf * B + tid]; }
+      if (sr >= 0) { dg += gg[(size_t)sr * B + tid]; Fr *= cc[(size_t)sr * B + tid]; }
+    }
+    const double lnkf = m.lnA[r] + m.beta[r] * lnT - m.TA[r] * invT;
+    const double lnKc = -dg + m.dn[r] * (m.ln_p_over_R - lnT);
+    const double qr = exp_tab(lnkf) * Ff - exp_tab(lnkf - lnKc) * Fr;
+#pragma unroll
+    for (int q = 0; q < kMaxSlots; ++q) {
+      const int sf = fs[q], sr = rs[q];
+      if (sf >= 0) wd[(size_t)sf * B + tid] -= qr;
+      if (sr >= 0) wd[(size_t)sr * B + tid] += qr;
+    }
+  }
+}
+
+// Production rates F_R = wdot / rho, one thread per cell (grid-stride): thermo and
+// concentrations of the cell, then thread_rates; wdot_i = W_i wd_i.
+__global__ void __launch_bounds__(64) k_rates_t(DevMech m, int n, int cs, const double *__restrict__ Y,
+                                                const double *__restrict__ T,
+                                                double *__restrict__ FR) {
+  extern __shared__ double rates_sm[];
+  const int B = blockDim.x, tid = threadIdx.x, N = m.N;
+  double *cc = rates_sm, *gg = cc + (size_t)N * B, *wd = gg + (size_t)N * B;
+  const double invrho = 1.0 / m.rho;
+  for (int c = blockIdx.x * B + tid; c < n; c += gridDim.x * B) {
+    const double Tc = T[c], lnT = log(Tc), invT = 1.0 / Tc;
+    for (int i = 0; i < N; ++i) {
+      double hRT, gRT;
+      species_hg(m, i, Tc, lnT, invT, hRT, gRT);
+      cc[(size_t)i * B + tid] = m.rho * Y[(size_t)i * cs + c] * m.invW[i];
+      gg[(size_t)i * B + tid] = gRT;
+      wd[(size_t)i * B + tid] = 0.0;
+    }
+    thread_rates(m, lnT, invT, cc, gg, wd, B, tid);
+    for (int i = 0; i < N; ++i) FR[(size_t)i * cs + c] = m.W[i] * wd[(size_t)i * B + tid] * invrho;
+  }
+}
+
 // Chord iterations, one thread per cell, over the cells certification left
 // (in_list; mixed precision with kept factors), persistent blocks taking rounds of
 // them. A cell with a usable FP64-built factor whose step through the kept
@@ -565,11 +591,10 @@ __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double w
   const int N = m.N, nn = N + 1, R = m.R;
   const int total = *in_n;
   double *xs = chord_sm;                         // [nn][B] iterate
-  double *cc = xs + (size_t)nn * B;              // [N][B]  concentrations
-  double *gg = cc + (size_t)N * B;               // [N][B]  g/RT
+  double *cc = xs + (size_t)nn * B;              // [nn][B] concentrations, then the residual
+  double *gg = cc + (size_t)nn * B;              // [N][B]  g/RT
   double *wd = gg + (size_t)N * B;               // [N][B]  sum_r nu_ri q_r
-  double *rr = wd + (size_t)N * B;              // [nn][B] residual
-  double *dx = rr + (size_t)nn * B;              // [nn][B] step
+  double *rr = cc;   // the residual reuses the concentrations, dead after the rates
 #define TH(a, k) a[(size_t)(k) * B + tid]
   // rounds of B items per block (uniform per block, so the statistics below see
   // every lane of a warp)
@@ -598,7 +623,8 @@ __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double w
     const double sT = ok ? cst.sT[c] : 0.0;
     const double hst = hstar[c];
     // the step Z r through the kept FP64 inverse (row-major, the cell's own block
-    // of the factor store); d = max(max|dY|, |dT|/T)
+    // of the factor store), added to the iterate (a first step that is not taken
+    // sends the cell, from its guess, to the warp kernel); d = max(max|dY|, |dT|/T)
     const double *Zc = cst.f + (size_t)c * cst.fs;
     auto step = [&](double T, double &d, bool &fin) {
       double dm = 0.0, dT = 0.0;
@@ -607,7 +633,7 @@ __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double w
         const double *Zi = Zc + (size_t)i * nn;
         double z = 0.0;
         for (int j = 0; j < nn; ++j) z = fma(Zi[j], TH(rr, j), z);
-        TH(dx, i) = z;
+        TH(xs, i) += z;
         fin = fin && isfinite(z);
         if (i < N) dm = fmax(dm, fabs(z));
         else dT = fabs(z);
@@ -626,8 +652,7 @@ __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double w
       bool fin;
       step(T0, d0, fin);
       if (fin && max_chord > 0 && maxit >= 2 && d0 <= 1e-4) {
-        // iteration 1: the step from the stored reaction term
-        for (int i = 0; i < nn; ++i) TH(xs, i) += TH(dx, i);
+        // iteration 1: the step from the stored reaction term (taken by step())
         double dprev = d0;
         it = 1;
         const double wr = wdt / m.rho;
@@ -646,32 +671,13 @@ __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double w
             TH(wd, i) = 0.0;
             sh = fma(y, kRu * m.invW[i] * T * hRT, sh);
           }
-          for (int r = 0; r < R; ++r) {
-            const signed char *fs = m.fwd + kMaxSlots * r, *rs = m.rev + kMaxSlots * r;
-            double dg = 0.0, Ff = 1.0, Fr = 1.0;
-#pragma unroll
-            for (int q = 0; q < kMaxSlots; ++q) {
-              const int sf = fs[q], sr = rs[q];
-              if (sf >= 0) { dg -= TH(gg, sf); Ff *= TH(cc, sf); }
-              if (sr >= 0) { dg += TH(gg, sr); Fr *= TH(cc, sr); }
-            }
-            const double lnkf = m.lnA[r] + m.beta[r] * lnT - m.TA[r] * invT;
-            const double lnKc = -dg + m.dn[r] * (m.ln_p_over_R - lnT);
-            const double qr = exp_tab(lnkf) * Ff - exp_tab(lnkf - lnKc) * Fr;
-#pragma unroll
-            for (int q = 0; q < kMaxSlots; ++q) {
-              const int sf = fs[q], sr = rs[q];
-              if (sf >= 0) TH(wd, sf) -= qr;
-              if (sr >= 0) TH(wd, sr) += qr;
-            }
-          }
+          thread_rates(m, lnT, invT, cc, gg, wd, B, tid);
           for (int i = 0; i < N; ++i)
             TH(rr, i) = fma(wr, m.W[i] * TH(wd, i), b[(size_t)i * cs + c] - TH(xs, i));
           TH(rr, N) = -(sh - hst) * sT;
           double d;
           step(T, d, fin);
           if (!fin) break;
-          for (int i = 0; i < nn; ++i) TH(xs, i) += TH(dx, i);
           if (d > 1e-4 || !(d < 0.1 * dprev)) break;   // not contracting: a new factor is due
           if (d * d <= rtol * (dprev - d)) { conv = true; break; }
           dprev = d;
@@ -720,7 +726,7 @@ __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double w
 
 size_t chord_smem_bytes(int N, int threads) {
   const size_t nn = N + 1;
-  return (size_t)threads * (3 * nn + 3 * (size_t)N) * sizeof(double);
+  return (size_t)threads * (2 * nn + 2 * (size_t)N) * sizeof(double);
 }
 
 // The reaction Newton of a run of work items of one solve (one warp per cell);
@@ -1587,9 +1593,9 @@ void prepare_chem_kernels(const DevMech &m) {
   std::lock_guard<std::mutex> lock(g_smem_mu);
   int ld, wpb;
   const size_t need[4] = {newton_smem(m, false, ld, wpb), newton_smem(m, true, ld, wpb),
-                          (size_t)4 * (5 * m.N + 4 * m.R) * sizeof(double), rates_mma_smem(m)};
+                          (size_t)64 * 3 * m.N * sizeof(double), rates_mma_smem(m)};
   const void *fn[4] = {(const void *)k_newton2<false>, (const void *)k_newton2<true>,
-                       (const void *)k_rates, (const void *)k_rates_mma};
+                       (const void *)k_rates_t, (const void *)k_rates_mma};
   for (int k = 0; k < 4; ++k) reserve_smem(k, fn[k], need[k]);
   const size_t chord = chord_smem_bytes(m.N, 64);
   if (chord <= 200 * 1024) reserve_smem(6, (const void *)k_chord, chord);
@@ -1617,11 +1623,13 @@ void launch_rates(const DevMech &m, int n, int cs, const double *Y, const double
     k_rates_mma<<<grid, 128, rates_mma_smem(m), s>>>(m, n, cs, Y, T, FR);
     return;
   }
-  const int wpb = 4;
-  size_t sm = (size_t)wpb * (5 * m.N + 4 * m.R) * sizeof(double);
-  int grid = (n + wpb - 1) / wpb;
-  grid = grid < sm_count() * 16 ? grid : sm_count() * 16;
-  k_rates<<<grid, wpb * 32, sm, s>>>(m, n, cs, Y, T, FR);
+  // one thread per cell (every FP64 lane busy: an FP64 warp instruction costs the
+  // pipe the same whether 21 or 32 of its lanes work)
+  const size_t sm = (size_t)64 * 3 * m.N * sizeof(double);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_rates_t, 64, sm);
+  const int grid = std::max(1, std::min((n + 63) / 64, sm_count() * std::max(per_sm, 1)));
+  k_rates_t<<<grid, 64, sm, s>>>(m, n, cs, Y, T, FR);
 }
 
 // Certification (k_certify, thread per cell, into `list`) and, where enabled and its
