@@ -49,7 +49,7 @@ def bf16_np(t):
 # magnitude) against the stored activations, and the error that dy inherits from
 # the forward output. Where gelu' is small the tolerance is small. (Measured: the
 # kernels stay within 0.09 of it; a derivative of GELU replaced by a plausible
-# wrong one, planted in a numpy copy of the kernels' arithmetic, exceeds it 2-7x.)
+# wrong one, planted in a numpy copy of the kernels' arithmetic, exceeds it 2-13x.)
 KU = 2.0 * 2.0 ** -8
 
 
