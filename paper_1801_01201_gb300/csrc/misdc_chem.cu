@@ -792,6 +792,16 @@ __device__ __forceinline__ void newton_items(const NewtonArgs &A, double *wsm, i
       vet = prw >= 0 && s0 > s_min && isfinite(s0);
     }
     __syncwarp();
+    if (MIXED && vet && cst.valid && (cst.valid[cell] & 1)) {
+      // a cell with a kept factor built within 1e-4 of x_p iterates from x_p on that
+      // factor without a new Jacobian; a guess elsewhere would cost one, so the
+      // learned guess is kept for the cells that need a new Jacobian anyway
+      const double *xf = cst.f + (size_t)cell * cst.fs + nn * nn + 2 * nn + 2;
+      bool near = true;
+      for (int i = lane; i < nn; i += 32)
+        near = near && fabs(w.xs[i] - xf[i]) <= ((i < N) ? 1e-4 : 1e-4 * w.xs[i]);
+      if (__all_sync(0xffffffffu, near)) vet = false;
+    }
     if (vet) {
       const float *pc = pred + (size_t)prw * ldp;
       for (int i = lane; i < nn; i += 32) {
