@@ -322,6 +322,15 @@ def train_params(Solver, mech, fl, dt, w, dev, args):
     return p, info
 
 
+def lin_rounds_for(args, fl):
+    """Refinement rounds of the mixed diffusion solve: the flag, else 2 on a 3D flame
+    (dx = 1e-4 m: two rounds meet the 1e-12 residual check) and the library's three
+    on the 1D/2D flames (dx = 4e-5 m, a stiffer operator)."""
+    if args.lin_rounds >= 0:
+        return args.lin_rounds
+    return 2 if fl.dim == 3 else 0
+
+
 class Runner:
     """One variant of the workload: a solver per flame (and a batch for several)."""
 
@@ -335,7 +344,7 @@ class Runner:
             sv = Solver(mech, fl, n_sweeps=w["sweeps"], nu=w["nu"], n_nodes=w["nodes"],
                         scheme=args.scheme, precision=precision, profile=len(entries) == 1,
                         mg_levels=args.mg_levels, rates_mma=bool(args.rates_mma),
-                        lin_rounds=args.lin_rounds, device=dev)
+                        lin_rounds=lin_rounds_for(args, fl), device=dev)
             st = sv.state_from_YT(fl.Y, fl.T)
             if params is not None:
                 sv.surrogate_load(params[id(mech)])
@@ -805,10 +814,11 @@ def main():
                     help="instead of the headline: serial MISDCQ against CISDCQ-nu on one and on two "
                          "streams and with adaptive nu, sweeps 1..K each: step times, stage costs, "
                          "sweep increments, sweeps to the MISDCQ tolerance, measured and modelled R_nu")
-    ap.add_argument("--lin-rounds", type=int, default=2,
+    ap.add_argument("--lin-rounds", type=int, default=-1,
                     help="mixed precision: FP64-residual refinement rounds of the diffusion solve "
-                         "(0: the library's default, 3); the line reports the residual and the "
-                         "error against the FP64 sweep")
+                         "(0: the library's default, 3; default: 2 on 3D flames, 3 on the stiffer "
+                         "1D/2D ones); the line reports the residual and the error against the "
+                         "FP64 sweep")
     ap.add_argument("--nodes", type=int, default=0,
                     help="--concurrency: Gauss-Lobatto nodes (default: the workload's)")
     ap.add_argument("--rates-compare", action="store_true",
@@ -1006,7 +1016,7 @@ def main():
            "autotuned": tune, "l2": "flushed between steps (256 MB write)",
            "run": "%d-step runs from the initial state, repeated (restart copy inside the timed region)"
                   % w["steps"],
-           "learned_sweeps": args.sg_sweeps or w["sweeps"], "lin_rounds": args.lin_rounds or 3,
+           "learned_sweeps": args.sg_sweeps or w["sweeps"], "lin_rounds": sorted({lin_rounds_for(args, fl) or 3 for _, fl, _ in entries}),
            "rates": "fp64 tensor cores" if args.rates_mma else "sparse fp64 fma",
            "diffusion": "multigrid %d levels" % args.mg_levels if args.mg_levels > 1 else "chebyshev"}
     if len(entries) == 1:

@@ -355,9 +355,10 @@ __global__ void k_cheb32(DevGrid g, FieldMap fm, const float *__restrict__ thf,
 }
 
 // First sweep of the first refinement round, whose iterate is the right-hand
-// side itself: its residual b - A b = c_f L_theta b is formed here in FP32 (from
-// b rounded to FP32; the inner solve's own reduction is 1e-6, and the FP64
-// residual of the next round corrects both), stored for the later sweeps, and
+// side itself: its residual b - A b = c_f L_theta b is formed here in FP32 from
+// the FP64 differences of b rounded to FP32 (relative error ~1e-7 of c L b, below
+// the inner solve's own 1e-6 reduction; the FP64 residual of the next round
+// corrects both), stored for the later sweeps, and
 // the sweep from e_0 = 0 is e_1 = D^{-1} r. A single planned sweep also writes
 // x + e in FP64.
 template <int DIM>
@@ -384,12 +385,13 @@ __global__ void k_cheb32_first(DevGrid g, FieldMap fm, const float *__restrict__
     const size_t off = (size_t)fm.fld[k] * cs;
     const double *x = b + off;
     const double xd = x[c];
-    const float xc = (float)xd;
+    // differences in FP64, rounded after: a field of large offset and small
+    // variation (the enthalpy) keeps its differences to FP32 precision
     float L = 0.0f;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      L = fmaf(thi[d], (float)x[cp[d]] - xc, L);
-      L = fmaf(-tlo[d], xc - (float)x[cm[d]], L);
+      L = fmaf(thi[d], (float)(x[cp[d]] - xd), L);
+      L = fmaf(-tlo[d], (float)(xd - x[cm[d]]), L);
     }
     const float r = (float)fm.cf[k] * L;
     r32[off + c] = r;
