@@ -66,3 +66,39 @@ def test_pde_entry_point_checks_arguments_on_the_host():
     for n_nodes, nx in ((5, 200), (3, 53)):
         M = n_nodes - 1
         assert S.pde_smem_bytes(n_nodes, nx) == 8 * ((9 + 19 * M) * nx + 33) + M * nx
+
+
+STRUCTS = {"MechDesc": "misdc_mech_desc", "GridDesc": "misdc_grid_desc", "Opts": "misdc_opts",
+           "Stats": "misdc_stats", "LowMachDesc": "misdc_lowmach_desc", "Tuning": "misdc_tuning"}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every structure the binding passes through the C ABI has, field by field,
+    the offset and the size the header gives it (a C program compiled against
+    include/misdc.h prints them), so no field added on one side only can shift
+    the others."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "misdc.h"', "int main(void) {"]
+    for py, cname in STRUCTS.items():
+        cls = getattr(L, py)
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (py, cname))
+        for f, _ in cls._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (py, f, cname, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for py in STRUCTS:
+        cls = getattr(L, py)
+        assert int(got[py + " size"]) == C.sizeof(cls), py
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (py, f)]) == getattr(cls, f).offset, (py, f)
