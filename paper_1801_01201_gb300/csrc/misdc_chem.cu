@@ -553,21 +553,22 @@ __global__ void __launch_bounds__(64) k_rates_t(DevMech m, int n, int cs, const 
 }
 
 // Chord iterations, one thread per cell, over the cells certification left
-// (in_list; mixed precision with kept factors), persistent blocks taking rounds of
-// them. A cell with a usable FP64-built factor whose step through the kept
-// inverse is at most 1e-4 (certification found it above 0.09 rtol) takes that step (iteration 1, from
-// the stored reaction term, as the warp kernel's stored first step) and then up to
-// max_chord chord iterations: the FP64 residual r = b - Y + (wdt/rho) W nu^T q at
-// the iterate (every rate of progress evaluated by the cell's own thread) and the
-// step Z r through the kept FP64 inverse, as in the warp kernel (the FP32 copy that
+// (in_list; mixed precision with kept factors), persistent blocks taking rounds
+// of them. A cell with a usable FP64-built factor near its guess, whose step
+// through the kept inverse is at most 1e-4 (certification found it above
+// 0.09 rtol), takes that step as iteration 1 (from the stored reaction term, as
+// the warp kernel's stored first step does) and then up to max_chord chord
+// iterations: the FP64 residual r = b - Y + (wdt/rho) W nu^T q at the iterate,
+// every rate of progress evaluated by the cell's own thread, and the step Z r
+// through the kept FP64 inverse, as in the warp kernel. (The FP32 copy that
 // certification uses is too coarse a chord inverse for stiff cells: its rounding
-// misled the stopping test by up to 1e-5 on the 9-species flames). It stops like
-// the warp kernel's
-// chord iteration: with th = d/d_prev < 0.1 and d th / (1 - th) <= rtol. A step
-// above 1e-4, a contraction of less than 10 or a non-finite value hands the cell,
-// from its original guess, to the warp-per-cell Newton kernel through `list`, as do
-// the cells certification cannot take (no usable FP64-built factor, a learned guess
-// to vet). Per-thread arrays live in shared memory as [element][thread].
+// misled the stopping test by up to 1e-5 on the 9-species flames.) It stops as
+// the warp kernel's chord iteration does, once th = d/d_prev < 0.1 and
+// d th / (1 - th) <= rtol. A step above 1e-4, a contraction of less than 10 or a
+// non-finite value hands the cell, from its original guess, to the
+// warp-per-cell Newton kernel through `list`, as do the cells certification
+// cannot take (no usable FP64-built factor, a learned guess to vet). Per-thread
+// arrays live in shared memory as [element][thread].
 __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double wdt, double rtol,
                                               int maxit, int max_chord,
                                               const double *__restrict__ b,
@@ -588,7 +589,7 @@ __global__ void __launch_bounds__(64) k_chord(DevMech m, int n, int cs, double w
                                               int *__restrict__ list, int *__restrict__ list_n) {
   extern __shared__ double chord_sm[];
   const int B = blockDim.x, tid = threadIdx.x;
-  const int N = m.N, nn = N + 1, R = m.R;
+  const int N = m.N, nn = N + 1;
   const int total = *in_n;
   double *xs = chord_sm;                         // [nn][B] iterate
   double *cc = xs + (size_t)nn * B;              // [nn][B] concentrations, then the residual
