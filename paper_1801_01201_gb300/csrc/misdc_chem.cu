@@ -172,13 +172,6 @@ struct WarpChem {
   double *q, *kf, *kr, *dqdT;       // [R]
 };
 
-__device__ __forceinline__ WarpChem carve(double *p, int N, int R) {
-  WarpChem w;
-  w.c = p; w.g = p + N; w.hRT = p + 2 * N; w.hm = p + 3 * N; w.cpm = p + 4 * N;
-  w.q = p + 5 * N; w.kf = w.q + R; w.kr = w.kf + R; w.dqdT = w.kr + R;
-  return w;
-}
-
 // thermo of every species at T, then every reaction's rate of progress (and
 // what the Jacobian needs); concentrations w.c must be set.
 __device__ void eval_chem(const DevMech &m, const WarpChem &w, int lane, double T, bool jac) {
